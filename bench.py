@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the GPU interior-point solver: time to the 1e-7 stopping tolerance
+(paper §3: ε_abs = ε_rel = 1e-7) on the minimum-fuel trajectory SOCP with N = 20000
+stages (N_K = 540018, ~2e6 KKT nonzeros; seeded synthetic data).
+
+One step = one complete solve from a fresh initial point to the stopping tolerance
+(every iteration: residuals, NT scaling, −W² update, LDLᵀ refactorisation, predictor
+and corrector solves with refinement, steps).  `value` is seconds per solve with the
+problem already resident in HBM (setup excluded, as in the paper's split of setup
+and solve time, §3.2); `e2e` is the same metric through the C ABI with host buffers:
+setup (host analysis + host→device copies), solve, copy of the solution back.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own replica; the reported time is the
+max over ranks ("replicas only": a single solve is not sharded).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time_to_1e-7_gap"
+WORKLOAD = "trajectory_socp_N20000"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Nominal FP64 rate of GB300 (non-tensor and tensor alike); see the design doc for the derivation.
+FP64_NOMINAL_GFLOPS = 1250.0
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--stages", type=int, default=20000, help="trajectory stages (default: the benchmark size)")
+    ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def workload(stages):
+    from workloads import trajectory_socp
+    return trajectory_socp(N=stages, seed=0)
+
+
+def golden_iters(stages):
+    path = os.path.join(ROOT, "tests", "golden", f"trajectory_socp_N{stages}.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return int(json.load(f)["iters"])
+    return None
+
+
+def config(prob, extra=None):
+    cfg = {"workload": f"trajectory_socp_N{prob.meta['N']}: min-fuel 3-D double integrator, "
+                       f"{prob.meta['N']} stages, one Q^4 per stage + 7 orthant rows per stage",
+           "n": prob.n, "m": prob.m, "p": prob.p, "kkt_dim": prob.kkt_dim(),
+           "size_nnzA_nnzG_nnzPupper": prob.size(), "tolerance": 1e-7,
+           "l2": "flushed between timed steps (256 MiB write); working set > L2"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_uuid=None):
+        self.uuid = dev_uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU baseline
+def cpu_baseline_child(stages):
+    """Runs in a subprocess with one BLAS/OpenMP thread: the oracle on a bounded sample
+    of the workload (its initial point, then two iterations), scaled to one solve."""
+    from oracle import ipm
+    prob = workload(stages)
+    t0 = time.perf_counter()
+    ipm.solve(prob, ipm.Settings(max_iter=0))
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ipm.solve(prob, ipm.Settings(max_iter=2))
+    t2 = time.perf_counter() - t0
+    per_iter = max(0.0, (t2 - t_init) / 2.0)
+    iters = golden_iters(stages) or 30
+    est = t_init + per_iter * iters
+    print(json.dumps({"value": est, "t_init": t_init, "per_iter": per_iter, "iters": iters,
+                      "sample_seconds": t_init + t2}))
+
+
+def run_cpu_baseline(stages):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-child",
+                        "--stages", str(stages)], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr.strip().splitlines()[-1] if r.stderr else "failed"}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["value"], "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle IPM on the same instance: initial point ({d['t_init']:.2f} s) plus 2 "
+                       f"iterations timed ({d['sample_seconds']:.1f} s of CPU work); "
+                       f"{d['per_iter']:.2f} s/iteration × {d['iters']} iterations (oracle's count) "
+                       f"+ initial point"),
+            "nproc": os.cpu_count()}
+
+
+# --------------------------------------------------------------------------- helpers
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def roofline(profile, info, stages):
+    """Roofline of the phase with the largest device time (CUDA events on the solver's
+    stream over the timed steps)."""
+    hbm, hbm_src = peaks()
+    N = info["kkt_dim"]
+    nnz = info["kkt_nnz"]
+    ph = max(profile, key=lambda k: profile[k]["ms"])
+    rec = profile[ph]
+    per_call_ms = rec["ms"] / max(1, rec["calls"])
+    if ph == "factor":
+        flops = info["factor_flops"]
+        ach = flops / (per_call_ms * 1e-3) / 1e9
+        return {"kernel": "k_front_factor (all level launches of one LDLᵀ factorisation)",
+                "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                "frac": ach / FP64_NOMINAL_GFLOPS, "traffic": None,
+                "per_launch_unit": f"{flops:.4g} algorithmic flops per factorisation",
+                "peak_source": "nominal FP64 rate (recipe table), not a measured peak",
+                "avg_ms": per_call_ms, "launches_per_call": rec["launches"] / max(1, rec["calls"])}
+    if ph == "solve":
+        by = 2.0 * info["l_nnz"] * 12.0 + N * 8.0 * 4.0
+        name = "k_fwd + k_bwd (all level launches of one triangular solve)"
+    elif ph == "row":
+        by = nnz * 12.0 + N * 8.0 * 3.0
+        name = "k_residual / k_spmv_res / k_norm_inf (one pass)"
+    else:
+        by = info.get("m_cone", 0) * 8.0 * 12.0
+        name = "cone kernels (one pass)"
+    ach = by / (per_call_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "traffic": None, "per_launch_unit": f"{by:.4g} algorithmic bytes per call",
+            "peak_source": f"{hbm_src} copy bandwidth", "avg_ms": per_call_ms,
+            "launches_per_call": rec["launches"] / max(1, rec["calls"])}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------- arms
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from oracle import ipm
+    prob = workload(args.stages)
+    iters = golden_iters(args.stages) or 30
+    t_init = []
+    for _ in range(max(1, args.warmup)):
+        t0 = time.perf_counter()
+        ipm.solve(prob, ipm.Settings(max_iter=0))
+        t_init.append(time.perf_counter() - t0)
+    ti = statistics.median(t_init)
+    vals, step_s = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ipm.solve(prob, ipm.Settings(max_iter=1))
+        dt = time.perf_counter() - t0
+        step_s.append(dt)
+        vals.append(ti + max(0.0, dt - ti) * iters)
+    v = statistics.mean(vals)
+    sample = (f"each step: oracle initial point + 1 iteration of the full instance "
+              f"({statistics.mean(step_s):.1f} s), scaled to {iters} iterations")
+    out = {"metric": METRIC, "value": v, "unit": "s", "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_s) * 1e3,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator)", "config": config(prob),
+           "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2603_29197_gb300 as q
+    from paper_2603_29197_gb300 import build as qbuild
+    if not os.path.exists(qbuild.LIB):
+        qbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prob = workload(args.stages)
+    stream = torch.cuda.current_stream(dev)
+    S = q.Solver(prob)
+    setup_info = S.info()
+    for _ in range(args.warmup):
+        st = S.solve(stream.cuda_stream)
+        if st != 0:
+            raise RuntimeError(f"warm-up solve returned {q.STATUS_NAMES.get(st, st)}")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        uuid = None
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    S.set_profiling(True)
+    times, launches, iters = [], 0, []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = S.solve(stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        if st != 0:
+            raise RuntimeError(f"solve returned {q.STATUS_NAMES.get(st, st)}")
+        times.append(e0.elapsed_time(e1))
+        inf = S.info()
+        launches += int(inf["kernel_launches"])
+        iters.append(int(inf["iters"]))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall0
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    prof = S.profile()
+    S.set_profiling(False)
+    info = S.info()
+    info["m_cone"] = prob.m
+    ms = statistics.mean(times)
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    rl = roofline(prof, info, args.stages)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(q, prob, args, stream, dev)
+        if ws > 1:
+            tt = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e["value"] = float(tt.item())
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(args.stages)
+    if rank == 0:
+        out = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic (seeded generator, no dataset)",
+               "config": config(prob, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                                       "ordering": info["ordering_used"], "iterations": iters[-1],
+                                       "n_supernodes": info["n_supernodes"], "tree_levels": info["n_levels"],
+                                       "factor_flops": info["factor_flops"], "l_nnz": info["l_nnz"],
+                                       "kkt_nnz": info["kkt_nnz"], "setup_s": setup_info["setup_time_s"],
+                                       "analysis_s": setup_info["analysis_time_s"]}),
+               "gpu_launches": launches,
+               "refactor_gflops": info["factor_flops"] / (prof["factor"]["ms"] / max(1, prof["factor"]["calls"]) * 1e-3) / 1e9
+               if prof["factor"]["calls"] else None,
+               "phase_ms_per_solve": {k: v["ms"] / args.steps for k, v in prof.items()},
+               "roofline": rl, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+               "wall_s_timed": wall}
+        print(json.dumps(out), flush=True)
+    S.close()
+
+
+def run_e2e(q, prob, args, stream, dev):
+    """Same metric through the C ABI with host buffers: setup (analysis + host→device
+    copies from pinned memory), solve, device→host copy of the solution, cleanup."""
+    import numpy as np
+    import torch
+
+    def pinned(a, dtype):
+        t = torch.empty(len(a), dtype=dtype, pin_memory=True)
+        t.numpy()[:] = a
+        return t.numpy()
+
+    class Pinned:
+        pass
+
+    pp = Pinned()
+    for k in ("n", "m", "p", "l", "q", "meta"):
+        setattr(pp, k, getattr(prob, k))
+    for k in ("c", "b", "h"):
+        setattr(pp, k, pinned(getattr(prob, k), torch.float64))
+    for k in ("P", "A", "G"):
+        M = getattr(prob, k).tocsc()
+        M2 = M.copy()
+        M2.data = pinned(M.data, torch.float64)
+        M2.indices = pinned(M.indices.astype(np.int32), torch.int32)
+        M2.indptr = pinned(M.indptr.astype(np.int32), torch.int32)
+        setattr(pp, k, M2)
+    times = []
+    h2d = d2h = 0
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        S = q.Solver(pp)
+        st = S.solve(stream.cuda_stream)
+        sol = S.solution()
+        S.close()
+        t1 = time.perf_counter()
+        if st != 0:
+            raise RuntimeError(f"e2e solve returned {st}")
+        if i >= args.warmup:
+            times.append(t1 - t0)
+        inf = sol["info"]
+        h2d = int(inf["h2d_bytes"])
+        d2h = int(inf["d2h_bytes"]) + 8 * (prob.n + 2 * prob.m + prob.p)
+    return {"value": statistics.mean(times), "unit": "s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h,
+            "note": "setup incl. host ordering + symbolic analysis, solve, solution copy-back"}
+
+
+def main():
+    args = parse()
+    if args.cpu_baseline_child:
+        cpu_baseline_child(args.stages)
+        return
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * qoco_gpu.h — C ABI of a GB300 (sm_103a) interior-point solver for
+ *
+ *     minimise ½xᵀPx + cᵀx   subject to   Gx ⪯_K h,  Ax = b            (paper §1, eq. (1))
+ *
+ * with K = R^l_+ × Q^{q_1} × … × Q^{q_nsoc} (non-negative orthant times second-order
+ * cones).  The call sequence follows the paper's interface (§2.1, Listing 1:
+ * setup(n, m, p, P, c, A, b, G, h, l, nsoc, q) then solve()).  One iteration factors
+ * the quasidefinite KKT matrix of eq. (2) once and solves with it twice (§2.2); the
+ * factorisation, the solves and the cone operations (§2.1, §2.3) all run in this
+ * library's own CUDA kernels; data cross host→device once at setup and device→host
+ * once at the end (§2.3).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are CSC, 0-based, row indices strictly increasing within a column,
+ *     no duplicates.  P holds the upper triangle (diagonal included) of a symmetric
+ *     PSD matrix (§3 sizes problems by "the upper half of P").
+ *   - G's rows are ordered: the l orthant rows first, then the SOC blocks in the
+ *     order of q; so m = l + Σ q[k].  A vector u is in Q^q when u_0 ≥ ‖u_{1:q}‖.
+ *   - Pointers documented "host" are read (or written) during the call only; the
+ *     caller keeps ownership.  Pointers documented "device" must be CUDA device
+ *     memory of the current device, 8-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Calls taking a stream are ordered on it and return before the GPU
+ *     work finishes unless stated otherwise.
+ *   - Return value: 0 (or a positive non-error status) on success, a negative
+ *     QOCO_GPU_ERR_* code on failure.  No global error state is kept; the solver's
+ *     info struct carries a message for the last failure.
+ */
+#ifndef QOCO_GPU_H
+#define QOCO_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define QOCO_GPU_SOLVED               0  /* stopping tests met at abstol/reltol          */
+#define QOCO_GPU_SOLVED_INACCURATE    1  /* max_iter reached, met the *_inacc tolerances  */
+#define QOCO_GPU_MAX_ITER             2  /* max_iter reached                               */
+#define QOCO_GPU_ERR_INVALID_DIMS    -1
+#define QOCO_GPU_ERR_INVALID_CSC     -2  /* unsorted / duplicate / out-of-range / P not upper */
+#define QOCO_GPU_ERR_INVALID_CONE    -3  /* l < 0, nsoc < 0, some q < 2, l + Σq ≠ m       */
+#define QOCO_GPU_ERR_NONFINITE_DATA  -4
+#define QOCO_GPU_ERR_NUMERICAL       -5  /* NaN/Inf in an iterate, or an iterate left the cone */
+#define QOCO_GPU_ERR_OOM             -6
+#define QOCO_GPU_ERR_CUDA            -7
+#define QOCO_GPU_ERR_DEVICE_TIMEOUT  -8
+#define QOCO_GPU_ERR_NO_FACTOR       -9  /* a call needs a factorisation that does not exist */
+#define QOCO_GPU_ERR_INVALID_ARG    -10
+#define QOCO_GPU_ERR_NOT_IMPLEMENTED -11
+
+/* ---- orderings for the symbolic analysis ---------------------------------- */
+#define QOCO_GPU_ORDER_AUTO     0  /* the cheaper of AMD and ND by the analysis' cost model */
+#define QOCO_GPU_ORDER_AMD      1  /* approximate minimum degree                           */
+#define QOCO_GPU_ORDER_ND       2  /* nested dissection, AMD inside the leaves             */
+#define QOCO_GPU_ORDER_NATURAL  3  /* identity (x, then y, then z)                         */
+
+typedef struct {
+    int n_rows, n_cols, nnz;
+    const int* colptr;     /* host, n_cols + 1 */
+    const int* rowidx;     /* host, nnz        */
+    const double* val;     /* host, nnz        */
+} qoco_csc;
+
+/* Settings.  The paper fixes only the tolerances (ε_abs = ε_rel = 1e-7, §3); every
+ * other default is a documented reading of the method the paper defers to. */
+typedef struct {
+    double abstol, reltol;              /* 1e-7, 1e-7 */
+    double abstol_inacc, reltol_inacc;  /* 1e-5, 1e-5 */
+    int max_iter;                       /* 200 */
+    double static_reg;                  /* ε: +ε on the x block, −ε on y and z (1e-8) */
+    double dyn_reg_thresh;              /* pivot with sign·d < thresh ... (1e-13) */
+    double dyn_reg_value;               /* ... is replaced by sign·value (1e-7) */
+    int max_refine;                     /* iterative-refinement steps per solve (10) */
+    double refine_tol;                  /* normwise backward-error target (1e-10) */
+    double step_fraction;               /* 0.99 */
+    int ordering;                       /* QOCO_GPU_ORDER_* (AUTO) */
+    int nd_leaf;                        /* ND stops splitting below this many nodes (64) */
+    int verbose;                        /* 0: silent; 1: one line per iteration on stdout */
+} qoco_gpu_settings;
+
+typedef struct {
+    int status;                 /* last solve's status code */
+    int iters;
+    double pobj, dobj, gap, pres, dres;
+    double setup_time_s;        /* whole qoco_gpu_setup call (host wall clock) */
+    double analysis_time_s;     /* ordering + symbolic factorisation (host) */
+    double solve_time_s;        /* last qoco_gpu_solve, host wall clock incl. its sync */
+    int64_t kkt_dim;            /* N_K = n + p + m */
+    int64_t kkt_nnz;            /* stored entries of the full symmetric KKT */
+    int64_t l_nnz;              /* entries of L below the diagonal (algorithmic, no amalgamation zeros) */
+    int64_t front_entries;      /* Σ f_s², the dense front storage in doubles */
+    double factor_flops;        /* Σ_j (c_j² + 2 c_j), c_j = below-diagonal count of L's column j */
+    int n_supernodes, n_levels, max_front;
+    int ordering_used;
+    int refine_steps;           /* refinement steps taken during the last solve */
+    double last_backward_error;
+    int64_t kernel_launches;    /* this library's kernel launches during the last solve */
+    int64_t h2d_bytes;          /* host→device bytes copied by setup */
+    int64_t d2h_bytes;          /* device→host bytes read back during the last solve */
+    char message[160];
+} qoco_gpu_info;
+
+/* Per-phase device time of the solves run while profiling is on (CUDA events recorded
+ * on the solver's stream around each phase; milliseconds summed over launches). */
+#define QOCO_GPU_PHASE_FACTOR  0   /* numeric LDLᵀ: every level launch of one factorisation */
+#define QOCO_GPU_PHASE_SOLVE   1   /* one forward + backward triangular solve */
+#define QOCO_GPU_PHASE_CONE    2   /* one cone kernel (scaling, rhs, Δs, step) */
+#define QOCO_GPU_PHASE_ROW     3   /* one residual / SpMV / norm pass */
+#define QOCO_GPU_NPHASE        4
+typedef struct {
+    double ms[QOCO_GPU_NPHASE];
+    int64_t calls[QOCO_GPU_NPHASE];
+    int64_t launches[QOCO_GPU_NPHASE];  /* kernel launches inside the timed phases */
+} qoco_gpu_profile;
+
+typedef struct qoco_gpu_solver qoco_gpu_solver;
+typedef struct qoco_gpu_cones qoco_gpu_cones;
+
+/* Fills `s` with the defaults listed in qoco_gpu_settings. */
+void qoco_gpu_default_settings(qoco_gpu_settings* s);
+
+/* ---- solver --------------------------------------------------------------- */
+
+/* Validates the data, assembles the KKT pattern of eq. (2) (with every diagonal
+ * slot present and the SOC blocks of −WᵀW dense), orders it, runs the symbolic
+ * supernodal analysis on the host, and copies everything to the current device
+ * (paper §2.3: copy once at setup).  P may be NULL (P = 0); A and b may be NULL
+ * when p = 0; q may be NULL when nsoc = 0; settings NULL = defaults.
+ * On success *out owns all device memory of the solver.  On failure *out is NULL
+ * and nothing is leaked.  Errors: INVALID_DIMS, INVALID_CSC, INVALID_CONE,
+ * NONFINITE_DATA, OOM, CUDA. */
+int qoco_gpu_setup(qoco_gpu_solver** out, int n, int m, int p,
+                   const qoco_csc* P, const double* c,
+                   const qoco_csc* A, const double* b,
+                   const qoco_csc* G, const double* h,
+                   int l, int nsoc, const int* q,
+                   const qoco_gpu_settings* settings);
+
+/* Runs the predictor–corrector interior-point loop on the GPU from a fresh initial
+ * point until the stopping tests hold or max_iter is reached (paper §2: one
+ * factorisation and two solves per iteration).  Blocks until the solve ends (one
+ * 64-byte device→host read per iteration carries the stopping test).  Returns the
+ * solve status (SOLVED, SOLVED_INACCURATE, MAX_ITER) or an error (NUMERICAL, CUDA). */
+int qoco_gpu_solve(qoco_gpu_solver* solver, void* stream);
+
+/* Copies the last iterate to host buffers (any may be NULL): x[n], s[m], y[p], z[m];
+ * info (may be NULL) receives the statistics.  Synchronises the solver's stream. */
+int qoco_gpu_get_solution(const qoco_gpu_solver* solver, double* x, double* s,
+                          double* y, double* z, qoco_gpu_info* info);
+
+/* Device pointers of the solver-owned iterate (valid until cleanup): x[n], s[m], y[p], z[m]. */
+int qoco_gpu_solution_device(const qoco_gpu_solver* solver, const double** x,
+                             const double** s, const double** y, const double** z);
+
+/* Statistics of setup and of the last solve. */
+int qoco_gpu_get_info(const qoco_gpu_solver* solver, qoco_gpu_info* info);
+
+/* Adjoint of the solution map (implicit differentiation of the KKT conditions at the
+ * final iterate, reusing its factorisation).  Not part of the paper; reserved. */
+int qoco_gpu_backward(qoco_gpu_solver* solver, const double* dx, const double* dy,
+                      const double* dz, double* dP_val, double* dc, double* dA_val,
+                      double* db, double* dG_val, double* dh);
+
+/* Turns per-phase CUDA-event timing on (1) or off (0) and clears the totals. */
+int qoco_gpu_set_profiling(qoco_gpu_solver* solver, int on);
+/* Reads the per-phase totals accumulated since profiling was turned on. */
+int qoco_gpu_get_profile(const qoco_gpu_solver* solver, qoco_gpu_profile* out);
+
+/* Releases every resource of the solver (NULL is accepted). */
+int qoco_gpu_cleanup(qoco_gpu_solver* solver);
+
+/* ---- KKT system at a caller-chosen iterate (shared-iterate parity) ---------- */
+
+/* Sets the scaling from interior points s, z (device, m each): NT scaling of every
+ * cone (§2.1 "Nesterov-Todd scalings"), writes −W² into the KKT value array through
+ * the index map, and refactors K_ε (§2.2, once per iteration).  Synchronous. */
+int qoco_gpu_kkt_factor_at(qoco_gpu_solver* solver, const double* s, const double* z,
+                           void* stream);
+
+/* Solves K x = r with the current factorisation plus iterative refinement against the
+ * unregularised K (device r, x of length N_K in the original x, y, z order).
+ * Synchronous; *refine_steps and *backward_error (host, may be NULL) report the
+ * refinement.  Errors: NO_FACTOR. */
+int qoco_gpu_kkt_solve(qoco_gpu_solver* solver, const double* r, double* x,
+                       int* refine_steps, double* backward_error, void* stream);
+
+/* Copies the current full symmetric KKT (original order, CSR) to host buffers:
+ * rowptr[N_K+1], colidx[kkt_nnz], val[kkt_nnz] (any may be NULL). */
+int qoco_gpu_get_kkt(const qoco_gpu_solver* solver, int64_t* rowptr, int* colidx, double* val);
+
+/* Copies the current factor as dense arrays (host), for N_K ≤ 4096 only:
+ * perm[N_K] (new → original index), L[N_K·N_K] row-major unit lower triangular in the
+ * permuted order, D[N_K].  Errors: INVALID_ARG (too large), NO_FACTOR. */
+int qoco_gpu_get_factor_dense(const qoco_gpu_solver* solver, int* perm, double* L, double* D);
+
+/* ---- stand-alone cone kernels (paper §2.1, §2.3) ---------------------------- */
+
+/* Creates a device descriptor of K = R^l_+ × Q^{q_0} × …; q host, nsoc entries ≥ 2. */
+int qoco_gpu_cones_create(qoco_gpu_cones** out, int l, int nsoc, const int* q);
+int qoco_gpu_cones_destroy(qoco_gpu_cones* cones);
+
+/* NT scaling of interior s, z (device, m each).  Outputs (device): w[m] (orthant:
+ * √(s_i/z_i); SOC block: w̄), eta[nsoc], lambda[m] = W z. */
+int qoco_gpu_cone_nt_scaling(const qoco_gpu_cones* cones, const double* s, const double* z,
+                             double* w, double* eta, double* lambda, void* stream);
+
+/* Jordan product out = u∘v and division out = λ\v (device vectors of length m). */
+int qoco_gpu_cone_product(const qoco_gpu_cones* cones, const double* u, const double* v,
+                          double* out, void* stream);
+int qoco_gpu_cone_division(const qoco_gpu_cones* cones, const double* lam, const double* v,
+                           double* out, void* stream);
+
+/* Largest α with u + α du ∈ K (u interior), capped at `cap` (pass +inf for none):
+ * per-cone closed forms and a min over cones.  Writes one double to alpha (device).
+ * `scratch` (device) must hold qoco_gpu_cone_max_step_scratch_bytes(cones) bytes. */
+size_t qoco_gpu_cone_max_step_scratch_bytes(const qoco_gpu_cones* cones);
+int qoco_gpu_cone_max_step(const qoco_gpu_cones* cones, const double* u, const double* du,
+                           double cap, double* alpha, void* scratch, void* stream);
+
+/* ---- host-only analysis (no GPU needed) ---------------------------------------- */
+
+/* Runs the same validation, KKT assembly, ordering and symbolic analysis as
+ * qoco_gpu_setup on the host only and reports their statistics in *info; perm
+ * (host, N_K, may be NULL) receives the final new → original ordering.
+ * sn_ptr (host, may be NULL) receives the first permuted column of each supernode
+ * followed by N_K (n_supernodes + 1 entries; call once with NULL to learn the count).
+ * Errors as for setup. */
+int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A,
+                     const qoco_csc* G, int l, int nsoc, const int* q,
+                     const qoco_gpu_settings* settings, qoco_gpu_info* info, int* perm,
+                     int* sn_ptr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QOCO_GPU_H */

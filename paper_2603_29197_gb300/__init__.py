@@ -1,0 +1,294 @@
+"""Python binding of the GB300 QOCO-style interior-point solver.
+
+Thin layer over the C ABI (include/qoco_gpu.h): it converts CSC matrices and numpy
+arrays to the ABI's plain pointers, passes torch CUDA tensors by data pointer and
+the current torch stream as the cudaStream_t.  Every step of the method runs in
+libqoco_gpu.so; nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ORDER_AMD, ORDER_AUTO, ORDER_ND, ORDER_NATURAL, STATUS_NAMES,  # noqa: F401
+                   Info, Settings)
+
+__all__ = ["Solver", "Cones", "analyze", "default_settings", "load", "STATUS_NAMES"]
+
+
+def load():
+    return _lib.load()
+
+
+def default_settings(**kw) -> Settings:
+    st = Settings()
+    load().qoco_gpu_default_settings(C.byref(st))
+    for k, v in kw.items():
+        if not hasattr(st, k):
+            raise TypeError(f"unknown setting {k!r}")
+        setattr(st, k, v)
+    return st
+
+
+class _CSCHold:
+    """Keeps the int32/float64 copies of one CSC matrix alive for a call."""
+
+    def __init__(self, M, rows, cols):
+        if M is None:
+            self.ptr = None
+            return
+        M = M.tocsc() if hasattr(M, "tocsc") else M
+        self.colptr = np.ascontiguousarray(M.indptr, dtype=np.int32)
+        self.rowidx = np.ascontiguousarray(M.indices, dtype=np.int32)
+        self.val = np.ascontiguousarray(M.data, dtype=np.float64)
+        self.s = _lib.CSC(int(M.shape[0]), int(M.shape[1]), int(self.rowidx.size),
+                          self.colptr.ctypes.data_as(C.POINTER(C.c_int)),
+                          self.rowidx.ctypes.data_as(C.POINTER(C.c_int)),
+                          self.val.ctypes.data_as(C.POINTER(C.c_double)))
+        self.ptr = C.byref(self.s)
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _vec(a, n):
+    if a is None or n == 0:
+        return None
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _settings(settings, kw):
+    if settings is None:
+        return default_settings(**kw)
+    for k, v in kw.items():
+        setattr(settings, k, v)
+    return settings
+
+
+def _problem_args(prob):
+    n, m, p = int(prob.n), int(prob.m), int(prob.p)
+    P = _CSCHold(prob.P if getattr(prob, "P", None) is not None and prob.P.nnz else None, n, n)
+    A = _CSCHold(prob.A if p else None, p, n)
+    G = _CSCHold(prob.G if m else None, m, n)
+    q = np.ascontiguousarray(list(prob.q), dtype=np.int32)
+    return n, m, p, P, A, G, q
+
+
+def _torch_stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _tptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def analyze(prob, settings=None, **kw):
+    """Host-only ordering + symbolic analysis (no GPU needed): returns (info, perm, sn_ptr)."""
+    lib = load()
+    st = _settings(settings, kw)
+    n, m, p, P, A, G, q = _problem_args(prob)
+    info = Info()
+    N = n + p + m
+    perm = np.zeros(N, dtype=np.int32)
+    rc = lib.qoco_gpu_analyze(n, m, p, P.ptr, A.ptr, G.ptr, int(prob.l), len(q),
+                              q.ctypes.data_as(C.POINTER(C.c_int)), C.byref(st), C.byref(info),
+                              perm.ctypes.data_as(C.POINTER(C.c_int)), None)
+    if rc != 0:
+        raise ValueError(f"analysis failed: {STATUS_NAMES.get(rc, rc)}: {info.message.decode()}")
+    sn = np.zeros(info.n_supernodes + 1, dtype=np.int32)
+    lib.qoco_gpu_analyze(n, m, p, P.ptr, A.ptr, G.ptr, int(prob.l), len(q),
+                         q.ctypes.data_as(C.POINTER(C.c_int)), C.byref(st), None, None,
+                         sn.ctypes.data_as(C.POINTER(C.c_int)))
+    return info.as_dict(), perm, sn
+
+
+class SolverError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{STATUS_NAMES.get(code, code)} ({code}) {msg}")
+        self.code = code
+
+
+class Solver:
+    """setup(n, m, p, P, c, A, b, G, h, l, nsoc, q) on construction, then solve()
+    (the paper's interface, §2.1).  `prob` is any object with those attributes
+    (P upper-triangular CSC)."""
+
+    def __init__(self, prob, settings=None, **kw):
+        self.lib = load()
+        self.st = _settings(settings, kw)
+        n, m, p, P, A, G, q = _problem_args(prob)
+        self.n, self.m, self.p = n, m, p
+        self.N = n + m + p
+        c = _vec(prob.c, n)
+        b = _vec(prob.b, p)
+        h = _vec(prob.h, m)
+        self._h = C.c_void_p()
+        rc = self.lib.qoco_gpu_setup(C.byref(self._h), n, m, p, P.ptr, _dptr(c), A.ptr, _dptr(b),
+                                     G.ptr, _dptr(h), int(prob.l), len(q),
+                                     q.ctypes.data_as(C.POINTER(C.c_int)) if len(q) else None,
+                                     C.byref(self.st))
+        if rc != 0:
+            self._h = None
+            raise SolverError(rc, "setup")
+
+    def solve(self, stream=None) -> int:
+        return int(self.lib.qoco_gpu_solve(self._h, _torch_stream(stream) if stream is not None else None))
+
+    def info(self) -> dict:
+        info = Info()
+        self.lib.qoco_gpu_get_info(self._h, C.byref(info))
+        return info.as_dict()
+
+    def solution(self):
+        x = np.zeros(self.n)
+        s = np.zeros(self.m)
+        y = np.zeros(self.p)
+        z = np.zeros(self.m)
+        info = Info()
+        rc = self.lib.qoco_gpu_get_solution(self._h, _dptr(x), _dptr(s), _dptr(y), _dptr(z),
+                                            C.byref(info))
+        if rc != 0:
+            raise SolverError(rc, "get_solution")
+        return dict(x=x, s=s, y=y, z=z, info=info.as_dict())
+
+    def device_solution(self):
+        """(x, s, y, z) as device addresses (ints) owned by the solver."""
+        ptrs = [C.c_void_p() for _ in range(4)]
+        self.lib.qoco_gpu_solution_device(self._h, *[C.byref(v) for v in ptrs])
+        return tuple(v.value for v in ptrs)
+
+    # ---- shared-iterate entry points (torch CUDA float64 tensors) ----
+    def kkt_factor_at(self, s, z, stream=None):
+        rc = self.lib.qoco_gpu_kkt_factor_at(self._h, _tptr(s), _tptr(z), _torch_stream(stream))
+        if rc != 0:
+            raise SolverError(rc, "kkt_factor_at")
+
+    def kkt_solve(self, r, x, stream=None):
+        steps = C.c_int()
+        be = C.c_double()
+        rc = self.lib.qoco_gpu_kkt_solve(self._h, _tptr(r), _tptr(x), C.byref(steps), C.byref(be),
+                                         _torch_stream(stream))
+        if rc != 0:
+            raise SolverError(rc, "kkt_solve")
+        return steps.value, be.value
+
+    def get_kkt(self):
+        info = self.info()
+        N, nnz = int(info["kkt_dim"]), int(info["kkt_nnz"])
+        rowptr = np.zeros(N + 1, dtype=np.int64)
+        col = np.zeros(nnz, dtype=np.int32)
+        val = np.zeros(nnz)
+        rc = self.lib.qoco_gpu_get_kkt(self._h, rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                                       col.ctypes.data_as(C.POINTER(C.c_int)), _dptr(val))
+        if rc != 0:
+            raise SolverError(rc, "get_kkt")
+        return rowptr, col, val
+
+    def factor_dense(self):
+        N = self.N
+        perm = np.zeros(N, dtype=np.int32)
+        L = np.zeros((N, N))
+        D = np.zeros(N)
+        rc = self.lib.qoco_gpu_get_factor_dense(self._h, perm.ctypes.data_as(C.POINTER(C.c_int)),
+                                                _dptr(L), _dptr(D))
+        if rc != 0:
+            raise SolverError(rc, "get_factor_dense")
+        return perm, L, D
+
+    def set_profiling(self, on=True):
+        rc = self.lib.qoco_gpu_set_profiling(self._h, 1 if on else 0)
+        if rc != 0:
+            raise SolverError(rc, "set_profiling")
+
+    def profile(self) -> dict:
+        pr = _lib.Profile()
+        self.lib.qoco_gpu_get_profile(self._h, C.byref(pr))
+        return pr.as_dict()
+
+    def backward(self, *args):
+        rc = self.lib.qoco_gpu_backward(self._h, *([None] * 9))
+        raise SolverError(rc, "backward")
+
+    def close(self):
+        if self._h:
+            self.lib.qoco_gpu_cleanup(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cones:
+    """Device descriptor of K = R^l_+ × Q^{q_0} × … for the stand-alone cone kernels."""
+
+    def __init__(self, l, q):
+        self.lib = load()
+        self.l = int(l)
+        self.q = np.ascontiguousarray(list(q), dtype=np.int32)
+        self.m = self.l + int(self.q.sum())
+        self._h = C.c_void_p()
+        rc = self.lib.qoco_gpu_cones_create(C.byref(self._h), self.l, len(self.q),
+                                            self.q.ctypes.data_as(C.POINTER(C.c_int)) if len(self.q) else None)
+        if rc != 0:
+            self._h = None
+            raise SolverError(rc, "cones_create")
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise SolverError(rc, what)
+
+    def nt_scaling(self, s, z, stream=None):
+        import torch
+        w = torch.empty_like(s)
+        lam = torch.empty_like(s)
+        eta = torch.empty(max(1, len(self.q)), dtype=s.dtype, device=s.device)
+        self._check(self.lib.qoco_gpu_cone_nt_scaling(self._h, _tptr(s), _tptr(z), _tptr(w), _tptr(eta),
+                                                      _tptr(lam), _torch_stream(stream)), "nt_scaling")
+        return w, eta[:len(self.q)], lam
+
+    def product(self, u, v, stream=None):
+        import torch
+        out = torch.empty_like(u)
+        self._check(self.lib.qoco_gpu_cone_product(self._h, _tptr(u), _tptr(v), _tptr(out),
+                                                   _torch_stream(stream)), "product")
+        return out
+
+    def division(self, lam, v, stream=None):
+        import torch
+        out = torch.empty_like(v)
+        self._check(self.lib.qoco_gpu_cone_division(self._h, _tptr(lam), _tptr(v), _tptr(out),
+                                                    _torch_stream(stream)), "division")
+        return out
+
+    def max_step_scratch_bytes(self):
+        return int(self.lib.qoco_gpu_cone_max_step_scratch_bytes(self._h))
+
+    def max_step(self, u, du, cap=float("inf"), scratch=None, stream=None):
+        import torch
+        if scratch is None:
+            scratch = torch.empty(self.max_step_scratch_bytes() // 8 + 1, dtype=torch.float64,
+                                  device=u.device)
+        out = torch.empty(1, dtype=torch.float64, device=u.device)
+        self._check(self.lib.qoco_gpu_cone_max_step(self._h, _tptr(u), _tptr(du), float(cap), _tptr(out),
+                                                    _tptr(scratch), _torch_stream(stream)), "max_step")
+        return out
+
+    def close(self):
+        if self._h:
+            self.lib.qoco_gpu_cones_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

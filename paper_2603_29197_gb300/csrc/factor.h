@@ -1,0 +1,53 @@
+// Device view of the supernodal structure and the per-level launch plan.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace qoco {
+
+constexpr int kSmemFront = 160;       // fronts up to this order are factored in shared memory
+constexpr int kMaxSolveFront = 26000; // solve kernels keep one front vector in shared memory
+
+struct FactorView {
+    const int* first = nullptr;      // ns: first permuted column
+    const int* ncol = nullptr;       // c_s
+    const int* nrow = nullptr;       // f_s
+    const int64_t* row_ptr = nullptr;
+    const int* rows = nullptr;       // R_s (permuted indices)
+    const int64_t* front_off = nullptr;
+    const int64_t* upd_off = nullptr;
+    const int* rel = nullptr;
+    const int* child_ptr = nullptr;
+    const int* child = nullptr;
+    const int64_t* amap_ptr = nullptr;
+    const int64_t* amap_slot = nullptr;
+    const int* amap_off = nullptr;
+    const signed char* dsign = nullptr;
+    const int* perm = nullptr;       // new → original
+    double* front = nullptr;         // Σ f_s² doubles
+    double* upd = nullptr;           // Σ r_s doubles (solve update vectors)
+    int* nreg = nullptr;             // dynamic-regularisation counter
+    double eps = 1e-8, dyn_thresh = 1e-13, dyn_value = 1e-7;
+};
+
+struct LevelPlan {
+    int count = 0, max_f = 0, off_all = 0;
+    int n_small = 0, max_small = 0, off_small = 0;
+    int n_large = 0, off_large = 0;
+};
+
+struct FactorPlan {
+    std::vector<LevelPlan> levels;
+    int* d_all = nullptr;    // supernodes of every level, level by level
+    int* d_small = nullptr;  // fronts with f ≤ kSmemFront
+    int* d_large = nullptr;  // the others
+};
+
+int factor_set_attributes();
+int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
+int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
+                 double* x, bool accumulate, cudaStream_t st);
+
+}  // namespace qoco

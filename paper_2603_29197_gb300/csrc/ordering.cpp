@@ -1,0 +1,362 @@
+// Fill-reducing orderings of the KKT graph, run once at set-up.
+//
+//  * order_amd: approximate minimum degree on the quotient graph (Amestoy, Davis &
+//    Duff, SIAM J. Matrix Anal. Appl. 17(4), 1996): eliminated nodes become elements,
+//    degrees are the approximate external degrees of that paper's bound, elements
+//    that become subsets of the new element are absorbed, indistinguishable
+//    variables are merged into supervariables (hash + exact comparison), and rows
+//    denser than dense_factor·√N are ordered last.  Written from the paper's
+//    description with per-node std::vector lists instead of one packed workspace.
+//  * order_nd: nested dissection by breadth-first level structures from a
+//    pseudo-peripheral node (George & Liu): a thin middle level is the vertex
+//    separator, parts are dissected recursively and ordered before their separator;
+//    parts at or below `leaf_size` nodes (or without a usable separator) are ordered
+//    by AMD.  Gives the O(log N)-deep elimination trees that level-scheduled GPU
+//    factorisation needs on banded / stage-structured problems.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <functional>
+#include <numeric>
+
+#include "symbolic.h"
+
+namespace qoco {
+
+namespace {
+
+enum : signed char { VAR = 0, ELEM = 1, DEAD = 2, DENSE = 3 };
+
+}  // namespace
+
+std::vector<int> order_amd(const Graph& g, double dense_factor) {
+    const int N = g.N;
+    std::vector<int> order;
+    order.reserve(N);
+    if (N == 0) return order;
+    int dense_thr = std::max(16, (int)(dense_factor * std::sqrt((double)N)));
+    std::vector<signed char> status(N, VAR);
+    int ndense = 0;
+    for (int i = 0; i < N; ++i)
+        if (N >= 1000 && g.ptr[i + 1] - g.ptr[i] > dense_thr) { status[i] = DENSE; ++ndense; }
+
+    std::vector<std::vector<int>> vars(N), elems(N), Le(N);
+    std::vector<int> nv(N, 1), deg(N, 0), wdeg(N, 0), w(N, 0);
+    std::vector<int> flag(N, 0), wflag(N, 0), merged_into(N, -1);
+    std::vector<uint64_t> hsh(N, 0);
+    for (int i = 0; i < N; ++i) {
+        if (status[i] == DENSE) continue;
+        for (int64_t t = g.ptr[i]; t < g.ptr[i + 1]; ++t)
+            if (status[g.adj[t]] != DENSE) vars[i].push_back(g.adj[t]);
+        deg[i] = (int)vars[i].size();
+    }
+    std::vector<int> head(N + 1, -1), nxt(N, -1), prv(N, -1);
+    int mindeg = N;
+    auto insert = [&](int i) {
+        int d = deg[i];
+        nxt[i] = head[d];
+        prv[i] = -1;
+        if (head[d] >= 0) prv[head[d]] = i;
+        head[d] = i;
+        if (d < mindeg) mindeg = d;
+    };
+    auto remove = [&](int i) {
+        if (prv[i] >= 0) nxt[prv[i]] = nxt[i];
+        else head[deg[i]] = nxt[i];
+        if (nxt[i] >= 0) prv[nxt[i]] = prv[i];
+    };
+    int nleft = 0;
+    for (int i = 0; i < N; ++i)
+        if (status[i] == VAR) { insert(i); ++nleft; }
+
+    int stamp = 0;
+    std::vector<int> Lp;
+    std::vector<int> tmpE, tmpV, tmpE2, tmpV2;
+    while (nleft > 0) {
+        while (mindeg <= N && head[mindeg] < 0) ++mindeg;
+        const int p = head[mindeg];
+        remove(p);
+        ++stamp;
+        Lp.clear();
+        flag[p] = stamp;
+        for (int e : elems[p]) {
+            if (status[e] != ELEM) continue;
+            for (int i : Le[e])
+                if (status[i] == VAR && flag[i] != stamp) { flag[i] = stamp; Lp.push_back(i); }
+            status[e] = DEAD;  // absorbed into the new element p
+            std::vector<int>().swap(Le[e]);
+        }
+        for (int i : vars[p])
+            if (status[i] == VAR && flag[i] != stamp) { flag[i] = stamp; Lp.push_back(i); }
+        status[p] = ELEM;
+        std::vector<int>().swap(vars[p]);
+        std::vector<int>().swap(elems[p]);
+        order.push_back(p);
+        nleft -= nv[p];
+
+        int degLp = 0;
+        for (int i : Lp) degLp += nv[i];
+        // |Le \ Lp| for every element adjacent to Lp
+        for (int i : Lp) {
+            remove(i);
+            for (int e : elems[i]) {
+                if (status[e] != ELEM) continue;
+                if (wflag[e] != stamp) { wflag[e] = stamp; w[e] = wdeg[e] - nv[i]; }
+                else w[e] -= nv[i];
+            }
+        }
+        // degree update, list pruning, aggressive absorption
+        for (int i : Lp) {
+            tmpE.clear();
+            int dext = 0;
+            for (int e : elems[i]) {
+                if (status[e] != ELEM) continue;
+                if (w[e] <= 0) {  // Le ⊆ Lp: absorb e into p
+                    status[e] = DEAD;
+                    std::vector<int>().swap(Le[e]);
+                    continue;
+                }
+                tmpE.push_back(e);
+                dext += w[e];
+            }
+            tmpE.push_back(p);
+            tmpV.clear();
+            int dv = 0;
+            for (int j : vars[i])
+                if (status[j] == VAR && flag[j] != stamp) { tmpV.push_back(j); dv += nv[j]; }
+            elems[i].swap(tmpE);
+            vars[i].swap(tmpV);
+            long d1 = (long)dv + degLp - nv[i] + dext;
+            long d2 = (long)deg[i] + degLp - nv[i];
+            long d3 = (long)nleft - nv[i];
+            long d = std::min(d1, std::min(d2, d3));
+            deg[i] = (int)std::max(0L, d);
+            uint64_t hv = 0;
+            for (int e : elems[i]) hv += (uint64_t)e * 0x9E3779B97F4A7C15ull + 1;
+            for (int j : vars[i]) hv += (uint64_t)j * 0xC2B2AE3D27D4EB4Full + 7;
+            hsh[i] = hv;
+        }
+        // supervariable detection among Lp
+        if (Lp.size() > 1) {
+            std::vector<int> idx(Lp);
+            std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+                if (hsh[a] != hsh[b]) return hsh[a] < hsh[b];
+                return a < b;
+            });
+            for (size_t a = 0; a < idx.size();) {
+                size_t b = a + 1;
+                while (b < idx.size() && hsh[idx[b]] == hsh[idx[a]]) ++b;
+                if (b - a > 1) {
+                    for (size_t x = a; x < b; ++x) {
+                        int i = idx[x];
+                        if (status[i] != VAR) continue;
+                        tmpE = elems[i]; std::sort(tmpE.begin(), tmpE.end());
+                        tmpV = vars[i]; std::sort(tmpV.begin(), tmpV.end());
+                        for (size_t y = x + 1; y < b; ++y) {
+                            int j = idx[y];
+                            if (status[j] != VAR) continue;
+                            if (elems[j].size() != tmpE.size() || vars[j].size() != tmpV.size()) continue;
+                            tmpE2 = elems[j]; std::sort(tmpE2.begin(), tmpE2.end());
+                            if (tmpE2 != tmpE) continue;
+                            tmpV2 = vars[j]; std::sort(tmpV2.begin(), tmpV2.end());
+                            if (tmpV2 != tmpV) continue;
+                            // merge j into i
+                            nv[i] += nv[j];
+                            deg[i] = std::max(0, deg[i] - nv[j]);
+                            nv[j] = 0;
+                            status[j] = DEAD;
+                            merged_into[j] = i;
+                            std::vector<int>().swap(vars[j]);
+                            std::vector<int>().swap(elems[j]);
+                        }
+                    }
+                }
+                a = b;
+            }
+        }
+        // the new element and the reinsertion of its variables
+        std::vector<int>& L = Le[p];
+        L.clear();
+        int wsum = 0;
+        for (int i : Lp)
+            if (status[i] == VAR) { L.push_back(i); wsum += nv[i]; }
+        wdeg[p] = wsum;
+        for (int i : L) {
+            deg[i] = std::min(deg[i], std::max(0, nleft - nv[i]));
+            insert(i);
+        }
+    }
+
+    // expand supervariables: each eliminated principal is followed by its members
+    std::vector<std::vector<int>> members(N);
+    for (int j = 0; j < N; ++j)
+        if (merged_into[j] >= 0) members[merged_into[j]].push_back(j);
+    std::vector<int> out;
+    out.reserve(N);
+    std::vector<int> stack;
+    for (int p : order) {
+        stack.assign(1, p);
+        while (!stack.empty()) {
+            int v = stack.back();
+            stack.pop_back();
+            out.push_back(v);
+            for (int u : members[v]) stack.push_back(u);
+        }
+    }
+    for (int i = 0; i < N; ++i)
+        if (status[i] == DENSE) out.push_back(i);
+    return out;
+}
+
+namespace {
+
+// AMD on the subgraph induced by `nodes`; appends the ordered nodes to `out`.
+void amd_subset(const Graph& g, const std::vector<int>& nodes, std::vector<int>& local,
+                std::vector<int>* out) {
+    const int n = (int)nodes.size();
+    if (n <= 2) {
+        out->insert(out->end(), nodes.begin(), nodes.end());
+        return;
+    }
+    for (int i = 0; i < n; ++i) local[nodes[i]] = i;
+    Graph sg;
+    sg.N = n;
+    sg.ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        int v = nodes[i];
+        for (int64_t t = g.ptr[v]; t < g.ptr[v + 1]; ++t) {
+            int u = g.adj[t];
+            if (local[u] >= 0) sg.adj.push_back(local[u]);
+        }
+        sg.ptr[i + 1] = (int64_t)sg.adj.size();
+    }
+    std::vector<int> o = order_amd(sg);
+    for (int i : o) out->push_back(nodes[i]);
+    for (int i = 0; i < n; ++i) local[nodes[i]] = -1;
+}
+
+struct ND {
+    const Graph& g;
+    int leaf;
+    std::vector<int> tag, local, lev, q;
+    int next_tag = 1;
+    std::vector<int>* out;
+
+    ND(const Graph& gg, int leaf_size, std::vector<int>* o)
+        : g(gg), leaf(leaf_size), tag(gg.N, 0), local(gg.N, -1), lev(gg.N, -1), q(), out(o) {}
+
+    // BFS within the nodes carrying tag t; returns levels (as offsets into q).
+    int bfs(int root, int t, std::vector<int>& lptr) {
+        q.clear();
+        lptr.clear();
+        q.push_back(root);
+        lev[root] = 0;
+        size_t h = 0;
+        lptr.push_back(0);
+        int cur = 0;
+        while (h < q.size()) {
+            int v = q[h];
+            if (lev[v] != cur) { lptr.push_back((int)h); cur = lev[v]; }
+            ++h;
+            for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; ++e) {
+                int u = g.adj[e];
+                if (tag[u] == t && lev[u] < 0) { lev[u] = lev[v] + 1; q.push_back(u); }
+            }
+        }
+        lptr.push_back((int)q.size());
+        return (int)lptr.size() - 1;  // number of levels
+    }
+    void clear_lev() { for (int v : q) lev[v] = -1; }
+
+    int local_degree(int v, int t) const {
+        int d = 0;
+        for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; ++e) d += tag[g.adj[e]] == t;
+        return d;
+    }
+
+    void run(std::vector<int> nodes) {
+        if ((int)nodes.size() <= leaf) { amd_subset(g, nodes, local, out); return; }
+        const int t = next_tag++;
+        for (int v : nodes) tag[v] = t;
+        // connected components
+        std::vector<int> lptr;
+        std::vector<std::vector<int>> comps;
+        {
+            std::vector<int> seen;
+            for (int v : nodes) {
+                if (lev[v] >= 0) continue;
+                bfs(v, t, lptr);
+                comps.emplace_back(q.begin(), q.end());
+                // keep lev marks until all components found
+                seen.insert(seen.end(), q.begin(), q.end());
+            }
+            for (int v : seen) lev[v] = -1;
+        }
+        if (comps.size() > 1) {
+            for (auto& c : comps) run(std::move(c));
+            return;
+        }
+        // pseudo-peripheral root
+        int root = nodes[0];
+        int nl = bfs(root, t, lptr);
+        for (int it = 0; it < 8; ++it) {
+            int best = -1, bd = 1 << 30;
+            for (int k = lptr[nl - 1]; k < lptr[nl]; ++k) {
+                int d = local_degree(q[k], t);
+                if (d < bd) { bd = d; best = q[k]; }
+            }
+            clear_lev();
+            int nl2 = bfs(best, t, lptr);
+            if (nl2 <= nl) { clear_lev(); nl = bfs(root, t, lptr); break; }
+            root = best;
+            nl = nl2;
+        }
+        const int S = (int)nodes.size();
+        if (nl < 3) { clear_lev(); amd_subset(g, nodes, local, out); return; }
+        // separator level: smallest level whose both sides hold ≥ 20% of the nodes,
+        // else the median level
+        int pick = -1, psize = 1 << 30, median = -1;
+        for (int k = 1; k < nl - 1; ++k) {
+            int before = lptr[k], after = S - lptr[k + 1];
+            int sz = lptr[k + 1] - lptr[k];
+            if (median < 0 && lptr[k + 1] >= S / 2) median = k;
+            if (before >= S / 5 && after >= S / 5 && sz < psize) { psize = sz; pick = k; }
+        }
+        if (pick < 0) pick = median < 0 ? nl / 2 : median;
+        // thin the separator: keep only level nodes touching the next level
+        std::vector<int> part1, part2, sep;
+        for (int k = 0; k < lptr[pick]; ++k) part1.push_back(q[k]);
+        for (int k = lptr[pick + 1]; k < S; ++k) part2.push_back(q[k]);
+        for (int k = lptr[pick]; k < lptr[pick + 1]; ++k) {
+            int v = q[k];
+            bool touches = false;
+            for (int64_t e = g.ptr[v]; e < g.ptr[v + 1] && !touches; ++e) {
+                int u = g.adj[e];
+                touches = tag[u] == t && lev[u] == pick + 1;
+            }
+            (touches ? sep : part1).push_back(v);
+        }
+        clear_lev();
+        if ((double)sep.size() > 0.4 * S || part1.empty() || part2.empty()) {
+            amd_subset(g, nodes, local, out);
+            return;
+        }
+        run(std::move(part1));
+        run(std::move(part2));
+        amd_subset(g, sep, local, out);
+    }
+};
+
+}  // namespace
+
+std::vector<int> order_nd(const Graph& g, int leaf_size) {
+    std::vector<int> out;
+    out.reserve(g.N);
+    ND nd(g, std::max(leaf_size, 4), &out);
+    std::vector<int> all(g.N);
+    std::iota(all.begin(), all.end(), 0);
+    nd.run(std::move(all));
+    return out;
+}
+
+}  // namespace qoco

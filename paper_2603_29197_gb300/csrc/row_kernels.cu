@@ -1,0 +1,229 @@
+// Row kernels over the full symmetric KKT (CSR, original x | y | z order): the
+// interior-point residuals with their ∞-norms and dot products (K6 + K8 inputs),
+// the refinement residual r − Kx, and ‖K‖∞.  A group of LPR lanes owns one row;
+// each block writes its partial sums / maxima to `partial[block][·]`, and one
+// single-block kernel reduces them in a fixed order (deterministic results).
+#include "row_kernels.h"
+
+namespace qoco {
+
+constexpr int kRowThreads = 256;
+
+template <int NV>
+__device__ __forceinline__ void store_partials(double (&v)[NV], const bool (&is_max)[NV], double* partial) {
+    __shared__ double sm[NV * 32];
+    block_reduce<NV>(v, is_max, sm);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) partial[(int64_t)blockIdx.x * NV + k] = v[k];
+}
+
+// residuals: r_x = Px + c + Aᵀy + Gᵀz, r_y = Ax − b, r_z = Gx + s − h
+// sums: xᵀPx, cᵀx, bᵀy, hᵀz, sᵀz   maxes: |Px|,|Aᵀy|,|Gᵀz|,|Ax|,|Gx|,|r_x|,|r_y|,|r_z|,|s|
+template <int LPR>
+__global__ void k_residual(KKTView K, const double* __restrict__ xyz, const double* __restrict__ s,
+                           const double* __restrict__ c, const double* __restrict__ b,
+                           const double* __restrict__ h, double* __restrict__ r, double* partial) {
+    const int gl = (blockIdx.x * blockDim.x + threadIdx.x);
+    const int row = gl / LPR, lane = gl % LPR;
+    const int n = K.n, p = K.p;
+    double v[kResNV];
+    bool is_max[kResNV];
+#pragma unroll
+    for (int k = 0; k < kResNV; ++k) { v[k] = 0.0; is_max[k] = k >= kResNSum; }
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    if (row < K.N) {
+        const int64_t beg = K.rowptr[row], end = K.rowptr[row + 1];
+        for (int64_t t = beg + lane; t < end; t += LPR) {
+            const int j = K.colidx[t];
+            const double kv = K.val[t] * xyz[j];
+            if (j < n) a0 += kv;
+            else if (j < n + p) a1 += kv;
+            else a2 += kv;
+        }
+    }
+    a0 = group_sum<LPR>(a0);  // every lane of the warp takes part in the shuffles
+    a1 = group_sum<LPR>(a1);
+    a2 = group_sum<LPR>(a2);
+    if (row < K.N) {
+        if (lane == 0) {
+            if (row < n) {
+                const double rx = a0 + c[row] + a1 + a2;
+                r[row] = rx;
+                v[0] = xyz[row] * a0;   // xᵀPx
+                v[1] = c[row] * xyz[row];
+                v[5] = fabs(a0);        // |Px|
+                v[6] = fabs(a1);        // |Aᵀy|
+                v[7] = fabs(a2);        // |Gᵀz|
+                v[10] = fabs(rx);
+            } else if (row < n + p) {
+                const int i = row - n;
+                const double ry = a0 - b[i];
+                r[row] = ry;
+                v[2] = b[i] * xyz[row];
+                v[8] = fabs(a0);        // |Ax|
+                v[11] = fabs(ry);
+            } else {
+                const int i = row - n - p;
+                const double rz = a0 + s[i] - h[i];
+                r[row] = rz;
+                v[3] = h[i] * xyz[row];
+                v[4] = s[i] * xyz[row];
+                v[9] = fabs(a0);        // |Gx|
+                v[12] = fabs(rz);
+                v[13] = fabs(s[i]);
+            }
+        }
+    }
+    store_partials<kResNV>(v, is_max, partial);
+}
+
+// res = r − K x (unregularised K), maxes |res|, |x|, |r|
+template <int LPR>
+__global__ void k_spmv_res(KKTView K, const double* __restrict__ x, const double* __restrict__ r,
+                           double* __restrict__ res, double* partial) {
+    const int gl = (blockIdx.x * blockDim.x + threadIdx.x);
+    const int row = gl / LPR, lane = gl % LPR;
+    double v[3] = {0.0, 0.0, 0.0};
+    const bool is_max[3] = {true, true, true};
+    double acc = 0.0;
+    if (row < K.N)
+        for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR)
+            acc += K.val[t] * x[K.colidx[t]];
+    acc = group_sum<LPR>(acc);
+    if (row < K.N) {
+        if (lane == 0) {
+            const double e = r[row] - acc;
+            res[row] = e;
+            v[0] = fabs(e);
+            v[1] = fabs(x[row]);
+            v[2] = fabs(r[row]);
+        }
+    }
+    store_partials<3>(v, is_max, partial);
+}
+
+// max_i Σ_j |K_ij|
+template <int LPR>
+__global__ void k_norm_inf(KKTView K, double* partial) {
+    const int gl = (blockIdx.x * blockDim.x + threadIdx.x);
+    const int row = gl / LPR, lane = gl % LPR;
+    double v[1] = {0.0};
+    const bool is_max[1] = {true};
+    double acc = 0.0;
+    if (row < K.N)
+        for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR) acc += fabs(K.val[t]);
+    acc = group_sum<LPR>(acc);
+    v[0] = acc;
+    store_partials<1>(v, is_max, partial);
+}
+
+// one block: reduce NV columns of partial[nb][NV] in a fixed order into out[NV]
+__device__ void reduce_columns(const double* partial, int nb, int NV, unsigned max_mask, double* out) {
+    __shared__ double sm[32];
+    for (int k = 0; k < NV; ++k) {
+        const bool mx = (max_mask >> k) & 1u;
+        double a = 0.0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const double t = partial[(int64_t)i * NV + k];
+            a = mx ? fmax(a, t) : a + t;
+        }
+        a = mx ? warp_max(a) : warp_sum(a);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) sm[wid] = a;
+        __syncthreads();
+        if (wid == 0) {
+            double t = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0.0;
+            t = mx ? warp_max(t) : warp_sum(t);
+            if (lane == 0) out[k] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_finalize_residual(const double* __restrict__ partial, int nb, IPMScalars* S) {
+    __shared__ double red[kResNV];
+    reduce_columns(partial, nb, kResNV, ((1u << kResNV) - 1) & ~((1u << kResNSum) - 1), red);
+    if (threadIdx.x != 0) return;
+    const double xPx = red[0], cx = red[1], by = red[2], hz = red[3], sz = red[4];
+    S->pobj = 0.5 * xPx + cx;
+    S->dobj = -0.5 * xPx - by - hz;
+    S->gap = sz;
+    S->mu = S->nu > 0 ? sz / S->nu : 0.0;
+    S->Px_inf = red[5]; S->Aty_inf = red[6]; S->Gtz_inf = red[7];
+    S->Ax_inf = red[8]; S->Gx_inf = red[9];
+    S->rx_inf = red[10]; S->ry_inf = red[11]; S->rz_inf = red[12]; S->s_inf = red[13];
+    bool finite = true;
+    for (int k = 0; k < kResNV; ++k) finite = finite && isfinite(red[k]);
+    S->nonfinite = finite ? 0 : 1;
+    auto conv = [&](double ea, double er) {
+        const bool oy = S->ry_inf <= ea + er * fmax(S->Ax_inf, S->b_inf);
+        const bool oz = S->rz_inf <= ea + er * fmax(S->Gx_inf, fmax(S->s_inf, S->h_inf));
+        const bool ox = S->rx_inf <= ea + er * fmax(fmax(S->Px_inf, S->Aty_inf), fmax(S->Gtz_inf, S->c_inf));
+        const bool og = fabs(S->gap) <= ea + er * fmax(1.0, fmax(fabs(S->pobj), fabs(S->dobj)));
+        return ox && oy && oz && og;
+    };
+    S->converged = conv(S->abstol, S->reltol) ? 1 : 0;
+    S->converged_inacc = conv(S->abstol_inacc, S->reltol_inacc) ? 1 : 0;
+}
+
+__global__ void k_finalize_refine(const double* __restrict__ partial, int nb, IPMScalars* S) {
+    __shared__ double red[3];
+    reduce_columns(partial, nb, 3, 7u, red);
+    if (threadIdx.x != 0) return;
+    const double den = S->normK * red[1] + red[2];
+    const double be = den > 0.0 ? red[0] / den : 0.0;
+    S->berr = be;
+    S->refine_done = (be <= S->refine_tol || !isfinite(be)) ? 1 : 0;
+}
+
+__global__ void k_finalize_norm(const double* __restrict__ partial, int nb, IPMScalars* S) {
+    __shared__ double red[1];
+    reduce_columns(partial, nb, 1, 1u, red);
+    if (threadIdx.x == 0) S->normK = red[0];
+}
+
+// ---- launchers ----------------------------------------------------------------
+static int rows_blocks(int N, int lpr) {
+    const int rows_per_block = kRowThreads / lpr;
+    return (N + rows_per_block - 1) / rows_per_block;
+}
+// partial-buffer size in doubles: the most blocks (32 lanes per row) times the most
+// values per block (the residual pass)
+int row_partials(int N) { return rows_blocks(N, 32) * kResNV; }
+
+#define QOCO_LPR_SWITCH(lpr, KERNEL, ...)                                          \
+    switch (lpr) {                                                                 \
+        case 4: KERNEL<4><<<rows_blocks(K.N, 4), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 4); break;   \
+        case 8: KERNEL<8><<<rows_blocks(K.N, 8), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 8); break;   \
+        case 16: KERNEL<16><<<rows_blocks(K.N, 16), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 16); break; \
+        default: KERNEL<32><<<rows_blocks(K.N, 32), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 32); break; \
+    }
+
+int launch_residual(const KKTView& K, int lpr, const double* xyz, const double* s, const double* c,
+                    const double* b, const double* h, double* r, double* partial, int64_t cap,
+                    IPMScalars* S, cudaStream_t st) {
+    if ((int64_t)rows_blocks(K.N, lpr) * kResNV > cap) return -1;
+    int nb = 0;
+    QOCO_LPR_SWITCH(lpr, k_residual, K, xyz, s, c, b, h, r, partial)
+    k_finalize_residual<<<1, 512, 0, st>>>(partial, nb, S);
+    return 0;
+}
+int launch_spmv_res(const KKTView& K, int lpr, const double* x, const double* r, double* res,
+                    double* partial, int64_t cap, IPMScalars* S, cudaStream_t st) {
+    if ((int64_t)rows_blocks(K.N, lpr) * 3 > cap) return -1;
+    int nb = 0;
+    QOCO_LPR_SWITCH(lpr, k_spmv_res, K, x, r, res, partial)
+    k_finalize_refine<<<1, 512, 0, st>>>(partial, nb, S);
+    return 0;
+}
+int launch_norm_inf(const KKTView& K, int lpr, double* partial, int64_t cap, IPMScalars* S,
+                    cudaStream_t st) {
+    if ((int64_t)rows_blocks(K.N, lpr) > cap) return -1;
+    int nb = 0;
+    QOCO_LPR_SWITCH(lpr, k_norm_inf, K, partial)
+    k_finalize_norm<<<1, 512, 0, st>>>(partial, nb, S);
+    return 0;
+}
+
+}  // namespace qoco

@@ -1,0 +1,859 @@
+// Device interior-point driver and the C ABI (include/qoco_gpu.h).
+//
+// One iteration (paper §2: one factorisation, two solves, cone operations):
+//   residuals + stopping test (K6/K8) → NT scaling and −W² into the KKT values
+//   (K1/K2) → numeric LDLᵀ (K5) → predictor rhs (K3), solve + refinement (K7/K6),
+//   Δs, affine step and σ (K4) → corrector rhs, solve + refinement, Δs, step (K4)
+//   → update.  All of it runs on the device; the host reads one small struct of
+//   scalars per iteration (the stopping test) and one flag per refinement check.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cone_kernels.h"
+#include "factor.h"
+#include "qoco_gpu.h"
+#include "row_kernels.h"
+#include "symbolic.h"
+
+namespace qoco {
+
+static thread_local char g_cuda_msg[160];
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_cuda_msg, sizeof g_cuda_msg, "CUDA error %s at %s:%d (%s)", cudaGetErrorString(e), file,
+             line, what);
+    if (e == cudaErrorMemoryAllocation) return QOCO_GPU_ERR_OOM;
+    return QOCO_GPU_ERR_CUDA;
+}
+
+// ---- small vector kernels ---------------------------------------------------------
+__global__ void k_init_rhs(double* rhs, const double* c, const double* b, const double* h, int n, int p,
+                           int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) rhs[i] = -c[i];
+    else if (i < n + p) rhs[i] = b[i - n];
+    else if (i < n + p + m) rhs[i] = h[i - n - p];
+}
+// xyz ← sol, s ← −z
+__global__ void k_init_iterate(const double* sol, double* xyz, double* s, int n, int p, int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n + p + m) xyz[i] = sol[i];
+    if (i >= n + p && i < n + p + m) s[i - n - p] = -sol[i];
+}
+__global__ void k_shift_finalize(const double* partial, int nb, IPMScalars* S) {
+    __shared__ double sm[64];
+    double a = -INFINITY, b = -INFINITY;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a = fmax(a, partial[2 * i]);
+        b = fmax(b, partial[2 * i + 1]);
+    }
+    a = -warp_min(-a);
+    b = -warp_min(-b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { sm[wid] = a; sm[32 + wid] = b; }
+    __syncthreads();
+    if (wid == 0) {
+        const bool ok = lane < (int)(blockDim.x >> 5);
+        double t1 = ok ? sm[lane] : -INFINITY, t2 = ok ? sm[32 + lane] : -INFINITY;
+        t1 = -warp_min(-t1);
+        t2 = -warp_min(-t2);
+        if (lane == 0) { S->shift[0] = t1; S->shift[1] = t2; }
+    }
+}
+__global__ void k_neg_copy(double* dst, const double* src, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = -src[i];
+}
+__global__ void k_sigma(IPMScalars* S, double exponent) {
+    const double aa = fmin(1.0, S->alpha_max);
+    S->alpha_a = aa;
+    const double sg = pow(1.0 - aa, exponent);
+    S->sigma = sg;
+    S->sigma_mu = sg * S->mu;
+}
+__global__ void k_set(double* p, double v) { *p = v; }
+__global__ void k_alpha(IPMScalars* S) { S->alpha = fmin(1.0, S->step_fraction * S->alpha_max); }
+__global__ void k_update(double* xyz, double* s, const double* d, const double* ds, const IPMScalars* S,
+                         int N, int m) {
+    const double a = S->alpha;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) xyz[i] += a * d[i];
+    if (i < m) s[i] += a * ds[i];
+}
+
+}  // namespace qoco
+
+using namespace qoco;
+
+struct qoco_gpu_cones {
+    ConeView v;
+    std::vector<void*> allocs;
+    double* partial = nullptr;
+};
+
+// CUDA-event timing of the iteration's phases (enabled by qoco_gpu_set_profiling).
+struct PhaseProfiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Rec { int phase; cudaEvent_t a, b; int64_t launches; };
+    std::vector<Rec> pending;
+    qoco_gpu_profile tot;
+    PhaseProfiler() { memset(&tot, 0, sizeof tot); }
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    // called after the stream was synchronised
+    void flush() {
+        for (const Rec& r : pending) {
+            float ms = 0.0f;
+            if (r.a && r.b && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                tot.ms[r.phase] += ms;
+                tot.calls[r.phase] += 1;
+                tot.launches[r.phase] += r.launches;
+            }
+        }
+        pending.clear();
+        used = 0;
+    }
+    ~PhaseProfiler() {
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct qoco_gpu_solver {
+    qoco_gpu_settings st;
+    PhaseProfiler prof;
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
+    KKTPattern K;
+    Symbolic S;
+    int n = 0, m = 0, p = 0, N = 0;
+    std::vector<void*> allocs;
+    // device data
+    int64_t* d_rowptr = nullptr;
+    int* d_colidx = nullptr;
+    double* d_val = nullptr;
+    int64_t* d_w2slot = nullptr;
+    int64_t* d_w2ptr = nullptr;
+    double *d_c = nullptr, *d_b = nullptr, *d_h = nullptr;
+    // iterate and work vectors
+    double *xyz = nullptr, *s = nullptr, *d_aff = nullptr, *ds_aff = nullptr, *d_cmb = nullptr,
+           *ds_cmb = nullptr;
+    double *r = nullptr, *rhs = nullptr, *wbar = nullptr, *eta = nullptr, *lam = nullptr, *t = nullptr,
+           *t1 = nullptr, *t2 = nullptr;
+    double *sol_w = nullptr, *sol_xp = nullptr, *res = nullptr;
+    double* partial = nullptr;
+    int64_t partial_cap = 0;
+    IPMScalars* d_S = nullptr;
+    IPMScalars* h_S = nullptr;  // pinned
+    KKTView kv;
+    ConeView cv;
+    FactorView fv;
+    FactorPlan plan;
+    int lpr = 4;
+    bool have_factor = false;
+    int64_t launches = 0;
+    int refine_steps = 0;
+    double last_berr = 0.0;
+    qoco_gpu_info info;
+    std::string msg;
+};
+
+namespace {
+
+template <class T>
+int dalloc(qoco_gpu_solver* S, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    QOCO_CUDA_TRY(cudaMalloc((void**)p, count * sizeof(T)));
+    S->allocs.push_back(*p);
+    return 0;
+}
+template <class T>
+int dcopy(qoco_gpu_solver* S, T** p, const std::vector<T>& v) {
+    int rc = dalloc(S, p, v.size());
+    if (rc) return rc;
+    if (!v.empty()) QOCO_CUDA_TRY(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    S->h2d_bytes += (int64_t)(v.size() * sizeof(T));
+    return 0;
+}
+
+// Records an event pair around one phase when profiling is on.
+struct Phase {
+    qoco_gpu_solver* S;
+    int phase;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    int64_t l0;
+    Phase(qoco_gpu_solver* s_, int ph, cudaStream_t st_) : S(s_), phase(ph), st(st_), l0(s_->launches) {
+        if (S->prof.on && (a = S->prof.next())) cudaEventRecord(a, st);
+    }
+    ~Phase() {
+        if (!a) return;
+        cudaEvent_t b = S->prof.next();
+        if (b) cudaEventRecord(b, st);
+        S->prof.pending.push_back({phase, a, b, S->launches - l0});
+    }
+};
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+int grid(int n, int t = 256) { return (n + t - 1) / t; }
+
+int build_cone_view(qoco_gpu_solver* S, const KKTPattern& K) {
+    ConeView& c = S->cv;
+    c.l = K.l;
+    c.nsoc = K.nsoc;
+    c.m = K.m;
+    std::vector<int> off(K.nsoc), dim(K.nsoc), sm, lg;
+    for (int k = 0; k < K.nsoc; ++k) {
+        off[k] = K.cone_off[k];
+        dim[k] = K.q[k];
+        (K.q[k] <= kSmallCone ? sm : lg).push_back(k);
+    }
+    int* p;
+    int rc;
+    if ((rc = dcopy(S, &p, off))) return rc;
+    c.off = p;
+    if ((rc = dcopy(S, &p, dim))) return rc;
+    c.dim = p;
+    if ((rc = dcopy(S, &p, sm))) return rc;
+    c.small = p;
+    if ((rc = dcopy(S, &p, lg))) return rc;
+    c.large = p;
+    c.nsmall = (int)sm.size();
+    c.nlarge = (int)lg.size();
+    return 0;
+}
+
+int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h) {
+    const KKTPattern& K = S->K;
+    const Symbolic& Y = S->S;
+    int rc;
+    const int N = K.N, m = K.m;
+    if ((rc = dcopy(S, &S->d_rowptr, K.rowptr))) return rc;
+    if ((rc = dcopy(S, &S->d_colidx, K.colidx))) return rc;
+    if ((rc = dcopy(S, &S->d_val, K.val0))) return rc;
+    if ((rc = dcopy(S, &S->d_w2slot, K.w2_slot))) return rc;
+    if ((rc = dcopy(S, &S->d_w2ptr, K.w2_ptr))) return rc;
+    std::vector<double> vc(c, c + K.n), vb(K.p, 0.0), vh(K.m, 0.0);
+    if (b) vb.assign(b, b + K.p);
+    if (h) vh.assign(h, h + K.m);
+    if ((rc = dcopy(S, &S->d_c, vc))) return rc;
+    if ((rc = dcopy(S, &S->d_b, vb))) return rc;
+    if ((rc = dcopy(S, &S->d_h, vh))) return rc;
+    if ((rc = build_cone_view(S, K))) return rc;
+    S->kv.N = N; S->kv.n = K.n; S->kv.p = K.p; S->kv.m = K.m;
+    S->kv.rowptr = S->d_rowptr; S->kv.colidx = S->d_colidx; S->kv.val = S->d_val;
+    const double avg = N ? (double)K.nnz() / N : 1.0;
+    S->lpr = avg <= 8 ? 4 : avg <= 24 ? 8 : avg <= 64 ? 16 : 32;
+
+    // symbolic structure
+    FactorView& f = S->fv;
+    int* pi;
+    int64_t* pl;
+    std::vector<int> first(Y.sn_first.begin(), Y.sn_first.end() - 1);
+    if ((rc = dcopy(S, &pi, first))) return rc; f.first = pi;
+    if ((rc = dcopy(S, &pi, Y.sn_ncol))) return rc; f.ncol = pi;
+    if ((rc = dcopy(S, &pi, Y.sn_nrow))) return rc; f.nrow = pi;
+    if ((rc = dcopy(S, &pl, Y.row_ptr))) return rc; f.row_ptr = pl;
+    if ((rc = dcopy(S, &pi, Y.rows))) return rc; f.rows = pi;
+    if ((rc = dcopy(S, &pl, Y.front_off))) return rc; f.front_off = pl;
+    if ((rc = dcopy(S, &pl, Y.upd_off))) return rc; f.upd_off = pl;
+    if ((rc = dcopy(S, &pi, Y.rel))) return rc; f.rel = pi;
+    if ((rc = dcopy(S, &pi, Y.child_ptr))) return rc; f.child_ptr = pi;
+    if ((rc = dcopy(S, &pi, Y.child))) return rc; f.child = pi;
+    if ((rc = dcopy(S, &pl, Y.amap_ptr))) return rc; f.amap_ptr = pl;
+    if ((rc = dcopy(S, &pl, Y.amap_slot))) return rc; f.amap_slot = pl;
+    if ((rc = dcopy(S, &pi, Y.amap_off))) return rc; f.amap_off = pi;
+    signed char* pc;
+    if ((rc = dcopy(S, &pc, Y.dsign))) return rc; f.dsign = pc;
+    if ((rc = dcopy(S, &pi, Y.perm))) return rc; f.perm = pi;
+    double* pd;
+    if ((rc = dalloc(S, &pd, (size_t)Y.front_entries))) return rc; f.front = pd;
+    if ((rc = dalloc(S, &pd, (size_t)Y.upd_off[Y.ns]))) return rc; f.upd = pd;
+    if ((rc = dalloc(S, &pi, 1))) return rc; f.nreg = pi;
+    f.eps = S->st.static_reg;
+    f.dyn_thresh = S->st.dyn_reg_thresh;
+    f.dyn_value = S->st.dyn_reg_value;
+
+    // level plan
+    FactorPlan& P = S->plan;
+    std::vector<int> all, small, large;
+    P.levels.resize(Y.n_levels);
+    for (int lv = 0; lv < Y.n_levels; ++lv) {
+        LevelPlan& L = P.levels[lv];
+        L.off_all = (int)all.size();
+        L.off_small = (int)small.size();
+        L.off_large = (int)large.size();
+        for (int k = Y.level_ptr[lv]; k < Y.level_ptr[lv + 1]; ++k) {
+            const int s2 = Y.level_list[k];
+            const int fs = Y.sn_nrow[s2];
+            all.push_back(s2);
+            L.max_f = std::max(L.max_f, fs);
+            if (fs <= kSmemFront) { small.push_back(s2); L.max_small = std::max(L.max_small, fs); }
+            else large.push_back(s2);
+        }
+        L.count = (int)all.size() - L.off_all;
+        L.n_small = (int)small.size() - L.off_small;
+        L.n_large = (int)large.size() - L.off_large;
+        if (L.max_f > kMaxSolveFront) {
+            S->msg = "a supernode front exceeds the solve kernel's shared-memory limit";
+            return QOCO_GPU_ERR_NOT_IMPLEMENTED;
+        }
+    }
+    if ((rc = dcopy(S, &P.d_all, all))) return rc;
+    if ((rc = dcopy(S, &P.d_small, small))) return rc;
+    if ((rc = dcopy(S, &P.d_large, large))) return rc;
+
+    // iterate / work vectors
+    double** vecN[] = {&S->xyz, &S->d_aff, &S->d_cmb, &S->r, &S->rhs, &S->sol_w, &S->sol_xp, &S->res};
+    for (double** v : vecN) if ((rc = dalloc(S, v, N))) return rc;
+    double** vecM[] = {&S->s, &S->ds_aff, &S->ds_cmb, &S->wbar, &S->lam, &S->t, &S->t1, &S->t2};
+    for (double** v : vecM) if ((rc = dalloc(S, v, m))) return rc;
+    if ((rc = dalloc(S, &S->eta, K.nsoc))) return rc;
+    const int np = std::max(row_partials(N), 2 * std::max(1, max_step_partials(S->cv)));
+    if ((rc = dalloc(S, &S->partial, np))) return rc;
+    S->partial_cap = np;
+    if ((rc = dalloc(S, &S->d_S, 1))) return rc;
+    QOCO_CUDA_TRY(cudaMallocHost((void**)&S->h_S, sizeof(IPMScalars)));
+
+    IPMScalars hs;
+    memset(&hs, 0, sizeof hs);
+    auto inf = [](const double* v, int len) {
+        double a = 0.0;
+        for (int i = 0; i < len; ++i) a = std::max(a, std::fabs(v[i]));
+        return a;
+    };
+    hs.c_inf = inf(vc.data(), K.n);
+    hs.b_inf = inf(vb.data(), K.p);
+    hs.h_inf = inf(vh.data(), K.m);
+    hs.nu = K.l + K.nsoc;
+    hs.abstol = S->st.abstol; hs.reltol = S->st.reltol;
+    hs.abstol_inacc = S->st.abstol_inacc; hs.reltol_inacc = S->st.reltol_inacc;
+    hs.refine_tol = S->st.refine_tol;
+    hs.step_fraction = S->st.step_fraction;
+    QOCO_CUDA_TRY(cudaMemcpy(S->d_S, &hs, sizeof hs, cudaMemcpyHostToDevice));
+    return factor_set_attributes();
+}
+
+// ---- steps of the iteration ----------------------------------------------------
+int sync_scalars(qoco_gpu_solver* S, cudaStream_t st) {
+    QOCO_CUDA_TRY(cudaMemcpyAsync(S->h_S, S->d_S, sizeof(IPMScalars), cudaMemcpyDeviceToHost, st));
+    QOCO_CUDA_TRY(cudaStreamSynchronize(st));
+    S->d2h_bytes += (int64_t)sizeof(IPMScalars);
+    if (S->prof.on) S->prof.flush();
+    return 0;
+}
+
+int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
+    {
+        Phase ph(S, QOCO_GPU_PHASE_ROW, st);
+        if (launch_norm_inf(S->kv, S->lpr, S->partial, S->partial_cap, S->d_S, st)) return QOCO_GPU_ERR_INVALID_ARG;
+        S->launches += 2;
+    }
+    {
+        Phase ph(S, QOCO_GPU_PHASE_FACTOR, st);
+        S->launches += launch_factor(S->plan, S->fv, S->d_val, st);
+    }
+    QOCO_CUDA_TRY(cudaGetLastError());
+    S->have_factor = true;
+    return 0;
+}
+
+int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStream_t st) {
+    Phase ph(S, QOCO_GPU_PHASE_SOLVE, st);
+    S->launches += launch_solve(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, st);
+    return 0;
+}
+
+// x = K_ε⁻¹ r refined against K until the backward error target (r, x device, N)
+int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st) {
+    tri_solve(S, r, x, false, st);
+    int steps = 0;
+    for (;;) {
+        {
+            Phase ph(S, QOCO_GPU_PHASE_ROW, st);
+            if (launch_spmv_res(S->kv, S->lpr, x, r, S->res, S->partial, S->partial_cap, S->d_S, st))
+                return QOCO_GPU_ERR_INVALID_ARG;
+            S->launches += 2;
+        }
+        QOCO_CUDA_TRY(cudaGetLastError());
+        int rc = sync_scalars(S, st);
+        if (rc) return rc;
+        if (S->h_S->refine_done || steps >= S->st.max_refine) break;
+        tri_solve(S, S->res, x, true, st);
+        ++steps;
+    }
+    S->refine_steps += steps;
+    S->last_berr = S->h_S->berr;
+    return 0;
+}
+
+int cone_launch_count(const ConeView& c) { return cone_grid(c).blocks() ? 1 : 0; }
+
+int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
+    const int n = S->n, p = S->p, m = S->m, N = S->N;
+    const ConeView& cv = S->cv;
+    const int cl = cone_launch_count(cv);
+    int rc;
+    S->refine_steps = 0;
+    // initial point: K(W = I) [x; y; z] = [−c; b; h], s = −z, shift s and z into the cone
+    launch_w2_identity(cv, S->d_val, S->d_w2slot, S->d_w2ptr, st);
+    S->launches += cl;
+    if ((rc = factor_now(S, st))) return rc;
+    k_init_rhs<<<grid(N), 256, 0, st>>>(S->rhs, S->d_c, S->d_b, S->d_h, n, p, m);
+    S->launches += 1;
+    if ((rc = solve_refine(S, S->rhs, S->d_cmb, st))) return rc;
+    k_init_iterate<<<grid(N), 256, 0, st>>>(S->d_cmb, S->xyz, S->s, n, p, m);
+    S->launches += 1;
+    double* z = S->xyz + n + p;
+    if (m > 0) {
+        launch_shift_measure(cv, S->s, z, S->partial, st);
+        k_shift_finalize<<<1, 256, 0, st>>>(S->partial, max_step_partials(cv), S->d_S);
+        launch_shift_apply(cv, S->s, &S->d_S->shift[0], st);
+        launch_shift_apply(cv, z, &S->d_S->shift[1], st);
+        S->launches += cl + 3;
+    }
+    QOCO_CUDA_TRY(cudaGetLastError());
+
+    int status = QOCO_GPU_MAX_ITER;
+    int it = 0;
+    for (it = 0;; ++it) {
+        {
+            Phase ph(S, QOCO_GPU_PHASE_ROW, st);
+            if (launch_residual(S->kv, S->lpr, S->xyz, S->s, S->d_c, S->d_b, S->d_h, S->r, S->partial,
+                                S->partial_cap, S->d_S, st))
+                return QOCO_GPU_ERR_INVALID_ARG;
+            S->launches += 2;
+        }
+        QOCO_CUDA_TRY(cudaGetLastError());
+        if ((rc = sync_scalars(S, st))) return rc;
+        const IPMScalars& h = *S->h_S;
+        S->info.pobj = h.pobj;
+        S->info.dobj = h.dobj;
+        S->info.gap = h.gap;
+        S->info.pres = std::max(h.ry_inf, h.rz_inf);
+        S->info.dres = h.rx_inf;
+        S->info.iters = it;
+        if (S->st.verbose)
+            printf("%3d  pobj %+.8e  dobj %+.8e  gap %.2e  pres %.2e  dres %.2e  alpha %.3f\n", it, h.pobj,
+                   h.dobj, h.gap, S->info.pres, h.rx_inf, it ? h.alpha : 0.0);
+        if (h.nonfinite) { status = QOCO_GPU_ERR_NUMERICAL; break; }
+        if (h.converged) { status = QOCO_GPU_SOLVED; break; }
+        if (it >= S->st.max_iter) {
+            status = h.converged_inacc ? QOCO_GPU_SOLVED_INACCURATE : QOCO_GPU_MAX_ITER;
+            break;
+        }
+        // NT scaling, −W² into the KKT values, factor
+        {
+            Phase ph(S, QOCO_GPU_PHASE_CONE, st);
+            launch_nt_scaling(cv, S->s, z, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot, S->d_w2ptr, st);
+            S->launches += cl;
+        }
+        if ((rc = factor_now(S, st))) return rc;
+        // predictor
+        if (n + p) { k_neg_copy<<<grid(n + p), 256, 0, st>>>(S->rhs, S->r, n + p); S->launches++; }
+        if (m) {
+            Phase ph(S, QOCO_GPU_PHASE_CONE, st);
+            launch_rhs_z(cv, S->lam, S->wbar, S->eta, S->r + n + p, nullptr, nullptr, nullptr, false, S->t,
+                         S->t1, S->t2, S->rhs + n + p, st);
+            S->launches += cl;
+        }
+        if ((rc = solve_refine(S, S->rhs, S->d_aff, st))) return rc;
+        if (m) {
+            Phase ph(S, QOCO_GPU_PHASE_CONE, st);
+            launch_ds(cv, S->wbar, S->eta, S->t, S->d_aff + n + p, S->t1, S->ds_aff, st);
+            launch_max_step(cv, S->s, S->ds_aff, z, S->d_aff + n + p, INFINITY, S->partial,
+                            &S->d_S->alpha_max, st);
+            S->launches += cl + 2;
+        } else {
+            k_set<<<1, 1, 0, st>>>(&S->d_S->alpha_max, INFINITY);  // no cone limits the step
+            S->launches++;
+        }
+        k_sigma<<<1, 1, 0, st>>>(S->d_S, 3.0);
+        S->launches++;
+        // corrector
+        if (m) {
+            Phase ph(S, QOCO_GPU_PHASE_CONE, st);
+            launch_rhs_z(cv, S->lam, S->wbar, S->eta, S->r + n + p, S->ds_aff, S->d_aff + n + p,
+                         &S->d_S->sigma_mu, true, S->t, S->t1, S->t2, S->rhs + n + p, st);
+            S->launches += cl;
+        }
+        if ((rc = solve_refine(S, S->rhs, S->d_cmb, st))) return rc;
+        if (m) {
+            Phase ph(S, QOCO_GPU_PHASE_CONE, st);
+            launch_ds(cv, S->wbar, S->eta, S->t, S->d_cmb + n + p, S->t1, S->ds_cmb, st);
+            launch_max_step(cv, S->s, S->ds_cmb, z, S->d_cmb + n + p, INFINITY, S->partial,
+                            &S->d_S->alpha_max, st);
+            S->launches += cl + 2;
+        } else {
+            k_set<<<1, 1, 0, st>>>(&S->d_S->alpha_max, INFINITY);
+            S->launches++;
+        }
+        k_alpha<<<1, 1, 0, st>>>(S->d_S);
+        k_update<<<grid(std::max(N, m)), 256, 0, st>>>(S->xyz, S->s, S->d_cmb, S->ds_cmb, S->d_S, N, m);
+        S->launches += 2;
+        QOCO_CUDA_TRY(cudaGetLastError());
+    }
+    return status;
+}
+
+void fill_info(const qoco_gpu_solver* S, qoco_gpu_info* info) {
+    *info = S->info;
+    info->kkt_dim = S->N;
+    info->kkt_nnz = S->K.nnz();
+    info->l_nnz = S->S.l_nnz;
+    info->front_entries = S->S.front_entries;
+    info->factor_flops = S->S.flops;
+    info->n_supernodes = S->S.ns;
+    info->n_levels = S->S.n_levels;
+    info->max_front = S->S.max_front;
+    info->refine_steps = S->refine_steps;
+    info->last_backward_error = S->last_berr;
+    info->kernel_launches = S->launches;
+    info->h2d_bytes = S->h2d_bytes;
+    info->d2h_bytes = S->d2h_bytes;
+    snprintf(info->message, sizeof info->message, "%s", S->msg.c_str());
+}
+
+int analyze_common(int n, int m, int p, const qoco_csc* P, const double* c, const qoco_csc* A,
+                   const double* b, const qoco_csc* G, const double* h, int l, int nsoc, const int* q,
+                   const qoco_gpu_settings* settings, bool check_vectors, qoco_gpu_settings* st,
+                   KKTPattern* K, Symbolic* Y, std::string* msg, double* t_analysis, int* used) {
+    if (settings) *st = *settings;
+    else qoco_gpu_default_settings(st);
+    int rc = validate_problem(n, m, p, P, c, A, b, G, h, l, nsoc, q, check_vectors, msg);
+    if (rc) return rc;
+    const double t0 = now_s();
+    build_kkt_pattern(K, n, m, p, P, A, G, l, nsoc, q);
+    *used = analyze(*K, *st, Y);
+    *t_analysis = now_s() - t0;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qoco_gpu_default_settings(qoco_gpu_settings* s) {
+    if (!s) return;
+    s->abstol = 1e-7;
+    s->reltol = 1e-7;
+    s->abstol_inacc = 1e-5;
+    s->reltol_inacc = 1e-5;
+    s->max_iter = 200;
+    s->static_reg = 1e-8;
+    s->dyn_reg_thresh = 1e-13;
+    s->dyn_reg_value = 1e-7;
+    s->max_refine = 10;
+    s->refine_tol = 1e-10;
+    s->step_fraction = 0.99;
+    s->ordering = QOCO_GPU_ORDER_AUTO;
+    s->nd_leaf = 64;
+    s->verbose = 0;
+}
+
+int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A, const qoco_csc* G, int l,
+                     int nsoc, const int* q, const qoco_gpu_settings* settings, qoco_gpu_info* info,
+                     int* perm, int* sn_ptr) {
+    qoco_gpu_settings st;
+    KKTPattern K;
+    Symbolic Y;
+    std::string msg;
+    double ta = 0.0;
+    int used = 0;
+    int rc;
+    try {
+        rc = analyze_common(n, m, p, P, nullptr, A, nullptr, G, nullptr, l, nsoc, q, settings, false, &st,
+                            &K, &Y, &msg, &ta, &used);
+    } catch (const std::bad_alloc&) {
+        return QOCO_GPU_ERR_OOM;
+    }
+    if (info) {
+        memset(info, 0, sizeof *info);
+        snprintf(info->message, sizeof info->message, "%s", msg.c_str());
+    }
+    if (rc) return rc;
+    if (info) {
+        info->analysis_time_s = ta;
+        info->kkt_dim = K.N;
+        info->kkt_nnz = K.nnz();
+        info->l_nnz = Y.l_nnz;
+        info->front_entries = Y.front_entries;
+        info->factor_flops = Y.flops;
+        info->n_supernodes = Y.ns;
+        info->n_levels = Y.n_levels;
+        info->max_front = Y.max_front;
+        info->ordering_used = used;
+    }
+    if (perm) memcpy(perm, Y.perm.data(), sizeof(int) * K.N);
+    if (sn_ptr) memcpy(sn_ptr, Y.sn_first.data(), sizeof(int) * (Y.ns + 1));
+    return 0;
+}
+
+int qoco_gpu_setup(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
+                   const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
+                   const int* q, const qoco_gpu_settings* settings) {
+    if (!out) return QOCO_GPU_ERR_INVALID_ARG;
+    *out = nullptr;
+    const double t0 = now_s();
+    qoco_gpu_solver* S = nullptr;
+    try {
+        S = new qoco_gpu_solver();
+    } catch (const std::bad_alloc&) {
+        return QOCO_GPU_ERR_OOM;
+    }
+    memset(&S->info, 0, sizeof S->info);
+    double ta = 0.0;
+    int used = 0;
+    int rc;
+    try {
+        rc = analyze_common(n, m, p, P, c, A, b, G, h, l, nsoc, q, settings, true, &S->st, &S->K, &S->S,
+                            &S->msg, &ta, &used);
+    } catch (const std::bad_alloc&) {
+        rc = QOCO_GPU_ERR_OOM;
+    }
+    if (rc) {
+        delete S;
+        return rc;
+    }
+    S->n = n; S->m = m; S->p = p; S->N = n + p + m;
+    rc = upload(S, c, b, h);
+    if (rc) {
+        qoco_gpu_cleanup(S);
+        return rc;
+    }
+    S->info.analysis_time_s = ta;
+    S->info.ordering_used = used;
+    S->info.setup_time_s = now_s() - t0;
+    *out = S;
+    return 0;
+}
+
+int qoco_gpu_solve(qoco_gpu_solver* S, void* stream) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double t0 = now_s();
+    S->launches = 0;
+    S->d2h_bytes = 0;
+    int status = run_solve(S, st);
+    if (status == QOCO_GPU_ERR_CUDA || status == QOCO_GPU_ERR_OOM) S->msg = g_cuda_msg;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess && status >= 0) status = cuda_fail(e, "stream sync", __FILE__, __LINE__);
+    S->info.status = status;
+    S->info.solve_time_s = now_s() - t0;
+    return status;
+}
+
+int qoco_gpu_get_solution(const qoco_gpu_solver* S, double* x, double* s, double* y, double* z,
+                          qoco_gpu_info* info) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    QOCO_CUDA_TRY(cudaDeviceSynchronize());
+    if (x) QOCO_CUDA_TRY(cudaMemcpy(x, S->xyz, sizeof(double) * S->n, cudaMemcpyDeviceToHost));
+    if (y && S->p) QOCO_CUDA_TRY(cudaMemcpy(y, S->xyz + S->n, sizeof(double) * S->p, cudaMemcpyDeviceToHost));
+    if (z && S->m)
+        QOCO_CUDA_TRY(cudaMemcpy(z, S->xyz + S->n + S->p, sizeof(double) * S->m, cudaMemcpyDeviceToHost));
+    if (s && S->m) QOCO_CUDA_TRY(cudaMemcpy(s, S->s, sizeof(double) * S->m, cudaMemcpyDeviceToHost));
+    if (info) fill_info(S, info);
+    return 0;
+}
+
+int qoco_gpu_solution_device(const qoco_gpu_solver* S, const double** x, const double** s, const double** y,
+                             const double** z) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    if (x) *x = S->xyz;
+    if (y) *y = S->xyz + S->n;
+    if (z) *z = S->xyz + S->n + S->p;
+    if (s) *s = S->s;
+    return 0;
+}
+
+int qoco_gpu_get_info(const qoco_gpu_solver* S, qoco_gpu_info* info) {
+    if (!S || !info) return QOCO_GPU_ERR_INVALID_ARG;
+    fill_info(S, info);
+    return 0;
+}
+
+int qoco_gpu_backward(qoco_gpu_solver* S, const double*, const double*, const double*, double*, double*,
+                      double*, double*, double*, double*) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    return QOCO_GPU_ERR_NOT_IMPLEMENTED;
+}
+
+int qoco_gpu_set_profiling(qoco_gpu_solver* S, int on) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    QOCO_CUDA_TRY(cudaDeviceSynchronize());
+    S->prof.flush();
+    S->prof.on = on != 0;
+    memset(&S->prof.tot, 0, sizeof S->prof.tot);
+    return 0;
+}
+
+int qoco_gpu_get_profile(const qoco_gpu_solver* S, qoco_gpu_profile* out) {
+    if (!S || !out) return QOCO_GPU_ERR_INVALID_ARG;
+    *out = S->prof.tot;
+    return 0;
+}
+
+int qoco_gpu_cleanup(qoco_gpu_solver* S) {
+    if (!S) return 0;
+    for (void* p : S->allocs) cudaFree(p);
+    if (S->h_S) cudaFreeHost(S->h_S);
+    delete S;
+    return 0;
+}
+
+int qoco_gpu_kkt_factor_at(qoco_gpu_solver* S, const double* s, const double* z, void* stream) {
+    if (!S || (S->m && (!s || !z))) return QOCO_GPU_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_nt_scaling(S->cv, s, z, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot, S->d_w2ptr, st);
+    int rc = factor_now(S, st);
+    if (rc) return rc;
+    QOCO_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+int qoco_gpu_kkt_solve(qoco_gpu_solver* S, const double* r, double* x, int* refine_steps,
+                       double* backward_error, void* stream) {
+    if (!S || !r || !x) return QOCO_GPU_ERR_INVALID_ARG;
+    if (!S->have_factor) return QOCO_GPU_ERR_NO_FACTOR;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int before = S->refine_steps;
+    int rc = solve_refine(S, r, x, st);
+    if (rc) return rc;
+    QOCO_CUDA_TRY(cudaStreamSynchronize(st));
+    if (refine_steps) *refine_steps = S->refine_steps - before;
+    if (backward_error) *backward_error = S->last_berr;
+    return 0;
+}
+
+int qoco_gpu_get_kkt(const qoco_gpu_solver* S, int64_t* rowptr, int* colidx, double* val) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    QOCO_CUDA_TRY(cudaDeviceSynchronize());
+    if (rowptr) memcpy(rowptr, S->K.rowptr.data(), sizeof(int64_t) * (S->N + 1));
+    if (colidx) memcpy(colidx, S->K.colidx.data(), sizeof(int) * S->K.nnz());
+    if (val) QOCO_CUDA_TRY(cudaMemcpy(val, S->d_val, sizeof(double) * S->K.nnz(), cudaMemcpyDeviceToHost));
+    return 0;
+}
+
+int qoco_gpu_get_factor_dense(const qoco_gpu_solver* S, int* perm, double* L, double* D) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    const int N = S->N;
+    if (N > 4096) return QOCO_GPU_ERR_INVALID_ARG;
+    if (!S->have_factor) return QOCO_GPU_ERR_NO_FACTOR;
+    const Symbolic& Y = S->S;
+    std::vector<double> fr((size_t)Y.front_entries);
+    QOCO_CUDA_TRY(cudaDeviceSynchronize());
+    QOCO_CUDA_TRY(cudaMemcpy(fr.data(), S->fv.front, sizeof(double) * fr.size(), cudaMemcpyDeviceToHost));
+    if (perm) memcpy(perm, Y.perm.data(), sizeof(int) * N);
+    if (L) {
+        memset(L, 0, sizeof(double) * (size_t)N * N);
+        for (int i = 0; i < N; ++i) L[(size_t)i * N + i] = 1.0;
+    }
+    for (int s = 0; s < Y.ns; ++s) {
+        const int f = Y.sn_nrow[s], c = Y.sn_ncol[s], first = Y.sn_first[s];
+        const double* F = fr.data() + Y.front_off[s];
+        const int* R = Y.rows.data() + Y.row_ptr[s];
+        for (int k = 0; k < c; ++k) {
+            if (D) D[first + k] = F[(size_t)k * f + k];
+            if (L)
+                for (int a = k + 1; a < f; ++a) L[(size_t)R[a] * N + first + k] = F[(size_t)k * f + a];
+        }
+    }
+    return 0;
+}
+
+int qoco_gpu_cones_create(qoco_gpu_cones** out, int l, int nsoc, const int* q) {
+    if (!out || l < 0 || nsoc < 0 || (nsoc && !q)) return QOCO_GPU_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto* C = new (std::nothrow) qoco_gpu_cones();
+    if (!C) return QOCO_GPU_ERR_OOM;
+    std::vector<int> off(nsoc), dim(nsoc), sm, lg;
+    int o = l;
+    for (int k = 0; k < nsoc; ++k) {
+        if (q[k] < 2) { delete C; return QOCO_GPU_ERR_INVALID_CONE; }
+        off[k] = o;
+        dim[k] = q[k];
+        o += q[k];
+        (q[k] <= kSmallCone ? sm : lg).push_back(k);
+    }
+    C->v.l = l; C->v.nsoc = nsoc; C->v.m = o;
+    C->v.nsmall = (int)sm.size(); C->v.nlarge = (int)lg.size();
+    std::vector<int>* src[4] = {&off, &dim, &sm, &lg};
+    const int** dst[4] = {&C->v.off, &C->v.dim, &C->v.small, &C->v.large};
+    for (int i = 0; i < 4; ++i) {
+        int* d = nullptr;
+        size_t bytes = std::max<size_t>(1, src[i]->size()) * sizeof(int);
+        cudaError_t e = cudaMalloc((void**)&d, bytes);
+        if (e == cudaSuccess && !src[i]->empty())
+            e = cudaMemcpy(d, src[i]->data(), src[i]->size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            if (d) cudaFree(d);
+            qoco_gpu_cones_destroy(C);
+            return cuda_fail(e, "cones_create", __FILE__, __LINE__);
+        }
+        C->allocs.push_back(d);
+        *dst[i] = d;
+    }
+    *out = C;
+    return 0;
+}
+
+int qoco_gpu_cones_destroy(qoco_gpu_cones* C) {
+    if (!C) return 0;
+    for (void* p : C->allocs) cudaFree(p);
+    delete C;
+    return 0;
+}
+
+int qoco_gpu_cone_nt_scaling(const qoco_gpu_cones* C, const double* s, const double* z, double* w, double* eta,
+                             double* lambda, void* stream) {
+    if (!C || (C->v.m && (!s || !z || !w || !lambda)) || (C->v.nsoc && !eta)) return QOCO_GPU_ERR_INVALID_ARG;
+    launch_nt_scaling(C->v, s, z, w, eta, lambda, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+    QOCO_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int qoco_gpu_cone_product(const qoco_gpu_cones* C, const double* u, const double* v, double* out, void* stream) {
+    if (!C || (C->v.m && (!u || !v || !out))) return QOCO_GPU_ERR_INVALID_ARG;
+    launch_prod(C->v, u, v, out, (cudaStream_t)stream);
+    QOCO_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int qoco_gpu_cone_division(const qoco_gpu_cones* C, const double* lam, const double* v, double* out,
+                           void* stream) {
+    if (!C || (C->v.m && (!lam || !v || !out))) return QOCO_GPU_ERR_INVALID_ARG;
+    launch_div(C->v, lam, v, out, (cudaStream_t)stream);
+    QOCO_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+size_t qoco_gpu_cone_max_step_scratch_bytes(const qoco_gpu_cones* C) {
+    if (!C) return 0;
+    return sizeof(double) * (size_t)std::max(1, max_step_partials(C->v));
+}
+
+int qoco_gpu_cone_max_step(const qoco_gpu_cones* C, const double* u, const double* du, double cap,
+                           double* alpha, void* scratch, void* stream) {
+    if (!C || !alpha || !scratch || (C->v.m && (!u || !du))) return QOCO_GPU_ERR_INVALID_ARG;
+    launch_max_step(C->v, u, du, nullptr, nullptr, cap, (double*)scratch, alpha, (cudaStream_t)stream);
+    QOCO_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,341 @@
+// Symbolic supernodal analysis of the permuted KKT matrix (set-up phase).
+//
+// Steps, all on the host, once per sparsity pattern:
+//   1. elimination tree of the permuted matrix (Liu's ancestor algorithm with path
+//      compression) and a postorder, composed into the ordering;
+//   2. column counts of L by row-subtree marking (each row i walks from every k with
+//      K_ik ≠ 0, k < i, up the tree until an already-marked node);
+//   3. fundamental supernodes (j+1 continues j's supernode when it is j's parent,
+//      has j as only child and count(j) = count(j+1) + 1), then relaxed
+//      amalgamation of a supernode with its last child when few explicit zeros
+//      are added;
+//   4. row structures R_s (own columns, then the rows below), the supernodal tree,
+//      levels (height above the leaves), front/update offsets, the extend-add
+//      relative indices and the map from KKT value slots to front positions.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "symbolic.h"
+
+namespace qoco {
+
+namespace {
+
+std::vector<int> etree(const Graph& g, const std::vector<int>& perm, const std::vector<int>& iperm) {
+    const int N = g.N;
+    std::vector<int> parent(N, -1), anc(N, -1);
+    for (int j = 0; j < N; ++j) {
+        int o = perm[j];
+        for (int64_t t = g.ptr[o]; t < g.ptr[o + 1]; ++t) {
+            int i = iperm[g.adj[t]];
+            if (i >= j) continue;
+            int r = i;
+            while (anc[r] != -1 && anc[r] != j) {
+                int nx = anc[r];
+                anc[r] = j;
+                r = nx;
+            }
+            if (anc[r] == -1) { anc[r] = j; parent[r] = j; }
+        }
+    }
+    return parent;
+}
+
+std::vector<int> postorder(const std::vector<int>& parent) {
+    const int N = (int)parent.size();
+    std::vector<int> head(N, -1), next(N, -1), post;
+    post.reserve(N);
+    for (int j = N - 1; j >= 0; --j)
+        if (parent[j] >= 0) { next[j] = head[parent[j]]; head[parent[j]] = j; }
+    std::vector<int> stack;
+    for (int r = 0; r < N; ++r) {
+        if (parent[r] != -1) continue;
+        stack.push_back(r);
+        while (!stack.empty()) {
+            int v = stack.back();
+            int c = head[v];
+            if (c == -1) { post.push_back(v); stack.pop_back(); }
+            else { head[v] = next[c]; stack.push_back(c); }
+        }
+    }
+    return post;  // post[k] = old index of the k-th node in postorder
+}
+
+// below-diagonal counts of every column of L
+std::vector<int> col_counts(const Graph& g, const std::vector<int>& perm,
+                            const std::vector<int>& iperm, const std::vector<int>& parent) {
+    const int N = g.N;
+    std::vector<int> cc(N, 0), mark(N, -1);
+    for (int i = 0; i < N; ++i) {
+        int o = perm[i];
+        mark[i] = i;
+        for (int64_t t = g.ptr[o]; t < g.ptr[o + 1]; ++t) {
+            int k = iperm[g.adj[t]];
+            if (k >= i) continue;
+            while (mark[k] != i) {
+                mark[k] = i;
+                cc[k]++;
+                k = parent[k];
+            }
+        }
+    }
+    return cc;
+}
+
+int sn_height_fundamental(const std::vector<int>& parent, const std::vector<int>& cc) {
+    // height of the fundamental-supernode tree: a column that continues its only
+    // child's supernode adds no level
+    const int N = (int)parent.size();
+    std::vector<int> nchild(N, 0);
+    for (int j = 0; j < N; ++j) if (parent[j] >= 0) nchild[parent[j]]++;
+    std::vector<int> h(N, 0);
+    int best = 0;
+    for (int j = 0; j < N; ++j) {
+        int p = parent[j];
+        if (p < 0) { best = std::max(best, h[j]); continue; }
+        bool cont = p == j + 1 && nchild[p] == 1 && cc[j] == cc[p] + 1;
+        h[p] = std::max(h[p], h[j] + (cont ? 0 : 1));
+    }
+    return best + 1;
+}
+
+}  // namespace
+
+OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm0) {
+    Graph g = kkt_graph(K);
+    const int N = K.N;
+    std::vector<int> iperm(N);
+    for (int j = 0; j < N; ++j) iperm[perm0[j]] = j;
+    std::vector<int> parent = etree(g, perm0, iperm);
+    std::vector<int> post = postorder(parent);
+    std::vector<int> perm(N), ip2(N);
+    for (int k = 0; k < N; ++k) perm[k] = perm0[post[k]];
+    for (int j = 0; j < N; ++j) ip2[perm[j]] = j;
+    std::vector<int> par2 = etree(g, perm, ip2);
+    std::vector<int> cc = col_counts(g, perm, ip2, par2);
+    OrderingCost c;
+    for (int j = 0; j < N; ++j) {
+        c.l_nnz += cc[j];
+        c.flops += (double)cc[j] * cc[j] + 2.0 * cc[j];
+    }
+    c.height = sn_height_fundamental(par2, cc);
+    return c;
+}
+
+int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S) {
+    const int N = K.N;
+    Graph g = kkt_graph(K);
+    std::vector<int> perm0;
+    int used = st.ordering;
+    if (st.ordering == QOCO_GPU_ORDER_NATURAL) {
+        perm0.resize(N);
+        std::iota(perm0.begin(), perm0.end(), 0);
+    } else if (st.ordering == QOCO_GPU_ORDER_AMD) {
+        perm0 = order_amd(g);
+    } else if (st.ordering == QOCO_GPU_ORDER_ND) {
+        perm0 = order_nd(g, st.nd_leaf);
+    } else {
+        // AUTO: cost model = factor flops at an effective FP64 rate plus a per-level
+        // latency for the level-scheduled factor and solves
+        std::vector<int> pa = order_amd(g);
+        std::vector<int> pn = order_nd(g, st.nd_leaf);
+        OrderingCost ca = ordering_cost(K, pa), cn = ordering_cost(K, pn);
+        auto cost = [](const OrderingCost& c) { return c.flops / 2e11 + c.height * 4e-5; };
+        if (cost(cn) < cost(ca)) { perm0 = std::move(pn); used = QOCO_GPU_ORDER_ND; }
+        else { perm0 = std::move(pa); used = QOCO_GPU_ORDER_AMD; }
+    }
+
+    // 1. etree + postorder
+    std::vector<int> iperm(N);
+    for (int j = 0; j < N; ++j) iperm[perm0[j]] = j;
+    std::vector<int> parent0 = etree(g, perm0, iperm);
+    // postorder (not for NATURAL, which keeps the identity: any order in which every
+    // column precedes its etree parent is valid for the supernodal pass below)
+    std::vector<int> post;
+    if (st.ordering == QOCO_GPU_ORDER_NATURAL) {
+        post.resize(N);
+        std::iota(post.begin(), post.end(), 0);
+    } else {
+        post = postorder(parent0);
+    }
+    S->N = N;
+    S->perm.resize(N);
+    S->iperm.resize(N);
+    for (int k = 0; k < N; ++k) S->perm[k] = perm0[post[k]];
+    for (int j = 0; j < N; ++j) S->iperm[S->perm[j]] = j;
+    const std::vector<int>& perm = S->perm;
+    const std::vector<int>& ip = S->iperm;
+    std::vector<int> parent = etree(g, perm, ip);
+
+    // 2. counts
+    std::vector<int> cc = col_counts(g, perm, ip, parent);
+    S->l_nnz = 0;
+    S->flops = 0.0;
+    for (int j = 0; j < N; ++j) {
+        S->l_nnz += cc[j];
+        S->flops += (double)cc[j] * cc[j] + 2.0 * cc[j];
+    }
+
+    // 3. fundamental supernodes
+    std::vector<int> nchild(N, 0);
+    for (int j = 0; j < N; ++j) if (parent[j] >= 0) nchild[parent[j]]++;
+    std::vector<int> fs_first;
+    for (int j = 0; j < N; ++j) {
+        bool cont = j > 0 && parent[j - 1] == j && nchild[j] == 1 && cc[j - 1] == cc[j] + 1;
+        if (!cont) fs_first.push_back(j);
+    }
+    const int nf = (int)fs_first.size();
+    fs_first.push_back(N);
+    std::vector<int> col2f(N);
+    for (int s = 0; s < nf; ++s)
+        for (int j = fs_first[s]; j < fs_first[s + 1]; ++j) col2f[j] = s;
+    std::vector<int> fparent(nf, -1);
+    for (int s = 0; s < nf; ++s) {
+        int last = fs_first[s + 1] - 1;
+        if (parent[last] >= 0) fparent[s] = col2f[parent[last]];
+    }
+    // relaxed amalgamation: merge the immediately preceding supernode (the last child)
+    struct SN { int first, ncol, f; double truenz; int fparent; };
+    std::vector<SN> stack;
+    stack.reserve(nf);
+    for (int s = 0; s < nf; ++s) {
+        SN cur;
+        cur.first = fs_first[s];
+        cur.ncol = fs_first[s + 1] - fs_first[s];
+        cur.f = cc[cur.first] + 1;
+        cur.truenz = 0;
+        for (int j = cur.first; j < cur.first + cur.ncol; ++j) cur.truenz += cc[j] + 1;
+        cur.fparent = fparent[s];
+        while (!stack.empty()) {
+            SN& c = stack.back();
+            if (c.fparent != s) break;
+            int ncol = c.ncol + cur.ncol;
+            int f = c.ncol + cur.f;
+            double dense = (double)ncol * f - 0.5 * (double)ncol * (ncol - 1);
+            double tnz = c.truenz + cur.truenz;
+            double zf = 1.0 - tnz / dense;
+            bool ok = (ncol <= 4) || (ncol <= 16 && zf <= 0.8) || (ncol <= 48 && zf <= 0.1) ||
+                      (zf <= 0.05);
+            if (!ok) break;
+            cur.first = c.first;
+            cur.ncol = ncol;
+            cur.f = f;
+            cur.truenz = tnz;
+            stack.pop_back();
+        }
+        stack.push_back(cur);
+    }
+    const int ns = (int)stack.size();
+    S->ns = ns;
+    S->sn_first.resize(ns + 1);
+    S->sn_ncol.resize(ns);
+    for (int s = 0; s < ns; ++s) { S->sn_first[s] = stack[s].first; S->sn_ncol[s] = stack[s].ncol; }
+    S->sn_first[ns] = N;
+    std::vector<int> col2s(N);
+    for (int s = 0; s < ns; ++s)
+        for (int j = S->sn_first[s]; j < S->sn_first[s + 1]; ++j) col2s[j] = s;
+    S->sn_parent.assign(ns, -1);
+    for (int s = 0; s < ns; ++s) {
+        int last = S->sn_first[s + 1] - 1;
+        if (parent[last] >= 0) S->sn_parent[s] = col2s[parent[last]];
+    }
+    // children lists
+    S->child_ptr.assign(ns + 1, 0);
+    for (int s = 0; s < ns; ++s) if (S->sn_parent[s] >= 0) S->child_ptr[S->sn_parent[s] + 1]++;
+    for (int s = 0; s < ns; ++s) S->child_ptr[s + 1] += S->child_ptr[s];
+    S->child.assign(S->child_ptr[ns], 0);
+    {
+        std::vector<int> fill(S->child_ptr.begin(), S->child_ptr.end() - 1);
+        for (int s = 0; s < ns; ++s) if (S->sn_parent[s] >= 0) S->child[fill[S->sn_parent[s]]++] = s;
+    }
+
+    // 4. row structures (children before parents: supernodes are in postorder)
+    S->row_ptr.assign(ns + 1, 0);
+    S->rows.clear();
+    S->sn_nrow.resize(ns);
+    std::vector<int> mark(N, -1), buf;
+    for (int s = 0; s < ns; ++s) {
+        int first = S->sn_first[s], last = S->sn_first[s + 1] - 1;
+        buf.clear();
+        for (int j = first; j <= last; ++j) { buf.push_back(j); mark[j] = s; }
+        for (int j = first; j <= last; ++j) {
+            int o = perm[j];
+            for (int64_t t = g.ptr[o]; t < g.ptr[o + 1]; ++t) {
+                int i = ip[g.adj[t]];
+                if (i > last && mark[i] != s) { mark[i] = s; buf.push_back(i); }
+            }
+        }
+        for (int k = S->child_ptr[s]; k < S->child_ptr[s + 1]; ++k) {
+            int c = S->child[k];
+            for (int64_t t = S->row_ptr[c] + S->sn_ncol[c]; t < S->row_ptr[c + 1]; ++t) {
+                int i = S->rows[t];
+                if (i > last && mark[i] != s) { mark[i] = s; buf.push_back(i); }
+            }
+        }
+        std::sort(buf.begin() + (last - first + 1), buf.end());
+        S->rows.insert(S->rows.end(), buf.begin(), buf.end());
+        S->row_ptr[s + 1] = (int64_t)S->rows.size();
+        S->sn_nrow[s] = (int)buf.size();
+    }
+    // levels, offsets
+    S->level.assign(ns, 0);
+    for (int s = 0; s < ns; ++s)
+        if (S->sn_parent[s] >= 0)
+            S->level[S->sn_parent[s]] = std::max(S->level[S->sn_parent[s]], S->level[s] + 1);
+    S->n_levels = 0;
+    for (int s = 0; s < ns; ++s) S->n_levels = std::max(S->n_levels, S->level[s] + 1);
+    S->level_ptr.assign(S->n_levels + 1, 0);
+    for (int s = 0; s < ns; ++s) S->level_ptr[S->level[s] + 1]++;
+    for (int k = 0; k < S->n_levels; ++k) S->level_ptr[k + 1] += S->level_ptr[k];
+    S->level_list.assign(ns, 0);
+    {
+        std::vector<int> fill(S->level_ptr.begin(), S->level_ptr.end() - 1);
+        for (int s = 0; s < ns; ++s) S->level_list[fill[S->level[s]]++] = s;
+    }
+    S->front_off.assign(ns + 1, 0);
+    S->upd_off.assign(ns + 1, 0);
+    S->max_front = 0;
+    for (int s = 0; s < ns; ++s) {
+        int64_t f = S->sn_nrow[s];
+        S->front_off[s + 1] = S->front_off[s] + f * f;
+        S->upd_off[s + 1] = S->upd_off[s] + (f - S->sn_ncol[s]);
+        S->max_front = std::max(S->max_front, (int)f);
+    }
+    S->front_entries = S->front_off[ns];
+    // relative indices of each child's update rows inside its parent
+    S->rel.assign(S->upd_off[ns], 0);
+    S->amap_ptr.assign(ns + 1, 0);
+    S->amap_slot.clear();
+    S->amap_off.clear();
+    std::vector<int> pos(N, -1);
+    for (int s = 0; s < ns; ++s) {
+        for (int64_t t = S->row_ptr[s]; t < S->row_ptr[s + 1]; ++t) pos[S->rows[t]] = (int)(t - S->row_ptr[s]);
+        for (int k = S->child_ptr[s]; k < S->child_ptr[s + 1]; ++k) {
+            int c = S->child[k];
+            int64_t o = S->upd_off[c];
+            for (int64_t t = S->row_ptr[c] + S->sn_ncol[c]; t < S->row_ptr[c + 1]; ++t)
+                S->rel[o++] = pos[S->rows[t]];
+        }
+        // assembly map for this supernode's columns
+        int first = S->sn_first[s], last = S->sn_first[s + 1] - 1;
+        int f = S->sn_nrow[s];
+        for (int j = first; j <= last; ++j) {
+            int o = perm[j];
+            for (int64_t t = K.rowptr[o]; t < K.rowptr[o + 1]; ++t) {
+                int i = ip[K.colidx[t]];
+                if (i < j) continue;
+                S->amap_slot.push_back(t);
+                S->amap_off.push_back((j - first) * f + pos[i]);
+            }
+        }
+        S->amap_ptr[s + 1] = (int64_t)S->amap_slot.size();
+        for (int64_t t = S->row_ptr[s]; t < S->row_ptr[s + 1]; ++t) pos[S->rows[t]] = -1;
+    }
+    if (ns == 0) S->amap_ptr.assign(1, 0);
+    S->dsign.resize(N);
+    for (int j = 0; j < N; ++j) S->dsign[j] = K.sign[perm[j]];
+    return used;
+}
+
+}  // namespace qoco

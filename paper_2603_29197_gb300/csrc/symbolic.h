@@ -1,0 +1,99 @@
+// Host-side set-up of the KKT system: validation, pattern assembly (paper §2.2,
+// eq. (2)), fill-reducing ordering and the symbolic supernodal analysis.  The paper
+// runs this phase once per problem on the CPU (inside cuDSS's analysis phase, §2.2,
+// whose cost dominates its set-up time, §3.2); here it is our own C++ code.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qoco_gpu.h"
+
+namespace qoco {
+
+// Full symmetric KKT pattern in CSR (row i lists all j with K_ij stored), original
+// x | y | z numbering.  Every diagonal slot exists; SOC blocks of −WᵀW are dense.
+struct KKTPattern {
+    int n = 0, m = 0, p = 0, l = 0, nsoc = 0;
+    int N = 0;                          // n + p + m
+    std::vector<int> q;                 // SOC dims
+    std::vector<int> cone_off;          // start (within z, i.e. 0..m) of each SOC
+    std::vector<int64_t> rowptr;        // N + 1
+    std::vector<int> colidx;            // nnz
+    std::vector<double> val0;           // initial values (P, A, G; zero elsewhere)
+    std::vector<int64_t> diag_slot;     // N
+    std::vector<int64_t> w2_slot;       // l + Σ q²: orthant diagonals, then each SOC block row-major
+    std::vector<int64_t> w2_ptr;        // nsoc + 1 offsets into the SOC part of w2_slot (after l)
+    std::vector<signed char> sign;      // +1 for x rows, −1 for y and z rows
+    // value sources for parametric updates: slot ← src index into [P.val | A.val | G.val]
+    std::vector<int64_t> src;           // nnz, −1 where the slot is not data
+    int64_t nnzP = 0, nnzA = 0, nnzG = 0;
+    int64_t nnz() const { return (int64_t)colidx.size(); }
+};
+
+// Validates the problem data; on failure returns a QOCO_GPU_ERR_* code and fills msg.
+int validate_problem(int n, int m, int p, const qoco_csc* P, const double* c,
+                     const qoco_csc* A, const double* b, const qoco_csc* G,
+                     const double* h, int l, int nsoc, const int* q, bool check_vectors,
+                     std::string* msg);
+
+// Builds the KKT pattern; assumes validate_problem succeeded.
+void build_kkt_pattern(KKTPattern* K, int n, int m, int p, const qoco_csc* P,
+                       const qoco_csc* A, const qoco_csc* G, int l, int nsoc, const int* q);
+
+// Adjacency of the KKT graph without the diagonal (CSR over the N nodes).
+struct Graph {
+    int N = 0;
+    std::vector<int64_t> ptr;
+    std::vector<int> adj;
+};
+Graph kkt_graph(const KKTPattern& K);
+
+// Orderings: perm[new] = old.
+std::vector<int> order_amd(const Graph& g, double dense_factor = 10.0);
+std::vector<int> order_nd(const Graph& g, int leaf_size);
+
+// Supernodal symbolic factorisation of the permuted KKT matrix.
+struct Symbolic {
+    int N = 0;
+    std::vector<int> perm, iperm;       // perm[new] = old; iperm[old] = new
+    // supernodes in topological (postorder) order: children before parents
+    int ns = 0;
+    std::vector<int> sn_first;          // ns + 1: first column of each supernode
+    std::vector<int> sn_ncol;           // c_s
+    std::vector<int> sn_nrow;           // f_s = c_s + r_s
+    std::vector<int> sn_parent;         // −1 for roots
+    std::vector<int64_t> row_ptr;       // ns + 1 into rows
+    std::vector<int> rows;              // R_s: sorted permuted row indices (own columns first)
+    std::vector<int64_t> front_off;     // ns + 1: Σ f² prefix (doubles)
+    std::vector<int64_t> upd_off;       // ns + 1: Σ r prefix (update vectors / relative maps)
+    std::vector<int> rel;               // Σ r: position of R_s[c_s + a] inside the parent's R
+    std::vector<int> child_ptr, child;  // children lists (CSR over supernodes)
+    std::vector<int> level;             // height in the supernodal tree (leaves 0)
+    int n_levels = 0;
+    std::vector<int> level_ptr, level_list;   // supernodes grouped by level
+    // assembly map: KKT lower entries (permuted) of each supernode's columns
+    std::vector<int64_t> amap_ptr;      // ns + 1
+    std::vector<int64_t> amap_slot;     // slot in the KKT value array
+    std::vector<int> amap_off;          // column-major offset inside the front (col·f + row)
+    std::vector<signed char> dsign;     // sign of each permuted column
+    // statistics
+    int64_t l_nnz = 0;                  // Σ c_j (below-diagonal counts)
+    double flops = 0.0;                 // Σ c_j² + 2 c_j
+    int max_front = 0;
+    int64_t front_entries = 0;
+};
+
+// Column counts and etree statistics of a candidate ordering (cheap, used by AUTO).
+struct OrderingCost {
+    double flops = 0.0;
+    int64_t l_nnz = 0;
+    int height = 0;
+};
+OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm);
+
+// Full analysis for a given ordering choice; returns the ordering actually used.
+int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S);
+
+}  // namespace qoco

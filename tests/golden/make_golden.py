@@ -1,0 +1,60 @@
+"""Writes the stored expected values for the full-size parity tests.
+
+Every value comes from the CPU oracle (oracle/ipm.py) run on the seeded generator
+instance; nothing here touches the CUDA library.  Usage:
+
+    python tests/golden/make_golden.py trajectory_socp_N20000 [portfolio_socp_n20000 ...]
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import ipm  # noqa: E402
+from workloads import portfolio_socp, trajectory_socp  # noqa: E402
+
+CASES = {
+    "trajectory_socp_N20000": lambda: trajectory_socp(N=20000, seed=0),
+    "portfolio_socp_n20000": lambda: portfolio_socp(n=20000, k=200, seed=0),
+}
+
+
+def sample_idx(n, k=64, seed=123):
+    rng = np.random.default_rng(seed)
+    return sorted(set(rng.choice(n, size=min(k, n), replace=False).tolist()))
+
+
+def make(name):
+    prob = CASES[name]()
+    t0 = time.time()
+    r = ipm.solve(prob)
+    dt = time.time() - t0
+    out = dict(name=name, status=r.status, iters=r.iters, pobj=r.pobj, dobj=r.dobj,
+               oracle_seconds=dt, n=prob.n, m=prob.m, p=prob.p,
+               x_inf=float(np.abs(r.x).max()), y_inf=float(np.abs(r.y).max(initial=0.0)),
+               z_inf=float(np.abs(r.z).max(initial=0.0)))
+    for key, vec in (("x", r.x), ("y", r.y), ("z", r.z), ("s", r.s)):
+        if vec.size:
+            idx = sample_idx(vec.size)
+            out[f"{key}_idx"] = idx
+            out[f"{key}_val"] = [float(vec[i]) for i in idx]
+    meta = {k: (v.tolist() if isinstance(v, np.ndarray) and v.size < 16 else v)
+            for k, v in prob.meta.items() if isinstance(v, (int, float, np.ndarray)) and
+            (not isinstance(v, np.ndarray) or v.size < 16)}
+    out["generator_meta"] = meta
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), name + ".json")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, r.status, r.iters, r.pobj, f"{dt:.1f}s")
+
+
+if __name__ == "__main__":
+    for nm in sys.argv[1:] or list(CASES):
+        make(nm)

@@ -1,0 +1,48 @@
+"""Full-size parity in the launch configuration bench.py times: the trajectory SOCP
+with N = 20000 stages (N_K = 540018) against stored oracle values
+(tests/golden/*.json, written by tests/golden/make_golden.py, which calls only the
+oracle), plus an independent KKT certificate of the returned point."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from workloads import portfolio_socp, trajectory_socp
+
+from _gpu_util import assert_certificate
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+CASES = {
+    "trajectory_socp_N20000": lambda: trajectory_socp(N=20000, seed=0),
+    "portfolio_socp_n20000": lambda: portfolio_socp(n=20000, k=200, seed=0),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_full_size_against_oracle_golden(name):
+    path = os.path.join(GOLDEN, name + ".json")
+    if not os.path.exists(path):
+        pytest.skip(f"no stored oracle values for {name}")
+    g = json.load(open(path))
+    import paper_2603_29197_gb300 as q
+    prob = CASES[name]()
+    if "x_init" in g.get("generator_meta", {}):
+        np.testing.assert_allclose(prob.meta["x_init"], g["generator_meta"]["x_init"], rtol=0, atol=0)
+    S = q.Solver(prob)
+    assert S.solve() == 0
+    sol = S.solution()
+    info = sol["info"]
+    assert g["status"] == "solved"
+    assert abs(info["pobj"] - g["pobj"]) <= 1e-6 * max(1.0, abs(g["pobj"])), (info["pobj"], g["pobj"])
+    for key in ("x", "y", "z"):
+        if f"{key}_idx" not in g:
+            continue
+        idx = np.asarray(g[f"{key}_idx"])
+        ref = np.asarray(g[f"{key}_val"])
+        scale = max(1.0, g[f"{key}_inf"])
+        assert np.max(np.abs(sol[key][idx] - ref)) <= 1e-5 * scale, key
+    assert abs(info["iters"] - g["iters"]) <= 4, (info["iters"], g["iters"])
+    assert_certificate(prob, sol)

@@ -1,0 +1,113 @@
+"""Whole interior-point solves on the GPU (qoco_gpu_setup → qoco_gpu_solve →
+qoco_gpu_get_solution) against the oracle on the same seeded instances: objective
+within 1e-6 relative, x, y, z within 1e-5 (‖Δ‖∞ / max(1, ‖v‖∞)), plus an
+independent KKT certificate of the returned point."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import ipm
+from workloads import (Problem, dense_qp, lasso_qp, mpc_batch, portfolio_socp,
+                       trajectory_socp)
+
+from _gpu_util import assert_certificate, rel_inf
+
+pytestmark = pytest.mark.gpu
+
+
+def _lp(n=4, seed=0):
+    rng = np.random.default_rng(seed)
+    G = np.vstack([np.eye(n), -np.eye(n), rng.standard_normal((2 * n, n))])
+    h = np.concatenate([np.ones(2 * n), rng.uniform(0.2, 1.0, 2 * n)])
+    return Problem(n=n, m=G.shape[0], p=0, P=sp.csc_matrix((n, n)), c=rng.standard_normal(n),
+                   A=sp.csc_matrix((0, n)), b=np.zeros(0), G=sp.csc_matrix(G), h=h,
+                   l=G.shape[0], q=[], name=f"lp_n{n}")
+
+
+def _soc_projection(v):
+    q = len(v)
+    return Problem(n=q, m=q, p=0, P=sp.identity(q, format="csc"), c=-np.asarray(v, float),
+                   A=sp.csc_matrix((0, q)), b=np.zeros(0), G=-sp.identity(q, format="csc"),
+                   h=np.zeros(q), l=0, q=[q], name=f"soc_proj_q{q}")
+
+
+def _eq_qp(seed=0):
+    rng = np.random.default_rng(seed)
+    n, p = 40, 10
+    B = rng.standard_normal((n, n))
+    P = B @ B.T + np.eye(n)
+    A = rng.standard_normal((p, n))
+    return Problem(n=n, m=0, p=p, P=sp.csc_matrix(np.triu(P)), c=rng.standard_normal(n),
+                   A=sp.csc_matrix(A), b=rng.standard_normal(p), G=sp.csc_matrix((0, n)),
+                   h=np.zeros(0), l=0, q=[], name="equality_qp")
+
+
+CASES = {
+    "dense_qp_c1": lambda: dense_qp(),
+    "dense_qp_small": lambda: dense_qp(n=60, p=10, m=90, rank=8, density=0.1, seed=4),
+    "trajectory_N200": lambda: trajectory_socp(N=200, seed=0),
+    "trajectory_N1000": lambda: trajectory_socp(N=1000, seed=3),
+    "portfolio_n200": lambda: portfolio_socp(n=200, k=20, seed=0),
+    "portfolio_n1500": lambda: portfolio_socp(n=1500, k=60, seed=1),
+    "lasso_small": lambda: lasso_qp(rows=300, cols=600, density=0.02, seed=4),
+    "mpc_T": lambda: mpc_batch(count=3, seed=5)[2],
+    "lp_n4": lambda: _lp(4, 1),
+    "soc_projection": lambda: _soc_projection([0.1, 0.0, 5.0, -1.0, 2.0]),
+    "equality_qp": lambda: _eq_qp(),
+}
+
+
+@pytest.fixture(scope="module")
+def q():
+    import paper_2603_29197_gb300 as qq
+    return qq
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_solve_matches_oracle(q, name):
+    prob = CASES[name]()
+    ref = ipm.solve(prob)
+    assert ref.status == "solved"
+    S = q.Solver(prob)
+    status = S.solve()
+    sol = S.solution()
+    info = sol["info"]
+    assert status == 0, info
+    assert abs(info["pobj"] - ref.pobj) <= 1e-6 * max(1.0, abs(ref.pobj)), (info["pobj"], ref.pobj)
+    assert rel_inf(sol["x"], ref.x) <= 1e-5
+    assert rel_inf(sol["y"], ref.y) <= 1e-5
+    assert rel_inf(sol["z"], ref.z) <= 1e-5
+    assert abs(info["iters"] - ref.iters) <= 3, (info["iters"], ref.iters)
+    assert_certificate(prob, sol)
+    assert info["kernel_launches"] > 0
+
+
+def test_repeated_solves_are_identical(q):
+    prob = trajectory_socp(N=300, seed=2)
+    S = q.Solver(prob)
+    assert S.solve() == 0
+    a = S.solution()
+    assert S.solve() == 0
+    b = S.solution()
+    np.testing.assert_array_equal(a["x"], b["x"])
+    np.testing.assert_array_equal(a["z"], b["z"])
+    assert a["info"]["iters"] == b["info"]["iters"]
+
+
+def test_max_iter_status(q):
+    prob = dense_qp(n=60, p=10, m=90, rank=8, density=0.1, seed=4)
+    S = q.Solver(prob, max_iter=2)
+    assert S.solve() in (1, 2)
+    assert S.info()["iters"] == 2
+
+
+def test_orderings_agree(q):
+    prob = trajectory_socp(N=150, seed=6)
+    sols = []
+    for order in (q.ORDER_AMD, q.ORDER_ND, q.ORDER_NATURAL):
+        S = q.Solver(prob, ordering=order)
+        assert S.solve() == 0
+        sols.append(S.solution())
+    for s in sols[1:]:
+        assert rel_inf(s["x"], sols[0]["x"]) <= 1e-6
+        assert abs(s["info"]["pobj"] - sols[0]["info"]["pobj"]) <= 1e-7 * abs(sols[0]["info"]["pobj"])

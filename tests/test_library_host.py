@@ -1,0 +1,141 @@
+"""CPU tests of the C-ABI library: it loads without a GPU, exports every function
+that include/qoco_gpu.h declares, validates problem data on the host, and its
+host-side symbolic analysis (ordering, column counts, supernodes) agrees with a
+brute-force symbolic elimination."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import paper_2603_29197_gb300 as q
+from paper_2603_29197_gb300 import _lib
+from workloads import Problem, dense_qp, portfolio_socp, trajectory_socp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "qoco_gpu.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = set(re.findall(r"^\s*(?:[\w\s\*]+?)\b(qoco_gpu_\w+)\s*\(", txt, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 15
+    for nm in names:
+        assert hasattr(lib, nm), nm
+        assert nm in _lib.SIGNATURES, f"{nm} missing from the binding"
+    assert set(_lib.SIGNATURES) == names
+
+
+def test_default_settings(lib):
+    st = q.default_settings()
+    assert st.abstol == 1e-7 and st.reltol == 1e-7
+    assert st.max_iter == 200 and st.static_reg == 1e-8 and st.step_fraction == 0.99
+    assert st.max_refine == 10 and st.refine_tol == 1e-10
+
+
+def _tiny(**kw):
+    P = sp.csc_matrix(np.array([[2.0, 0.5], [0.0, 1.0]]))
+    A = sp.csc_matrix(np.array([[1.0, 1.0]]))
+    G = sp.csc_matrix(np.array([[1.0, 0.0], [0.0, 1.0], [-1.0, 0.0]]))
+    d = dict(n=2, m=3, p=1, P=P, c=np.zeros(2), A=A, b=np.ones(1), G=G, h=np.ones(3), l=1, q=[2])
+    d.update(kw)
+    return Problem(**d)
+
+
+@pytest.mark.parametrize("mut,code", [
+    (dict(l=2), _lib.ERR_INVALID_CONE),                      # l + Σq ≠ m
+    (dict(q=[1, 1], l=1), _lib.ERR_INVALID_CONE),            # SOC of dimension 1
+    (dict(P=sp.csc_matrix(np.array([[2.0, 0.0], [0.5, 1.0]]))), _lib.ERR_INVALID_CSC),  # lower P
+    (dict(G=sp.csc_matrix(np.ones((2, 2)))), _lib.ERR_INVALID_DIMS),
+    (dict(A=sp.csc_matrix(np.array([[np.nan, 1.0]]))), _lib.ERR_NONFINITE_DATA),
+])
+def test_host_validation(lib, mut, code):
+    with pytest.raises(ValueError) as e:
+        q.analyze(_tiny(**mut))
+    assert _lib.STATUS_NAMES[code] in str(e.value)
+
+
+def test_unsorted_rows_rejected(lib):
+    pr = _tiny()
+    G = pr.G.copy()
+    G.indices = G.indices.copy()
+    # column 0 has rows [0, 2]; swap them
+    G.indices[0], G.indices[1] = G.indices[1], G.indices[0]
+    pr.G = G
+    with pytest.raises(ValueError, match="invalid_csc"):
+        q.analyze(pr)
+
+
+def _kkt_pattern(prob):
+    n, p, m = prob.n, prob.p, prob.m
+    N = n + p + m
+    Pu = prob.P.toarray() != 0
+    B = np.zeros((N, N), dtype=bool)
+    B[:n, :n] = Pu | Pu.T
+    B[n:n + p, :n] = prob.A.toarray() != 0
+    B[n + p:, :n] = prob.G.toarray() != 0
+    B = B | B.T
+    o = n + p + prob.l
+    for qk in prob.q:
+        B[o:o + qk, o:o + qk] = True
+        o += qk
+    np.fill_diagonal(B, True)
+    return B
+
+
+def _symbolic_counts(B):
+    """Below-diagonal counts of L by explicit boolean elimination."""
+    B = B.copy()
+    N = B.shape[0]
+    counts = np.zeros(N, dtype=np.int64)
+    for j in range(N):
+        below = np.nonzero(B[j + 1:, j])[0] + j + 1
+        counts[j] = below.size
+        if below.size:
+            B[np.ix_(below, below)] = True
+    return counts
+
+
+@pytest.mark.parametrize("make", [lambda: dense_qp(n=40, p=8, m=60, rank=5, density=0.1, seed=3),
+                                  lambda: trajectory_socp(N=30, seed=1),
+                                  lambda: portfolio_socp(n=60, k=6, seed=2)],
+                         ids=["dense_qp", "trajectory", "portfolio"])
+@pytest.mark.parametrize("order", [q.ORDER_AMD, q.ORDER_ND, q.ORDER_NATURAL, q.ORDER_AUTO])
+def test_symbolic_counts_match_brute_force(lib, make, order):
+    prob = make()
+    info, perm, sn = q.analyze(prob, ordering=order, nd_leaf=16)
+    N = prob.n + prob.p + prob.m
+    assert sorted(perm.tolist()) == list(range(N))
+    B = _kkt_pattern(prob)[np.ix_(perm, perm)]
+    cnt = _symbolic_counts(B)
+    assert info["l_nnz"] == cnt.sum()
+    assert np.isclose(info["factor_flops"], float(np.sum(cnt.astype(float) ** 2 + 2 * cnt)))
+    assert sn[0] == 0 and sn[-1] == N and np.all(np.diff(sn) > 0)
+    assert info["kkt_nnz"] == B.sum()
+    if order == q.ORDER_NATURAL:
+        np.testing.assert_array_equal(perm, np.arange(N))
+
+
+def test_nested_dissection_gives_shallow_tree_on_stage_chains(lib):
+    prob = trajectory_socp(N=2000)
+    i_amd, _, _ = q.analyze(prob, ordering=q.ORDER_AMD)
+    i_nd, _, _ = q.analyze(prob, ordering=q.ORDER_ND)
+    i_auto, _, _ = q.analyze(prob)
+    assert i_nd["n_levels"] <= 30 < i_amd["n_levels"]
+    assert i_auto["ordering_used"] == q.ORDER_ND
+
+
+def test_amd_orders_dense_rows_last(lib):
+    prob = portfolio_socp(n=2000, k=40, seed=1)
+    info, perm, _ = q.analyze(prob, ordering=q.ORDER_AMD)
+    # the budget row and the risk-cone rows Fᵀx couple every asset: they end up last
+    n, p = prob.n, prob.p
+    core = {n} | set(range(n + p + prob.l + 1, n + p + prob.m))
+    assert set(perm[-len(core):].tolist()) == core
+    assert info["n_levels"] <= 4
