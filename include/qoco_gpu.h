@@ -79,6 +79,9 @@ typedef struct {
     double step_fraction;               /* 0.99 */
     int ordering;                       /* QOCO_GPU_ORDER_* (AUTO) */
     int nd_leaf;                        /* ND stops splitting below this many nodes (64) */
+    int subtree_tasks;                  /* factor/solve scheduling: > 0 = target number of warp
+                                           subtree tasks below the level launches; ≤ 0 = none,
+                                           every supernode in level launches (default 0) */
     int verbose;                        /* 0: silent; 1: one line per iteration on stdout */
 } qoco_gpu_settings;
 
@@ -197,6 +200,11 @@ int qoco_gpu_get_kkt(const qoco_gpu_solver* solver, int64_t* rowptr, int* colidx
  * permuted order, D[N_K].  Errors: INVALID_ARG (too large), NO_FACTOR. */
 int qoco_gpu_get_factor_dense(const qoco_gpu_solver* solver, int* perm, double* L, double* D);
 
+/* Copies the reciprocal pivots 1/d_j that the factorisation stored for the solves
+ * (host dinv[N_K], permuted order; computed on the device by two Newton–Raphson steps
+ * from the hardware's approximate reciprocal).  Errors: NO_FACTOR. */
+int qoco_gpu_get_pivot_reciprocals(const qoco_gpu_solver* solver, double* dinv);
+
 /* ---- stand-alone cone kernels (paper §2.1, §2.3) ---------------------------- */
 
 /* Creates a device descriptor of K = R^l_+ × Q^{q_0} × …; q host, nsoc entries ≥ 2. */
@@ -227,12 +235,14 @@ int qoco_gpu_cone_max_step(const qoco_gpu_cones* cones, const double* u, const d
  * qoco_gpu_setup on the host only and reports their statistics in *info; perm
  * (host, N_K, may be NULL) receives the final new → original ordering.
  * sn_ptr (host, may be NULL) receives the first permuted column of each supernode
- * followed by N_K (n_supernodes + 1 entries; call once with NULL to learn the count).
+ * followed by N_K (n_supernodes + 1 entries; call once with NULL to learn the count);
+ * sn_nrow and sn_level (host, n_supernodes entries each, may be NULL) receive each
+ * supernode's front order f_s and its height in the supernodal tree.
  * Errors as for setup. */
 int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A,
                      const qoco_csc* G, int l, int nsoc, const int* q,
                      const qoco_gpu_settings* settings, qoco_gpu_info* info, int* perm,
-                     int* sn_ptr);
+                     int* sn_ptr, int* sn_nrow, int* sn_level);
 
 #ifdef __cplusplus
 }

@@ -88,8 +88,9 @@ def _tptr(t):
     return C.c_void_p(0 if t is None else t.data_ptr())
 
 
-def analyze(prob, settings=None, **kw):
-    """Host-only ordering + symbolic analysis (no GPU needed): returns (info, perm, sn_ptr)."""
+def analyze(prob, settings=None, structure=False, **kw):
+    """Host-only ordering + symbolic analysis (no GPU needed): returns (info, perm, sn_ptr),
+    plus (f_s, level_s) per supernode when structure=True."""
     lib = load()
     st = _settings(settings, kw)
     n, m, p, P, A, G, q = _problem_args(prob)
@@ -98,13 +99,18 @@ def analyze(prob, settings=None, **kw):
     perm = np.zeros(N, dtype=np.int32)
     rc = lib.qoco_gpu_analyze(n, m, p, P.ptr, A.ptr, G.ptr, int(prob.l), len(q),
                               q.ctypes.data_as(C.POINTER(C.c_int)), C.byref(st), C.byref(info),
-                              perm.ctypes.data_as(C.POINTER(C.c_int)), None)
+                              perm.ctypes.data_as(C.POINTER(C.c_int)), None, None, None)
     if rc != 0:
         raise ValueError(f"analysis failed: {STATUS_NAMES.get(rc, rc)}: {info.message.decode()}")
     sn = np.zeros(info.n_supernodes + 1, dtype=np.int32)
+    fs = np.zeros(max(1, info.n_supernodes), dtype=np.int32)
+    lv = np.zeros(max(1, info.n_supernodes), dtype=np.int32)
+    ip = C.POINTER(C.c_int)
     lib.qoco_gpu_analyze(n, m, p, P.ptr, A.ptr, G.ptr, int(prob.l), len(q),
-                         q.ctypes.data_as(C.POINTER(C.c_int)), C.byref(st), None, None,
-                         sn.ctypes.data_as(C.POINTER(C.c_int)))
+                         q.ctypes.data_as(ip), C.byref(st), None, None, sn.ctypes.data_as(ip),
+                         fs.ctypes.data_as(ip), lv.ctypes.data_as(ip))
+    if structure:
+        return info.as_dict(), perm, sn, fs[:info.n_supernodes], lv[:info.n_supernodes]
     return info.as_dict(), perm, sn
 
 
@@ -200,6 +206,13 @@ class Solver:
         if rc != 0:
             raise SolverError(rc, "get_factor_dense")
         return perm, L, D
+
+    def pivot_reciprocals(self):
+        out = np.zeros(self.N)
+        rc = self.lib.qoco_gpu_get_pivot_reciprocals(self._h, _dptr(out))
+        if rc != 0:
+            raise SolverError(rc, "get_pivot_reciprocals")
+        return out
 
     def set_profiling(self, on=True):
         rc = self.lib.qoco_gpu_set_profiling(self._h, 1 if on else 0)

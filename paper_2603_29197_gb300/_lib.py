@@ -38,7 +38,7 @@ class Settings(C.Structure):
                 ("dyn_reg_thresh", C.c_double), ("dyn_reg_value", C.c_double),
                 ("max_refine", C.c_int), ("refine_tol", C.c_double),
                 ("step_fraction", C.c_double), ("ordering", C.c_int), ("nd_leaf", C.c_int),
-                ("verbose", C.c_int)]
+                ("subtree_tasks", C.c_int), ("verbose", C.c_int)]
 
 
 class Info(C.Structure):
@@ -95,6 +95,7 @@ SIGNATURES = {
     "qoco_gpu_kkt_solve": (C.c_int, [_VP, _VP, _VP, _IP, _DP, _VP]),
     "qoco_gpu_get_kkt": (C.c_int, [_VP, C.POINTER(C.c_int64), _IP, _DP]),
     "qoco_gpu_get_factor_dense": (C.c_int, [_VP, _IP, _DP, _DP]),
+    "qoco_gpu_get_pivot_reciprocals": (C.c_int, [_VP, _DP]),
     "qoco_gpu_cones_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, _IP]),
     "qoco_gpu_cones_destroy": (C.c_int, [_VP]),
     "qoco_gpu_cone_nt_scaling": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -104,7 +105,7 @@ SIGNATURES = {
     "qoco_gpu_cone_max_step": (C.c_int, [_VP, _VP, _VP, C.c_double, _VP, _VP, _VP]),
     "qoco_gpu_analyze": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(CSC), C.POINTER(CSC),
                                    C.POINTER(CSC), C.c_int, C.c_int, _IP, C.POINTER(Settings),
-                                   C.POINTER(Info), _IP, _IP]),
+                                   C.POINTER(Info), _IP, _IP, _IP, _IP]),
 }
 
 _lib = None

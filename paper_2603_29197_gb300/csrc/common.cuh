@@ -27,6 +27,41 @@ __device__ __forceinline__ double warp_min(double v) {
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+// max / min of non-negative doubles through their bit patterns (IEEE order of
+// non-negative doubles equals the integer order of their bits, +inf included): runs on
+// the integer pipe, which on GB300 is far wider than the FP64 pipe
+__device__ __forceinline__ double warp_max_nonneg(double v) {
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t > b ? t : b;
+    }
+    return __longlong_as_double(b);
+}
+__device__ __forceinline__ double warp_min_nonneg(double v) {
+    long long b = __double_as_longlong(v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = t < b ? t : b;
+    }
+    return __longlong_as_double(b);
+}
+
+// 1/d by two Newton–Raphson steps r ← r + r(1 − d·r) from the hardware's approximate
+// reciprocal (relative error of the seed ≲ 2^-22, so two quadratic steps reach the
+// FP64 rounding level).  Four FMAs instead of an IEEE division sequence; d must be a
+// normal number (pivots are kept away from zero by the dynamic regularisation).
+__device__ __forceinline__ double recip(double d) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
 // sub-warp reductions over aligned groups of G lanes (G a power of two ≤ 32)
 template <int G>
 __device__ __forceinline__ double group_sum(double v) {
@@ -41,13 +76,13 @@ __device__ __forceinline__ double group_max(double v) {
     return v;
 }
 
-// Block-wide reduction of NV values (sum or max selected per value by `is_max`),
+// Block-wide reduction of NV values (sum, or max of non-negative values, per `is_max`),
 // result valid in thread 0.  `sm` holds NV * 32 doubles.  All threads must call.
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], const bool (&is_max)[NV], double* sm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = is_max[k] ? warp_max(v[k]) : warp_sum(v[k]);
+    for (int k = 0; k < NV; ++k) v[k] = is_max[k] ? warp_max_nonneg(v[k]) : warp_sum(v[k]);
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < NV; ++k) sm[k * 32 + wid] = v[k];
@@ -55,8 +90,8 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], const bool (&is_ma
     if (wid == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double t = lane < nw ? sm[k * 32 + lane] : (is_max[k] ? 0.0 : 0.0);
-            v[k] = is_max[k] ? warp_max(t) : warp_sum(t);
+            double t = lane < nw ? sm[k * 32 + lane] : 0.0;
+            v[k] = is_max[k] ? warp_max_nonneg(t) : warp_sum(t);
         }
     }
     __syncthreads();

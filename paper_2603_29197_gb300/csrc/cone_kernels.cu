@@ -157,13 +157,13 @@ __global__ void k_max_step(ConeView c, ConeGrid g, const double* __restrict__ u1
             }
         }
     }
-    a = warp_min(a);
+    a = warp_min_nonneg(a);  // step lengths are ≥ 0 (or +inf)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) sm[wid] = a;
     __syncthreads();
     if (wid == 0) {
         double t = lane < (int)(blockDim.x >> 5) ? sm[lane] : INFINITY;
-        t = warp_min(t);
+        t = warp_min_nonneg(t);
         if (lane == 0) partial[blockIdx.x] = t;
     }
 }

@@ -4,11 +4,10 @@
 #include <vector>
 
 #include "common.cuh"
+#include "plan.h"
 
 namespace qoco {
 
-constexpr int kSmemFront = 160;       // fronts up to this order are factored in shared memory
-constexpr int kMaxSolveFront = 26000; // solve kernels keep one front vector in shared memory
 
 struct FactorView {
     const int* first = nullptr;      // ns: first permuted column
@@ -28,21 +27,20 @@ struct FactorView {
     const int* perm = nullptr;       // new → original
     double* front = nullptr;         // Σ f_s² doubles
     double* upd = nullptr;           // Σ r_s doubles (solve update vectors)
+    double* dinv = nullptr;          // N: reciprocal pivots 1/d_j (permuted order)
     int* nreg = nullptr;             // dynamic-regularisation counter
     double eps = 1e-8, dyn_thresh = 1e-13, dyn_value = 1e-7;
 };
 
-struct LevelPlan {
-    int count = 0, max_f = 0, off_all = 0;
-    int n_small = 0, max_small = 0, off_small = 0;
-    int n_large = 0, off_large = 0;
-};
-
 struct FactorPlan {
     std::vector<LevelPlan> levels;
-    int* d_all = nullptr;    // supernodes of every level, level by level
-    int* d_small = nullptr;  // fronts with f ≤ kSmemFront
-    int* d_large = nullptr;  // the others
+    int ntasks = 0, task_max_f = 0, task_height = 0;
+    int* d_task = nullptr;   // 2·ntasks: lo, hi (inclusive) supernode ranges
+    int* d_thread = nullptr; // level lists
+    int* d_warp = nullptr;
+    int* d_small = nullptr;
+    int* d_large = nullptr;
+    int* d_cta = nullptr;
 };
 
 int factor_set_attributes();

@@ -1,0 +1,45 @@
+// Launch plan of the supernodal factorisation and solves (host side, plain C++).
+#pragma once
+
+#include <vector>
+
+#include "symbolic.h"
+
+namespace qoco {
+
+constexpr int kSmemFront = 160;       // fronts up to this order are factored in shared memory
+constexpr int kMaxSolveFront = 26000; // solve kernels keep one front vector in shared memory
+constexpr int kThreadFront = 8;     // fronts up to this order are handled by one thread
+constexpr int kWarpFront = 48;      // fronts up to this order are handled by one warp
+constexpr int kWarpsPerBlock = 4;    // warps per block of the warp-level kernels
+
+// Launch plan of one factorisation / solve.  Supernodes are split into
+//  * subtree tasks: a task is a whole subtree of small fronts whose supernodes occupy a
+//    contiguous range [lo, hi] of the postorder; one warp processes it children-first
+//    (factor, forward) or parents-first (backward) with no grid-wide synchronisation;
+//  * the remaining (upper) supernodes, processed one tree level per launch: fronts up
+//    to kThreadFront by one thread each (so that every FP64 warp instruction serves 32
+//    fronts), up to kWarpFront by one warp each, up to kSmemFront by a CTA in shared
+//    memory, larger ones by a CTA in global memory.
+struct LevelPlan {
+    int n_thread = 0, off_thread = 0;
+    int n_warp = 0, off_warp = 0, max_warp_f = 0;
+    int n_small = 0, off_small = 0, max_small = 0;
+    int n_large = 0, off_large = 0;
+    int n_cta = 0, off_cta = 0, max_cta_f = 0;  // small + large, for the solve kernels
+};
+
+// Host-side lists from which the device plan is uploaded.
+struct PlanHost {
+    std::vector<LevelPlan> levels;
+    std::vector<int> task, thread, warp, small, large, cta;
+    int task_max_f = 0, task_height = 0;
+    int max_f = 0;
+};
+
+// Builds the plan: subtree tasks below the height that still leaves at least
+// `target_tasks` tasks (or, on small trees, the height with the most tasks), and the
+// per-level lists of the remaining supernodes.  No tasks when `allow_tasks` is false.
+void build_plan(const Symbolic& S, bool allow_tasks, int target_tasks, PlanHost* P);
+
+}  // namespace qoco

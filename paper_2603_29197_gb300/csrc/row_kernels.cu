@@ -8,6 +8,7 @@
 namespace qoco {
 
 constexpr int kRowThreads = 256;
+constexpr int kMaxRowBlocks = 152 * 2;  // grid cap: 2 blocks (16 warps) per SM
 
 template <int NV>
 __device__ __forceinline__ void store_partials(double (&v)[NV], const bool (&is_max)[NV], double* partial) {
@@ -18,60 +19,69 @@ __device__ __forceinline__ void store_partials(double (&v)[NV], const bool (&is_
         for (int k = 0; k < NV; ++k) partial[(int64_t)blockIdx.x * NV + k] = v[k];
 }
 
+// Grid-stride over rows: a block of kRowThreads threads holds kRowThreads/LPR row groups;
+// every lane of a block runs the same number of loop trips, so the shuffles inside
+// group_sum always see full warps.  The grid is capped (kMaxRowBlocks) so that the
+// single-block finalisation reduces few partials.
+
 // residuals: r_x = Px + c + Aᵀy + Gᵀz, r_y = Ax − b, r_z = Gx + s − h
 // sums: xᵀPx, cᵀx, bᵀy, hᵀz, sᵀz   maxes: |Px|,|Aᵀy|,|Gᵀz|,|Ax|,|Gx|,|r_x|,|r_y|,|r_z|,|s|
 template <int LPR>
-__global__ void k_residual(KKTView K, const double* __restrict__ xyz, const double* __restrict__ s,
-                           const double* __restrict__ c, const double* __restrict__ b,
-                           const double* __restrict__ h, double* __restrict__ r, double* partial) {
-    const int gl = (blockIdx.x * blockDim.x + threadIdx.x);
-    const int row = gl / LPR, lane = gl % LPR;
+__global__ void __launch_bounds__(kRowThreads) k_residual(KKTView K, const double* __restrict__ xyz,
+                                                         const double* __restrict__ s,
+                                                         const double* __restrict__ c,
+                                                         const double* __restrict__ b,
+                                                         const double* __restrict__ h,
+                                                         double* __restrict__ r, double* partial) {
+    constexpr int GPB = kRowThreads / LPR;
+    const int grp = threadIdx.x / LPR, lane = threadIdx.x % LPR;
     const int n = K.n, p = K.p;
     double v[kResNV];
     bool is_max[kResNV];
 #pragma unroll
     for (int k = 0; k < kResNV; ++k) { v[k] = 0.0; is_max[k] = k >= kResNSum; }
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    if (row < K.N) {
-        const int64_t beg = K.rowptr[row], end = K.rowptr[row + 1];
-        for (int64_t t = beg + lane; t < end; t += LPR) {
-            const int j = K.colidx[t];
-            const double kv = K.val[t] * xyz[j];
-            if (j < n) a0 += kv;
-            else if (j < n + p) a1 += kv;
-            else a2 += kv;
+    for (int base = blockIdx.x * GPB; base < K.N; base += gridDim.x * GPB) {
+        const int row = base + grp;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        if (row < K.N) {
+            const int64_t beg = K.rowptr[row], end = K.rowptr[row + 1];
+            for (int64_t t = beg + lane; t < end; t += LPR) {
+                const int j = K.colidx[t];
+                const double kv = K.val[t] * xyz[j];
+                if (j < n) a0 += kv;
+                else if (j < n + p) a1 += kv;
+                else a2 += kv;
+            }
         }
-    }
-    a0 = group_sum<LPR>(a0);  // every lane of the warp takes part in the shuffles
-    a1 = group_sum<LPR>(a1);
-    a2 = group_sum<LPR>(a2);
-    if (row < K.N) {
-        if (lane == 0) {
+        a0 = group_sum<LPR>(a0);
+        a1 = group_sum<LPR>(a1);
+        a2 = group_sum<LPR>(a2);
+        if (row < K.N && lane == 0) {
             if (row < n) {
                 const double rx = a0 + c[row] + a1 + a2;
                 r[row] = rx;
-                v[0] = xyz[row] * a0;   // xᵀPx
-                v[1] = c[row] * xyz[row];
-                v[5] = fabs(a0);        // |Px|
-                v[6] = fabs(a1);        // |Aᵀy|
-                v[7] = fabs(a2);        // |Gᵀz|
-                v[10] = fabs(rx);
+                v[0] += xyz[row] * a0;  // xᵀPx
+                v[1] += c[row] * xyz[row];
+                v[5] = fmax(v[5], fabs(a0));   // |Px|
+                v[6] = fmax(v[6], fabs(a1));   // |Aᵀy|
+                v[7] = fmax(v[7], fabs(a2));   // |Gᵀz|
+                v[10] = fmax(v[10], fabs(rx));
             } else if (row < n + p) {
                 const int i = row - n;
                 const double ry = a0 - b[i];
                 r[row] = ry;
-                v[2] = b[i] * xyz[row];
-                v[8] = fabs(a0);        // |Ax|
-                v[11] = fabs(ry);
+                v[2] += b[i] * xyz[row];
+                v[8] = fmax(v[8], fabs(a0));   // |Ax|
+                v[11] = fmax(v[11], fabs(ry));
             } else {
                 const int i = row - n - p;
                 const double rz = a0 + s[i] - h[i];
                 r[row] = rz;
-                v[3] = h[i] * xyz[row];
-                v[4] = s[i] * xyz[row];
-                v[9] = fabs(a0);        // |Gx|
-                v[12] = fabs(rz);
-                v[13] = fabs(s[i]);
+                v[3] += h[i] * xyz[row];
+                v[4] += s[i] * xyz[row];
+                v[9] = fmax(v[9], fabs(a0));   // |Gx|
+                v[12] = fmax(v[12], fabs(rz));
+                v[13] = fmax(v[13], fabs(s[i]));
             }
         }
     }
@@ -80,24 +90,26 @@ __global__ void k_residual(KKTView K, const double* __restrict__ xyz, const doub
 
 // res = r − K x (unregularised K), maxes |res|, |x|, |r|
 template <int LPR>
-__global__ void k_spmv_res(KKTView K, const double* __restrict__ x, const double* __restrict__ r,
-                           double* __restrict__ res, double* partial) {
-    const int gl = (blockIdx.x * blockDim.x + threadIdx.x);
-    const int row = gl / LPR, lane = gl % LPR;
+__global__ void __launch_bounds__(kRowThreads) k_spmv_res(KKTView K, const double* __restrict__ x,
+                                                         const double* __restrict__ r,
+                                                         double* __restrict__ res, double* partial) {
+    constexpr int GPB = kRowThreads / LPR;
+    const int grp = threadIdx.x / LPR, lane = threadIdx.x % LPR;
     double v[3] = {0.0, 0.0, 0.0};
     const bool is_max[3] = {true, true, true};
-    double acc = 0.0;
-    if (row < K.N)
-        for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR)
-            acc += K.val[t] * x[K.colidx[t]];
-    acc = group_sum<LPR>(acc);
-    if (row < K.N) {
-        if (lane == 0) {
+    for (int base = blockIdx.x * GPB; base < K.N; base += gridDim.x * GPB) {
+        const int row = base + grp;
+        double acc = 0.0;
+        if (row < K.N)
+            for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR)
+                acc += K.val[t] * x[K.colidx[t]];
+        acc = group_sum<LPR>(acc);
+        if (row < K.N && lane == 0) {
             const double e = r[row] - acc;
             res[row] = e;
-            v[0] = fabs(e);
-            v[1] = fabs(x[row]);
-            v[2] = fabs(r[row]);
+            v[0] = fmax(v[0], fabs(e));
+            v[1] = fmax(v[1], fabs(x[row]));
+            v[2] = fmax(v[2], fabs(r[row]));
         }
     }
     store_partials<3>(v, is_max, partial);
@@ -105,16 +117,19 @@ __global__ void k_spmv_res(KKTView K, const double* __restrict__ x, const double
 
 // max_i Σ_j |K_ij|
 template <int LPR>
-__global__ void k_norm_inf(KKTView K, double* partial) {
-    const int gl = (blockIdx.x * blockDim.x + threadIdx.x);
-    const int row = gl / LPR, lane = gl % LPR;
+__global__ void __launch_bounds__(kRowThreads) k_norm_inf(KKTView K, double* partial) {
+    constexpr int GPB = kRowThreads / LPR;
+    const int grp = threadIdx.x / LPR, lane = threadIdx.x % LPR;
     double v[1] = {0.0};
     const bool is_max[1] = {true};
-    double acc = 0.0;
-    if (row < K.N)
-        for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR) acc += fabs(K.val[t]);
-    acc = group_sum<LPR>(acc);
-    v[0] = acc;
+    for (int base = blockIdx.x * GPB; base < K.N; base += gridDim.x * GPB) {
+        const int row = base + grp;
+        double acc = 0.0;
+        if (row < K.N)
+            for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR) acc += fabs(K.val[t]);
+        acc = group_sum<LPR>(acc);
+        v[0] = fmax(v[0], acc);
+    }
     store_partials<1>(v, is_max, partial);
 }
 
@@ -126,15 +141,20 @@ __device__ void reduce_columns(const double* partial, int nb, int NV, unsigned m
         double a = 0.0;
         for (int i = threadIdx.x; i < nb; i += blockDim.x) {
             const double t = partial[(int64_t)i * NV + k];
-            a = mx ? fmax(a, t) : a + t;
+            if (mx) {
+                const long long bt = __double_as_longlong(t), ba = __double_as_longlong(a);
+                a = bt > ba ? t : a;
+            } else {
+                a += t;
+            }
         }
-        a = mx ? warp_max(a) : warp_sum(a);
+        a = mx ? warp_max_nonneg(a) : warp_sum(a);
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (lane == 0) sm[wid] = a;
         __syncthreads();
         if (wid == 0) {
             double t = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0.0;
-            t = mx ? warp_max(t) : warp_sum(t);
+            t = mx ? warp_max_nonneg(t) : warp_sum(t);
             if (lane == 0) out[k] = t;
         }
         __syncthreads();
@@ -186,7 +206,8 @@ __global__ void k_finalize_norm(const double* __restrict__ partial, int nb, IPMS
 // ---- launchers ----------------------------------------------------------------
 static int rows_blocks(int N, int lpr) {
     const int rows_per_block = kRowThreads / lpr;
-    return (N + rows_per_block - 1) / rows_per_block;
+    const int need = (N + rows_per_block - 1) / rows_per_block;
+    return need < kMaxRowBlocks ? (need > 0 ? need : 1) : kMaxRowBlocks;
 }
 // partial-buffer size in doubles: the most blocks (32 lanes per row) times the most
 // values per block (the residual pass)

@@ -16,6 +16,7 @@
 
 #include "cone_kernels.h"
 #include "factor.h"
+#include "plan.h"
 #include "qoco_gpu.h"
 #include "row_kernels.h"
 #include "symbolic.h"
@@ -285,39 +286,30 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     double* pd;
     if ((rc = dalloc(S, &pd, (size_t)Y.front_entries))) return rc; f.front = pd;
     if ((rc = dalloc(S, &pd, (size_t)Y.upd_off[Y.ns]))) return rc; f.upd = pd;
+    if ((rc = dalloc(S, &pd, (size_t)N))) return rc; f.dinv = pd;
     if ((rc = dalloc(S, &pi, 1))) return rc; f.nreg = pi;
     f.eps = S->st.static_reg;
     f.dyn_thresh = S->st.dyn_reg_thresh;
     f.dyn_value = S->st.dyn_reg_value;
 
-    // level plan
-    FactorPlan& P = S->plan;
-    std::vector<int> all, small, large;
-    P.levels.resize(Y.n_levels);
-    for (int lv = 0; lv < Y.n_levels; ++lv) {
-        LevelPlan& L = P.levels[lv];
-        L.off_all = (int)all.size();
-        L.off_small = (int)small.size();
-        L.off_large = (int)large.size();
-        for (int k = Y.level_ptr[lv]; k < Y.level_ptr[lv + 1]; ++k) {
-            const int s2 = Y.level_list[k];
-            const int fs = Y.sn_nrow[s2];
-            all.push_back(s2);
-            L.max_f = std::max(L.max_f, fs);
-            if (fs <= kSmemFront) { small.push_back(s2); L.max_small = std::max(L.max_small, fs); }
-            else large.push_back(s2);
-        }
-        L.count = (int)all.size() - L.off_all;
-        L.n_small = (int)small.size() - L.off_small;
-        L.n_large = (int)large.size() - L.off_large;
-        if (L.max_f > kMaxSolveFront) {
-            S->msg = "a supernode front exceeds the solve kernel's shared-memory limit";
-            return QOCO_GPU_ERR_NOT_IMPLEMENTED;
-        }
+    // launch plan: subtree tasks + level lists
+    PlanHost ph;
+    build_plan(Y, S->st.subtree_tasks > 0, S->st.subtree_tasks, &ph);
+    if (ph.max_f > kMaxSolveFront) {
+        S->msg = "a supernode front exceeds the solve kernel's shared-memory limit";
+        return QOCO_GPU_ERR_NOT_IMPLEMENTED;
     }
-    if ((rc = dcopy(S, &P.d_all, all))) return rc;
-    if ((rc = dcopy(S, &P.d_small, small))) return rc;
-    if ((rc = dcopy(S, &P.d_large, large))) return rc;
+    FactorPlan& P = S->plan;
+    P.levels = ph.levels;
+    P.ntasks = (int)ph.task.size() / 2;
+    P.task_max_f = ph.task_max_f;
+    P.task_height = ph.task_height;
+    if ((rc = dcopy(S, &P.d_task, ph.task))) return rc;
+    if ((rc = dcopy(S, &P.d_thread, ph.thread))) return rc;
+    if ((rc = dcopy(S, &P.d_warp, ph.warp))) return rc;
+    if ((rc = dcopy(S, &P.d_small, ph.small))) return rc;
+    if ((rc = dcopy(S, &P.d_large, ph.large))) return rc;
+    if ((rc = dcopy(S, &P.d_cta, ph.cta))) return rc;
 
     // iterate / work vectors
     double** vecN[] = {&S->xyz, &S->d_aff, &S->d_cmb, &S->r, &S->rhs, &S->sol_w, &S->sol_xp, &S->res};
@@ -564,12 +556,13 @@ void qoco_gpu_default_settings(qoco_gpu_settings* s) {
     s->step_fraction = 0.99;
     s->ordering = QOCO_GPU_ORDER_AUTO;
     s->nd_leaf = 64;
+    s->subtree_tasks = 0;
     s->verbose = 0;
 }
 
 int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A, const qoco_csc* G, int l,
                      int nsoc, const int* q, const qoco_gpu_settings* settings, qoco_gpu_info* info,
-                     int* perm, int* sn_ptr) {
+                     int* perm, int* sn_ptr, int* sn_nrow, int* sn_level) {
     qoco_gpu_settings st;
     KKTPattern K;
     Symbolic Y;
@@ -602,6 +595,8 @@ int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A, 
     }
     if (perm) memcpy(perm, Y.perm.data(), sizeof(int) * K.N);
     if (sn_ptr) memcpy(sn_ptr, Y.sn_first.data(), sizeof(int) * (Y.ns + 1));
+    if (sn_nrow) memcpy(sn_nrow, Y.sn_nrow.data(), sizeof(int) * Y.ns);
+    if (sn_level) memcpy(sn_level, Y.level.data(), sizeof(int) * Y.ns);
     return 0;
 }
 
@@ -774,6 +769,14 @@ int qoco_gpu_get_factor_dense(const qoco_gpu_solver* S, int* perm, double* L, do
                 for (int a = k + 1; a < f; ++a) L[(size_t)R[a] * N + first + k] = F[(size_t)k * f + a];
         }
     }
+    return 0;
+}
+
+int qoco_gpu_get_pivot_reciprocals(const qoco_gpu_solver* S, double* dinv) {
+    if (!S || !dinv) return QOCO_GPU_ERR_INVALID_ARG;
+    if (!S->have_factor) return QOCO_GPU_ERR_NO_FACTOR;
+    QOCO_CUDA_TRY(cudaDeviceSynchronize());
+    QOCO_CUDA_TRY(cudaMemcpy(dinv, S->fv.dinv, sizeof(double) * S->N, cudaMemcpyDeviceToHost));
     return 0;
 }
 

@@ -117,3 +117,18 @@ def test_refined_solve_matches_oracle(name, spread):
         cond = np.linalg.cond(K.toarray(), p=np.inf)
         tol = max(1e-9, 10.0 * cond * max(be, 1e-16))
         assert rel_inf(x, xo, floor=0.0) <= tol, (rel_inf(x, xo, floor=0.0), tol, cond)
+
+
+@pytest.mark.parametrize("name", ["dense_qp_c1", "trajectory_N12", "portfolio_n300"])
+def test_pivot_reciprocals_within_two_ulp(name):
+    """The factor stores 1/d_j computed by Newton–Raphson from the hardware's approximate
+    reciprocal; it must agree with the correctly rounded quotient to ≤ 2 ulp."""
+    prob = SMALL[name]()
+    s, z, _, _ = random_cone_iterate(prob.l, prob.q, seed=8, scale_spread=3.0)
+    S = _setup(prob)
+    S.kkt_factor_at(T(s), T(z))
+    _, _, D = S.factor_dense()
+    dinv = S.pivot_reciprocals()
+    exact = 1.0 / D
+    ulp = np.spacing(np.abs(exact))
+    assert np.all(np.abs(dinv - exact) <= 2 * ulp)
