@@ -51,6 +51,7 @@ extern "C" {
 #define QOCO_GPU_ERR_NO_FACTOR       -9  /* a call needs a factorisation that does not exist */
 #define QOCO_GPU_ERR_INVALID_ARG    -10
 #define QOCO_GPU_ERR_NOT_IMPLEMENTED -11
+#define QOCO_GPU_ERR_TOO_LARGE      -12  /* exceeds a fixed-size buffer of an allocation-free entry point */
 
 /* ---- orderings for the symbolic analysis ---------------------------------- */
 #define QOCO_GPU_ORDER_AUTO     0  /* the cheaper of AMD and ND by the analysis' cost model */
@@ -228,6 +229,26 @@ int qoco_gpu_cone_division(const qoco_gpu_cones* cones, const double* lam, const
 size_t qoco_gpu_cone_max_step_scratch_bytes(const qoco_gpu_cones* cones);
 int qoco_gpu_cone_max_step(const qoco_gpu_cones* cones, const double* u, const double* du,
                            double cap, double* alpha, void* scratch, void* stream);
+
+/* Allocation-free variant of qoco_gpu_cone_max_step (the paper has no counterpart):
+ * for callers that must not allocate device memory while they run — code that is being
+ * captured into a CUDA graph, real-time control loops that reserve all memory up front,
+ * or hosts whose allocator is owned by another framework — this call takes no scratch
+ * argument and calls no cudaMalloc, cudaFree or allocating library routine.  Its block
+ * partials live in one fixed 64 KiB device array (8192 doubles) that every GPU loading
+ * the library holds until the process exits.
+ *   - Same inputs, output and result as qoco_gpu_cone_max_step (the cones descriptor is
+ *     created beforehand by qoco_gpu_cones_create).
+ *   - Returns QOCO_GPU_ERR_TOO_LARGE, without launching, when the cone grid needs more
+ *     than 8192 partials (⌈l/256⌉ + ⌈#SOC of dim ≤ 32 / 256⌉ + ⌈#SOC of dim > 32 / 8⌉).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the array; every slot a call reads is written earlier
+ *     in the same call, so nothing carries over, but calls whose kernels overlap on the
+ *     GPU (different streams, or threads) race on it and must be serialised. */
+int qoco_gpu_cone_max_step_noalloc(const qoco_gpu_cones* cones, const double* u, const double* du,
+                                   double cap, double* alpha, void* stream);
 
 /* ---- host-only analysis (no GPU needed) ---------------------------------------- */
 

@@ -295,6 +295,13 @@ class Cones:
                                                     _tptr(scratch), _torch_stream(stream)), "max_step")
         return out
 
+    def max_step_noalloc(self, u, du, out, cap=float("inf"), stream=None):
+        """Allocation-free max step: writes the step into `out` (a 1-element float64 CUDA
+        tensor the caller owns) using the library's fixed device scratch; returns the C
+        status code instead of raising, so callers can see TOO_LARGE."""
+        return int(self.lib.qoco_gpu_cone_max_step_noalloc(self._h, _tptr(u), _tptr(du), float(cap),
+                                                           _tptr(out), _torch_stream(stream)))
+
     def close(self):
         if self._h:
             self.lib.qoco_gpu_cones_destroy(self._h)

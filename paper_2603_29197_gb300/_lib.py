@@ -16,11 +16,12 @@ LIB_PATH = os.path.join(HERE, "libqoco_gpu.so")
 SOLVED, SOLVED_INACCURATE, MAX_ITER = 0, 1, 2
 ERR_INVALID_DIMS, ERR_INVALID_CSC, ERR_INVALID_CONE, ERR_NONFINITE_DATA = -1, -2, -3, -4
 ERR_NUMERICAL, ERR_OOM, ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_NO_FACTOR = -5, -6, -7, -8, -9
-ERR_INVALID_ARG, ERR_NOT_IMPLEMENTED = -10, -11
+ERR_INVALID_ARG, ERR_NOT_IMPLEMENTED, ERR_TOO_LARGE = -10, -11, -12
 STATUS_NAMES = {
     0: "solved", 1: "solved_inaccurate", 2: "max_iter", -1: "invalid_dims", -2: "invalid_csc",
     -3: "invalid_cone", -4: "nonfinite_data", -5: "numerical", -6: "oom", -7: "cuda",
     -8: "device_timeout", -9: "no_factor", -10: "invalid_arg", -11: "not_implemented",
+    -12: "too_large",
 }
 ORDER_AUTO, ORDER_AMD, ORDER_ND, ORDER_NATURAL = 0, 1, 2, 3
 
@@ -103,6 +104,7 @@ SIGNATURES = {
     "qoco_gpu_cone_division": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "qoco_gpu_cone_max_step_scratch_bytes": (C.c_size_t, [_VP]),
     "qoco_gpu_cone_max_step": (C.c_int, [_VP, _VP, _VP, C.c_double, _VP, _VP, _VP]),
+    "qoco_gpu_cone_max_step_noalloc": (C.c_int, [_VP, _VP, _VP, C.c_double, _VP, _VP]),
     "qoco_gpu_analyze": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(CSC), C.POINTER(CSC),
                                    C.POINTER(CSC), C.c_int, C.c_int, _IP, C.POINTER(Settings),
                                    C.POINTER(Info), _IP, _IP, _IP, _IP]),

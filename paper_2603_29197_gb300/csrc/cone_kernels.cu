@@ -2,6 +2,10 @@
 // entry points of the C ABI.
 #include "cone_kernels.h"
 
+#include <mutex>
+
+#include "qoco_gpu.h"
+
 namespace qoco {
 
 // ---------------------------------------------------------------------------
@@ -301,5 +305,47 @@ void launch_div(const ConeView& c, const double* lam, const double* v, double* o
     if (g.blocks()) k_div<<<g.blocks(), kConeThreads, 0, st>>>(c, g, lam, v, out);
 }
 int cone_kernel_launches(const ConeView& c) { return cone_grid(c).blocks() ? 1 : 0; }
+
+// ---------------------------------------------------------------------------
+// Allocation-free max step.  Same kernels as launch_max_step; the block partials live
+// in this fixed device array instead of caller-provided scratch.  One array per device
+// (every GPU that loads the library holds it until the process exits), shared by every
+// call on that device: the kernels write every slot they later read, so nothing needs
+// clearing, but calls whose kernels overlap on the GPU race on it.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxPartials];
+
+namespace {
+std::mutex g_noalloc_mutex;
+constexpr int kNoAllocDevices = 64;
+double* g_noalloc_ptr[kNoAllocDevices] = {};
+}  // namespace
+
+// Device address of g_noalloc_partials on the current device, looked up once per device
+// (the array's name in host code is only a stand-in for it).
+static int noalloc_partials(double** out) {
+    int dev = 0;
+    QOCO_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocDevices) return QOCO_GPU_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        QOCO_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_partials));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return 0;
+}
+
+int launch_max_step_noalloc(const ConeView& c, const double* u, const double* du, double cap, double* out,
+                            cudaStream_t st) {
+    if (max_step_partials(c) > kNoAllocMaxPartials) return QOCO_GPU_ERR_TOO_LARGE;
+    double* partial = nullptr;
+    const int rc = noalloc_partials(&partial);
+    if (rc) return rc;
+    launch_max_step(c, u, du, nullptr, nullptr, cap, partial, out, st);
+    QOCO_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
 
 }  // namespace qoco

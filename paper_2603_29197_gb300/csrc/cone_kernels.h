@@ -23,6 +23,14 @@ void launch_shift_measure(const ConeView& c, const double* u1, const double* u2,
                           cudaStream_t st);
 void launch_shift_apply(const ConeView& c, double* u, const double* alpha, cudaStream_t st);
 void launch_prod(const ConeView& c, const double* u, const double* v, double* out, cudaStream_t st);
+
+// Block partials the allocation-free max step can hold (one per block of the cone grid:
+// ⌈l/256⌉ + ⌈#SOC ≤ 32/256⌉ + ⌈#SOC > 32/8⌉); 8192 doubles = 64 KiB per device.
+constexpr int kNoAllocMaxPartials = 8192;
+// Max step with the partials in a fixed device array (no allocation); returns 0 or a
+// QOCO_GPU_ERR_* code (TOO_LARGE when the cone grid needs more than kNoAllocMaxPartials).
+int launch_max_step_noalloc(const ConeView& c, const double* u, const double* du, double cap, double* out,
+                            cudaStream_t st);
 void launch_div(const ConeView& c, const double* lam, const double* v, double* out, cudaStream_t st);
 
 }  // namespace qoco

@@ -772,6 +772,12 @@ int qoco_gpu_get_factor_dense(const qoco_gpu_solver* S, int* perm, double* L, do
     return 0;
 }
 
+int qoco_gpu_cone_max_step_noalloc(const qoco_gpu_cones* C, const double* u, const double* du, double cap,
+                                   double* alpha, void* stream) {
+    if (!C || !alpha || (C->v.m && (!u || !du))) return QOCO_GPU_ERR_INVALID_ARG;
+    return launch_max_step_noalloc(C->v, u, du, cap, alpha, (cudaStream_t)stream);
+}
+
 int qoco_gpu_get_pivot_reciprocals(const qoco_gpu_solver* S, double* dinv) {
     if (!S || !dinv) return QOCO_GPU_ERR_INVALID_ARG;
     if (!S->have_factor) return QOCO_GPU_ERR_NO_FACTOR;
