@@ -206,6 +206,14 @@ int qoco_gpu_get_factor_dense(const qoco_gpu_solver* solver, int* perm, double* 
  * from the hardware's approximate reciprocal).  Errors: NO_FACTOR. */
 int qoco_gpu_get_pivot_reciprocals(const qoco_gpu_solver* solver, double* dinv);
 
+/* Failure-detection self-test of the grid barrier used by the persistent solve kernel
+ * (the paper has no counterpart): launches a small cooperative kernel in which one
+ * block never arrives, so every other block's wait runs out after max_spins polls
+ * (~64 ns each) and sets an error flag instead of hanging.  Returns
+ * QOCO_GPU_ERR_DEVICE_TIMEOUT when that happened (the expected outcome), 0 if the
+ * barrier completed, or a CUDA error.  Synchronous; the context stays usable. */
+int qoco_gpu_selftest_barrier_timeout(long long max_spins, void* stream);
+
 /* ---- stand-alone cone kernels (paper §2.1, §2.3) ---------------------------- */
 
 /* Creates a device descriptor of K = R^l_+ × Q^{q_0} × …; q host, nsoc entries ≥ 2. */

@@ -97,6 +97,7 @@ SIGNATURES = {
     "qoco_gpu_get_kkt": (C.c_int, [_VP, C.POINTER(C.c_int64), _IP, _DP]),
     "qoco_gpu_get_factor_dense": (C.c_int, [_VP, _IP, _DP, _DP]),
     "qoco_gpu_get_pivot_reciprocals": (C.c_int, [_VP, _DP]),
+    "qoco_gpu_selftest_barrier_timeout": (C.c_int, [C.c_longlong, _VP]),
     "qoco_gpu_cones_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, _IP]),
     "qoco_gpu_cones_destroy": (C.c_int, [_VP]),
     "qoco_gpu_cone_nt_scaling": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),

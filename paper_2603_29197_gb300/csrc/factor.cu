@@ -19,6 +19,8 @@
 // L (unit diagonal implied) with D on the diagonal.
 #include "factor.h"
 
+#include "qoco_gpu.h"
+
 namespace qoco {
 
 // Entry t of the column-major lower triangle (diagonal included) of an m×m block →
@@ -42,6 +44,99 @@ __device__ __forceinline__ void pivot(const FactorView& a, int col, double& d, d
     const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
     if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
     inv = recip(d);
+}
+
+
+// ---------------------------------------------------------------------------
+// Blocked right-looking partial LDLᵀ of the first c columns of the front F (order f,
+// column-major, lower triangle), shared by the warp (NT = 32, __syncwarp) and the CTA
+// (__syncthreads) kernels.  Panels of kPanel columns: each panel is factored column by
+// column (pivot and its reciprocal by thread 0, broadcast through bc[0]), its unscaled
+// columns are kept in W (W[i·kPanel + p] = d_p·l_ip), then the trailing lower triangle
+// is updated by one rank-kPanel pass F_ij −= Σ_p l_ip·W_jp whose entries are spread
+// over the threads with incrementally advanced (row, column) indices.
+// ---------------------------------------------------------------------------
+constexpr int kPanel = 4;
+
+template <bool WARP>
+__device__ __forceinline__ void group_sync() {
+    if constexpr (WARP) __syncwarp();
+    else __syncthreads();
+}
+
+// first entry t0 of the column-major lower triangle of an m×m block handled by a thread
+// and the advance by `stride` entries
+__device__ __forceinline__ void tri_advance(int m, int stride, int& ii, int& jj) {
+    ii += stride;
+    while (ii >= m && jj < m) {
+        ii = ii - m + jj + 1;
+        ++jj;
+    }
+}
+
+// bc: broadcast slot bc[0], then the pivot signs of the front's c columns (bc[1..c]),
+// loaded in one parallel pass so that no pivot waits on a global load
+template <bool WARP>
+__device__ __forceinline__ int blocked_ldlt(double* F, double* W, double* bc, int f, int c, int first,
+                                            const FactorView& a, int tid, int nt) {
+    int nreg = 0;
+    double* dinv = a.dinv + first;
+    double* sgn = bc + 1;
+    for (int k = tid; k < c; k += nt) sgn[k] = a.dsign[first + k] > 0 ? 1.0 : -1.0;
+    group_sync<WARP>();
+    for (int k0 = 0; k0 < c; k0 += kPanel) {
+        const int nb = min(kPanel, c - k0);
+        for (int p = 0; p < nb; ++p) {
+            const int k = k0 + p;
+            double* colk = F + (size_t)k * f;
+            if (tid == 0) {
+                double d = colk[k];
+                const bool pos = sgn[k] > 0.0;
+                const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
+                if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
+                const double inv = recip(d);
+                colk[k] = d;
+                dinv[k] = inv;
+                bc[0] = inv;
+            }
+            group_sync<WARP>();
+            const double inv = bc[0];
+            for (int i = k + 1 + tid; i < f; i += nt) {
+                const double v = colk[i];
+                W[i * kPanel + p] = v;
+                colk[i] = v * inv;
+            }
+            group_sync<WARP>();
+            // remaining columns of this panel
+            for (int j = k + 1; j < k0 + nb; ++j) {
+                const double wj = W[j * kPanel + p];
+                double* colj = F + (size_t)j * f;
+                for (int i = j + tid; i < f; i += nt) colj[i] -= colk[i] * wj;
+            }
+            group_sync<WARP>();
+        }
+        // trailing rank-nb update of rows/columns k0+nb .. f−1
+        const int base = k0 + nb, m = f - base;
+        if (m > 0) {
+            const double* L0 = F + (size_t)k0 * f;
+            int ii, jj;
+            tri_index(min(tid, m * (m + 1) / 2), m, ii, jj);
+            if (tid >= m * (m + 1) / 2) jj = m;
+            while (jj < m) {
+                const int i = base + ii, j = base + jj;
+                const double* wj = W + j * kPanel;
+                double acc = F[(size_t)j * f + i];
+                acc -= L0[i] * wj[0];
+                if (nb > 1) acc -= L0[f + i] * wj[1];
+                if (nb > 2) acc -= L0[2 * f + i] * wj[2];
+                if (nb > 3) acc -= L0[3 * f + i] * wj[3];
+                F[(size_t)j * f + i] = acc;
+                tri_advance(m, nt, ii, jj);
+            }
+        }
+        group_sync<WARP>();
+    }
+    return nreg;
 }
 
 // ---------------------------------------------------------------------------
@@ -89,17 +184,28 @@ __device__ __forceinline__ void thread_factor_front(int s, const FactorView& a, 
     if (nreg) atomicAdd(a.nreg, nreg);
 }
 
-__device__ __forceinline__ void thread_fwd_front(int s, const FactorView& a, const double* __restrict__ rhs,
-                                                 double* __restrict__ w) {
+// No dependency to wait for (level-synchronous callers).
+struct NoWait {
+    __device__ __forceinline__ bool operator()() const { return true; }
+};
+
+// The solve steps of one front are written as: loads that do not depend on other
+// fronts, then wait() (the dataflow kernel waits there for the fronts this one depends
+// on), then the dependent loads and the arithmetic.  Results of other fronts are read
+// through L2 (__ldcg): in the dataflow kernel they were written in the same launch.
+template <class Wait>
+__device__ __forceinline__ bool thread_fwd_front(int s, const FactorView& a, const double* __restrict__ rhs,
+                                                 double* __restrict__ w, const Wait& wait) {
     double v[kThreadFront];
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     for (int i = 0; i < f; ++i) v[i] = i < c ? rhs[a.perm[first + i]] : 0.0;
+    if (!wait()) return false;
     for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
         const int ch = a.child[k];
         const int r = a.nrow[ch] - a.ncol[ch];
         const int* rel = a.rel + a.upd_off[ch];
         const double* u = a.upd + a.upd_off[ch];
-        for (int i = 0; i < r; ++i) v[rel[i]] += u[i];
+        for (int i = 0; i < r; ++i) v[rel[i]] += __ldcg(u + i);
     }
     const double* L = a.front + a.front_off[s];
     for (int k = 0; k < c; ++k) {
@@ -109,14 +215,20 @@ __device__ __forceinline__ void thread_fwd_front(int s, const FactorView& a, con
     for (int i = 0; i < c; ++i) w[first + i] = v[i] * a.dinv[first + i];
     double* u = a.upd + a.upd_off[s];
     for (int i = c; i < f; ++i) u[i - c] = v[i];
+    return true;
 }
 
-__device__ __forceinline__ void thread_bwd_front(int s, const FactorView& a, const double* __restrict__ w,
-                                                 double* __restrict__ xp, double* __restrict__ x, int accumulate) {
+template <class Wait>
+__device__ __forceinline__ bool thread_bwd_front(int s, const FactorView& a, const double* __restrict__ w,
+                                                 double* __restrict__ xp, double* __restrict__ x, int accumulate,
+                                                 const Wait& wait) {
     double v[kThreadFront];
+    int R[kThreadFront];
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
-    const int* R = a.rows + a.row_ptr[s];
-    for (int i = 0; i < f; ++i) v[i] = i < c ? w[first + i] : xp[R[i]];
+    const int* Rg = a.rows + a.row_ptr[s];
+    for (int i = c; i < f; ++i) R[i] = Rg[i];
+    if (!wait()) return false;
+    for (int i = 0; i < f; ++i) v[i] = __ldcg(i < c ? w + first + i : xp + R[i]);
     const double* L = a.front + a.front_off[s];
     for (int k = c - 1; k >= 0; --k) {
         double acc = v[k];
@@ -128,6 +240,7 @@ __device__ __forceinline__ void thread_bwd_front(int s, const FactorView& a, con
         if (accumulate) x[a.perm[first + i]] += v[i];
         else x[a.perm[first + i]] = v[i];
     }
+    return true;
 }
 
 __global__ void __launch_bounds__(128) k_thread_factor(const int* __restrict__ list, int n, FactorView a,
@@ -138,13 +251,13 @@ __global__ void __launch_bounds__(128) k_thread_factor(const int* __restrict__ l
 __global__ void __launch_bounds__(128) k_thread_fwd(const int* __restrict__ list, int n, FactorView a,
                                                     const double* __restrict__ rhs, double* __restrict__ w) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) thread_fwd_front(list[t], a, rhs, w);
+    if (t < n) thread_fwd_front(list[t], a, rhs, w, NoWait());
 }
 __global__ void __launch_bounds__(128) k_thread_bwd(const int* __restrict__ list, int n, FactorView a,
                                                     const double* __restrict__ w, double* __restrict__ xp,
                                                     double* __restrict__ x, int accumulate) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) thread_bwd_front(list[t], a, w, xp, x, accumulate);
+    if (t < n) thread_bwd_front(list[t], a, w, xp, x, accumulate, NoWait());
 }
 
 
@@ -158,8 +271,7 @@ __global__ void __launch_bounds__(256) k_front_factor(const int* __restrict__ li
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     double* G = a.front + a.front_off[s];
     double* F = SMEM ? smem : G;
-    double* lk = SMEM ? smem + (size_t)f * f : smem;
-    double* bc = lk + f;  // [0] = 1/d of the current column
+    double* lk = SMEM ? smem + (size_t)f * f : smem;  // W panel (kPanel·f) then the broadcast slot
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t ff = (int64_t)f * f;
 
@@ -186,33 +298,7 @@ __global__ void __launch_bounds__(256) k_front_factor(const int* __restrict__ li
         }
         __syncthreads();
     }
-    int nreg = 0;
-    double* dinv = a.dinv + first;
-    for (int k = 0; k < c; ++k) {
-        double* colk = F + (int64_t)k * f;
-        if (tid == 0) {
-            double d = colk[k], inv;
-            pivot(a, first + k, d, inv, nreg);
-            colk[k] = d;
-            dinv[k] = inv;
-            bc[0] = inv;
-        }
-        __syncthreads();
-        const double inv = bc[0];
-        const int m = f - k - 1;
-        for (int i = k + 1 + tid; i < f; i += nt) lk[i] = colk[i] * inv;
-        __syncthreads();
-        const int T = m * (m + 1) / 2;
-        for (int t = tid; t < T; t += nt) {
-            int ii, jj;
-            tri_index(t, m, ii, jj);
-            const int i = k + 1 + ii, j = k + 1 + jj;
-            F[(int64_t)j * f + i] -= lk[i] * colk[j];
-        }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < f; i += nt) colk[i] = lk[i];
-        __syncthreads();
-    }
+    const int nreg = blocked_ldlt<false>(F, lk, lk + (size_t)kPanel * f, f, c, first, a, tid, nt);
     if (tid == 0 && nreg) atomicAdd(a.nreg, nreg);
     if (SMEM)
         for (int64_t i = tid; i < ff; i += nt) G[i] = F[i];
@@ -293,6 +379,10 @@ __global__ void __launch_bounds__(128) k_bwd(const int* __restrict__ list, Facto
     }
 }
 
+// per-warp shared memory of the warp factor kernels: front (fmax²), W panel (kPanel·fmax)
+// and the broadcast slot
+__host__ __device__ constexpr int wfactor_stride(int fmax) { return fmax * (fmax + kPanel) + 1 + fmax; }
+
 // ---------------------------------------------------------------------------
 // warp-level variants for fronts of order ≤ kWarpFront (one warp per front, the front
 // in the warp's slice of shared memory, __syncwarp instead of block barriers)
@@ -339,33 +429,7 @@ __device__ __forceinline__ void warp_factor_front(int s, const FactorView& a, co
         }
         __syncwarp();
     }
-    // right-looking partial LDLᵀ of the first c columns
-    int nreg = 0;
-    double* dinv = a.dinv + first;
-    for (int k = 0; k < c; ++k) {
-        double* colk = F + k * f;
-        double d = 0.0, inv = 0.0;
-        if (lane == 0) {
-            d = colk[k];
-            pivot(a, first + k, d, inv, nreg);
-            colk[k] = d;
-            dinv[k] = inv;
-        }
-        inv = __shfl_sync(0xffffffffu, inv, 0);
-        const int m = f - k - 1;
-        for (int i = k + 1 + lane; i < f; i += 32) lk[i] = colk[i] * inv;
-        __syncwarp();
-        const int T = m * (m + 1) / 2;
-        for (int t = lane; t < T; t += 32) {
-            int ii, jj;
-            tri_index(t, m, ii, jj);
-            const int i = k + 1 + ii, j = k + 1 + jj;
-            F[j * f + i] -= lk[i] * colk[j];
-        }
-        __syncwarp();
-        for (int i = k + 1 + lane; i < f; i += 32) colk[i] = lk[i];
-        __syncwarp();
-    }
+    const int nreg = blocked_ldlt<true>(F, lk, lk + kPanel * f, f, c, first, a, lane, 32);
     double* G = a.front + a.front_off[s];
     for (int i = lane; i < ff; i += 32) G[i] = F[i];
     if (lane == 0 && nreg) atomicAdd(a.nreg, nreg);
@@ -382,18 +446,21 @@ __device__ __forceinline__ void warp_load_panel(const double* __restrict__ L, in
     for (; i < n; i += 32) P[i] = L[i];
 }
 
-__device__ __forceinline__ void warp_fwd_front(int s, const FactorView& a, const double* __restrict__ rhs,
-                                               double* __restrict__ w, double* v, double* P, int lane) {
+template <class Wait>
+__device__ __forceinline__ bool warp_fwd_front(int s, const FactorView& a, const double* __restrict__ rhs,
+                                               double* __restrict__ w, double* v, double* P, int lane,
+                                               const Wait& wait) {
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     warp_load_panel(a.front + a.front_off[s], f * c, P, lane);
     for (int i = lane; i < f; i += 32) v[i] = i < c ? rhs[a.perm[first + i]] : 0.0;
     __syncwarp();
+    if (!wait()) return false;
     for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
         const int ch = a.child[k];
         const int r = a.nrow[ch] - a.ncol[ch];
         const int* rel = a.rel + a.upd_off[ch];
         const double* u = a.upd + a.upd_off[ch];
-        for (int i = lane; i < r; i += 32) v[rel[i]] += u[i];
+        for (int i = lane; i < r; i += 32) v[rel[i]] += __ldcg(u + i);
         __syncwarp();
     }
     for (int k = 0; k < c; ++k) {
@@ -407,17 +474,22 @@ __device__ __forceinline__ void warp_fwd_front(int s, const FactorView& a, const
     double* u = a.upd + a.upd_off[s];
     for (int i = c + lane; i < f; i += 32) u[i - c] = v[i];
     __syncwarp();
+    return true;
 }
 
 // Column-oriented backward solve: each known x_i (i ≥ c first, then i = c−1 … 1) is
 // subtracted from the own-column entries v_k, k < i, one lane per k (no reductions).
-__device__ __forceinline__ void warp_bwd_front(int s, const FactorView& a, const double* __restrict__ w,
+template <class Wait>
+__device__ __forceinline__ bool warp_bwd_front(int s, const FactorView& a, const double* __restrict__ w,
                                                double* __restrict__ xp, double* __restrict__ x, int accumulate,
-                                               double* v, double* P, int lane) {
+                                               double* v, double* P, int lane, const Wait& wait) {
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     const int* R = a.rows + a.row_ptr[s];
     warp_load_panel(a.front + a.front_off[s], f * c, P, lane);
-    for (int i = lane; i < f; i += 32) v[i] = i < c ? w[first + i] : xp[R[i]];
+    const int r0 = lane < f ? R[lane] : 0, r1 = lane + 32 < f ? R[lane + 32] : 0;  // f ≤ 64
+    if (!wait()) return false;
+    if (lane < f) v[lane] = __ldcg(lane < c ? w + first + lane : xp + r0);
+    if (lane + 32 < f) v[lane + 32] = __ldcg(lane + 32 < c ? w + first + lane + 32 : xp + r1);
     __syncwarp();
     for (int i = c; i < f; ++i) {
         const double xi = v[i];
@@ -436,6 +508,7 @@ __device__ __forceinline__ void warp_bwd_front(int s, const FactorView& a, const
         else x[a.perm[first + i]] = xi;
     }
     __syncwarp();
+    return true;
 }
 
 // one warp per subtree task (children before parents)
@@ -446,7 +519,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_factor(const int* 
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * kWarpsPerBlock + wid;
     if (t >= ntask) return;
-    double* F = smem + (size_t)wid * fmax * (fmax + 1);
+    double* F = smem + (size_t)wid * wfactor_stride(fmax);
     const int lo = task[2 * t], hi = task[2 * t + 1];
     for (int s = lo; s <= hi; ++s) warp_factor_front(s, a, kval, F, F + fmax * fmax, lane);
 }
@@ -459,7 +532,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_fwd(const int* __r
     if (t >= ntask) return;
     double* v = smem + (size_t)wid * fmax * (fmax + 1);
     const int lo = task[2 * t], hi = task[2 * t + 1];
-    for (int s = lo; s <= hi; ++s) warp_fwd_front(s, a, rhs, w, v, v + fmax, lane);
+    for (int s = lo; s <= hi; ++s) warp_fwd_front(s, a, rhs, w, v, v + fmax, lane, NoWait());
 }
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_bwd(const int* __restrict__ task, int ntask,
                                                                  FactorView a, const double* __restrict__ w,
@@ -471,7 +544,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_bwd(const int* __r
     if (t >= ntask) return;
     double* v = smem + (size_t)wid * fmax * (fmax + 1);
     const int lo = task[2 * t], hi = task[2 * t + 1];
-    for (int s = hi; s >= lo; --s) warp_bwd_front(s, a, w, xp, x, accumulate, v, v + fmax, lane);
+    for (int s = hi; s >= lo; --s) warp_bwd_front(s, a, w, xp, x, accumulate, v, v + fmax, lane, NoWait());
 }
 // one warp per listed supernode of a level
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_factor(const int* __restrict__ list, int n,
@@ -481,7 +554,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_factor(const int* 
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * kWarpsPerBlock + wid;
     if (t >= n) return;
-    double* F = smem + (size_t)wid * fmax * (fmax + 1);
+    double* F = smem + (size_t)wid * wfactor_stride(fmax);
     warp_factor_front(list[t], a, kval, F, F + fmax * fmax, lane);
 }
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_fwd(const int* __restrict__ list, int n,
@@ -492,7 +565,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_fwd(const int* __r
     const int t = blockIdx.x * kWarpsPerBlock + wid;
     if (t >= n) return;
     double* v = smem + (size_t)wid * fmax * (fmax + 1);
-    warp_fwd_front(list[t], a, rhs, w, v, v + fmax, lane);
+    warp_fwd_front(list[t], a, rhs, w, v, v + fmax, lane, NoWait());
 }
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_bwd(const int* __restrict__ list, int n,
                                                                  FactorView a, const double* __restrict__ w,
@@ -503,19 +576,257 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_bwd(const int* __r
     const int t = blockIdx.x * kWarpsPerBlock + wid;
     if (t >= n) return;
     double* v = smem + (size_t)wid * fmax * (fmax + 1);
-    warp_bwd_front(list[t], a, w, xp, x, accumulate, v, v + fmax, lane);
+    warp_bwd_front(list[t], a, w, xp, x, accumulate, v, v + fmax, lane, NoWait());
+}
+
+// ---------------------------------------------------------------------------
+// Persistent level-synchronous solve: one cooperative launch walks the levels of the
+// tree (forward, then backward), each level's thread fronts spread over all threads
+// of the grid and its warp fronts over all warps, with a bounded grid barrier between
+// levels instead of a kernel launch.
+// ---------------------------------------------------------------------------
+constexpr int kPersistentThreads = 256;
+
+__global__ void __launch_bounds__(kPersistentThreads) k_solve_persistent(
+    const LevelPlan* __restrict__ lv, int nlev, const int* __restrict__ tlist, const int* __restrict__ wlist,
+    FactorView a, const double* __restrict__ rhs, double* __restrict__ w, double* __restrict__ xp,
+    double* __restrict__ x, int accumulate, int fmax, GridBarrier bar) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double* v = smem + (size_t)wid * fmax * (fmax + 1);
+    double* P = v + fmax;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const int gw = blockIdx.x * nw + wid, ngw = gridDim.x * nw;
+    for (int l = 0; l < nlev; ++l) {
+        const LevelPlan L = lv[l];
+        for (int t = gt; t < L.n_sthread; t += nt) thread_fwd_front(tlist[L.off_sthread + t], a, rhs, w, NoWait());
+        for (int t = gw; t < L.n_swarp; t += ngw)
+            warp_fwd_front(wlist[L.off_swarp + t], a, rhs, w, v, P, lane, NoWait());
+        if (!grid_sync(bar)) return;
+    }
+    for (int l = nlev - 1; l >= 0; --l) {
+        const LevelPlan L = lv[l];
+        for (int t = gt; t < L.n_sthread; t += nt)
+            thread_bwd_front(tlist[L.off_sthread + t], a, w, xp, x, accumulate, NoWait());
+        for (int t = gw; t < L.n_swarp; t += ngw)
+            warp_bwd_front(wlist[L.off_swarp + t], a, w, xp, x, accumulate, v, P, lane, NoWait());
+        if (l > 0 && !grid_sync(bar)) return;
+    }
+}
+
+// Self-test of the barrier's timeout path: block 0 leaves without arriving (the wait
+// of every other block is on an arrival that never comes), so the others give up after
+// max_spins polls and set the error flag.
+__global__ void k_barrier_timeout_probe(GridBarrier bar) {
+    if (blockIdx.x == 0) return;
+    grid_sync(bar);
+}
+
+int selftest_barrier_timeout(long long max_spins, cudaStream_t st) {
+    unsigned int* buf = nullptr;
+    QOCO_CUDA_TRY(cudaMalloc((void**)&buf, 4 * sizeof(unsigned int)));
+    int rc = 0;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 4 * sizeof(unsigned int), st);
+    GridBarrier b;
+    b.count = buf;
+    b.gen = buf + 1;
+    b.err = (int*)(buf + 2);
+    b.max_spins = max_spins;
+    if (e == cudaSuccess) {
+        void* args[] = {(void*)&b};
+        e = cudaLaunchCooperativeKernel((const void*)k_barrier_timeout_probe, dim3(4), dim3(32), args, 0, st);
+    }
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, buf + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "barrier self-test", __FILE__, __LINE__);
+    else rc = err ? QOCO_GPU_ERR_DEVICE_TIMEOUT : 0;
+    cudaFree(buf);
+    return rc;
+}
+
+static size_t persistent_smem(int fmax) {
+    return (size_t)(kPersistentThreads / 32) * fmax * (fmax + 1) * sizeof(double);
+}
+
+int plan_persistent_solve(FactorPlan& P, int max_warp_f, bool any_cta_front) {
+    P.persistent = false;
+    if (any_cta_front || P.ntasks || P.levels.empty()) return 0;
+    const int fmax = max(1, max_warp_f);
+    const size_t sm = persistent_smem(fmax);
+    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int dev = 0, nsm = 0, coop = 0, occ = 0;
+    QOCO_CUDA_TRY(cudaGetDevice(&dev));
+    QOCO_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    QOCO_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    QOCO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent, kPersistentThreads, sm));
+    if (!coop || occ < 1) return 0;
+    P.persistent = true;
+    P.persistent_grid = nsm * occ;
+    P.persistent_fmax = fmax;
+    return 0;
+}
+
+int launch_solve_persistent(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
+                            double* x, bool accumulate, const GridBarrier& bar, cudaStream_t st) {
+    const LevelPlan* lv = P.d_levels;
+    int nlev = (int)P.levels.size();
+    const int* tl = P.d_sthread;
+    const int* wl = P.d_swarp;
+    FactorView av = a;
+    const double* r = rhs;
+    double *ww = w, *xx = xp, *x0 = x;
+    int acc = accumulate ? 1 : 0, fm = P.persistent_fmax;
+    GridBarrier b = bar;
+    void* args[] = {(void*)&lv, (void*)&nlev, (void*)&tl, (void*)&wl, (void*)&av, (void*)&r, (void*)&ww,
+                    (void*)&xx, (void*)&x0, (void*)&acc, (void*)&fm, (void*)&b};
+    QOCO_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_persistent, dim3(P.persistent_grid),
+                                              dim3(kPersistentThreads), args, persistent_smem(fm), st));
+    return 1;
+}
+
+// ---------------------------------------------------------------------------
+// Dataflow solve: one launch, no barriers.  Work items (warp fronts and batches of 32
+// one-thread fronts) are handed out by an atomic counter: first the forward items in
+// level order, then the backward items in reverse order.  A forward item waits until
+// its fronts' children have finished their forward step; a backward item waits for
+// its parent's backward step (a root for its own forward step).  Since every item
+// only waits on items handed out before it, which are owned by running warps, the
+// scheme cannot deadlock and needs no co-residency.  Flags hold the launch's epoch
+// (no reset between launches); producers fence before raising a flag, consumers fence
+// after seeing it and read the produced data through L2 (__ldcg).  Every wait polls a
+// bounded number of times, then raises the error flag; all warps then leave.
+// ---------------------------------------------------------------------------
+constexpr int kDataflowThreads = 128;
+
+__device__ __forceinline__ bool wait_epoch(const int* flag, int epoch, int* err, long long max_spins) {
+    const volatile int* vf = flag;
+    const volatile int* ve = err;
+    long long spins = 0;
+    while (*vf != epoch) {
+        if (*ve) return false;
+        if (++spins > max_spins) {
+            atomicExch(err, 1);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kDataflowThreads) k_solve_dataflow(
+    const int* __restrict__ items, int nitems, const int* __restrict__ tb_ptr, const int* __restrict__ sthread,
+    FactorView a, const double* __restrict__ rhs, double* w, double* xp, double* x, int accumulate, int fmax,
+    int* fdone, int* bdone, DataflowState ds) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* v = smem + (size_t)wid * fmax * (fmax + 1);
+    double* P = v + fmax;
+    for (;;) {
+        int it = 0, stop = 0;
+        if (lane == 0) {
+            it = (int)atomicAdd(ds.next, 1u);
+            stop = *(volatile int*)ds.err;
+        }
+        it = __shfl_sync(0xffffffffu, it, 0);
+        stop = __shfl_sync(0xffffffffu, stop, 0);
+        if (stop || it >= 2 * nitems) return;
+        const bool fwd = it < nitems;
+        const int item = fwd ? items[it] : items[2 * nitems - 1 - it];
+        int* done = fwd ? fdone : bdone;
+        if (item >= 0) {
+            const int s = item;
+            // warp-wide wait: lanes share the children (forward) or lane 0 waits for the
+            // parent (backward); every lane then fences before the dependent loads
+            auto wait = [&]() {
+                bool ok = true;
+                if (fwd) {
+                    for (int k = a.child_ptr[s] + lane; k < a.child_ptr[s + 1]; k += 32)
+                        ok = ok && wait_epoch(fdone + a.child[k], ds.epoch, ds.err, ds.max_spins);
+                } else if (lane == 0) {
+                    const int p = a.parent[s];
+                    ok = wait_epoch(p >= 0 ? bdone + p : fdone + s, ds.epoch, ds.err, ds.max_spins);
+                }
+                ok = __all_sync(0xffffffffu, ok);
+                __threadfence();
+                return ok;
+            };
+            const bool ok = fwd ? warp_fwd_front(s, a, rhs, w, v, P, lane, wait)
+                                : warp_bwd_front(s, a, w, xp, x, accumulate, v, P, lane, wait);
+            if (!ok) return;
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicExch(done + s, ds.epoch);
+        } else {
+            const int b = -item - 1;
+            const int t = tb_ptr[b] + lane;
+            bool ok = true;
+            if (t < tb_ptr[b + 1]) {
+                const int s = sthread[t];
+                auto wait = [&]() {
+                    bool good = true;
+                    if (fwd) {
+                        for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1] && good; ++k)
+                            good = wait_epoch(fdone + a.child[k], ds.epoch, ds.err, ds.max_spins);
+                    } else {
+                        const int p = a.parent[s];
+                        good = wait_epoch(p >= 0 ? bdone + p : fdone + s, ds.epoch, ds.err, ds.max_spins);
+                    }
+                    __threadfence();
+                    return good;
+                };
+                ok = fwd ? thread_fwd_front(s, a, rhs, w, wait) : thread_bwd_front(s, a, w, xp, x, accumulate, wait);
+                if (ok) {
+                    __threadfence();
+                    atomicExch(done + s, ds.epoch);
+                }
+            }
+            if (!__all_sync(0xffffffffu, ok)) return;
+        }
+    }
+}
+
+static size_t dataflow_smem(int fmax) {
+    return (size_t)(kDataflowThreads / 32) * fmax * (fmax + 1) * sizeof(double);
+}
+
+int plan_dataflow_solve(FactorPlan& P, int max_warp_f, bool any_cta_front) {
+    P.dataflow = false;
+    if (any_cta_front || P.ntasks || P.nitems == 0) return 0;
+    const int fmax = max(1, max_warp_f);
+    const size_t sm = dataflow_smem(fmax);
+    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_solve_dataflow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int dev = 0, nsm = 0, occ = 0;
+    QOCO_CUDA_TRY(cudaGetDevice(&dev));
+    QOCO_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    QOCO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_dataflow, kDataflowThreads, sm));
+    if (occ < 1) return 0;
+    P.dataflow = true;
+    P.dataflow_grid = nsm * occ;
+    P.dataflow_fmax = fmax;
+    return 0;
+}
+
+int launch_solve_dataflow(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
+                          double* x, bool accumulate, const DataflowState& ds, cudaStream_t st) {
+    QOCO_CUDA_TRY(cudaMemsetAsync(ds.next, 0, sizeof(unsigned int), st));
+    k_solve_dataflow<<<P.dataflow_grid, kDataflowThreads, dataflow_smem(P.dataflow_fmax), st>>>(
+        P.d_items, P.nitems, P.d_tb_ptr, P.d_sthread, a, rhs, w, xp, x, accumulate ? 1 : 0, P.dataflow_fmax,
+        P.d_fdone, P.d_bdone, ds);
+    return 1;
 }
 
 // ---- launchers ----------------------------------------------------------------
 static int wblocks(int n) { return (n + kWarpsPerBlock - 1) / kWarpsPerBlock; }
 // per warp: the front vector (fmax) and the panel (≤ fmax·fmax)
 static size_t wsolve_smem(int fmax) { return (size_t)kWarpsPerBlock * fmax * (fmax + 1) * sizeof(double); }
+static size_t wfactor_smem(int fmax) { return (size_t)kWarpsPerBlock * wfactor_stride(fmax) * sizeof(double); }
 
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st) {
     int launches = 0;
     if (P.ntasks) {
         const int fm = P.task_max_f;
-        k_task_factor<<<wblocks(P.ntasks), kWarpsPerBlock * 32, wsolve_smem(fm), st>>>(
+        k_task_factor<<<wblocks(P.ntasks), kWarpsPerBlock * 32, wfactor_smem(fm), st>>>(
             P.d_task, P.ntasks, a, kval, fm);
         ++launches;
     }
@@ -527,18 +838,18 @@ int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, 
         }
         if (L.n_warp) {
             const int fm = L.max_warp_f;
-            k_warp_factor<<<wblocks(L.n_warp), kWarpsPerBlock * 32, wsolve_smem(fm), st>>>(
+            k_warp_factor<<<wblocks(L.n_warp), kWarpsPerBlock * 32, wfactor_smem(fm), st>>>(
                 P.d_warp + L.off_warp, L.n_warp, a, kval, fm);
             ++launches;
         }
         if (L.n_small) {
-            const size_t sm = ((size_t)L.max_small * (L.max_small + 1) + 1) * sizeof(double);
+            const size_t sm = ((size_t)L.max_small * (L.max_small + kPanel + 1) + 1) * sizeof(double);
             const int threads = L.max_small <= 64 ? 128 : 256;
             k_front_factor<true><<<L.n_small, threads, sm, st>>>(P.d_small + L.off_small, a, kval);
             ++launches;
         }
         if (L.n_large) {
-            const size_t sm = ((size_t)L.max_cta_f + 1) * sizeof(double);
+            const size_t sm = ((size_t)(kPanel + 1) * L.max_large_f + 1) * sizeof(double);
             k_front_factor<false><<<L.n_large, 256, sm, st>>>(P.d_large + L.off_large, a, kval);
             ++launches;
         }
@@ -558,13 +869,14 @@ int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, do
     }
     for (int lv = 0; lv < nl; ++lv) {
         const LevelPlan& L = P.levels[lv];
-        if (L.n_thread) {
-            k_thread_fwd<<<(L.n_thread + 127) / 128, 128, 0, st>>>(P.d_thread + L.off_thread, L.n_thread, a, rhs, w);
+        if (L.n_sthread) {
+            k_thread_fwd<<<(L.n_sthread + 127) / 128, 128, 0, st>>>(P.d_sthread + L.off_sthread, L.n_sthread, a,
+                                                                   rhs, w);
             ++launches;
         }
-        if (L.n_warp) {
-            k_warp_fwd<<<wblocks(L.n_warp), kWarpsPerBlock * 32, wsolve_smem(L.max_warp_f), st>>>(
-                P.d_warp + L.off_warp, L.n_warp, a, rhs, w, L.max_warp_f);
+        if (L.n_swarp) {
+            k_warp_fwd<<<wblocks(L.n_swarp), kWarpsPerBlock * 32, wsolve_smem(L.max_swarp_f), st>>>(
+                P.d_swarp + L.off_swarp, L.n_swarp, a, rhs, w, L.max_swarp_f);
             ++launches;
         }
         if (L.n_cta) {
@@ -574,14 +886,14 @@ int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, do
     }
     for (int lv = nl - 1; lv >= 0; --lv) {
         const LevelPlan& L = P.levels[lv];
-        if (L.n_thread) {
-            k_thread_bwd<<<(L.n_thread + 127) / 128, 128, 0, st>>>(P.d_thread + L.off_thread, L.n_thread, a, w, xp, x,
-                                                                  acc);
+        if (L.n_sthread) {
+            k_thread_bwd<<<(L.n_sthread + 127) / 128, 128, 0, st>>>(P.d_sthread + L.off_sthread, L.n_sthread, a, w,
+                                                                   xp, x, acc);
             ++launches;
         }
-        if (L.n_warp) {
-            k_warp_bwd<<<wblocks(L.n_warp), kWarpsPerBlock * 32, wsolve_smem(L.max_warp_f), st>>>(
-                P.d_warp + L.off_warp, L.n_warp, a, w, xp, x, acc, L.max_warp_f);
+        if (L.n_swarp) {
+            k_warp_bwd<<<wblocks(L.n_swarp), kWarpsPerBlock * 32, wsolve_smem(L.max_swarp_f), st>>>(
+                P.d_swarp + L.off_swarp, L.n_swarp, a, w, xp, x, acc, L.max_swarp_f);
             ++launches;
         }
         if (L.n_cta) {
@@ -598,11 +910,11 @@ int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, do
 }
 
 int factor_set_attributes() {
-    const int warp_smem = kWarpsPerBlock * kWarpFront * (kWarpFront + 1) * (int)sizeof(double);
+    const int warp_smem = (int)wfactor_smem(kWarpFront);
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_front_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (kSmemFront * (kSmemFront + 1) + 1) * (int)sizeof(double)));
+                                       (kSmemFront * (kSmemFront + kPanel + 1) + 1) * (int)sizeof(double)));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_front_factor<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (kMaxSolveFront + 1) * (int)sizeof(double)));
+                                       ((kPanel + 1) * kMaxFactorFront + 1) * (int)sizeof(double)));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_task_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_warp_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem));
     const int wsolve = kWarpsPerBlock * kWarpFront * (kWarpFront + 1) * (int)sizeof(double);

@@ -25,6 +25,7 @@ struct FactorView {
     const int* amap_off = nullptr;
     const signed char* dsign = nullptr;
     const int* perm = nullptr;       // new → original
+    const int* parent = nullptr;     // supernodal tree parent (−1 for roots)
     double* front = nullptr;         // Σ f_s² doubles
     double* upd = nullptr;           // Σ r_s doubles (solve update vectors)
     double* dinv = nullptr;          // N: reciprocal pivots 1/d_j (permuted order)
@@ -41,9 +42,42 @@ struct FactorPlan {
     int* d_small = nullptr;
     int* d_large = nullptr;
     int* d_cta = nullptr;
+    int* d_sthread = nullptr;
+    int* d_swarp = nullptr;
+    // persistent level-synchronous solve (used when every front is a thread or warp front)
+    LevelPlan* d_levels = nullptr;
+    bool persistent = false;
+    int persistent_grid = 0, persistent_fmax = 0;
+    // dataflow solve (items in topological order, see PlanHost)
+    bool dataflow = false;
+    int nitems = 0, dataflow_grid = 0, dataflow_fmax = 0;
+    int* d_items = nullptr;
+    int* d_tb_ptr = nullptr;
+    int* d_fdone = nullptr;  // per supernode: epoch of its finished forward step
+    int* d_bdone = nullptr;  // per supernode: epoch of its finished backward step
+};
+
+// Shared state of one dataflow solve launch.
+struct DataflowState {
+    unsigned int* next;  // work-item counter (zeroed before each launch)
+    int* err;            // set when a dependency wait ran out of polls
+    int epoch;           // flag value that marks "done in this launch"
+    long long max_spins;
 };
 
 int factor_set_attributes();
+// Decides whether the persistent solve applies and sizes its cooperative grid.
+int plan_persistent_solve(FactorPlan& P, int max_warp_f, bool any_cta_front);
+// Launches a 4-block cooperative kernel whose block 0 never reaches the barrier; returns
+// QOCO_GPU_ERR_DEVICE_TIMEOUT when the other blocks' bounded waits ran out as designed.
+int selftest_barrier_timeout(long long max_spins, cudaStream_t st);
+int plan_dataflow_solve(FactorPlan& P, int max_warp_f, bool any_cta_front);
+int launch_solve_dataflow(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
+                          double* x, bool accumulate, const DataflowState& ds, cudaStream_t st);
+// One cooperative launch for the forward, diagonal and backward solves.
+int launch_solve_persistent(const FactorPlan& P, const FactorView& a, const double* rhs, double* w,
+                            double* xp, double* x, bool accumulate, const GridBarrier& bar,
+                            cudaStream_t st);
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
 int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
                  double* x, bool accumulate, cudaStream_t st);

@@ -68,40 +68,70 @@ void build_plan(const Symbolic& S, bool allow_tasks, int target_tasks, PlanHost*
         if (!in_task[s]) byl[lev[s]].push_back(s);
     for (int l = 0; l < S.n_levels; ++l) {
         LevelPlan& L = P->levels[l];
-        // one-thread fronts sorted by decreasing order so that a warp's lanes run
-        // similar trip counts
+        // fronts sorted by decreasing order so that the lanes of a one-thread-per-front
+        // warp run similar trip counts
         std::stable_sort(byl[l].begin(), byl[l].end(), [&](int x, int y) { return f[x] > f[y]; });
         L.off_thread = (int)P->thread.size();
         L.off_warp = (int)P->warp.size();
         L.off_small = (int)P->small.size();
         L.off_large = (int)P->large.size();
+        L.off_sthread = (int)P->sthread.size();
+        L.off_swarp = (int)P->swarp.size();
         L.off_cta = (int)P->cta.size();
+        // A level with few fronts cannot fill the GPU with one warp per front, and each
+        // warp would walk its front's long dependent FP64 chain alone: in the
+        // factorisation such levels get a CTA per front (its threads split every
+        // update).  Wide levels keep one warp (or one thread) per front for throughput.
+        int nmid = 0;
+        for (int s : byl[l]) nmid += f[s] > kThreadFront;
+        const bool wide = nmid >= kWideLevel;
         for (int s : byl[l]) {
-            if (f[s] <= kThreadFront) {
+            if (f[s] <= kThreadFront && (wide || nmid == 0)) {
                 P->thread.push_back(s);
-            } else if (f[s] <= kWarpFront) {
+            } else if (f[s] <= kWarpFront && wide) {
                 P->warp.push_back(s);
                 L.max_warp_f = std::max(L.max_warp_f, f[s]);
+            } else if (f[s] <= kSmemFront) {
+                P->small.push_back(s);
+                L.max_small = std::max(L.max_small, f[s]);
+            } else {
+                P->large.push_back(s);
+                L.max_large_f = std::max(L.max_large_f, f[s]);
+            }
+            if (f[s] <= kThreadFront) {
+                P->sthread.push_back(s);
+            } else if (f[s] <= kWarpFront) {
+                P->swarp.push_back(s);
+                L.max_swarp_f = std::max(L.max_swarp_f, f[s]);
             } else {
                 P->cta.push_back(s);
                 L.max_cta_f = std::max(L.max_cta_f, f[s]);
-                if (f[s] <= kSmemFront) {
-                    P->small.push_back(s);
-                    L.max_small = std::max(L.max_small, f[s]);
-                } else {
-                    P->large.push_back(s);
-                }
             }
         }
         L.n_thread = (int)P->thread.size() - L.off_thread;
         L.n_warp = (int)P->warp.size() - L.off_warp;
         L.n_small = (int)P->small.size() - L.off_small;
         L.n_large = (int)P->large.size() - L.off_large;
+        L.n_sthread = (int)P->sthread.size() - L.off_sthread;
+        L.n_swarp = (int)P->swarp.size() - L.off_swarp;
         L.n_cta = (int)P->cta.size() - L.off_cta;
+    }
+    // dataflow items, level by level: batches of 32 one-thread fronts, then warp fronts.
+    // The one-thread fronts of consecutive levels are contiguous in sthread, so batch b
+    // covers sthread[tb_ptr[b] .. tb_ptr[b+1]).
+    P->tb_ptr.assign(1, 0);
+    for (int l = 0; l < (int)P->levels.size(); ++l) {
+        const LevelPlan& L = P->levels[l];
+        for (int t = 0; t < L.n_sthread; t += 32) {
+            const int b = (int)P->tb_ptr.size() - 1;  // its start tb_ptr[b] = off_sthread + t
+            P->tb_ptr.push_back(L.off_sthread + std::min(t + 32, L.n_sthread));
+            P->items.push_back(-(b + 1));
+        }
+        for (int t = 0; t < L.n_swarp; ++t) P->items.push_back(P->swarp[L.off_swarp + t]);
     }
     // drop empty trailing levels
     while (!P->levels.empty() &&
-           P->levels.back().n_thread + P->levels.back().n_warp + P->levels.back().n_cta == 0)
+           P->levels.back().n_sthread + P->levels.back().n_swarp + P->levels.back().n_cta == 0)
         P->levels.pop_back();
 }
 

@@ -9,9 +9,11 @@ namespace qoco {
 
 constexpr int kSmemFront = 160;       // fronts up to this order are factored in shared memory
 constexpr int kMaxSolveFront = 26000; // solve kernels keep one front vector in shared memory
+constexpr int kMaxFactorFront = 5600;  // CTA factor keeps a 4-column panel + signs in shared memory
 constexpr int kThreadFront = 8;     // fronts up to this order are handled by one thread
 constexpr int kWarpFront = 48;      // fronts up to this order are handled by one warp
 constexpr int kWarpsPerBlock = 4;    // warps per block of the warp-level kernels
+constexpr int kWideLevel = 2432;     // levels with at least this many fronts (16 per SM) use warps
 
 // Launch plan of one factorisation / solve.  Supernodes are split into
 //  * subtree tasks: a task is a whole subtree of small fronts whose supernodes occupy a
@@ -22,17 +24,26 @@ constexpr int kWarpsPerBlock = 4;    // warps per block of the warp-level kernel
 //    fronts), up to kWarpFront by one warp each, up to kSmemFront by a CTA in shared
 //    memory, larger ones by a CTA in global memory.
 struct LevelPlan {
+    // factorisation lists
     int n_thread = 0, off_thread = 0;
     int n_warp = 0, off_warp = 0, max_warp_f = 0;
     int n_small = 0, off_small = 0, max_small = 0;
-    int n_large = 0, off_large = 0;
-    int n_cta = 0, off_cta = 0, max_cta_f = 0;  // small + large, for the solve kernels
+    int n_large = 0, off_large = 0, max_large_f = 0;
+    // solve lists (by front order only: a solve front's dependent chain is short)
+    int n_sthread = 0, off_sthread = 0;
+    int n_swarp = 0, off_swarp = 0, max_swarp_f = 0;
+    int n_cta = 0, off_cta = 0, max_cta_f = 0;
 };
 
 // Host-side lists from which the device plan is uploaded.
 struct PlanHost {
     std::vector<LevelPlan> levels;
-    std::vector<int> task, thread, warp, small, large, cta;
+    std::vector<int> task, thread, warp, small, large;  // factorisation
+    std::vector<int> sthread, swarp, cta;               // solves
+    // dataflow solve: work items in topological (level) order; item ≥ 0 is a warp
+    // front, item < 0 is the batch −(item+1) of ≤ 32 one-thread fronts
+    // (sthread[tb_ptr[b] .. tb_ptr[b+1]))
+    std::vector<int> items, tb_ptr;
     int task_max_f = 0, task_height = 0;
     int max_f = 0;
 };

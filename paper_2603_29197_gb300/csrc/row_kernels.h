@@ -30,6 +30,10 @@ struct IPMScalars {
     // refinement
     double normK, berr;
     int refine_done, pad1;
+    // grid barrier of the persistent solve kernel (count, generation, timeout flag)
+    unsigned int bar_count, bar_gen;
+    int bar_err;
+    unsigned int sched_next;  // work-item counter of the dataflow solve
 };
 
 constexpr int kResNSum = 5;

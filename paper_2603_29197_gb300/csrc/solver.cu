@@ -166,6 +166,9 @@ struct qoco_gpu_solver {
     int64_t launches = 0;
     int refine_steps = 0;
     double last_berr = 0.0;
+    // polls a grid-barrier wait may take before it gives up (each poll sleeps ~64 ns)
+    long long barrier_spins = 20000000;
+    int solve_epoch = 0;  // flag value of the latest dataflow solve
     qoco_gpu_info info;
     std::string msg;
 };
@@ -283,6 +286,7 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     signed char* pc;
     if ((rc = dcopy(S, &pc, Y.dsign))) return rc; f.dsign = pc;
     if ((rc = dcopy(S, &pi, Y.perm))) return rc; f.perm = pi;
+    if ((rc = dcopy(S, &pi, Y.sn_parent))) return rc; f.parent = pi;
     double* pd;
     if ((rc = dalloc(S, &pd, (size_t)Y.front_entries))) return rc; f.front = pd;
     if ((rc = dalloc(S, &pd, (size_t)Y.upd_off[Y.ns]))) return rc; f.upd = pd;
@@ -295,8 +299,8 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     // launch plan: subtree tasks + level lists
     PlanHost ph;
     build_plan(Y, S->st.subtree_tasks > 0, S->st.subtree_tasks, &ph);
-    if (ph.max_f > kMaxSolveFront) {
-        S->msg = "a supernode front exceeds the solve kernel's shared-memory limit";
+    if (ph.max_f > kMaxSolveFront || ph.max_f > kMaxFactorFront) {
+        S->msg = "a supernode front exceeds the factor/solve kernels' shared-memory limit";
         return QOCO_GPU_ERR_NOT_IMPLEMENTED;
     }
     FactorPlan& P = S->plan;
@@ -310,6 +314,21 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     if ((rc = dcopy(S, &P.d_small, ph.small))) return rc;
     if ((rc = dcopy(S, &P.d_large, ph.large))) return rc;
     if ((rc = dcopy(S, &P.d_cta, ph.cta))) return rc;
+    if ((rc = dcopy(S, &P.d_sthread, ph.sthread))) return rc;
+    if ((rc = dcopy(S, &P.d_swarp, ph.swarp))) return rc;
+    if ((rc = dcopy(S, &P.d_levels, ph.levels))) return rc;
+    {
+        int mwf = 0;
+        for (const LevelPlan& L : ph.levels) mwf = std::max(mwf, L.max_swarp_f);
+        P.nitems = (int)ph.items.size();
+        if ((rc = dcopy(S, &P.d_items, ph.items))) return rc;
+        if ((rc = dcopy(S, &P.d_tb_ptr, ph.tb_ptr))) return rc;
+        std::vector<int> zeros(Y.ns, 0);
+        if ((rc = dcopy(S, &P.d_fdone, zeros))) return rc;
+        if ((rc = dcopy(S, &P.d_bdone, zeros))) return rc;
+        if ((rc = plan_dataflow_solve(P, mwf, !ph.cta.empty()))) return rc;
+        if (!P.dataflow && (rc = plan_persistent_solve(P, mwf, !ph.cta.empty()))) return rc;
+    }
 
     // iterate / work vectors
     double** vecN[] = {&S->xyz, &S->d_aff, &S->d_cmb, &S->r, &S->rhs, &S->sol_w, &S->sol_xp, &S->res};
@@ -368,13 +387,34 @@ int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
 
 int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStream_t st) {
     Phase ph(S, QOCO_GPU_PHASE_SOLVE, st);
-    S->launches += launch_solve(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, st);
+    if (S->plan.dataflow) {
+        DataflowState ds;
+        ds.next = &S->d_S->sched_next;
+        ds.err = &S->d_S->bar_err;
+        ds.epoch = ++S->solve_epoch;
+        ds.max_spins = S->barrier_spins;
+        const int rc = launch_solve_dataflow(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, ds, st);
+        if (rc < 0) return rc;
+        S->launches += rc;
+    } else if (S->plan.persistent) {
+        GridBarrier bar;
+        bar.count = &S->d_S->bar_count;
+        bar.gen = &S->d_S->bar_gen;
+        bar.err = &S->d_S->bar_err;
+        bar.max_spins = S->barrier_spins;
+        const int rc = launch_solve_persistent(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, bar, st);
+        if (rc < 0) return rc;
+        S->launches += rc;
+    } else {
+        S->launches += launch_solve(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, st);
+    }
     return 0;
 }
 
 // x = K_ε⁻¹ r refined against K until the backward error target (r, x device, N)
 int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st) {
-    tri_solve(S, r, x, false, st);
+    int rc0 = tri_solve(S, r, x, false, st);
+    if (rc0) return rc0;
     int steps = 0;
     for (;;) {
         {
@@ -386,8 +426,9 @@ int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
         QOCO_CUDA_TRY(cudaGetLastError());
         int rc = sync_scalars(S, st);
         if (rc) return rc;
+        if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
         if (S->h_S->refine_done || steps >= S->st.max_refine) break;
-        tri_solve(S, S->res, x, true, st);
+        if ((rc = tri_solve(S, S->res, x, true, st))) return rc;
         ++steps;
     }
     S->refine_steps += steps;
@@ -397,12 +438,18 @@ int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
 
 int cone_launch_count(const ConeView& c) { return cone_grid(c).blocks() ? 1 : 0; }
 
+int reset_barrier(qoco_gpu_solver* S, cudaStream_t st) {
+    QOCO_CUDA_TRY(cudaMemsetAsync(&S->d_S->bar_count, 0, 4 * sizeof(unsigned int), st));
+    return 0;
+}
+
 int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
     const int n = S->n, p = S->p, m = S->m, N = S->N;
     const ConeView& cv = S->cv;
     const int cl = cone_launch_count(cv);
     int rc;
     S->refine_steps = 0;
+    if ((rc = reset_barrier(S, st))) return rc;
     // initial point: K(W = I) [x; y; z] = [−c; b; h], s = −z, shift s and z into the cone
     launch_w2_identity(cv, S->d_val, S->d_w2slot, S->d_w2ptr, st);
     S->launches += cl;
@@ -728,7 +775,9 @@ int qoco_gpu_kkt_solve(qoco_gpu_solver* S, const double* r, double* x, int* refi
     if (!S->have_factor) return QOCO_GPU_ERR_NO_FACTOR;
     cudaStream_t st = (cudaStream_t)stream;
     const int before = S->refine_steps;
-    int rc = solve_refine(S, r, x, st);
+    int rc = reset_barrier(S, st);
+    if (rc) return rc;
+    rc = solve_refine(S, r, x, st);
     if (rc) return rc;
     QOCO_CUDA_TRY(cudaStreamSynchronize(st));
     if (refine_steps) *refine_steps = S->refine_steps - before;
@@ -776,6 +825,10 @@ int qoco_gpu_cone_max_step_noalloc(const qoco_gpu_cones* C, const double* u, con
                                    double* alpha, void* stream) {
     if (!C || !alpha || (C->v.m && (!u || !du))) return QOCO_GPU_ERR_INVALID_ARG;
     return launch_max_step_noalloc(C->v, u, du, cap, alpha, (cudaStream_t)stream);
+}
+
+int qoco_gpu_selftest_barrier_timeout(long long max_spins, void* stream) {
+    return selftest_barrier_timeout(max_spins, (cudaStream_t)stream);
 }
 
 int qoco_gpu_get_pivot_reciprocals(const qoco_gpu_solver* S, double* dinv) {

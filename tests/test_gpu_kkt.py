@@ -132,3 +132,18 @@ def test_pivot_reciprocals_within_two_ulp(name):
     exact = 1.0 / D
     ulp = np.spacing(np.abs(exact))
     assert np.all(np.abs(dinv - exact) <= 2 * ulp)
+
+
+def test_grid_barrier_wait_times_out_into_an_error_status():
+    """The persistent solve's grid barrier never waits without bound: with one block that
+    never arrives, the other blocks give up after a short poll budget and report
+    DEVICE_TIMEOUT; the context stays usable afterwards."""
+    import torch
+    import paper_2603_29197_gb300 as q
+    from paper_2603_29197_gb300 import _lib
+    lib = q.load()
+    rc = lib.qoco_gpu_selftest_barrier_timeout(200000, None)
+    assert rc == _lib.ERR_DEVICE_TIMEOUT
+    # the device still works
+    a = torch.ones(4, dtype=torch.float64, device="cuda")
+    assert float((a * 2).sum().item()) == 8.0
