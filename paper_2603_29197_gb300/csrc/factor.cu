@@ -36,6 +36,33 @@ __device__ __forceinline__ void tri_index(int t, int m, int& ii, int& jj) {
     ii = t - (j * m - (j * (j - 1)) / 2) + j;
 }
 
+// F[rel_j, rel_i] += U_ij over the lower triangle of a child's r×r update block (leading
+// dimension fc), spread over nt threads with four independent entries per step; the
+// block was written by another thread block (read through L2).
+__device__ __forceinline__ void extend_add(double* F, int f, const double* U, int fc, const int* rel, int r,
+                                           int tid, int nt) {
+    const int T = r * (r + 1) / 2;
+    for (int t = tid; t < T; t += 4 * nt) {
+        int off[4];
+        double u4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int tu = t + u * nt;
+            off[u] = -1;
+            u4[u] = 0.0;
+            if (tu < T) {
+                int i, j;
+                tri_index(tu, r, i, j);
+                off[u] = rel[j] * f + rel[i];
+                u4[u] = __ldcg(U + (int64_t)j * fc + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (off[u] >= 0) F[off[u]] += u4[u];
+    }
+}
+
 // Pivot of column k (dynamic regularisation) and its reciprocal: computed once by the
 // calling thread; the caller broadcasts.  FP64 work on GB300 is scarce, so nothing is
 // recomputed per lane.
@@ -74,67 +101,96 @@ __device__ __forceinline__ void tri_advance(int m, int stride, int& ii, int& jj)
     }
 }
 
-// bc: broadcast slot bc[0], then the pivot signs of the front's c columns (bc[1..c]),
-// loaded in one parallel pass so that no pivot waits on a global load
+// bc: broadcast slots bc[0..kPanel] (reciprocal pivots of the current panel's
+// columns), then the pivot signs of the front's c columns (bc[kPanel+1 ..]), loaded in
+// one parallel pass so that no pivot waits on a global load.
+//
+// GB300 runs a dependent FP64 FMA in ~64 cycles, so the panel step is arranged around
+// its serial pivot chain.  Within a panel the columns stay unscaled; thread t owns rows
+// k+1+t (+nt …), so thread 0 owns row k+1 and, as soon as it has applied column k to
+// its own diagonal entry, computes the next pivot and its reciprocal while the other
+// threads apply column k to their rows: one barrier per column.  At the end of the
+// panel the columns are scaled in place (L) and their unscaled copy kept in W, then the
+// trailing rank-kPanel update gives each thread four independent entries per step.
 template <bool WARP>
 __device__ __forceinline__ int blocked_ldlt(double* F, double* W, double* bc, int f, int c, int first,
                                             const FactorView& a, int tid, int nt) {
     int nreg = 0;
     double* dinv = a.dinv + first;
-    double* sgn = bc + 1;
+    double* sgn = bc + kPanel + 1;
     for (int k = tid; k < c; k += nt) sgn[k] = a.dsign[first + k] > 0 ? 1.0 : -1.0;
     group_sync<WARP>();
+    auto do_pivot = [&](int k) {  // thread 0 only
+        double* colk = F + (size_t)k * f;
+        double d = colk[k];
+        const bool pos = sgn[k] > 0.0;
+        const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
+        if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
+        const double inv = recip(d);
+        colk[k] = d;
+        dinv[k] = inv;
+        bc[k % kPanel] = inv;
+    };
+    if (tid == 0 && c > 0) do_pivot(0);
     for (int k0 = 0; k0 < c; k0 += kPanel) {
         const int nb = min(kPanel, c - k0);
         for (int p = 0; p < nb; ++p) {
             const int k = k0 + p;
-            double* colk = F + (size_t)k * f;
-            if (tid == 0) {
-                double d = colk[k];
-                const bool pos = sgn[k] > 0.0;
-                const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
-                if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
-                const double inv = recip(d);
-                colk[k] = d;
-                dinv[k] = inv;
-                bc[0] = inv;
+            group_sync<WARP>();  // pivot k and column k final
+            const double* colk = F + (size_t)k * f;
+            const double inv = bc[k % kPanel];
+            const int jend = k0 + nb;  // later columns of this panel: k+1 .. jend−1
+            for (int i = k + 1 + tid; i < f; i += nt) {
+                const double l = colk[i] * inv;
+                for (int j = k + 1; j < jend && j <= i; ++j) F[(size_t)j * f + i] -= l * colk[j];
+                if (i == k + 1 && k + 1 < jend) do_pivot(k + 1);  // i == k+1 only for tid 0
             }
-            group_sync<WARP>();
-            const double inv = bc[0];
+        }
+        group_sync<WARP>();
+        // scale the panel's columns (L) and keep their unscaled values in W
+        for (int p = 0; p < nb; ++p) {
+            const int k = k0 + p;
+            double* colk = F + (size_t)k * f;
+            const double inv = bc[k % kPanel];
             for (int i = k + 1 + tid; i < f; i += nt) {
                 const double v = colk[i];
                 W[i * kPanel + p] = v;
                 colk[i] = v * inv;
             }
-            group_sync<WARP>();
-            // remaining columns of this panel
-            for (int j = k + 1; j < k0 + nb; ++j) {
-                const double wj = W[j * kPanel + p];
-                double* colj = F + (size_t)j * f;
-                for (int i = j + tid; i < f; i += nt) colj[i] -= colk[i] * wj;
-            }
-            group_sync<WARP>();
         }
-        // trailing rank-nb update of rows/columns k0+nb .. f−1
+        group_sync<WARP>();
+        // trailing rank-nb update of rows/columns k0+nb .. f−1, four entries per thread
         const int base = k0 + nb, m = f - base;
         if (m > 0) {
             const double* L0 = F + (size_t)k0 * f;
-            int ii, jj;
-            tri_index(min(tid, m * (m + 1) / 2), m, ii, jj);
-            if (tid >= m * (m + 1) / 2) jj = m;
-            while (jj < m) {
-                const int i = base + ii, j = base + jj;
-                const double* wj = W + j * kPanel;
-                double acc = F[(size_t)j * f + i];
-                acc -= L0[i] * wj[0];
-                if (nb > 1) acc -= L0[f + i] * wj[1];
-                if (nb > 2) acc -= L0[2 * f + i] * wj[2];
-                if (nb > 3) acc -= L0[3 * f + i] * wj[3];
-                F[(size_t)j * f + i] = acc;
-                tri_advance(m, nt, ii, jj);
+            const int T = m * (m + 1) / 2;
+            for (int t = tid; t < T; t += 4 * nt) {
+                int ii[4], jj[4];
+                double acc[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int tu = t + u * nt;
+                    if (tu < T) tri_index(tu, m, ii[u], jj[u]);
+                    else { ii[u] = 0; jj[u] = 0; }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = base + ii[u], j = base + jj[u];
+                    const double* wr = W + j * kPanel;
+                    double x = F[(size_t)j * f + i];
+                    x -= L0[i] * wr[0];
+                    if (nb > 1) x -= L0[f + i] * wr[1];
+                    if (nb > 2) x -= L0[2 * f + i] * wr[2];
+                    if (nb > 3) x -= L0[3 * f + i] * wr[3];
+                    acc[u] = x;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (t + u * nt < T) F[(size_t)(base + jj[u]) * f + base + ii[u]] = acc[u];
             }
         }
         group_sync<WARP>();
+        if (tid == 0 && base < c) do_pivot(base);
     }
     return nreg;
 }
@@ -144,7 +200,18 @@ __device__ __forceinline__ int blocked_ldlt(double* F, double* W, double* bc, in
 // (column-major, leading dimension kThreadFront); used for the many tiny fronts at the
 // bottom of the tree, where a warp per front would leave most FP64 lanes idle
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void thread_factor_front(int s, const FactorView& a, const double* __restrict__ kval) {
+// No dependency to wait for (level-synchronous callers).
+struct NoWait {
+    __device__ __forceinline__ bool operator()() const { return true; }
+};
+
+// The factorisation of one front: zero it and assemble the KKT entries (independent of
+// other fronts), wait() (the dataflow kernel waits there for the children), then the
+// extend-add of the children's update blocks (read through L2: in the dataflow kernel
+// they were written in the same launch) and the partial LDLᵀ.
+template <class Wait>
+__device__ __forceinline__ bool thread_factor_front(int s, const FactorView& a, const double* __restrict__ kval,
+                                                    const Wait& wait) {
     constexpr int LD = kThreadFront;
     double F[LD * LD];
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
@@ -157,13 +224,14 @@ __device__ __forceinline__ void thread_factor_front(int s, const FactorView& a, 
         if (row == col) v += a.dsign[first + col] > 0 ? a.eps : -a.eps;
         F[col * LD + row] = v;
     }
+    if (!wait()) return false;
     for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
         const int ch = a.child[k];
         const int fc = a.nrow[ch], cc = a.ncol[ch], r = fc - cc;
         const double* U = a.front + a.front_off[ch] + (int64_t)cc * fc + cc;
         const int* rel = a.rel + a.upd_off[ch];
         for (int j = 0; j < r; ++j)
-            for (int i = j; i < r; ++i) F[rel[j] * LD + rel[i]] += U[j * fc + i];
+            for (int i = j; i < r; ++i) F[rel[j] * LD + rel[i]] += __ldcg(U + j * fc + i);
     }
     int nreg = 0;
     for (int k = 0; k < c; ++k) {
@@ -182,12 +250,8 @@ __device__ __forceinline__ void thread_factor_front(int s, const FactorView& a, 
     for (int j = 0; j < f; ++j)
         for (int i = 0; i < f; ++i) G[j * f + i] = i >= j ? F[j * LD + i] : 0.0;
     if (nreg) atomicAdd(a.nreg, nreg);
+    return true;
 }
-
-// No dependency to wait for (level-synchronous callers).
-struct NoWait {
-    __device__ __forceinline__ bool operator()() const { return true; }
-};
 
 // The solve steps of one front are written as: loads that do not depend on other
 // fronts, then wait() (the dataflow kernel waits there for the fronts this one depends
@@ -246,7 +310,7 @@ __device__ __forceinline__ bool thread_bwd_front(int s, const FactorView& a, con
 __global__ void __launch_bounds__(128) k_thread_factor(const int* __restrict__ list, int n, FactorView a,
                                                        const double* __restrict__ kval) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) thread_factor_front(list[t], a, kval);
+    if (t < n) thread_factor_front(list[t], a, kval, NoWait());
 }
 __global__ void __launch_bounds__(128) k_thread_fwd(const int* __restrict__ list, int n, FactorView a,
                                                     const double* __restrict__ rhs, double* __restrict__ w) {
@@ -261,20 +325,16 @@ __global__ void __launch_bounds__(128) k_thread_bwd(const int* __restrict__ list
 }
 
 
-// One CTA per front.  Dynamic shared memory: the front (f² doubles, SMEM variant) plus the
-// scaled pivot column (f doubles) and the broadcast pivot reciprocal.
-template <bool SMEM>
-__global__ void __launch_bounds__(256) k_front_factor(const int* __restrict__ list, FactorView a,
-                                                      const double* __restrict__ kval) {
-    extern __shared__ double smem[];
-    const int s = list[blockIdx.x];
+// One front factored by a whole CTA.  F is the front (shared memory, or the front's
+// global slot G itself), lk the W panel (kPanel·f) followed by the broadcast slot and
+// the pivot signs.  wait() must be called by every thread.
+template <class Wait>
+__device__ __forceinline__ bool cta_factor_front(int s, const FactorView& a, const double* __restrict__ kval,
+                                                 double* F, double* lk, bool in_smem, const Wait& wait) {
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     double* G = a.front + a.front_off[s];
-    double* F = SMEM ? smem : G;
-    double* lk = SMEM ? smem + (size_t)f * f : smem;  // W panel (kPanel·f) then the broadcast slot
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t ff = (int64_t)f * f;
-
     for (int64_t i = tid; i < ff; i += nt) F[i] = 0.0;
     __syncthreads();
     for (int64_t e = a.amap_ptr[s] + tid; e < a.amap_ptr[s + 1]; e += nt) {
@@ -285,23 +345,40 @@ __global__ void __launch_bounds__(256) k_front_factor(const int* __restrict__ li
         F[off] = v;
     }
     __syncthreads();
-    for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
-        const int ch = a.child[k];
-        const int fc = a.nrow[ch], cc = a.ncol[ch], r = fc - cc;
-        const double* U = a.front + a.front_off[ch] + (int64_t)cc * fc + cc;
-        const int* rel = a.rel + a.upd_off[ch];
-        const int T = r * (r + 1) / 2;
-        for (int t = tid; t < T; t += nt) {
-            int i, j;
-            tri_index(t, r, i, j);
-            F[(int64_t)rel[j] * f + rel[i]] += U[(int64_t)j * fc + i];
-        }
+    const int k0 = a.child_ptr[s], nch = a.child_ptr[s + 1] - k0;
+    // the first 32 child records, fetched by warp 0 before the wait and broadcast through
+    // a small shared table
+    __shared__ ChildInfo s_ci[32];
+    if (tid < nch && tid < 32) s_ci[tid] = a.cinfo[k0 + tid];
+    __syncthreads();
+    if (!wait()) return false;
+    for (int k = 0; k < nch; ++k) {
+        const ChildInfo ci = k < 32 ? s_ci[k] : a.cinfo[k0 + k];
+        const int fc = ci.fc, r = ci.r;
+        const double* U = a.front + ci.u_off;
+        const int* rel = a.rel + ci.rel_off;
+        extend_add(F, f, U, fc, rel, r, tid, nt);
         __syncthreads();
     }
     const int nreg = blocked_ldlt<false>(F, lk, lk + (size_t)kPanel * f, f, c, first, a, tid, nt);
     if (tid == 0 && nreg) atomicAdd(a.nreg, nreg);
-    if (SMEM)
+    if (in_smem)
         for (int64_t i = tid; i < ff; i += nt) G[i] = F[i];
+    __syncthreads();
+    return true;
+}
+
+// One CTA per front of a level.  Dynamic shared memory: the front (f² doubles, SMEM
+// variant), then the W panel, broadcast slot and pivot signs.
+template <bool SMEM>
+__global__ void __launch_bounds__(256) k_front_factor(const int* __restrict__ list, FactorView a,
+                                                      const double* __restrict__ kval) {
+    extern __shared__ double smem[];
+    const int s = list[blockIdx.x];
+    const int f = a.nrow[s];
+    double* F = SMEM ? smem : a.front + a.front_off[s];
+    double* lk = SMEM ? smem + (size_t)f * f : smem;
+    cta_factor_front(s, a, kval, F, lk, SMEM, NoWait());
 }
 
 // Forward solve L u = b and diagonal scaling w = D⁻¹u, one CTA per supernode of the
@@ -381,14 +458,15 @@ __global__ void __launch_bounds__(128) k_bwd(const int* __restrict__ list, Facto
 
 // per-warp shared memory of the warp factor kernels: front (fmax²), W panel (kPanel·fmax)
 // and the broadcast slot
-__host__ __device__ constexpr int wfactor_stride(int fmax) { return fmax * (fmax + kPanel) + 1 + fmax; }
+__host__ __device__ constexpr int wfactor_stride(int fmax) { return fmax * (fmax + kPanel) + kPanel + 1 + fmax; }
 
 // ---------------------------------------------------------------------------
 // warp-level variants for fronts of order ≤ kWarpFront (one warp per front, the front
 // in the warp's slice of shared memory, __syncwarp instead of block barriers)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void warp_factor_front(int s, const FactorView& a, const double* __restrict__ kval,
-                                                  double* F, double* lk, int lane) {
+template <class Wait>
+__device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, const double* __restrict__ kval,
+                                                  double* F, double* lk, int lane, const Wait& wait) {
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     const int ff = f * f;
     for (int i = lane; i < ff; i += 32) F[i] = 0.0;
@@ -414,19 +492,27 @@ __device__ __forceinline__ void warp_factor_front(int s, const FactorView& a, co
             }
         }
     }
+    // child records of the first 32 children, one per lane (loaded before the wait)
+    const int k0 = a.child_ptr[s], nch = a.child_ptr[s + 1] - k0;
+    ChildInfo mine;
+    if (lane < nch) mine = a.cinfo[k0 + lane];
     __syncwarp();
+    if (!wait()) return false;
     // extend-add of each child's update block, its lower triangle spread over the lanes
-    for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
-        const int ch = a.child[k];
-        const int fc = a.nrow[ch], cc = a.ncol[ch], r = fc - cc;
-        const double* U = a.front + a.front_off[ch] + (int64_t)cc * fc + cc;
-        const int* rel = a.rel + a.upd_off[ch];
-        const int T = r * (r + 1) / 2;
-        for (int t = lane; t < T; t += 32) {
-            int i, j;
-            tri_index(t, r, i, j);
-            F[rel[j] * f + rel[i]] += U[(int64_t)j * fc + i];
+    for (int k = 0; k < nch; ++k) {
+        ChildInfo ci;
+        if (k < 32) {
+            ci.u_off = __shfl_sync(0xffffffffu, mine.u_off, k);
+            ci.rel_off = __shfl_sync(0xffffffffu, mine.rel_off, k);
+            ci.fc = __shfl_sync(0xffffffffu, mine.fc, k);
+            ci.r = __shfl_sync(0xffffffffu, mine.r, k);
+        } else {
+            ci = a.cinfo[k0 + k];
         }
+        const double* U = a.front + ci.u_off;
+        const int* rel = a.rel + ci.rel_off;
+        const int r = ci.r, fc = ci.fc;
+        extend_add(F, f, U, fc, rel, r, lane, 32);
         __syncwarp();
     }
     const int nreg = blocked_ldlt<true>(F, lk, lk + kPanel * f, f, c, first, a, lane, 32);
@@ -434,6 +520,7 @@ __device__ __forceinline__ void warp_factor_front(int s, const FactorView& a, co
     for (int i = lane; i < ff; i += 32) G[i] = F[i];
     if (lane == 0 && nreg) atomicAdd(a.nreg, nreg);
     __syncwarp();
+    return true;
 }
 
 // copy the f×c panel of supernode s (L and D) into shared memory with independent loads
@@ -453,13 +540,23 @@ __device__ __forceinline__ bool warp_fwd_front(int s, const FactorView& a, const
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     warp_load_panel(a.front + a.front_off[s], f * c, P, lane);
     for (int i = lane; i < f; i += 32) v[i] = i < c ? rhs[a.perm[first + i]] : 0.0;
+    const int k0 = a.child_ptr[s], nch = a.child_ptr[s + 1] - k0;
+    ChildInfo mine;
+    if (lane < nch) mine = a.cinfo[k0 + lane];
     __syncwarp();
     if (!wait()) return false;
-    for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
-        const int ch = a.child[k];
-        const int r = a.nrow[ch] - a.ncol[ch];
-        const int* rel = a.rel + a.upd_off[ch];
-        const double* u = a.upd + a.upd_off[ch];
+    for (int k = 0; k < nch; ++k) {
+        int64_t ro;
+        int r;
+        if (k < 32) {
+            ro = __shfl_sync(0xffffffffu, mine.rel_off, k);
+            r = __shfl_sync(0xffffffffu, mine.r, k);
+        } else {
+            ro = a.cinfo[k0 + k].rel_off;
+            r = a.cinfo[k0 + k].r;
+        }
+        const int* rel = a.rel + ro;
+        const double* u = a.upd + ro;
         for (int i = lane; i < r; i += 32) v[rel[i]] += __ldcg(u + i);
         __syncwarp();
     }
@@ -521,7 +618,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_factor(const int* 
     if (t >= ntask) return;
     double* F = smem + (size_t)wid * wfactor_stride(fmax);
     const int lo = task[2 * t], hi = task[2 * t + 1];
-    for (int s = lo; s <= hi; ++s) warp_factor_front(s, a, kval, F, F + fmax * fmax, lane);
+    for (int s = lo; s <= hi; ++s) warp_factor_front(s, a, kval, F, F + fmax * fmax, lane, NoWait());
 }
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_fwd(const int* __restrict__ task, int ntask,
                                                                  FactorView a, const double* __restrict__ rhs,
@@ -555,7 +652,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_factor(const int* 
     const int t = blockIdx.x * kWarpsPerBlock + wid;
     if (t >= n) return;
     double* F = smem + (size_t)wid * wfactor_stride(fmax);
-    warp_factor_front(list[t], a, kval, F, F + fmax * fmax, lane);
+    warp_factor_front(list[t], a, kval, F, F + fmax * fmax, lane, NoWait());
 }
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_fwd(const int* __restrict__ list, int n,
                                                                  FactorView a, const double* __restrict__ rhs,
@@ -816,6 +913,120 @@ int launch_solve_dataflow(const FactorPlan& P, const FactorView& a, const double
     return 1;
 }
 
+// ---------------------------------------------------------------------------
+// Dataflow factorisation: one launch, blocks of kDataflowThreads take items in level
+// order from an atomic counter.  Item kinds (low two bits): 0 = batch of up to 128
+// one-thread fronts, 1 = group of up to 4 warp fronts, 2 = one front for the whole
+// CTA.  A front waits (bounded polls) for its children's completion flags after its
+// independent assembly; the deadlock argument is the one of the dataflow solve.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
+    const int* __restrict__ items, int nitems, const int* __restrict__ tb_ptr, const int* __restrict__ tlist,
+    const int* __restrict__ wg_ptr, const int* __restrict__ wlist, FactorView a, const double* __restrict__ kval,
+    int fmax, int* cdone, DataflowState ds) {
+    extern __shared__ double smem[];
+    __shared__ int s_it, s_stop;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_it = (int)atomicAdd(ds.next, 1u);
+            s_stop = *(volatile int*)ds.err;
+        }
+        __syncthreads();
+        const int it = s_it, stop = s_stop;
+        __syncthreads();
+        if (stop || it >= nitems) return;
+        const int item = items[it];
+        const int kind = item & 3, idx = item >> 2;
+        bool ok = true;
+        if (kind == 0) {
+            const int t = tb_ptr[idx] + threadIdx.x;
+            if (t < tb_ptr[idx + 1]) {
+                const int s = tlist[t];
+                auto wait = [&]() {
+                    bool good = true;
+                    for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1] && good; ++k)
+                        good = wait_epoch(cdone + a.child[k], ds.epoch, ds.err, ds.max_spins);
+                    __threadfence();
+                    return good;
+                };
+                ok = thread_factor_front(s, a, kval, wait);
+                if (ok) {
+                    __threadfence();
+                    atomicExch(cdone + s, ds.epoch);
+                }
+            }
+        } else if (kind == 1) {
+            const int t = wg_ptr[idx] + wid;
+            if (t < wg_ptr[idx + 1]) {
+                const int s = wlist[t];
+                double* F = smem + (size_t)wid * wfactor_stride(fmax);
+                auto wait = [&]() {
+                    bool good = true;
+                    for (int k = a.child_ptr[s] + lane; k < a.child_ptr[s + 1]; k += 32)
+                        good = good && wait_epoch(cdone + a.child[k], ds.epoch, ds.err, ds.max_spins);
+                    good = __all_sync(0xffffffffu, good);
+                    __threadfence();
+                    return good;
+                };
+                ok = warp_factor_front(s, a, kval, F, F + fmax * fmax, lane, wait);
+                if (ok) {
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) atomicExch(cdone + s, ds.epoch);
+                }
+            }
+        } else {
+            const int s = idx;
+            const int f = a.nrow[s];
+            auto wait = [&]() {
+                bool good = true;
+                for (int k = a.child_ptr[s] + (int)threadIdx.x; k < a.child_ptr[s + 1]; k += blockDim.x)
+                    good = good && wait_epoch(cdone + a.child[k], ds.epoch, ds.err, ds.max_spins);
+                good = __syncthreads_and(good) != 0;
+                __threadfence();
+                return good;
+            };
+            ok = cta_factor_front(s, a, kval, smem, smem + (size_t)f * f, true, wait);
+            if (ok) {
+                __threadfence();
+                if (threadIdx.x == 0) atomicExch(cdone + s, ds.epoch);
+            }
+        }
+        if (!__syncthreads_and(ok)) return;
+    }
+}
+
+static size_t fdataflow_smem(int fmax) {
+    return (size_t)(kDataflowThreads / 32) * wfactor_stride(fmax) * sizeof(double);
+}
+
+int plan_dataflow_factor(FactorPlan& P, int fmax, bool any_large) {
+    P.fdataflow = false;
+    if (any_large || P.ntasks || P.nfitems == 0 || fmax > kWarpFront) return 0;
+    fmax = max(fmax, 1);
+    const size_t sm = fdataflow_smem(fmax);
+    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_factor_dataflow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int dev = 0, nsm = 0, occ = 0;
+    QOCO_CUDA_TRY(cudaGetDevice(&dev));
+    QOCO_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    QOCO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_dataflow, kDataflowThreads, sm));
+    if (occ < 1) return 0;
+    P.fdataflow = true;
+    P.fdataflow_grid = nsm * occ;
+    P.fdataflow_fmax = fmax;
+    return 0;
+}
+
+int launch_factor_dataflow(const FactorPlan& P, const FactorView& a, const double* kval, const DataflowState& ds,
+                           cudaStream_t st) {
+    QOCO_CUDA_TRY(cudaMemsetAsync(ds.next, 0, sizeof(unsigned int), st));
+    k_factor_dataflow<<<P.fdataflow_grid, kDataflowThreads, fdataflow_smem(P.fdataflow_fmax), st>>>(
+        P.d_fitems, P.nfitems, P.d_ftb_ptr, P.d_thread, P.d_fwg_ptr, P.d_warp, a, kval, P.fdataflow_fmax,
+        P.d_cdone, ds);
+    return 1;
+}
+
 // ---- launchers ----------------------------------------------------------------
 static int wblocks(int n) { return (n + kWarpsPerBlock - 1) / kWarpsPerBlock; }
 // per warp: the front vector (fmax) and the panel (≤ fmax·fmax)
@@ -843,13 +1054,13 @@ int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, 
             ++launches;
         }
         if (L.n_small) {
-            const size_t sm = ((size_t)L.max_small * (L.max_small + kPanel + 1) + 1) * sizeof(double);
+            const size_t sm = ((size_t)L.max_small * (L.max_small + kPanel + 1) + kPanel + 1) * sizeof(double);
             const int threads = L.max_small <= 64 ? 128 : 256;
             k_front_factor<true><<<L.n_small, threads, sm, st>>>(P.d_small + L.off_small, a, kval);
             ++launches;
         }
         if (L.n_large) {
-            const size_t sm = ((size_t)(kPanel + 1) * L.max_large_f + 1) * sizeof(double);
+            const size_t sm = ((size_t)(kPanel + 1) * L.max_large_f + kPanel + 1) * sizeof(double);
             k_front_factor<false><<<L.n_large, 256, sm, st>>>(P.d_large + L.off_large, a, kval);
             ++launches;
         }
@@ -912,9 +1123,9 @@ int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, do
 int factor_set_attributes() {
     const int warp_smem = (int)wfactor_smem(kWarpFront);
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_front_factor<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (kSmemFront * (kSmemFront + kPanel + 1) + 1) * (int)sizeof(double)));
+                                       (kSmemFront * (kSmemFront + kPanel + 1) + kPanel + 1) * (int)sizeof(double)));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_front_factor<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       ((kPanel + 1) * kMaxFactorFront + 1) * (int)sizeof(double)));
+                                       ((kPanel + 1) * kMaxFactorFront + kPanel + 1) * (int)sizeof(double)));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_task_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_warp_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem));
     const int wsolve = kWarpsPerBlock * kWarpFront * (kWarpFront + 1) * (int)sizeof(double);

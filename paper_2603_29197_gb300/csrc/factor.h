@@ -9,6 +9,16 @@
 namespace qoco {
 
 
+// One child edge of the supernodal tree, in the parent's child order: where the child's
+// update block starts in the front array (its trailing r×r block, leading dimension
+// fc), and where its relative indices / solve update vector start (upd_off).
+struct ChildInfo {
+    int64_t u_off;
+    int64_t rel_off;
+    int fc;
+    int r;
+};
+
 struct FactorView {
     const int* first = nullptr;      // ns: first permuted column
     const int* ncol = nullptr;       // c_s
@@ -20,6 +30,7 @@ struct FactorView {
     const int* rel = nullptr;
     const int* child_ptr = nullptr;
     const int* child = nullptr;
+    const ChildInfo* cinfo = nullptr;  // parallel to child
     const int64_t* amap_ptr = nullptr;
     const int64_t* amap_slot = nullptr;
     const int* amap_off = nullptr;
@@ -55,6 +66,13 @@ struct FactorPlan {
     int* d_tb_ptr = nullptr;
     int* d_fdone = nullptr;  // per supernode: epoch of its finished forward step
     int* d_bdone = nullptr;  // per supernode: epoch of its finished backward step
+    // dataflow factorisation
+    bool fdataflow = false;
+    int nfitems = 0, fdataflow_grid = 0, fdataflow_fmax = 0;
+    int* d_fitems = nullptr;
+    int* d_ftb_ptr = nullptr;
+    int* d_fwg_ptr = nullptr;
+    int* d_cdone = nullptr;  // per supernode: epoch of its finished factorisation
 };
 
 // Shared state of one dataflow solve launch.
@@ -72,6 +90,9 @@ int plan_persistent_solve(FactorPlan& P, int max_warp_f, bool any_cta_front);
 // QOCO_GPU_ERR_DEVICE_TIMEOUT when the other blocks' bounded waits ran out as designed.
 int selftest_barrier_timeout(long long max_spins, cudaStream_t st);
 int plan_dataflow_solve(FactorPlan& P, int max_warp_f, bool any_cta_front);
+int plan_dataflow_factor(FactorPlan& P, int fmax, bool any_large);
+int launch_factor_dataflow(const FactorPlan& P, const FactorView& a, const double* kval, const DataflowState& ds,
+                           cudaStream_t st);
 int launch_solve_dataflow(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
                           double* x, bool accumulate, const DataflowState& ds, cudaStream_t st);
 // One cooperative launch for the forward, diagonal and backward solves.

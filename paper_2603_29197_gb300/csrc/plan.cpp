@@ -129,6 +129,23 @@ void build_plan(const Symbolic& S, bool allow_tasks, int target_tasks, PlanHost*
         }
         for (int t = 0; t < L.n_swarp; ++t) P->items.push_back(P->swarp[L.off_swarp + t]);
     }
+    // dataflow factorisation items, level by level
+    P->ftb_ptr.assign(1, 0);
+    P->fwg_ptr.assign(1, 0);
+    for (int l = 0; l < (int)P->levels.size(); ++l) {
+        const LevelPlan& L = P->levels[l];
+        for (int t = 0; t < L.n_thread; t += 128) {
+            const int b = (int)P->ftb_ptr.size() - 1;
+            P->ftb_ptr.push_back(L.off_thread + std::min(t + 128, L.n_thread));
+            P->fitems.push_back((b << 2) | 0);
+        }
+        for (int t = 0; t < L.n_warp; t += 4) {
+            const int g = (int)P->fwg_ptr.size() - 1;
+            P->fwg_ptr.push_back(L.off_warp + std::min(t + 4, L.n_warp));
+            P->fitems.push_back((g << 2) | 1);
+        }
+        for (int t = 0; t < L.n_small; ++t) P->fitems.push_back((P->small[L.off_small + t] << 2) | 2);
+    }
     // drop empty trailing levels
     while (!P->levels.empty() &&
            P->levels.back().n_sthread + P->levels.back().n_swarp + P->levels.back().n_cta == 0)

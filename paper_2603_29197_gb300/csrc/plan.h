@@ -44,6 +44,10 @@ struct PlanHost {
     // front, item < 0 is the batch −(item+1) of ≤ 32 one-thread fronts
     // (sthread[tb_ptr[b] .. tb_ptr[b+1]))
     std::vector<int> items, tb_ptr;
+    // dataflow factorisation items (kind in the low two bits, see factor.cu):
+    // batches of ≤ 128 one-thread fronts (thread[ftb_ptr[b] ..]), groups of ≤ 4 warp
+    // fronts (warp[fwg_ptr[g] ..]) and single CTA fronts
+    std::vector<int> fitems, ftb_ptr, fwg_ptr;
     int task_max_f = 0, task_height = 0;
     int max_f = 0;
 };

@@ -168,7 +168,8 @@ struct qoco_gpu_solver {
     double last_berr = 0.0;
     // polls a grid-barrier wait may take before it gives up (each poll sleeps ~64 ns)
     long long barrier_spins = 20000000;
-    int solve_epoch = 0;  // flag value of the latest dataflow solve
+    int solve_epoch = 0;   // flag value of the latest dataflow solve
+    int factor_epoch = 0;  // flag value of the latest dataflow factorisation
     qoco_gpu_info info;
     std::string msg;
 };
@@ -280,6 +281,20 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     if ((rc = dcopy(S, &pi, Y.rel))) return rc; f.rel = pi;
     if ((rc = dcopy(S, &pi, Y.child_ptr))) return rc; f.child_ptr = pi;
     if ((rc = dcopy(S, &pi, Y.child))) return rc; f.child = pi;
+    {
+        std::vector<ChildInfo> ci(Y.child.size());
+        for (size_t k = 0; k < Y.child.size(); ++k) {
+            const int ch = Y.child[k];
+            const int fc = Y.sn_nrow[ch], cc = Y.sn_ncol[ch];
+            ci[k].u_off = Y.front_off[ch] + (int64_t)cc * fc + cc;
+            ci[k].rel_off = Y.upd_off[ch];
+            ci[k].fc = fc;
+            ci[k].r = fc - cc;
+        }
+        ChildInfo* pc;
+        if ((rc = dcopy(S, &pc, ci))) return rc;
+        f.cinfo = pc;
+    }
     if ((rc = dcopy(S, &pl, Y.amap_ptr))) return rc; f.amap_ptr = pl;
     if ((rc = dcopy(S, &pl, Y.amap_slot))) return rc; f.amap_slot = pl;
     if ((rc = dcopy(S, &pi, Y.amap_off))) return rc; f.amap_off = pi;
@@ -327,6 +342,12 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         if ((rc = dcopy(S, &P.d_fdone, zeros))) return rc;
         if ((rc = dcopy(S, &P.d_bdone, zeros))) return rc;
         if ((rc = plan_dataflow_solve(P, mwf, !ph.cta.empty()))) return rc;
+        P.nfitems = (int)ph.fitems.size();
+        if ((rc = dcopy(S, &P.d_fitems, ph.fitems))) return rc;
+        if ((rc = dcopy(S, &P.d_ftb_ptr, ph.ftb_ptr))) return rc;
+        if ((rc = dcopy(S, &P.d_fwg_ptr, ph.fwg_ptr))) return rc;
+        if ((rc = dcopy(S, &P.d_cdone, zeros))) return rc;
+        if ((rc = plan_dataflow_factor(P, ph.max_f, !ph.large.empty()))) return rc;
         if (!P.dataflow && (rc = plan_persistent_solve(P, mwf, !ph.cta.empty()))) return rc;
     }
 
@@ -378,7 +399,18 @@ int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
     }
     {
         Phase ph(S, QOCO_GPU_PHASE_FACTOR, st);
-        S->launches += launch_factor(S->plan, S->fv, S->d_val, st);
+        if (S->plan.fdataflow) {
+            DataflowState ds;
+            ds.next = &S->d_S->sched_next;
+            ds.err = &S->d_S->bar_err;
+            ds.epoch = ++S->factor_epoch;
+            ds.max_spins = S->barrier_spins;
+            const int rc = launch_factor_dataflow(S->plan, S->fv, S->d_val, ds, st);
+            if (rc < 0) return rc;
+            S->launches += rc;
+        } else {
+            S->launches += launch_factor(S->plan, S->fv, S->d_val, st);
+        }
     }
     QOCO_CUDA_TRY(cudaGetLastError());
     S->have_factor = true;
