@@ -175,6 +175,35 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def kernel_source_digest():
+    """Digest of the CUDA sources: DRAM traffic measured by ncu is only reported while
+    the kernels are the ones it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2603_29197_gb300", "csrc")
+    for name in sorted(os.listdir(src)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(src, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, stages):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel`, from the ncu
+    summary in profiles/ (a line `traffic <kernel> <stages> <bytes> <source digest>`),
+    or None when no capture matches this workload and these sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = kernel_source_digest()
+    with open(path) as f:
+        for line in f:
+            t = line.split()
+            if len(t) == 5 and t[0] == "traffic" and t[1] == kernel and t[2] == str(stages) and t[4] == digest:
+                return float(t[3])
+    return None
+
+
 def roofline(profile, info, stages):
     """Roofline of the phase with the largest device time (CUDA events on the solver's
     stream over the timed steps)."""
@@ -187,15 +216,15 @@ def roofline(profile, info, stages):
     if ph == "factor":
         flops = info["factor_flops"]
         ach = flops / (per_call_ms * 1e-3) / 1e9
-        return {"kernel": "k_front_factor (all level launches of one LDLᵀ factorisation)",
+        return {"kernel": "k_factor_dataflow (one launch per LDLᵀ factorisation)",
                 "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                "frac": ach / FP64_NOMINAL_GFLOPS, "traffic": None,
+                "frac": ach / FP64_NOMINAL_GFLOPS, "traffic": ncu_traffic("k_factor_dataflow", stages),
                 "per_launch_unit": f"{flops:.4g} algorithmic flops per factorisation",
                 "peak_source": "nominal FP64 rate (recipe table), not a measured peak",
                 "avg_ms": per_call_ms, "launches_per_call": rec["launches"] / max(1, rec["calls"])}
     if ph == "solve":
         by = 2.0 * info["l_nnz"] * 12.0 + N * 8.0 * 4.0
-        name = "k_fwd + k_bwd (all level launches of one triangular solve)"
+        name = "k_solve_dataflow (forward, diagonal and backward solve in one launch)"
     elif ph == "row":
         by = nnz * 12.0 + N * 8.0 * 3.0
         name = "k_residual / k_spmv_res / k_norm_inf (one pass)"
@@ -204,7 +233,7 @@ def roofline(profile, info, stages):
         name = "cone kernels (one pass)"
     ach = by / (per_call_ms * 1e-3) / 1e9
     return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm, "traffic": None, "per_launch_unit": f"{by:.4g} algorithmic bytes per call",
+            "frac": ach / hbm, "traffic": ncu_traffic(name.split()[0], stages), "per_launch_unit": f"{by:.4g} algorithmic bytes per call",
             "peak_source": f"{hbm_src} copy bandwidth", "avg_ms": per_call_ms,
             "launches_per_call": rec["launches"] / max(1, rec["calls"])}
 
