@@ -160,14 +160,60 @@ int qoco_gpu_get_solution(const qoco_gpu_solver* solver, double* x, double* s,
 int qoco_gpu_solution_device(const qoco_gpu_solver* solver, const double** x,
                              const double** s, const double** y, const double** z);
 
+/* Copies the solver's iterate into caller DEVICE buffers x[n], s[m], y[p], z[m] (any may
+ * be NULL), ordered on `stream` (device-to-device copies, no host round trip). */
+int qoco_gpu_copy_solution(const qoco_gpu_solver* solver, double* x, double* s, double* y,
+                           double* z, void* stream);
+
 /* Statistics of setup and of the last solve. */
 int qoco_gpu_get_info(const qoco_gpu_solver* solver, qoco_gpu_info* info);
 
-/* Adjoint of the solution map (implicit differentiation of the KKT conditions at the
- * final iterate, reusing its factorisation).  Not part of the paper; reserved. */
+/* Adjoint of the solution map (not in the paper; one of the forms grown beyond the
+ * plain solver): implicit differentiation of the optimality conditions of eq. (1) at
+ * the final iterate (x, s, y, z) of the last qoco_gpu_solve,
+ *
+ *     Px + c + Aᵀy + Gᵀz = 0,   Ax = b,   Gx + s = h,   s ∘ z = (final value),
+ *
+ * with the complementarity linearised exactly in the cone's Jordan algebra,
+ * z ∘ ds + s ∘ dz = 0, i.e. ds = −Arw(z)⁻¹Arw(s) dz (for the orthant ds = −(s/z) dz).
+ * For g = ∂L/∂(x, y, z) it solves K̂ᵀv = g, where K̂ is eq. (2)'s matrix with that
+ * block in place of −WᵀW, by iterative refinement preconditioned with the final LDLᵀ
+ * factor (reused; the NT scaling of the iterate before the last step); if the
+ * refinement stalls, it refactors once at the final iterate's NT scaling.  Then
+ *
+ *     dc = −v_x,  db = v_y,  dh = v_z,
+ *     dA_rc = −(y_r v_x,c + v_y,r x_c),  dG_rc = −(z_r v_x,c + v_z,r x_c),
+ *     dP_ij = −(v_x,i x_j + v_x,j x_i) for a stored upper entry i < j,  dP_ii = −v_x,i x_i.
+ *
+ * All pointers are DEVICE memory of the solver's device.  dx[n], dy[p], dz[m] are the
+ * incoming gradients (NULL = zero); outputs (NULL = not wanted): dP_val[nnz(P)] on P's
+ * stored upper pattern in CSC order, dc[n], dA_val[nnz(A)], db[p], dG_val[nnz(G)],
+ * dh[m].  Synchronous (the refinement reads its backward error on the host).  The
+ * derivative exists where the solution is strictly complementary; on degenerate
+ * solutions the refinement may not converge and QOCO_GPU_ERR_NUMERICAL is returned.
+ * The call overwrites the −WᵀW slots of the solver's KKT values and its work vectors
+ * (the next qoco_gpu_solve starts from its own initial point, so it is unaffected).
+ * Errors: NO_FACTOR (no completed solve), NUMERICAL, CUDA, DEVICE_TIMEOUT. */
 int qoco_gpu_backward(qoco_gpu_solver* solver, const double* dx, const double* dy,
                       const double* dz, double* dP_val, double* dc, double* dA_val,
-                      double* db, double* dG_val, double* dh);
+                      double* db, double* dG_val, double* dh, void* stream);
+
+/* Refinement statistics of the last qoco_gpu_backward: steps taken, final normwise
+ * backward error of K̂ᵀv = g, and whether it refactored (host outputs, may be NULL). */
+int qoco_gpu_backward_info(const qoco_gpu_solver* solver, int* refine_steps,
+                           double* backward_error, int* refactored);
+
+/* Parametric re-solve (paper §3.2 names set-up as QOCO-GPU's bottleneck; this keeps
+ * the ordering, symbolic analysis and every device buffer): replaces the values of the
+ * problem data without changing any sparsity pattern.  P_val[nnz(P)], A_val[nnz(A)],
+ * G_val[nnz(G)] follow the CSC order given at setup; c[n], b[p], h[m]; NULL keeps the
+ * current values.  on_device = 0: host pointers, checked for finiteness
+ * (NONFINITE_DATA); on_device = 1: device pointers, not checked (a non-finite value
+ * surfaces as NUMERICAL in the next solve).  Ordered on `stream`; the next
+ * qoco_gpu_solve starts from a fresh initial point. */
+int qoco_gpu_update_data(qoco_gpu_solver* solver, const double* P_val, const double* c,
+                         const double* A_val, const double* b, const double* G_val,
+                         const double* h, int on_device, void* stream);
 
 /* Turns per-phase CUDA-event timing on (1) or off (0) and clears the totals. */
 int qoco_gpu_set_profiling(qoco_gpu_solver* solver, int on);

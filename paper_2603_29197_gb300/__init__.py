@@ -142,6 +142,8 @@ class Solver:
         if rc != 0:
             self._h = None
             raise SolverError(rc, "setup")
+        self._nnz = (P.s.nnz if P.ptr is not None else 0, A.s.nnz if A.ptr is not None else 0,
+                     G.s.nnz if G.ptr is not None else 0)
 
     def solve(self, stream=None) -> int:
         return int(self.lib.qoco_gpu_solve(self._h, _torch_stream(stream) if stream is not None else None))
@@ -224,9 +226,57 @@ class Solver:
         self.lib.qoco_gpu_get_profile(self._h, C.byref(pr))
         return pr.as_dict()
 
-    def backward(self, *args):
-        rc = self.lib.qoco_gpu_backward(self._h, *([None] * 9))
-        raise SolverError(rc, "backward")
+    def solution_tensors(self, stream=None):
+        """Copies of x, y, z in new torch CUDA float64 tensors (device-to-device)."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        x, y, z = (torch.empty(k, dtype=torch.float64, device=dev) for k in (self.n, self.p, self.m))
+        rc = self.lib.qoco_gpu_copy_solution(self._h, _tptr(x), None, _tptr(y), _tptr(z), _torch_stream(stream))
+        if rc != 0:
+            raise SolverError(rc, "copy_solution")
+        return x, y, z
+
+    # ---- adjoint and parametric update -------------------------------------------
+    def nnz(self):
+        """Stored entries of P (upper), A and G as given at setup."""
+        return self._nnz
+
+    def backward(self, dx=None, dy=None, dz=None, stream=None):
+        """Gradients of a loss with respect to (P values, c, A values, b, G values, h)
+        given its gradients with respect to x, y, z (torch CUDA float64 tensors or None).
+        Returns a dict of torch CUDA tensors dP, dc, dA, db, dG, dh."""
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        nP, nA, nG = self._nnz
+        out = {k: torch.empty(sz, dtype=torch.float64, device=dev)
+               for k, sz in (("dP", nP), ("dc", self.n), ("dA", nA), ("db", self.p), ("dG", nG), ("dh", self.m))}
+        rc = self.lib.qoco_gpu_backward(self._h, _tptr(dx), _tptr(dy), _tptr(dz), _tptr(out["dP"]),
+                                        _tptr(out["dc"]), _tptr(out["dA"]), _tptr(out["db"]),
+                                        _tptr(out["dG"]), _tptr(out["dh"]), _torch_stream(stream))
+        if rc != 0:
+            raise SolverError(rc, "backward")
+        return out
+
+    def backward_info(self):
+        steps = C.c_int()
+        be = C.c_double()
+        rf = C.c_int()
+        self.lib.qoco_gpu_backward_info(self._h, C.byref(steps), C.byref(be), C.byref(rf))
+        return dict(refine_steps=steps.value, backward_error=be.value, refactored=bool(rf.value))
+
+    def update_data(self, P=None, c=None, A=None, b=None, G=None, h=None, stream=None):
+        """New values on the setup's sparsity patterns (P, A, G: value arrays in CSC
+        order).  All given arrays are numpy (host) or all torch CUDA tensors (device)."""
+        given = [a for a in (P, c, A, b, G, h) if a is not None]
+        on_device = bool(given) and hasattr(given[0], "data_ptr")
+        if on_device:
+            args = [_tptr(a) for a in (P, c, A, b, G, h)]
+        else:
+            keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (P, c, A, b, G, h)]
+            args = [C.c_void_p(0) if a is None else C.c_void_p(a.ctypes.data) for a in keep]
+        rc = self.lib.qoco_gpu_update_data(self._h, *args, 1 if on_device else 0, _torch_stream(stream))
+        if rc != 0:
+            raise SolverError(rc, "update_data")
 
     def close(self):
         if self._h:
@@ -238,6 +288,38 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def _solve_function():
+    import torch
+
+    class SolveFunction(torch.autograd.Function):
+        """(P values, c, A values, b, G values, h) ↦ (x, y, z) through a Solver whose
+        sparsity patterns are fixed: forward is update_data + solve, backward is the
+        adjoint (qoco_gpu_backward).  Inputs are torch CUDA float64 tensors."""
+
+        @staticmethod
+        def forward(ctx, solver, P_val, c, A_val, b, G_val, h):
+            solver.update_data(P=P_val, c=c, A=A_val, b=b, G=G_val, h=h)
+            st = solver.solve(torch.cuda.current_stream().cuda_stream)
+            if st != 0:
+                raise SolverError(st, "solve")
+            ctx.solver = solver
+            return solver.solution_tensors()
+
+        @staticmethod
+        def backward(ctx, gx, gy, gz):
+            g = ctx.solver.backward(gx.contiguous() if gx is not None else None,
+                                    gy.contiguous() if gy is not None else None,
+                                    gz.contiguous() if gz is not None else None)
+            return None, g["dP"], g["dc"], g["dA"], g["db"], g["dG"], g["dh"]
+
+    return SolveFunction
+
+
+def solve_function():
+    """The torch.autograd.Function class wrapping solve + adjoint."""
+    return _solve_function()
 
 
 class Cones:

@@ -88,7 +88,10 @@ SIGNATURES = {
     "qoco_gpu_solution_device": (C.c_int, [_VP, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP),
                                            C.POINTER(_VP)]),
     "qoco_gpu_get_info": (C.c_int, [_VP, C.POINTER(Info)]),
-    "qoco_gpu_backward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "qoco_gpu_backward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "qoco_gpu_copy_solution": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "qoco_gpu_backward_info": (C.c_int, [_VP, _IP, _DP, _IP]),
+    "qoco_gpu_update_data": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int, _VP]),
     "qoco_gpu_cleanup": (C.c_int, [_VP]),
     "qoco_gpu_set_profiling": (C.c_int, [_VP, C.c_int]),
     "qoco_gpu_get_profile": (C.c_int, [_VP, C.POINTER(Profile)]),

@@ -87,6 +87,72 @@ __global__ void k_update(double* xyz, double* s, const double* d, const double* 
     if (i < m) s[i] += a * ds[i];
 }
 
+
+// ---- adjoint and parametric-update kernels ----------------------------------------
+// rp = g, plus t2 on the z rows: the exact complementarity block's term s∘(z\v_z),
+// moved to the right-hand side so that the plain KKT SpMV gives K̂ᵀ's residual
+__global__ void k_adj_rhs(double* rp, const double* g, const double* t2, int np, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) rp[i] = g[i] + (i >= np && t2 ? t2[i - np] : 0.0);
+}
+__global__ void k_w2_zero(double* kval, const int64_t* slot, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) kval[slot[i]] = 0.0;
+}
+// ∂L/∂(data entry) for the entry at KKT position (a, b): −(u_a v_b + v_a u_b), halved
+// on the diagonal (P_ii); entries [0, nP) are P's, then A's, then G's
+__global__ void k_adj_data_grad(const int* __restrict__ ca, const int* __restrict__ cb, int64_t nnz,
+                                int64_t nP, int64_t nA, const double* __restrict__ u,
+                                const double* __restrict__ v, double* dP, double* dA, double* dG) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    double* out;
+    int64_t j;
+    if (k < nP) { out = dP; j = k; }
+    else if (k < nP + nA) { out = dA; j = k - nP; }
+    else { out = dG; j = k - nP - nA; }
+    if (!out) return;
+    const int a = ca[k], b = cb[k];
+    const double gk = -(u[a] * v[b] + v[a] * u[b]);
+    out[j] = a == b ? 0.5 * gk : gk;
+}
+__global__ void k_adj_vec_grad(const double* v, double* dc, double* db, double* dh, int n, int p, int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { if (dc) dc[i] = -v[i]; }
+    else if (i < n + p) { if (db) db[i - n] = v[i]; }
+    else if (i < n + p + m) { if (dh) dh[i - n - p] = v[i]; }
+}
+// KKT value slots fed by problem data ← the new values (src indexes [P | A | G])
+__global__ void k_scatter_data(double* kval, const int64_t* __restrict__ slot, const int64_t* __restrict__ src,
+                               int64_t n, const double* Pv, const double* Av, const double* Gv, int64_t nP,
+                               int64_t nA) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t k = src[i];
+    const double* p = k < nP ? Pv : k < nP + nA ? Av : Gv;
+    const int64_t j = k < nP ? k : k < nP + nA ? k - nP : k - nP - nA;
+    if (p) kval[slot[i]] = p[j];
+}
+// ‖c‖∞, ‖b‖∞, ‖h‖∞ (stopping-test scales) of the current data; one block
+__global__ void k_data_norms(const double* c, const double* b, const double* h, int n, int p, int m,
+                             IPMScalars* S) {
+    __shared__ double sm[3 * 32];
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a[0] = fmax(a[0], fabs(c[i]));
+    for (int i = threadIdx.x; i < p; i += blockDim.x) a[1] = fmax(a[1], fabs(b[i]));
+    for (int i = threadIdx.x; i < m; i += blockDim.x) a[2] = fmax(a[2], fabs(h[i]));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < 3; ++k) {
+        a[k] = warp_max_nonneg(a[k]);
+        if (lane == 0) sm[k * 32 + wid] = a[k];
+    }
+    __syncthreads();
+    if (wid == 0) {
+        for (int k = 0; k < 3; ++k) a[k] = warp_max_nonneg(lane < nw ? sm[k * 32 + lane] : 0.0);
+        if (lane == 0) { S->c_inf = a[0]; S->b_inf = a[1]; S->h_inf = a[2]; }
+    }
+}
+
 }  // namespace qoco
 
 using namespace qoco;
@@ -168,6 +234,14 @@ struct qoco_gpu_solver {
     double last_berr = 0.0;
     // polls a grid-barrier wait may take before it gives up (each poll sleeps ~64 ns)
     long long barrier_spins = 20000000;
+    bool have_solution = false;  // a solve completed (adjoint available)
+    // adjoint: KKT position (row, column) of one slot of each data entry [P | A | G]
+    int *d_adj_a = nullptr, *d_adj_b = nullptr;
+    int adj_steps = 0, adj_refactored = 0;
+    double adj_berr = 0.0;
+    // parametric update: KKT slots fed by data and their source index in [P | A | G]
+    int64_t *d_data_slot = nullptr, *d_data_src = nullptr;
+    int64_t n_data_slot = 0;
     int solve_epoch = 0;   // flag value of the latest dataflow solve
     int factor_epoch = 0;  // flag value of the latest dataflow factorisation
     qoco_gpu_info info;
@@ -349,6 +423,26 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         if ((rc = dcopy(S, &P.d_cdone, zeros))) return rc;
         if ((rc = plan_dataflow_factor(P, ph.max_f, !ph.large.empty()))) return rc;
         if (!P.dataflow && (rc = plan_persistent_solve(P, mwf, !ph.cta.empty()))) return rc;
+    }
+
+    // data-entry maps (adjoint coordinates, parametric-update scatter list)
+    {
+        const int64_t nd = K.nnzP + K.nnzA + K.nnzG;
+        std::vector<int> ca(nd, -1), cb(nd, -1);
+        std::vector<int64_t> dslot, dsrc;
+        for (int i = 0; i < N; ++i)
+            for (int64_t t = K.rowptr[i]; t < K.rowptr[i + 1]; ++t) {
+                const int64_t k = K.src[t];
+                if (k < 0) continue;
+                if (ca[k] < 0) { ca[k] = i; cb[k] = K.colidx[t]; }
+                dslot.push_back(t);
+                dsrc.push_back(k);
+            }
+        if ((rc = dcopy(S, &S->d_adj_a, ca))) return rc;
+        if ((rc = dcopy(S, &S->d_adj_b, cb))) return rc;
+        if ((rc = dcopy(S, &S->d_data_slot, dslot))) return rc;
+        if ((rc = dcopy(S, &S->d_data_src, dsrc))) return rc;
+        S->n_data_slot = (int64_t)dslot.size();
     }
 
     // iterate / work vectors
@@ -730,6 +824,7 @@ int qoco_gpu_solve(qoco_gpu_solver* S, void* stream) {
     if (e != cudaSuccess && status >= 0) status = cuda_fail(e, "stream sync", __FILE__, __LINE__);
     S->info.status = status;
     S->info.solve_time_s = now_s() - t0;
+    S->have_solution = status >= 0;
     return status;
 }
 
@@ -756,16 +851,165 @@ int qoco_gpu_solution_device(const qoco_gpu_solver* S, const double** x, const d
     return 0;
 }
 
+int qoco_gpu_copy_solution(const qoco_gpu_solver* S, double* x, double* s, double* y, double* z, void* stream) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (x && S->n) QOCO_CUDA_TRY(cudaMemcpyAsync(x, S->xyz, sizeof(double) * S->n, k, st));
+    if (y && S->p) QOCO_CUDA_TRY(cudaMemcpyAsync(y, S->xyz + S->n, sizeof(double) * S->p, k, st));
+    if (z && S->m) QOCO_CUDA_TRY(cudaMemcpyAsync(z, S->xyz + S->n + S->p, sizeof(double) * S->m, k, st));
+    if (s && S->m) QOCO_CUDA_TRY(cudaMemcpyAsync(s, S->s, sizeof(double) * S->m, k, st));
+    return 0;
+}
+
 int qoco_gpu_get_info(const qoco_gpu_solver* S, qoco_gpu_info* info) {
     if (!S || !info) return QOCO_GPU_ERR_INVALID_ARG;
     fill_info(S, info);
     return 0;
 }
 
-int qoco_gpu_backward(qoco_gpu_solver* S, const double*, const double*, const double*, double*, double*,
-                      double*, double*, double*, double*) {
+namespace {
+
+// v ← K̂⁻ᵀ g by refinement preconditioned with the current factor (see the header);
+// returns true when the backward error reached the refinement target
+int adjoint_refine(qoco_gpu_solver* S, const double* g, double* v, bool* ok, cudaStream_t st) {
+    const int n = S->n, p = S->p, m = S->m, N = S->N;
+    double* rp = S->d_cmb;
+    double* z = S->xyz + n + p;
+    const int64_t nw2 = (int64_t)S->K.w2_slot.size();
+    if (nw2) k_w2_zero<<<(unsigned)((nw2 + 255) / 256), 256, 0, st>>>(S->d_val, S->d_w2slot, nw2);
+    ++S->launches;
+    int rc = tri_solve(S, g, v, false, st);
+    if (rc) return rc;
+    const int max_steps = std::max(3 * S->st.max_refine, 10);
+    double best = INFINITY;
+    int stall = 0;
+    *ok = false;
+    for (int steps = 0;; ++steps) {
+        if (m) {
+            launch_div(S->cv, z, v + n + p, S->t1, st);
+            launch_prod(S->cv, S->s, S->t1, S->t2, st);
+            S->launches += 2 * cone_launch_count(S->cv);
+        }
+        k_adj_rhs<<<grid(N), 256, 0, st>>>(rp, g, m ? S->t2 : nullptr, n + p, N);
+        ++S->launches;
+        if (launch_spmv_res(S->kv, S->lpr, v, rp, S->res, S->partial, S->partial_cap, S->d_S, st))
+            return QOCO_GPU_ERR_INVALID_ARG;
+        S->launches += 2;
+        QOCO_CUDA_TRY(cudaGetLastError());
+        if ((rc = sync_scalars(S, st))) return rc;
+        if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
+        const double berr = S->h_S->berr;
+        S->adj_steps = steps;
+        S->adj_berr = berr;
+        if (!std::isfinite(berr)) return 0;
+        if (berr <= S->st.refine_tol) { *ok = true; return 0; }
+        if (berr < 0.5 * best) { best = berr; stall = 0; }
+        else if (++stall >= 4) return 0;
+        if (steps >= max_steps) return 0;
+        if ((rc = tri_solve(S, S->res, v, true, st))) return rc;
+    }
+}
+
+}  // namespace
+
+int qoco_gpu_backward(qoco_gpu_solver* S, const double* dx, const double* dy, const double* dz, double* dP_val,
+                      double* dc, double* dA_val, double* db, double* dG_val, double* dh, void* stream) {
     if (!S) return QOCO_GPU_ERR_INVALID_ARG;
-    return QOCO_GPU_ERR_NOT_IMPLEMENTED;
+    if (!S->have_solution || !S->have_factor) return QOCO_GPU_ERR_NO_FACTOR;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = S->n, p = S->p, m = S->m, N = S->N;
+    double* g = S->rhs;
+    double* v = S->d_aff;
+    QOCO_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(double) * N, st));
+    if (dx && n) QOCO_CUDA_TRY(cudaMemcpyAsync(g, dx, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    if (dy && p) QOCO_CUDA_TRY(cudaMemcpyAsync(g + n, dy, sizeof(double) * p, cudaMemcpyDeviceToDevice, st));
+    if (dz && m) QOCO_CUDA_TRY(cudaMemcpyAsync(g + n + p, dz, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+    int rc = reset_barrier(S, st);
+    if (rc) return rc;
+    S->adj_refactored = 0;
+    bool ok = false;
+    if ((rc = adjoint_refine(S, g, v, &ok, st))) return rc;
+    if (!ok && m) {
+        // refactor once at the final iterate's NT scaling, then refine again
+        launch_nt_scaling(S->cv, S->s, S->xyz + n + p, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot,
+                          S->d_w2ptr, st);
+        S->launches += cone_launch_count(S->cv);
+        if ((rc = factor_now(S, st))) return rc;
+        S->adj_refactored = 1;
+        if ((rc = adjoint_refine(S, g, v, &ok, st))) return rc;
+    }
+    if (!ok) return QOCO_GPU_ERR_NUMERICAL;
+    const int64_t nd = S->K.nnzP + S->K.nnzA + S->K.nnzG;
+    if (nd && (dP_val || dA_val || dG_val)) {
+        k_adj_data_grad<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(S->d_adj_a, S->d_adj_b, nd, S->K.nnzP,
+                                                                      S->K.nnzA, S->xyz, v, dP_val, dA_val, dG_val);
+        ++S->launches;
+    }
+    k_adj_vec_grad<<<grid(N), 256, 0, st>>>(v, dc, db, dh, n, p, m);
+    ++S->launches;
+    QOCO_CUDA_TRY(cudaGetLastError());
+    QOCO_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+int qoco_gpu_backward_info(const qoco_gpu_solver* S, int* refine_steps, double* backward_error, int* refactored) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    if (refine_steps) *refine_steps = S->adj_steps;
+    if (backward_error) *backward_error = S->adj_berr;
+    if (refactored) *refactored = S->adj_refactored;
+    return 0;
+}
+
+int qoco_gpu_update_data(qoco_gpu_solver* S, const double* P_val, const double* c, const double* A_val,
+                         const double* b, const double* G_val, const double* h, int on_device, void* stream) {
+    if (!S) return QOCO_GPU_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const KKTPattern& K = S->K;
+    const int n = S->n, p = S->p, m = S->m;
+    if (!on_device) {
+        auto finite = [](const double* v, int64_t len) {
+            for (int64_t i = 0; v && i < len; ++i)
+                if (!std::isfinite(v[i])) return false;
+            return true;
+        };
+        if (!finite(P_val, K.nnzP) || !finite(c, n) || !finite(A_val, K.nnzA) || !finite(b, p) ||
+            !finite(G_val, K.nnzG) || !finite(h, m)) {
+            S->msg = "update_data: non-finite value";
+            return QOCO_GPU_ERR_NONFINITE_DATA;
+        }
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // matrix values: host values are staged through the work vectors' storage so that one
+    // scatter kernel serves both cases
+    const double* src[3] = {P_val, A_val, G_val};
+    const int64_t len[3] = {K.nnzP, K.nnzA, K.nnzG};
+    double* dev[3] = {nullptr, nullptr, nullptr};
+    std::vector<void*> tmp;
+    for (int k = 0; k < 3; ++k) {
+        if (!src[k] || !len[k]) continue;
+        if (on_device) { dev[k] = const_cast<double*>(src[k]); continue; }
+        void* d = nullptr;
+        QOCO_CUDA_TRY(cudaMallocAsync(&d, sizeof(double) * len[k], st));
+        tmp.push_back(d);
+        QOCO_CUDA_TRY(cudaMemcpyAsync(d, src[k], sizeof(double) * len[k], kind, st));
+        S->h2d_bytes += (int64_t)sizeof(double) * len[k];
+        dev[k] = (double*)d;
+    }
+    if (S->n_data_slot && (dev[0] || dev[1] || dev[2])) {
+        k_scatter_data<<<(unsigned)((S->n_data_slot + 255) / 256), 256, 0, st>>>(
+            S->d_val, S->d_data_slot, S->d_data_src, S->n_data_slot, dev[0], dev[1], dev[2], K.nnzP, K.nnzA);
+    }
+    if (c && n) QOCO_CUDA_TRY(cudaMemcpyAsync(S->d_c, c, sizeof(double) * n, kind, st));
+    if (b && p) QOCO_CUDA_TRY(cudaMemcpyAsync(S->d_b, b, sizeof(double) * p, kind, st));
+    if (h && m) QOCO_CUDA_TRY(cudaMemcpyAsync(S->d_h, h, sizeof(double) * m, kind, st));
+    if (!on_device) S->h2d_bytes += (int64_t)sizeof(double) * ((c ? n : 0) + (b ? p : 0) + (h ? m : 0));
+    k_data_norms<<<1, 256, 0, st>>>(S->d_c, S->d_b, S->d_h, n, p, m, S->d_S);
+    for (void* d : tmp) QOCO_CUDA_TRY(cudaFreeAsync(d, st));
+    QOCO_CUDA_TRY(cudaGetLastError());
+    S->have_solution = false;
+    S->have_factor = false;
+    return 0;
 }
 
 int qoco_gpu_set_profiling(qoco_gpu_solver* S, int on) {
