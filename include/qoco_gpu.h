@@ -84,6 +84,11 @@ typedef struct {
                                            subtree tasks below the level launches; ≤ 0 = none,
                                            every supernode in level launches (default 0) */
     int verbose;                        /* 0: silent; 1: one line per iteration on stdout */
+    int mixed_precision;                /* 1: fronts of order ≥ 256 factored in FP32 (FP32
+                                           accumulation), solves and refinement in FP64; a
+                                           solve whose refinement misses refine_tol within
+                                           max_refine steps refactors in FP64, and the rest
+                                           of that qoco_gpu_solve stays FP64 (default 0) */
 } qoco_gpu_settings;
 
 typedef struct {
@@ -105,6 +110,10 @@ typedef struct {
     int64_t kernel_launches;    /* this library's kernel launches during the last solve */
     int64_t h2d_bytes;          /* host→device bytes copied by setup */
     int64_t d2h_bytes;          /* device→host bytes read back during the last solve */
+    int large_fronts;           /* fronts factored by the grid-wide large-front kernels */
+    int fp32_factors;           /* factorisations of the last solve with FP32 large fronts */
+    int fp64_escalations;       /* refinements that missed the target on an FP32 factor */
+    int pad_info;
     char message[160];
 } qoco_gpu_info;
 

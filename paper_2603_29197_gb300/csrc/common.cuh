@@ -39,6 +39,13 @@ __device__ __forceinline__ double warp_max_nonneg(double v) {
     }
     return __longlong_as_double(b);
 }
+// max of a non-negative accumulator a and |b| through bit patterns, with b's sign bit
+// cleared on the integer pipe: a NaN of either sign ends above +inf in that order and
+// propagates, where fmax would drop it
+__device__ __forceinline__ double amax(double a, double b) {
+    const long long bb = __double_as_longlong(b) & 0x7fffffffffffffffLL;
+    return bb > __double_as_longlong(a) ? __longlong_as_double(bb) : a;
+}
 __device__ __forceinline__ double warp_min_nonneg(double v) {
     long long b = __double_as_longlong(v);
 #pragma unroll

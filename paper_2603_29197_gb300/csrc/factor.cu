@@ -1064,6 +1064,7 @@ int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, 
             k_front_factor<false><<<L.n_large, 256, sm, st>>>(P.d_large + L.off_large, a, kval);
             ++launches;
         }
+        for (int t = 0; t < L.n_big; ++t) launches += launch_big_factor(P, a, kval, L.off_big + t, st);
     }
     return launches;
 }
@@ -1094,6 +1095,7 @@ int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, do
             k_fwd<<<L.n_cta, 128, (size_t)L.max_cta_f * sizeof(double), st>>>(P.d_cta + L.off_cta, a, rhs, w);
             ++launches;
         }
+        for (int t = 0; t < L.n_big; ++t) launches += launch_big_fwd(P, a, rhs, w, L.off_big + t, st);
     }
     for (int lv = nl - 1; lv >= 0; --lv) {
         const LevelPlan& L = P.levels[lv];
@@ -1111,6 +1113,7 @@ int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, do
             k_bwd<<<L.n_cta, 128, (size_t)L.max_cta_f * sizeof(double), st>>>(P.d_cta + L.off_cta, a, w, xp, x, acc);
             ++launches;
         }
+        for (int t = 0; t < L.n_big; ++t) launches += launch_big_bwd(P, a, w, xp, x, accumulate, L.off_big + t, st);
     }
     if (P.ntasks) {
         k_task_bwd<<<wblocks(P.ntasks), kWarpsPerBlock * 32, wsolve_smem(P.task_max_f), st>>>(

@@ -73,6 +73,16 @@ struct FactorPlan {
     int* d_ftb_ptr = nullptr;
     int* d_fwg_ptr = nullptr;
     int* d_cdone = nullptr;  // per supernode: epoch of its finished factorisation
+    // large fronts (grid-wide kernel sequences, bigfront.cu); host lists indexed by the
+    // levels' off_big/n_big
+    std::vector<int> big_s, big_f, big_c;
+    std::vector<int64_t> big_front_off, big_amap_n;
+    int max_big_f = 0;
+    bool big_fp32 = false;         // factor large fronts in FP32 (mixed precision)
+    float* big_work32 = nullptr;   // max_big_f² FP32 working front
+    void* big_w = nullptr;         // max_big_f × kBigNB (FP64 or FP32) panel rows W
+    double* big_v = nullptr;       // max_big_f solve work vector
+    double* big_y = nullptr;       // max_big_f solved block values
 };
 
 // Shared state of one dataflow solve launch.
@@ -100,6 +110,12 @@ int launch_solve_persistent(const FactorPlan& P, const FactorView& a, const doub
                             double* xp, double* x, bool accumulate, const GridBarrier& bar,
                             cudaStream_t st);
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
+// One large front (P.big_*[idx]): partial LDLᵀ, or the forward / backward solve step.
+int launch_big_factor(const FactorPlan& P, const FactorView& a, const double* kval, int idx, cudaStream_t st);
+int launch_big_fwd(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, int idx,
+                   cudaStream_t st);
+int launch_big_bwd(const FactorPlan& P, const FactorView& a, const double* w, double* xp, double* x,
+                   bool accumulate, int idx, cudaStream_t st);
 int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
                  double* x, bool accumulate, cudaStream_t st);
 

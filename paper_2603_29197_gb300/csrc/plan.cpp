@@ -78,14 +78,22 @@ void build_plan(const Symbolic& S, bool allow_tasks, int target_tasks, PlanHost*
         L.off_sthread = (int)P->sthread.size();
         L.off_swarp = (int)P->swarp.size();
         L.off_cta = (int)P->cta.size();
+        L.off_big = (int)P->big.size();
         // A level with few fronts cannot fill the GPU with one warp per front, and each
         // warp would walk its front's long dependent FP64 chain alone: in the
         // factorisation such levels get a CTA per front (its threads split every
         // update).  Wide levels keep one warp (or one thread) per front for throughput.
-        int nmid = 0;
-        for (int s : byl[l]) nmid += f[s] > kThreadFront;
+        int nmid = 0, nbig = 0;
+        for (int s : byl[l]) {
+            nmid += f[s] > kThreadFront;
+            nbig += f[s] >= kBigFront;
+        }
         const bool wide = nmid >= kWideLevel;
         for (int s : byl[l]) {
+            if (f[s] >= kHugeFront || (f[s] >= kBigFront && nbig <= kBigPerLevel)) {
+                P->big.push_back(s);
+                continue;
+            }
             if (f[s] <= kThreadFront && (wide || nmid == 0)) {
                 P->thread.push_back(s);
             } else if (f[s] <= kWarpFront && wide) {
@@ -115,6 +123,7 @@ void build_plan(const Symbolic& S, bool allow_tasks, int target_tasks, PlanHost*
         L.n_sthread = (int)P->sthread.size() - L.off_sthread;
         L.n_swarp = (int)P->swarp.size() - L.off_swarp;
         L.n_cta = (int)P->cta.size() - L.off_cta;
+        L.n_big = (int)P->big.size() - L.off_big;
     }
     // dataflow items, level by level: batches of 32 one-thread fronts, then warp fronts.
     // The one-thread fronts of consecutive levels are contiguous in sthread, so batch b
@@ -148,7 +157,8 @@ void build_plan(const Symbolic& S, bool allow_tasks, int target_tasks, PlanHost*
     }
     // drop empty trailing levels
     while (!P->levels.empty() &&
-           P->levels.back().n_sthread + P->levels.back().n_swarp + P->levels.back().n_cta == 0)
+           P->levels.back().n_sthread + P->levels.back().n_swarp + P->levels.back().n_cta +
+                   P->levels.back().n_big == 0)
         P->levels.pop_back();
 }
 

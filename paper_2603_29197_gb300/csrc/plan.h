@@ -14,6 +14,13 @@ constexpr int kThreadFront = 8;     // fronts up to this order are handled by on
 constexpr int kWarpFront = 48;      // fronts up to this order are handled by one warp
 constexpr int kWarpsPerBlock = 4;    // warps per block of the warp-level kernels
 constexpr int kWideLevel = 2432;     // levels with at least this many fronts (16 per SM) use warps
+// Fronts at least this large are factored and solved by grid-wide kernel sequences
+// (panels of kBigNB columns), one front after the other, when their level holds at most
+// kBigPerLevel of them; fronts of at least kHugeFront always are.
+constexpr int kBigFront = 256;
+constexpr int kHugeFront = 1024;
+constexpr int kBigPerLevel = 64;
+constexpr int kBigNB = 64;
 
 // Launch plan of one factorisation / solve.  Supernodes are split into
 //  * subtree tasks: a task is a whole subtree of small fronts whose supernodes occupy a
@@ -33,6 +40,8 @@ struct LevelPlan {
     int n_sthread = 0, off_sthread = 0;
     int n_swarp = 0, off_swarp = 0, max_swarp_f = 0;
     int n_cta = 0, off_cta = 0, max_cta_f = 0;
+    // large fronts (factor and solves): big[off_big .. off_big + n_big)
+    int n_big = 0, off_big = 0;
 };
 
 // Host-side lists from which the device plan is uploaded.
@@ -40,6 +49,7 @@ struct PlanHost {
     std::vector<LevelPlan> levels;
     std::vector<int> task, thread, warp, small, large;  // factorisation
     std::vector<int> sthread, swarp, cta;               // solves
+    std::vector<int> big;                               // large fronts (factor and solves)
     // dataflow solve: work items in topological (level) order; item ≥ 0 is a warp
     // front, item < 0 is the batch −(item+1) of ≤ 32 one-thread fronts
     // (sthread[tb_ptr[b] .. tb_ptr[b+1]))

@@ -62,26 +62,26 @@ __global__ void __launch_bounds__(kRowThreads) k_residual(KKTView K, const doubl
                 r[row] = rx;
                 v[0] += xyz[row] * a0;  // xᵀPx
                 v[1] += c[row] * xyz[row];
-                v[5] = fmax(v[5], fabs(a0));   // |Px|
-                v[6] = fmax(v[6], fabs(a1));   // |Aᵀy|
-                v[7] = fmax(v[7], fabs(a2));   // |Gᵀz|
-                v[10] = fmax(v[10], fabs(rx));
+                v[5] = amax(v[5], a0);   // |Px|
+                v[6] = amax(v[6], a1);   // |Aᵀy|
+                v[7] = amax(v[7], a2);   // |Gᵀz|
+                v[10] = amax(v[10], rx);
             } else if (row < n + p) {
                 const int i = row - n;
                 const double ry = a0 - b[i];
                 r[row] = ry;
                 v[2] += b[i] * xyz[row];
-                v[8] = fmax(v[8], fabs(a0));   // |Ax|
-                v[11] = fmax(v[11], fabs(ry));
+                v[8] = amax(v[8], a0);   // |Ax|
+                v[11] = amax(v[11], ry);
             } else {
                 const int i = row - n - p;
                 const double rz = a0 + s[i] - h[i];
                 r[row] = rz;
                 v[3] += h[i] * xyz[row];
                 v[4] += s[i] * xyz[row];
-                v[9] = fmax(v[9], fabs(a0));   // |Gx|
-                v[12] = fmax(v[12], fabs(rz));
-                v[13] = fmax(v[13], fabs(s[i]));
+                v[9] = amax(v[9], a0);   // |Gx|
+                v[12] = amax(v[12], rz);
+                v[13] = amax(v[13], s[i]);
             }
         }
     }
@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_res(KKTView K, const doubl
         if (row < K.N && lane == 0) {
             const double e = r[row] - acc;
             res[row] = e;
-            v[0] = fmax(v[0], fabs(e));
-            v[1] = fmax(v[1], fabs(x[row]));
-            v[2] = fmax(v[2], fabs(r[row]));
+            v[0] = amax(v[0], e);
+            v[1] = amax(v[1], x[row]);
+            v[2] = amax(v[2], r[row]);
         }
     }
     store_partials<3>(v, is_max, partial);
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kRowThreads) k_norm_inf(KKTView K, double* par
         if (row < K.N)
             for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR) acc += fabs(K.val[t]);
         acc = group_sum<LPR>(acc);
-        v[0] = fmax(v[0], acc);
+        v[0] = amax(v[0], acc);
     }
     store_partials<1>(v, is_max, partial);
 }
@@ -191,10 +191,13 @@ __global__ void k_finalize_refine(const double* __restrict__ partial, int nb, IP
     __shared__ double red[3];
     reduce_columns(partial, nb, 3, 7u, red);
     if (threadIdx.x != 0) return;
+    // a non-finite residual, iterate or right-hand side ends the refinement with a
+    // non-finite backward error (the caller sees it and does not accept the solve)
+    const bool finite = isfinite(red[0]) && isfinite(red[1]) && isfinite(red[2]);
     const double den = S->normK * red[1] + red[2];
-    const double be = den > 0.0 ? red[0] / den : 0.0;
+    const double be = !finite ? __longlong_as_double(0x7ff8000000000000LL) : den > 0.0 ? red[0] / den : 0.0;
     S->berr = be;
-    S->refine_done = (be <= S->refine_tol || !isfinite(be)) ? 1 : 0;
+    S->refine_done = (!finite || be <= S->refine_tol) ? 1 : 0;
 }
 
 __global__ void k_finalize_norm(const double* __restrict__ partial, int nb, IPMScalars* S) {

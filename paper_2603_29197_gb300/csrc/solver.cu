@@ -235,6 +235,7 @@ struct qoco_gpu_solver {
     // polls a grid-barrier wait may take before it gives up (each poll sleeps ~64 ns)
     long long barrier_spins = 20000000;
     bool have_solution = false;  // a solve completed (adjoint available)
+    int fp32_factors = 0, fp64_escalations = 0;
     // adjoint: KKT position (row, column) of one slot of each data entry [P | A | G]
     int *d_adj_a = nullptr, *d_adj_b = nullptr;
     int adj_steps = 0, adj_refactored = 0;
@@ -388,12 +389,36 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     // launch plan: subtree tasks + level lists
     PlanHost ph;
     build_plan(Y, S->st.subtree_tasks > 0, S->st.subtree_tasks, &ph);
-    if (ph.max_f > kMaxSolveFront || ph.max_f > kMaxFactorFront) {
-        S->msg = "a supernode front exceeds the factor/solve kernels' shared-memory limit";
-        return QOCO_GPU_ERR_NOT_IMPLEMENTED;
+    {
+        int max_small = 0, max_big = 0;
+        std::vector<char> is_big(Y.ns, 0);
+        for (int s : ph.big) is_big[s] = 1;
+        for (int s = 0; s < Y.ns; ++s)
+            (is_big[s] ? max_big : max_small) = std::max(is_big[s] ? max_big : max_small, Y.sn_nrow[s]);
+        if (max_small > kMaxSolveFront || max_small > kMaxFactorFront || max_big > 46340) {
+            S->msg = "a supernode front exceeds the factor/solve kernels' limits";
+            return QOCO_GPU_ERR_NOT_IMPLEMENTED;
+        }
     }
     FactorPlan& P = S->plan;
     P.levels = ph.levels;
+    for (int s : ph.big) {
+        P.big_s.push_back(s);
+        P.big_f.push_back(Y.sn_nrow[s]);
+        P.big_c.push_back(Y.sn_ncol[s]);
+        P.big_front_off.push_back(Y.front_off[s]);
+        P.big_amap_n.push_back(Y.amap_ptr[s + 1] - Y.amap_ptr[s]);
+        P.max_big_f = std::max(P.max_big_f, Y.sn_nrow[s]);
+    }
+    if (P.max_big_f) {
+        double* pw;
+        if ((rc = dalloc(S, &pw, (size_t)P.max_big_f * kBigNB))) return rc;
+        P.big_w = pw;
+        if ((rc = dalloc(S, &P.big_v, P.max_big_f))) return rc;
+        if ((rc = dalloc(S, &P.big_y, P.max_big_f))) return rc;
+        if (S->st.mixed_precision && (rc = dalloc(S, &P.big_work32, (size_t)P.max_big_f * P.max_big_f))) return rc;
+    }
+    S->info.large_fronts = (int)ph.big.size();
     P.ntasks = (int)ph.task.size() / 2;
     P.task_max_f = ph.task_max_f;
     P.task_height = ph.task_height;
@@ -415,14 +440,15 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         std::vector<int> zeros(Y.ns, 0);
         if ((rc = dcopy(S, &P.d_fdone, zeros))) return rc;
         if ((rc = dcopy(S, &P.d_bdone, zeros))) return rc;
-        if ((rc = plan_dataflow_solve(P, mwf, !ph.cta.empty()))) return rc;
+        const bool any_cta = !ph.cta.empty() || !ph.big.empty();
+        if ((rc = plan_dataflow_solve(P, mwf, any_cta))) return rc;
         P.nfitems = (int)ph.fitems.size();
         if ((rc = dcopy(S, &P.d_fitems, ph.fitems))) return rc;
         if ((rc = dcopy(S, &P.d_ftb_ptr, ph.ftb_ptr))) return rc;
         if ((rc = dcopy(S, &P.d_fwg_ptr, ph.fwg_ptr))) return rc;
         if ((rc = dcopy(S, &P.d_cdone, zeros))) return rc;
-        if ((rc = plan_dataflow_factor(P, ph.max_f, !ph.large.empty()))) return rc;
-        if (!P.dataflow && (rc = plan_persistent_solve(P, mwf, !ph.cta.empty()))) return rc;
+        if ((rc = plan_dataflow_factor(P, ph.max_f, !ph.large.empty() || !ph.big.empty()))) return rc;
+        if (!P.dataflow && (rc = plan_persistent_solve(P, mwf, any_cta))) return rc;
     }
 
     // data-entry maps (adjoint coordinates, parametric-update scatter list)
@@ -507,6 +533,7 @@ int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
         }
     }
     QOCO_CUDA_TRY(cudaGetLastError());
+    if (S->plan.big_fp32) ++S->fp32_factors;
     S->have_factor = true;
     return 0;
 }
@@ -537,29 +564,38 @@ int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStre
     return 0;
 }
 
-// x = K_ε⁻¹ r refined against K until the backward error target (r, x device, N)
+// x = K_ε⁻¹ r refined against K until the backward error target (r, x device, N).  On a
+// factor with FP32 large fronts, a refinement that misses the target refactors in FP64
+// (for the rest of the current solve) and starts over.
 int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st) {
-    int rc0 = tri_solve(S, r, x, false, st);
-    if (rc0) return rc0;
-    int steps = 0;
     for (;;) {
-        {
-            Phase ph(S, QOCO_GPU_PHASE_ROW, st);
-            if (launch_spmv_res(S->kv, S->lpr, x, r, S->res, S->partial, S->partial_cap, S->d_S, st))
-                return QOCO_GPU_ERR_INVALID_ARG;
-            S->launches += 2;
+        int rc0 = tri_solve(S, r, x, false, st);
+        if (rc0) return rc0;
+        int steps = 0;
+        for (;;) {
+            {
+                Phase ph(S, QOCO_GPU_PHASE_ROW, st);
+                if (launch_spmv_res(S->kv, S->lpr, x, r, S->res, S->partial, S->partial_cap, S->d_S, st))
+                    return QOCO_GPU_ERR_INVALID_ARG;
+                S->launches += 2;
+            }
+            QOCO_CUDA_TRY(cudaGetLastError());
+            int rc = sync_scalars(S, st);
+            if (rc) return rc;
+            if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
+            if (S->h_S->refine_done || steps >= S->st.max_refine) break;
+            if ((rc = tri_solve(S, S->res, x, true, st))) return rc;
+            ++steps;
         }
-        QOCO_CUDA_TRY(cudaGetLastError());
-        int rc = sync_scalars(S, st);
+        S->refine_steps += steps;
+        S->last_berr = S->h_S->berr;
+        const bool ok = S->h_S->refine_done && std::isfinite(S->h_S->berr);
+        if (ok || !S->plan.big_fp32) return 0;
+        S->plan.big_fp32 = false;
+        ++S->fp64_escalations;
+        int rc = factor_now(S, st);
         if (rc) return rc;
-        if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
-        if (S->h_S->refine_done || steps >= S->st.max_refine) break;
-        if ((rc = tri_solve(S, S->res, x, true, st))) return rc;
-        ++steps;
     }
-    S->refine_steps += steps;
-    S->last_berr = S->h_S->berr;
-    return 0;
 }
 
 int cone_launch_count(const ConeView& c) { return cone_grid(c).blocks() ? 1 : 0; }
@@ -575,6 +611,9 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
     const int cl = cone_launch_count(cv);
     int rc;
     S->refine_steps = 0;
+    S->fp32_factors = 0;
+    S->fp64_escalations = 0;
+    S->plan.big_fp32 = S->st.mixed_precision != 0 && S->plan.max_big_f > 0 && S->plan.big_work32;
     if ((rc = reset_barrier(S, st))) return rc;
     // initial point: K(W = I) [x; y; z] = [−c; b; h], s = −z, shift s and z into the cone
     launch_w2_identity(cv, S->d_val, S->d_w2slot, S->d_w2ptr, st);
@@ -692,6 +731,8 @@ void fill_info(const qoco_gpu_solver* S, qoco_gpu_info* info) {
     info->kernel_launches = S->launches;
     info->h2d_bytes = S->h2d_bytes;
     info->d2h_bytes = S->d2h_bytes;
+    info->fp32_factors = S->fp32_factors;
+    info->fp64_escalations = S->fp64_escalations;
     snprintf(info->message, sizeof info->message, "%s", S->msg.c_str());
 }
 
@@ -731,6 +772,7 @@ void qoco_gpu_default_settings(qoco_gpu_settings* s) {
     s->nd_leaf = 64;
     s->subtree_tasks = 0;
     s->verbose = 0;
+    s->mixed_precision = 0;
 }
 
 int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A, const qoco_csc* G, int l,
@@ -1039,6 +1081,7 @@ int qoco_gpu_kkt_factor_at(qoco_gpu_solver* S, const double* s, const double* z,
     if (!S || (S->m && (!s || !z))) return QOCO_GPU_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     launch_nt_scaling(S->cv, s, z, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot, S->d_w2ptr, st);
+    S->plan.big_fp32 = S->st.mixed_precision != 0 && S->plan.max_big_f > 0 && S->plan.big_work32;
     int rc = factor_now(S, st);
     if (rc) return rc;
     QOCO_CUDA_TRY(cudaStreamSynchronize(st));

@@ -18,11 +18,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 from oracle import ipm  # noqa: E402
-from workloads import portfolio_socp, trajectory_socp  # noqa: E402
+from workloads import lasso_qp, portfolio_socp, trajectory_socp  # noqa: E402
 
 CASES = {
     "trajectory_socp_N20000": lambda: trajectory_socp(N=20000, seed=0),
     "portfolio_socp_n20000": lambda: portfolio_socp(n=20000, k=200, seed=0),
+    # the lasso QP scaled by 1/10 per dimension with the same 50 nonzeros per row of F
+    "lasso_qp_r5000_c10000": lambda: lasso_qp(rows=5000, cols=10000, density=5e-3, seed=0),
 }
 
 
