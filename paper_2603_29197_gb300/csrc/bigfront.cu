@@ -58,74 +58,116 @@ __global__ void k_big_assemble(int s, FactorView a, const double* __restrict__ k
     }
 }
 
-// extend-add of every child's update block; one warp per parent column j
+// extend-add of every child's update block; one warp per parent column j walks the
+// child columns that land on j (precomputed list, child order) and adds them
 template <class T>
-__global__ void k_big_extend_add(int s, FactorView a, T* __restrict__ F) {
+__global__ void k_big_extend_add(int s, FactorView a, const int64_t* __restrict__ ea_ptr,
+                                 const int* __restrict__ ea_child, const int* __restrict__ ea_pos, T* __restrict__ F) {
     const int f = a.nrow[s];
     const int lane = threadIdx.x & 31;
     const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (j >= f) return;
-    for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
-        const ChildInfo ci = a.cinfo[k];
+    T* Fj = F + (int64_t)j * f;
+    for (int64_t e = ea_ptr[j]; e < ea_ptr[j + 1]; ++e) {
+        const ChildInfo ci = a.cinfo[ea_child[e]];
+        const int jj = ea_pos[e];
         const int* rel = a.rel + ci.rel_off;
-        // the child column that lands in parent column j (rel is increasing)
-        int lo = 0, hi = ci.r;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (rel[mid] < j) lo = mid + 1;
-            else hi = mid;
-        }
-        if (lo >= ci.r || rel[lo] != j) continue;
-        const double* U = a.front + ci.u_off + (int64_t)lo * ci.fc;
-        T* Fj = F + (int64_t)j * f;
-        for (int ii = lo + lane; ii < ci.r; ii += 32) Fj[rel[ii]] += (T)U[ii];
+        const double* U = a.front + ci.u_off + (int64_t)jj * ci.fc;
+        for (int ii = jj + lane; ii < ci.r; ii += 32) Fj[rel[ii]] += (T)U[ii];
     }
 }
 
-// LDLᵀ of the nb×nb diagonal block at (k0, k0); one CTA
+// LDLᵀ of the nb×nb diagonal block at (k0, k0); one CTA.  Columns stay unscaled until
+// the end, and the thread that owns the next diagonal entry computes the next pivot as
+// soon as it has applied the current column to it, so each column costs one barrier.
+// Entry (i, j) of the lower triangle belongs to thread (i·(i+1)/2 + j) mod blockDim.
 template <class T>
-__global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorView a, T* __restrict__ F) {
+__global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorView a, T* __restrict__ F,
+                                                  double* __restrict__ Xinv) {
+    constexpr int kOwn = (kBigNB * (kBigNB + 1) / 2 + 255) / 256;  // entries per thread
     __shared__ T D[kBigNB][kBigNB + 1];
-    __shared__ T s_inv;
+    __shared__ T s_inv[kBigNB];
     const int f = a.nrow[s], first = a.first[s];
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int ntri = nb * (nb + 1) / 2;
     for (int t = tid; t < nb * nb; t += nt) {
         const int j = t / nb, i = t - j * nb;
         if (i >= j) D[i][j] = F[(int64_t)(k0 + j) * f + k0 + i];
     }
+    // this thread's entries (i, j) of the lower triangle, i ≥ j, in a fixed order
+    int oi[kOwn], oj[kOwn];
+#pragma unroll
+    for (int u = 0; u < kOwn; ++u) {
+        const int t = tid + u * 256;
+        if (t < ntri) {
+            int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while ((i + 1) * (i + 2) / 2 <= t) ++i;
+            while (i * (i + 1) / 2 > t) --i;
+            oi[u] = i;
+            oj[u] = t - i * (i + 1) / 2;
+        } else {
+            oi[u] = -1;
+            oj[u] = kBigNB;
+        }
+    }
     __syncthreads();
     int nreg = 0;
+    auto pivot = [&](int k) {
+        double d = (double)D[k][k];
+        const bool pos = a.dsign[first + k0 + k] > 0;
+        const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
+        if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
+        const T dt = (T)d;
+        D[k][k] = dt;
+        s_inv[k] = rcp_t<T>(dt);
+    };
+    if (tid == 0) pivot(0);
+    __syncthreads();
     for (int k = 0; k < nb; ++k) {
-        if (tid == 0) {
-            double d = (double)D[k][k];
-            const bool pos = a.dsign[first + k0 + k] > 0;
-            const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
-            if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
-            const T dt = (T)d;
-            D[k][k] = dt;
-            s_inv = rcp_t<T>(dt);
-            a.dinv[first + k0 + k] = recip((double)dt);
+        const T inv = s_inv[k];
+#pragma unroll
+        for (int u = 0; u < kOwn; ++u) {
+            const int i = oi[u], j = oj[u];
+            if (j <= k) continue;
+            D[i][j] -= D[i][k] * D[j][k] * inv;
+            if (i == k + 1 && j == k + 1) pivot(k + 1);
         }
-        __syncthreads();
-        const T inv = s_inv;
-        const int m = nb - k - 1;
-        // rank-1 update of the block's trailing lower triangle with the unscaled column
-        for (int t = tid; t < m * m; t += nt) {
-            const int jj = t / m, ii = t - jj * m;
-            if (ii >= jj) {
-                const int i = k + 1 + ii, j = k + 1 + jj;
-                D[i][j] -= D[i][k] * D[j][k] * inv;
-            }
-        }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < nb; i += nt) D[i][k] *= inv;
         __syncthreads();
     }
+    // FP64 reciprocal pivots for the solves (off the pivot chain)
+    for (int k = tid; k < nb; k += nt) a.dinv[first + k0 + k] = recip((double)D[k][k]);
+    // L (scaled columns) and D back to the front; the strictly lower part of D becomes L
     for (int t = tid; t < nb * nb; t += nt) {
         const int j = t / nb, i = t - j * nb;
-        if (i >= j) F[(int64_t)(k0 + j) * f + k0 + i] = D[i][j];
+        if (i > j) {
+            const T l = D[i][j] * s_inv[j];
+            F[(int64_t)(k0 + j) * f + k0 + i] = l;
+            D[i][j] = l;
+        } else if (i == j) {
+            F[(int64_t)(k0 + j) * f + k0 + i] = D[i][j];
+        }
     }
-    if (tid == 0 && nreg) atomicAdd(a.nreg, nreg);
+    __syncthreads();
+    // in-place inverse of the unit lower triangle (in the working precision): after step
+    // k, rows ≤ k hold L⁻¹'s rows; row i > k takes X_ij ← X_ij − L_ik·X_kj for j < k and
+    // X_ik ← −L_ik (L_ik is read from column k before that column is overwritten)
+    for (int k = 0; k < nb - 1; ++k) {
+        const int m = nb - 1 - k;  // rows k+1 .. nb−1
+        for (int t = tid; t < m * k; t += nt) {
+            const int ii = t / k, j = t - ii * k;
+            const int i = k + 1 + ii;
+            D[i][j] -= D[i][k] * D[k][j];
+        }
+        __syncthreads();
+        for (int i = k + 1 + tid; i < nb; i += nt) D[i][k] = -D[i][k];
+        __syncthreads();
+    }
+    // store row-major: Xinv[i·kBigNB + j] = (L_bb⁻¹)_ij (unit diagonal, zero above)
+    for (int t = tid; t < nb * nb; t += nt) {
+        const int i = t / nb, j = t - i * nb;
+        Xinv[i * kBigNB + j] = j < i ? (double)D[i][j] : (j == i ? 1.0 : 0.0);
+    }
+    if (nreg) atomicAdd(a.nreg, nreg);
 }
 
 // rows i ≥ k0+nb: w = a_i· L11⁻ᵀ, l_i· = w D⁻¹ (into F), w into W[i·kBigNB + k]
@@ -244,48 +286,58 @@ __global__ void k_big_writeback(const float* __restrict__ Fw, double* __restrict
 }
 
 // ---- solves ------------------------------------------------------------------------
-// forward gather: v = rhs on the pivot rows, 0 below, plus the children's update vectors
-__global__ void k_big_fwd_gather(int s, FactorView a, const double* __restrict__ rhs, double* __restrict__ v) {
+// forward gather: v = rhs on the pivot rows, 0 below, plus the children's update
+// vectors; one thread per row sums the child entries that land on it, in child order
+__global__ void k_big_fwd_gather(int s, FactorView a, const int64_t* __restrict__ ea_ptr,
+                                 const int* __restrict__ ea_child, const int* __restrict__ ea_pos,
+                                 const double* __restrict__ rhs, double* __restrict__ v) {
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
-    for (int i = threadIdx.x; i < f; i += blockDim.x) v[i] = i < c ? rhs[a.perm[first + i]] : 0.0;
-    __syncthreads();
-    for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
-        const int ch = a.child[k];
-        const int r = a.nrow[ch] - a.ncol[ch];
-        const int* rel = a.rel + a.upd_off[ch];
-        const double* u = a.upd + a.upd_off[ch];
-        for (int i = threadIdx.x; i < r; i += blockDim.x) v[rel[i]] += u[i];
-        __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < f; i += gridDim.x * blockDim.x) {
+        double acc = i < c ? rhs[a.perm[first + i]] : 0.0;
+        for (int64_t e = ea_ptr[i]; e < ea_ptr[i + 1]; ++e) acc += a.upd[a.cinfo[ea_child[e]].rel_off + ea_pos[e]];
+        v[i] = acc;
     }
 }
 
-// one forward block: y_b = L_bb⁻¹ v_b (every CTA, redundantly), CTA 0 stores y_b; each
-// CTA updates its rows i ≥ k0+nb: v_i −= Σ_k L_{i,k0+k} y_k
-__global__ void __launch_bounds__(256) k_big_fwd_step(int s, int k0, int nb, FactorView a, double* __restrict__ v,
+// one forward block: y_b = L_bb⁻¹ v_b with the inverse stored by the factorisation
+// (every CTA, redundantly: a 64×64 matrix-vector product, no dependent chain), CTA 0
+// stores y_b; each CTA updates its rows i ≥ k0+nb: v_i −= Σ_k L_{i,k0+k} y_k
+__global__ void __launch_bounds__(256) k_big_fwd_step(int s, int k0, int nb, FactorView a,
+                                                      const double* __restrict__ Xb, double* __restrict__ v,
                                                       double* __restrict__ y) {
-    __shared__ double yb[kBigNB];
+    __shared__ double vb[kBigNB], yb[kBigNB];
     const int f = a.nrow[s];
     const double* L = a.front + a.front_off[s];
-    const int tid = threadIdx.x;
-    if (tid < 32) {
-        // column-oriented substitution on warp 0: lanes own rows (two per lane)
-        double r0 = tid < nb ? v[k0 + tid] : 0.0, r1 = tid + 32 < nb ? v[k0 + tid + 32] : 0.0;
-        for (int k = 0; k < nb; ++k) {
-            const double yk = __shfl_sync(0xffffffffu, k < 32 ? r0 : r1, k & 31);
-            const double* colk = L + (int64_t)(k0 + k) * f + k0;
-            if (tid > k && tid < nb) r0 -= colk[tid] * yk;
-            if (tid + 32 > k && tid + 32 < nb) r1 -= colk[tid + 32] * yk;
-        }
-        if (tid < nb) yb[tid] = r0;
-        if (tid + 32 < nb) yb[tid + 32] = r1;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int k = tid; k < nb; k += blockDim.x) vb[k] = v[k0 + k];
+    __syncthreads();
+    for (int i = wid; i < nb; i += blockDim.x >> 5) {
+        const double* xr = Xb + i * kBigNB;
+        double acc = 0.0;
+        for (int j = lane; j < i; j += 32) acc += xr[j] * vb[j];
+        acc = warp_sum(acc);
+        if (lane == 0) yb[i] = vb[i] + acc;
     }
     __syncthreads();
     if (blockIdx.x == 0)
         for (int k = tid; k < nb; k += blockDim.x) y[k0 + k] = yb[k];
-    for (int i = k0 + nb + blockIdx.x * blockDim.x + tid; i < f; i += gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int k = 0; k < nb; ++k) acc += L[(int64_t)(k0 + k) * f + i] * yb[k];
-        v[i] -= acc;
+    // rows below: four threads per row (lane bits 0–1 pick a quarter of the block's
+    // columns), reduced with two shuffles
+    const int q = tid & 3;
+    const int64_t nrow = f - (k0 + nb);
+    for (int64_t r0 = (int64_t)blockIdx.x * (blockDim.x >> 2); r0 < nrow; r0 += (int64_t)gridDim.x * (blockDim.x >> 2)) {
+        const int64_t r = r0 + (tid >> 2);
+        const int i = k0 + nb + (int)r;
+        double acc0 = 0.0, acc1 = 0.0;
+        if (r < nrow)
+            for (int k = q; k < nb; k += 8) {
+                acc0 += L[(int64_t)(k0 + k) * f + i] * yb[k];
+                if (k + 4 < nb) acc1 += L[(int64_t)(k0 + k + 4) * f + i] * yb[k + 4];
+            }
+        double acc = acc0 + acc1;
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (r < nrow && q == 0) v[i] -= acc;
     }
 }
 
@@ -315,33 +367,40 @@ __global__ void k_big_bwd_below(int s, FactorView a, const double* __restrict__ 
     if (lane == 0) v[k] = w[first + k] - acc;
 }
 
-// one backward block (from the last): x_b = L_bb⁻ᵀ v_b (every CTA, redundantly), CTA 0
-// stores x_b; each CTA updates its rows k < k0: v_k −= Σ_j L_{k0+j,k} x_j
-__global__ void __launch_bounds__(256) k_big_bwd_step(int s, int k0, int nb, FactorView a, double* __restrict__ v,
+// one backward block (from the last): x_b = L_bb⁻ᵀ v_b with the stored inverse (every
+// CTA, redundantly), CTA 0 stores x_b; each CTA updates its rows k < k0:
+// v_k −= Σ_j L_{k0+j,k} x_j
+__global__ void __launch_bounds__(256) k_big_bwd_step(int s, int k0, int nb, FactorView a,
+                                                      const double* __restrict__ Xb, double* __restrict__ v,
                                                       double* __restrict__ x) {
-    __shared__ double xb[kBigNB];
+    __shared__ double vb[kBigNB], xb[kBigNB];
     const int f = a.nrow[s];
     const double* L = a.front + a.front_off[s];
-    const int tid = threadIdx.x;
-    if (tid < 32) {
-        // row-oriented substitution with Lᵀ: x_k = v_k − Σ_{j>k} L_{j,k} x_j
-        for (int k = nb - 1; k >= 0; --k) {
-            const double* colk = L + (int64_t)(k0 + k) * f + k0;
-            double acc = 0.0;
-            for (int j = k + 1 + tid; j < nb; j += 32) acc += colk[j] * xb[j];
-            acc = warp_sum(acc);
-            if (tid == 0) xb[k] = v[k0 + k] - acc;
-            __syncwarp();
-        }
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int k = tid; k < nb; k += blockDim.x) vb[k] = v[k0 + k];
+    __syncthreads();
+    for (int j = wid; j < nb; j += blockDim.x >> 5) {
+        double acc = 0.0;
+        for (int i = j + 1 + lane; i < nb; i += 32) acc += Xb[i * kBigNB + j] * vb[i];
+        acc = warp_sum(acc);
+        if (lane == 0) xb[j] = vb[j] + acc;
     }
     __syncthreads();
     if (blockIdx.x == 0)
         for (int k = tid; k < nb; k += blockDim.x) x[k0 + k] = xb[k];
-    for (int k = blockIdx.x * blockDim.x + tid; k < k0; k += gridDim.x * blockDim.x) {
-        const double* colk = L + (int64_t)k * f + k0;
+    // earlier rows: eight threads per row k read consecutive entries of its column
+    const int q = tid & 7;
+    for (int r0 = blockIdx.x * (blockDim.x >> 3); r0 < k0; r0 += gridDim.x * (blockDim.x >> 3)) {
+        const int k = r0 + (tid >> 3);
         double acc = 0.0;
-        for (int j = 0; j < nb; ++j) acc += colk[j] * xb[j];
-        v[k] -= acc;
+        if (k < k0) {
+            const double* colk = L + (int64_t)k * f + k0;
+            for (int j = q; j < nb; j += 8) acc += colk[j] * xb[j];
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        if (k < k0 && q == 0) v[k] -= acc;
     }
 }
 
@@ -380,11 +439,13 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
     const int64_t ff = (int64_t)f * f;
     k_big_zero<T><<<gridfor(ff, 256), 256, 0, st>>>(F, ff);
     k_big_assemble<T><<<gridfor(P.big_amap_n[idx], 256), 256, 0, st>>>(s, a, kval, F);
-    k_big_extend_add<T><<<(unsigned)((f + 7) / 8), 256, 0, st>>>(s, a, F);
+    k_big_extend_add<T><<<(unsigned)((f + 7) / 8), 256, 0, st>>>(s, a, P.d_ea_ptr + P.big_ea_off[idx],
+                                                                  P.d_ea_child, P.d_ea_pos, F);
     launches += 3;
     for (int k0 = 0; k0 < c; k0 += kBigNB) {
         const int nb = std::min(kBigNB, c - k0);
-        k_big_diag<T><<<1, 256, 0, st>>>(s, k0, nb, a, F);
+        k_big_diag<T><<<1, 256, 0, st>>>(s, k0, nb, a, F, P.big_linv + P.big_linv_off[idx] +
+                                                              (int64_t)(k0 / kBigNB) * kBigNB * kBigNB);
         const int rows = f - k0 - nb;
         ++launches;
         if (rows <= 0) continue;
@@ -418,11 +479,14 @@ int launch_big_fwd(const FactorPlan& P, const FactorView& a, const double* rhs, 
                    cudaStream_t st) {
     const int s = P.big_s[idx], f = P.big_f[idx], c = P.big_c[idx];
     int launches = 0;
-    k_big_fwd_gather<<<1, 1024, 0, st>>>(s, a, rhs, P.big_v);
+    k_big_fwd_gather<<<gridfor(f, 256), 256, 0, st>>>(s, a, P.d_ea_ptr + P.big_ea_off[idx], P.d_ea_child,
+                                                       P.d_ea_pos, rhs, P.big_v);
     ++launches;
     for (int k0 = 0; k0 < c; k0 += kBigNB) {
         const int nb = std::min(kBigNB, c - k0);
-        k_big_fwd_step<<<gridfor(std::max(1, f - k0 - nb), 256), 256, 0, st>>>(s, k0, nb, a, P.big_v, P.big_y);
+        const double* Xb = P.big_linv + P.big_linv_off[idx] + (int64_t)(k0 / kBigNB) * kBigNB * kBigNB;
+        k_big_fwd_step<<<gridfor(4 * (int64_t)std::max(1, f - k0 - nb), 256), 256, 0, st>>>(s, k0, nb, a, Xb,
+                                                                                          P.big_v, P.big_y);
         ++launches;
     }
     k_big_fwd_finish<<<gridfor(f, 256), 256, 0, st>>>(s, a, P.big_v, P.big_y, w);
@@ -438,7 +502,9 @@ int launch_big_bwd(const FactorPlan& P, const FactorView& a, const double* w, do
     const int nblk = (c + kBigNB - 1) / kBigNB;
     for (int b = nblk - 1; b >= 0; --b) {
         const int k0 = b * kBigNB, nb = std::min(kBigNB, c - k0);
-        k_big_bwd_step<<<gridfor(std::max(1, k0), 256), 256, 0, st>>>(s, k0, nb, a, P.big_v, P.big_y);
+        const double* Xb = P.big_linv + P.big_linv_off[idx] + (int64_t)b * kBigNB * kBigNB;
+        k_big_bwd_step<<<gridfor(8 * (int64_t)std::max(1, k0), 256), 256, 0, st>>>(s, k0, nb, a, Xb, P.big_v,
+                                                                                 P.big_y);
         ++launches;
     }
     k_big_bwd_finish<<<gridfor(c, 256), 256, 0, st>>>(s, a, P.big_y, xp, x, accumulate ? 1 : 0);

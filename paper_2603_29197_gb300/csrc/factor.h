@@ -77,6 +77,17 @@ struct FactorPlan {
     // levels' off_big/n_big
     std::vector<int> big_s, big_f, big_c;
     std::vector<int64_t> big_front_off, big_amap_n;
+    // per large front, for each of its f rows p: the child entries (child edge index into
+    // FactorView::cinfo, position in that child's update rows) that land on row p, in
+    // child order: segment ea_ptr[big_ea_off[idx] + p .. + p + 1) of ea_child / ea_pos
+    std::vector<int64_t> big_ea_off;
+    // inverses of the 64×64 unit-lower diagonal blocks of each large front (row-major,
+    // block b of front idx at big_linv + big_linv_off[idx] + b·64·64), for the solves
+    std::vector<int64_t> big_linv_off;
+    double* big_linv = nullptr;
+    int64_t* d_ea_ptr = nullptr;
+    int* d_ea_child = nullptr;
+    int* d_ea_pos = nullptr;
     int max_big_f = 0;
     bool big_fp32 = false;         // factor large fronts in FP32 (mixed precision)
     float* big_work32 = nullptr;   // max_big_f² FP32 working front

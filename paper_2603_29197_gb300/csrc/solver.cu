@@ -411,6 +411,43 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         P.max_big_f = std::max(P.max_big_f, Y.sn_nrow[s]);
     }
     if (P.max_big_f) {
+        // row-ownership lists of the large fronts' children (extend-add and solve gather)
+        std::vector<int64_t> ea_ptr;
+        std::vector<int> ea_child, ea_pos;
+        for (size_t idx = 0; idx < P.big_s.size(); ++idx) {
+            const int s = P.big_s[idx], f = Y.sn_nrow[s];
+            P.big_ea_off.push_back((int64_t)ea_ptr.size());
+            std::vector<int64_t> cnt(f + 1, 0);
+            for (int k = Y.child_ptr[s]; k < Y.child_ptr[s + 1]; ++k) {
+                const int ch = Y.child[k], r = Y.sn_nrow[ch] - Y.sn_ncol[ch];
+                for (int jj = 0; jj < r; ++jj) cnt[Y.rel[Y.upd_off[ch] + jj] + 1]++;
+            }
+            for (int q = 0; q < f; ++q) cnt[q + 1] += cnt[q];
+            const int64_t base = (int64_t)ea_child.size();
+            for (int q = 0; q <= f; ++q) ea_ptr.push_back(base + cnt[q]);
+            ea_child.resize(base + cnt[f]);
+            ea_pos.resize(base + cnt[f]);
+            std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+            for (int k = Y.child_ptr[s]; k < Y.child_ptr[s + 1]; ++k) {
+                const int ch = Y.child[k], r = Y.sn_nrow[ch] - Y.sn_ncol[ch];
+                for (int jj = 0; jj < r; ++jj) {
+                    const int64_t e = base + fill[Y.rel[Y.upd_off[ch] + jj]]++;
+                    ea_child[e] = k;
+                    ea_pos[e] = jj;
+                }
+            }
+        }
+        if ((rc = dcopy(S, &P.d_ea_ptr, ea_ptr))) return rc;
+        if (!ea_child.empty()) {
+            if ((rc = dcopy(S, &P.d_ea_child, ea_child))) return rc;
+            if ((rc = dcopy(S, &P.d_ea_pos, ea_pos))) return rc;
+        }
+        int64_t nlinv = 0;
+        for (size_t idx = 0; idx < P.big_s.size(); ++idx) {
+            P.big_linv_off.push_back(nlinv);
+            nlinv += (int64_t)((P.big_c[idx] + kBigNB - 1) / kBigNB) * kBigNB * kBigNB;
+        }
+        if ((rc = dalloc(S, &P.big_linv, std::max<int64_t>(nlinv, 1)))) return rc;
         double* pw;
         if ((rc = dalloc(S, &pw, (size_t)P.max_big_f * kBigNB))) return rc;
         P.big_w = pw;
