@@ -169,6 +169,47 @@ int qoco_gpu_get_solution(const qoco_gpu_solver* solver, double* x, double* s,
 int qoco_gpu_solution_device(const qoco_gpu_solver* solver, const double** x,
                              const double** s, const double** y, const double** z);
 
+/* ---- batches of independent problems ------------------------------------------ */
+
+/* Sets up `batch` independent instances of eq. (1) (paper §1) as one solver: the
+ * instances are stacked block-diagonally and solved by one interior-point loop whose
+ * scalars — residual norms, gap, μ, step lengths, σ, the stopping test — are kept per
+ * instance; an instance that meets the stopping test takes zero steps from then on, and
+ * the loop ends when every instance has (or at max_iter).  One factorisation and two
+ * solves per iteration serve the whole batch (the KKT matrix of eq. (2) is block
+ * diagonal, its supernodal tree a forest).  The paper solves one problem at a time;
+ * this is one of the forms grown beyond it.
+ *
+ * Arrays of length `batch` (host): n, m, p, l, nsoc; P, A, G are arrays of `batch` CSC
+ * matrices (P[i] with colptr == NULL means P_i = 0; A[i] is ignored when p[i] = 0);
+ * c, b, h, q are arrays of `batch` host pointers (b[i] may be NULL when p[i] = 0).
+ * Each instance follows the conventions above (orthant rows first in its G).  Layout of
+ * the stacked iterate returned by qoco_gpu_get_solution: see qoco_gpu_batch_offsets.
+ * Errors: as qoco_gpu_setup (the message names the failing instance);
+ * NOT_IMPLEMENTED when no instance has a cone row. */
+int qoco_gpu_setup_batch(qoco_gpu_solver** out, int batch, const int* n, const int* m,
+                         const int* p, const qoco_csc* P, const double* const* c,
+                         const qoco_csc* A, const double* const* b, const qoco_csc* G,
+                         const double* const* h, const int* l, const int* nsoc,
+                         const int* const* q, const qoco_gpu_settings* settings);
+
+/* Number of instances (0 for a solver made by qoco_gpu_setup). */
+int qoco_gpu_batch_size(const qoco_gpu_solver* solver);
+
+/* Offsets (host arrays of batch + 1 ints, any may be NULL) of the stacked iterate:
+ * instance i's x is x[xo[i] .. xo[i+1]), its y is y[yo[i] .. yo[i+1]); its s and z
+ * are the orthant part [lo[i], lo[i+1]) followed by the SOC part L + [so[i], so[i+1])
+ * with L = lo[batch]; its cones are ko[i] .. ko[i+1]. */
+int qoco_gpu_batch_offsets(const qoco_gpu_solver* solver, int* xo, int* yo, int* lo, int* ko,
+                           int* so);
+
+/* Per-instance results of the last solve (host arrays of length batch, any may be NULL):
+ * status (QOCO_GPU_SOLVED, _SOLVED_INACCURATE, _MAX_ITER or _ERR_NUMERICAL), the
+ * iteration at which the instance met the stopping test, primal and dual objective,
+ * and sᵀz.  Synchronises the device. */
+int qoco_gpu_batch_info(const qoco_gpu_solver* solver, int* status, int* iters, double* pobj,
+                        double* dobj, double* gap);
+
 /* Copies the solver's iterate into caller DEVICE buffers x[n], s[m], y[p], z[m] (any may
  * be NULL), ordered on `stream` (device-to-device copies, no host round trip). */
 int qoco_gpu_copy_solution(const qoco_gpu_solver* solver, double* x, double* s, double* y,

@@ -15,7 +15,8 @@ from . import _lib
 from ._lib import (ORDER_AMD, ORDER_AUTO, ORDER_ND, ORDER_NATURAL, STATUS_NAMES,  # noqa: F401
                    Info, Settings)
 
-__all__ = ["Solver", "Cones", "analyze", "default_settings", "load", "STATUS_NAMES"]
+__all__ = ["Solver", "BatchSolver", "Cones", "analyze", "default_settings", "load", "STATUS_NAMES",
+           "solve_function"]
 
 
 def load():
@@ -288,6 +289,77 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class BatchSolver(Solver):
+    """Independent instances (objects with the attributes Solver takes) solved together
+    by one interior-point loop with per-instance scalars (qoco_gpu_setup_batch)."""
+
+    def __init__(self, probs, settings=None, **kw):  # noqa: D401  (own set-up)
+        self.lib = load()
+        self.st = _settings(settings, kw)
+        nb = len(probs)
+        holds = []
+        ns, ms, ps, ls, nsocs = [], [], [], [], []
+        Ps, As, Gs = (_lib.CSC * nb)(), (_lib.CSC * nb)(), (_lib.CSC * nb)()
+        cs, bs, hs, qs = ((C.POINTER(C.c_double) * nb)(), (C.POINTER(C.c_double) * nb)(),
+                          (C.POINTER(C.c_double) * nb)(), (C.POINTER(C.c_int) * nb)())
+        for i, pr in enumerate(probs):
+            n, m, p, P, A, G, q = _problem_args(pr)
+            c, b, h = _vec(pr.c, n), _vec(pr.b, p), _vec(pr.h, m)
+            holds += [P, A, G, q, c, b, h]
+            ns.append(n); ms.append(m); ps.append(p); ls.append(int(pr.l)); nsocs.append(len(q))
+            if P.ptr is not None:
+                Ps[i] = P.s
+            if A.ptr is not None:
+                As[i] = A.s
+            Gs[i] = G.s
+            cs[i] = _dptr(c)
+            bs[i] = _dptr(b) if b is not None else C.POINTER(C.c_double)()
+            hs[i] = _dptr(h)
+            qs[i] = q.ctypes.data_as(C.POINTER(C.c_int)) if len(q) else C.POINTER(C.c_int)()
+        arr = lambda v: (C.c_int * nb)(*v)  # noqa: E731
+        self.n, self.m, self.p = sum(ns), sum(ms), sum(ps)
+        self.N = self.n + self.m + self.p
+        self.batch = nb
+        self._sizes = (ns, ms, ps)
+        self._h = C.c_void_p()
+        rc = self.lib.qoco_gpu_setup_batch(C.byref(self._h), nb, arr(ns), arr(ms), arr(ps), Ps, cs, As, bs, Gs,
+                                           hs, arr(ls), arr(nsocs), qs, C.byref(self.st))
+        if rc != 0:
+            self._h = None
+            raise SolverError(rc, "setup_batch")
+        self._nnz = (sum(int(pr.P.nnz) for pr in probs if getattr(pr, "P", None) is not None),
+                     sum(int(pr.A.nnz) for pr, p in zip(probs, ps) if p),
+                     sum(int(pr.G.nnz) for pr in probs))
+        k = nb + 1
+        self.offsets = {key: np.zeros(k, dtype=np.int32) for key in ("xo", "yo", "lo", "ko", "so")}
+        self.lib.qoco_gpu_batch_offsets(self._h, *[self.offsets[key].ctypes.data_as(C.POINTER(C.c_int))
+                                                   for key in ("xo", "yo", "lo", "ko", "so")])
+
+    def batch_info(self):
+        nb = self.batch
+        st = np.zeros(nb, dtype=np.int32)
+        it = np.zeros(nb, dtype=np.int32)
+        po, do, gp = np.zeros(nb), np.zeros(nb), np.zeros(nb)
+        rc = self.lib.qoco_gpu_batch_info(self._h, st.ctypes.data_as(C.POINTER(C.c_int)),
+                                          it.ctypes.data_as(C.POINTER(C.c_int)), _dptr(po), _dptr(do), _dptr(gp))
+        if rc != 0:
+            raise SolverError(rc, "batch_info")
+        return dict(status=st, iters=it, pobj=po, dobj=do, gap=gp)
+
+    def instance_solutions(self):
+        """Per-instance x, s, y, z sliced from the stacked iterate."""
+        sol = self.solution()
+        o = self.offsets
+        L = int(o["lo"][-1])
+        out = []
+        for i in range(self.batch):
+            def cone(v):
+                return np.concatenate([v[o["lo"][i]:o["lo"][i + 1]], v[L + o["so"][i]:L + o["so"][i + 1]]])
+            out.append(dict(x=sol["x"][o["xo"][i]:o["xo"][i + 1]], y=sol["y"][o["yo"][i]:o["yo"][i + 1]],
+                            s=cone(sol["s"]), z=cone(sol["z"])))
+        return out
 
 
 def _solve_function():

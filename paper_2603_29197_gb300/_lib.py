@@ -91,6 +91,12 @@ SIGNATURES = {
     "qoco_gpu_get_info": (C.c_int, [_VP, C.POINTER(Info)]),
     "qoco_gpu_backward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "qoco_gpu_copy_solution": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "qoco_gpu_setup_batch": (C.c_int, [C.POINTER(_VP), C.c_int, _IP, _IP, _IP, C.POINTER(CSC), C.POINTER(_DP),
+                                       C.POINTER(CSC), C.POINTER(_DP), C.POINTER(CSC), C.POINTER(_DP), _IP, _IP,
+                                       C.POINTER(_IP), C.POINTER(Settings)]),
+    "qoco_gpu_batch_size": (C.c_int, [_VP]),
+    "qoco_gpu_batch_offsets": (C.c_int, [_VP, _IP, _IP, _IP, _IP, _IP]),
+    "qoco_gpu_batch_info": (C.c_int, [_VP, _IP, _IP, _DP, _DP, _DP]),
     "qoco_gpu_backward_info": (C.c_int, [_VP, _IP, _DP, _IP]),
     "qoco_gpu_update_data": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_int, _VP]),
     "qoco_gpu_cleanup": (C.c_int, [_VP]),

@@ -90,7 +90,10 @@ __global__ void k_rhs_z(ConeView c, ConeGrid g, const double* __restrict__ lam,
                         int combined, double* t, double* t1, double* t2, double* rhs) {
     ConeItem it;
     if (!cone_item(c, g, &it)) return;
-    const double smu = combined ? *smu_ptr : 0.0;
+    // σμ of the item's instance (per instance in a batch)
+    int inst = 0;
+    if (c.inst_orth) inst = it.kind == 0 ? c.inst_orth[it.idx] : c.inst_soc[it.idx];
+    const double smu = combined ? smu_ptr[inst] : 0.0;
     if (it.kind == 0) {
         const int i = it.idx;
         const double li = lam[i], wi = wbar[i];

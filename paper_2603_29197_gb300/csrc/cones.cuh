@@ -18,6 +18,10 @@ struct ConeView {
     const int* small = nullptr;  // ids of SOCs with dim ≤ kSmallCone
     const int* large = nullptr;  // ids of SOCs with dim > kSmallCone
     int nsmall = 0, nlarge = 0;
+    // batched problems: instance of each orthant entry (l) and of each SOC (nsoc); null
+    // for a single problem (everything is instance 0)
+    const int* inst_orth = nullptr;
+    const int* inst_soc = nullptr;
 };
 
 constexpr int kConeThreads = 256;

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.h"
 #include "cone_kernels.h"
 #include "factor.h"
 #include "plan.h"
@@ -235,6 +236,12 @@ struct qoco_gpu_solver {
     // polls a grid-barrier wait may take before it gives up (each poll sleeps ~64 ns)
     long long barrier_spins = 20000000;
     bool have_solution = false;  // a solve completed (adjoint available)
+    // batch of independent instances (qoco_gpu_setup_batch)
+    bool batch = false;
+    BatchView bv;
+    int batch_L = 0;                   // stacked orthant dimension
+    double *b_items = nullptr, *b_shift = nullptr, *b_aux = nullptr;
+    std::vector<int> h_xo, h_yo, h_lo, h_ko, h_so;
     int fp32_factors = 0, fp64_escalations = 0;
     // adjoint: KKT position (row, column) of one slot of each data entry [P | A | G]
     int *d_adj_a = nullptr, *d_adj_b = nullptr;
@@ -662,7 +669,15 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
     k_init_iterate<<<grid(N), 256, 0, st>>>(S->d_cmb, S->xyz, S->s, n, p, m);
     S->launches += 1;
     double* z = S->xyz + n + p;
-    if (m > 0) {
+    const bool B = S->batch;
+    if (B) {
+        // per-instance iteration counts and convergence flags start over
+        QOCO_CUDA_TRY(cudaMemsetAsync(S->bv.conv, 0, sizeof(int) * S->bv.nb, st));
+        QOCO_CUDA_TRY(cudaMemsetAsync(S->bv.iters, 0xff, sizeof(int) * S->bv.nb, st));
+    }
+    if (B && m > 0) {
+        S->launches += launch_batch_shift(cv, S->bv, S->s, z, S->b_items, S->b_shift, st);
+    } else if (m > 0) {
         launch_shift_measure(cv, S->s, z, S->partial, st);
         k_shift_finalize<<<1, 256, 0, st>>>(S->partial, max_step_partials(cv), S->d_S);
         launch_shift_apply(cv, S->s, &S->d_S->shift[0], st);
@@ -676,10 +691,18 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
     for (it = 0;; ++it) {
         {
             Phase ph(S, QOCO_GPU_PHASE_ROW, st);
-            if (launch_residual(S->kv, S->lpr, S->xyz, S->s, S->d_c, S->d_b, S->d_h, S->r, S->partial,
-                                S->partial_cap, S->d_S, st))
-                return QOCO_GPU_ERR_INVALID_ARG;
-            S->launches += 2;
+            if (B) {
+                IPMScalars tol;
+                tol.abstol = S->st.abstol; tol.reltol = S->st.reltol;
+                tol.abstol_inacc = S->st.abstol_inacc; tol.reltol_inacc = S->st.reltol_inacc;
+                S->launches += launch_batch_residual(S->kv, S->bv, S->batch_L, S->xyz, S->s, S->d_c, S->d_b,
+                                                     S->d_h, S->r, S->b_aux, it, tol, S->d_S, st);
+            } else {
+                if (launch_residual(S->kv, S->lpr, S->xyz, S->s, S->d_c, S->d_b, S->d_h, S->r, S->partial,
+                                    S->partial_cap, S->d_S, st))
+                    return QOCO_GPU_ERR_INVALID_ARG;
+                S->launches += 2;
+            }
         }
         QOCO_CUDA_TRY(cudaGetLastError());
         if ((rc = sync_scalars(S, st))) return rc;
@@ -718,36 +741,51 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
         if (m) {
             Phase ph(S, QOCO_GPU_PHASE_CONE, st);
             launch_ds(cv, S->wbar, S->eta, S->t, S->d_aff + n + p, S->t1, S->ds_aff, st);
-            launch_max_step(cv, S->s, S->ds_aff, z, S->d_aff + n + p, INFINITY, S->partial,
-                            &S->d_S->alpha_max, st);
-            S->launches += cl + 2;
+            if (B) {
+                S->launches += cl + launch_batch_max_step(cv, S->bv, S->s, S->ds_aff, z, S->d_aff + n + p,
+                                                          S->b_items, st);
+            } else {
+                launch_max_step(cv, S->s, S->ds_aff, z, S->d_aff + n + p, INFINITY, S->partial,
+                                &S->d_S->alpha_max, st);
+                S->launches += cl + 2;
+            }
         } else {
             k_set<<<1, 1, 0, st>>>(&S->d_S->alpha_max, INFINITY);  // no cone limits the step
             S->launches++;
         }
-        k_sigma<<<1, 1, 0, st>>>(S->d_S, 3.0);
-        S->launches++;
+        if (B) S->launches += launch_batch_sigma(S->bv, st);
+        else { k_sigma<<<1, 1, 0, st>>>(S->d_S, 3.0); S->launches++; }
         // corrector
         if (m) {
             Phase ph(S, QOCO_GPU_PHASE_CONE, st);
             launch_rhs_z(cv, S->lam, S->wbar, S->eta, S->r + n + p, S->ds_aff, S->d_aff + n + p,
-                         &S->d_S->sigma_mu, true, S->t, S->t1, S->t2, S->rhs + n + p, st);
+                         B ? S->bv.sigma_mu : &S->d_S->sigma_mu, true, S->t, S->t1, S->t2, S->rhs + n + p, st);
             S->launches += cl;
         }
         if ((rc = solve_refine(S, S->rhs, S->d_cmb, st))) return rc;
         if (m) {
             Phase ph(S, QOCO_GPU_PHASE_CONE, st);
             launch_ds(cv, S->wbar, S->eta, S->t, S->d_cmb + n + p, S->t1, S->ds_cmb, st);
-            launch_max_step(cv, S->s, S->ds_cmb, z, S->d_cmb + n + p, INFINITY, S->partial,
-                            &S->d_S->alpha_max, st);
-            S->launches += cl + 2;
+            if (B) {
+                S->launches += cl + launch_batch_max_step(cv, S->bv, S->s, S->ds_cmb, z, S->d_cmb + n + p,
+                                                          S->b_items, st);
+            } else {
+                launch_max_step(cv, S->s, S->ds_cmb, z, S->d_cmb + n + p, INFINITY, S->partial,
+                                &S->d_S->alpha_max, st);
+                S->launches += cl + 2;
+            }
         } else {
             k_set<<<1, 1, 0, st>>>(&S->d_S->alpha_max, INFINITY);
             S->launches++;
         }
-        k_alpha<<<1, 1, 0, st>>>(S->d_S);
-        k_update<<<grid(std::max(N, m)), 256, 0, st>>>(S->xyz, S->s, S->d_cmb, S->ds_cmb, S->d_S, N, m);
-        S->launches += 2;
+        if (B) {
+            S->launches += launch_batch_step(S->bv, S->st.step_fraction, S->xyz, S->s, S->d_cmb, S->ds_cmb, N,
+                                             n + p, m, st);
+        } else {
+            k_alpha<<<1, 1, 0, st>>>(S->d_S);
+            k_update<<<grid(std::max(N, m)), 256, 0, st>>>(S->xyz, S->s, S->d_cmb, S->ds_cmb, S->d_S, N, m);
+            S->launches += 2;
+        }
         QOCO_CUDA_TRY(cudaGetLastError());
     }
     return status;
@@ -785,6 +823,125 @@ int analyze_common(int n, int m, int p, const qoco_csc* P, const double* c, cons
     build_kkt_pattern(K, n, m, p, P, A, G, l, nsoc, q);
     *used = analyze(*K, *st, Y);
     *t_analysis = now_s() - t0;
+    return 0;
+}
+
+// ---- batches --------------------------------------------------------------------
+struct Stacked {
+    int n = 0, m = 0, p = 0, l = 0, nsoc = 0;
+    std::vector<int> Pp{0}, Pi, Ap{0}, Ai, Gp{0}, Gi, q;
+    std::vector<double> Pv, Av, Gv, c, b, h;
+    std::vector<int> xo{0}, yo{0}, lo{0}, ko{0}, so{0};
+    std::vector<double> nu, c_inf, b_inf, h_inf;
+};
+
+bool csc_present(const qoco_csc* M) { return M && M->colptr && M->n_cols > 0; }
+
+// Block-diagonal stack of the instances: x and y in instance order; the cone's rows are
+// every instance's orthant rows (instance order), then every instance's SOC rows.
+int stack_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc* P, const double* const* c,
+                const qoco_csc* A, const double* const* b, const qoco_csc* G, const double* const* h,
+                const int* l, const int* nsoc, const int* const* q, Stacked* T, std::string* msg) {
+    for (int i = 0; i < nb; ++i) {
+        int rc = validate_problem(n[i], m[i], p[i], csc_present(&P[i]) ? &P[i] : nullptr, c[i],
+                                  p[i] ? &A[i] : nullptr, b[i], &G[i], h[i], l[i], nsoc[i], q[i], true, msg);
+        if (rc) {
+            *msg = "instance " + std::to_string(i) + ": " + *msg;
+            return rc;
+        }
+        T->n += n[i]; T->p += p[i]; T->m += m[i]; T->l += l[i]; T->nsoc += nsoc[i];
+    }
+    const int L = T->l;
+    for (int i = 0; i < nb; ++i) {
+        T->xo.push_back(T->xo.back() + n[i]);
+        T->yo.push_back(T->yo.back() + p[i]);
+        T->lo.push_back(T->lo.back() + l[i]);
+        T->ko.push_back(T->ko.back() + nsoc[i]);
+        T->so.push_back(T->so.back() + m[i] - l[i]);
+    }
+    T->h.assign(T->m, 0.0);
+    for (int i = 0; i < nb; ++i) {
+        const int xo = T->xo[i], yo = T->yo[i], lo = T->lo[i], so = T->so[i];
+        double ci = 0.0, bi = 0.0, hi = 0.0;
+        for (int j = 0; j < n[i]; ++j) {
+            T->c.push_back(c[i][j]);
+            ci = std::max(ci, std::fabs(c[i][j]));
+            // column j of the instance's P, A and G
+            if (csc_present(&P[i]))
+                for (int t = P[i].colptr[j]; t < P[i].colptr[j + 1]; ++t) {
+                    T->Pi.push_back(xo + P[i].rowidx[t]);
+                    T->Pv.push_back(P[i].val[t]);
+                }
+            T->Pp.push_back((int)T->Pi.size());
+            if (p[i])
+                for (int t = A[i].colptr[j]; t < A[i].colptr[j + 1]; ++t) {
+                    T->Ai.push_back(yo + A[i].rowidx[t]);
+                    T->Av.push_back(A[i].val[t]);
+                }
+            T->Ap.push_back((int)T->Ai.size());
+            for (int t = G[i].colptr[j]; t < G[i].colptr[j + 1]; ++t) {
+                const int r = G[i].rowidx[t];
+                T->Gi.push_back(r < l[i] ? lo + r : L + so + (r - l[i]));
+                T->Gv.push_back(G[i].val[t]);
+            }
+            T->Gp.push_back((int)T->Gi.size());
+        }
+        for (int j = 0; j < p[i]; ++j) {
+            T->b.push_back(b[i][j]);
+            bi = std::max(bi, std::fabs(b[i][j]));
+        }
+        for (int r = 0; r < m[i]; ++r) {
+            T->h[r < l[i] ? lo + r : L + so + (r - l[i])] = h[i][r];
+            hi = std::max(hi, std::fabs(h[i][r]));
+        }
+        for (int k = 0; k < nsoc[i]; ++k) T->q.push_back(q[i][k]);
+        T->nu.push_back((double)(l[i] + nsoc[i]));
+        T->c_inf.push_back(ci);
+        T->b_inf.push_back(bi);
+        T->h_inf.push_back(hi);
+    }
+    return 0;
+}
+
+int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
+    int rc;
+    BatchView& B = S->bv;
+    B.nb = nb;
+    int* pi;
+    double* pd;
+    if ((rc = dcopy(S, &pi, T.xo))) return rc; B.xo = pi;
+    if ((rc = dcopy(S, &pi, T.yo))) return rc; B.yo = pi;
+    if ((rc = dcopy(S, &pi, T.lo))) return rc; B.lo = pi;
+    if ((rc = dcopy(S, &pi, T.ko))) return rc; B.ko = pi;
+    if ((rc = dcopy(S, &pi, T.so))) return rc; B.so = pi;
+    if ((rc = dcopy(S, &pd, T.nu))) return rc; B.nu = pd;
+    if ((rc = dcopy(S, &pd, T.c_inf))) return rc; B.c_inf = pd;
+    if ((rc = dcopy(S, &pd, T.b_inf))) return rc; B.b_inf = pd;
+    if ((rc = dcopy(S, &pd, T.h_inf))) return rc; B.h_inf = pd;
+    // instance of every KKT row, of every orthant entry and of every SOC
+    const int n = T.n, p = T.p, L = T.l;
+    std::vector<int> row(n + p + T.m), orth(L), soc(T.nsoc);
+    for (int i = 0; i < nb; ++i) {
+        for (int j = T.xo[i]; j < T.xo[i + 1]; ++j) row[j] = i;
+        for (int j = T.yo[i]; j < T.yo[i + 1]; ++j) row[n + j] = i;
+        for (int j = T.lo[i]; j < T.lo[i + 1]; ++j) { row[n + p + j] = i; orth[j] = i; }
+        for (int j = T.so[i]; j < T.so[i + 1]; ++j) row[n + p + L + j] = i;
+        for (int k = T.ko[i]; k < T.ko[i + 1]; ++k) soc[k] = i;
+    }
+    if ((rc = dcopy(S, &pi, row))) return rc; B.inst_row = pi;
+    if (L) { if ((rc = dcopy(S, &pi, orth))) return rc; S->cv.inst_orth = pi; }
+    if (T.nsoc) { if ((rc = dcopy(S, &pi, soc))) return rc; S->cv.inst_soc = pi; }
+    double** vd[] = {&B.pobj, &B.dobj, &B.gap, &B.mu, &B.alpha_max, &B.sigma_mu, &B.alpha};
+    for (double** v : vd) if ((rc = dalloc(S, v, nb))) return rc;
+    if ((rc = dalloc(S, &B.res, 3 * (size_t)nb))) return rc;
+    int** vi[] = {&B.conv, &B.conv_inacc, &B.nonfinite, &B.iters};
+    for (int** v : vi) if ((rc = dalloc(S, v, nb))) return rc;
+    if ((rc = dalloc(S, &S->b_items, 2 * (size_t)std::max(1, L + T.nsoc)))) return rc;
+    if ((rc = dalloc(S, &S->b_shift, 2 * (size_t)nb))) return rc;
+    if ((rc = dalloc(S, &S->b_aux, 3 * (size_t)(n + p + T.m)))) return rc;
+    S->batch = true;
+    S->batch_L = L;
+    S->h_xo = T.xo; S->h_yo = T.yo; S->h_lo = T.lo; S->h_ko = T.ko; S->h_so = T.so;
     return 0;
 }
 
@@ -888,6 +1045,82 @@ int qoco_gpu_setup(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P
     S->info.ordering_used = used;
     S->info.setup_time_s = now_s() - t0;
     *out = S;
+    return 0;
+}
+
+int qoco_gpu_setup_batch(qoco_gpu_solver** out, int nb, const int* n, const int* m, const int* p,
+                         const qoco_csc* P, const double* const* c, const qoco_csc* A, const double* const* b,
+                         const qoco_csc* G, const double* const* h, const int* l, const int* nsoc,
+                         const int* const* q, const qoco_gpu_settings* settings) {
+    if (!out || nb <= 0 || !n || !m || !p || !P || !c || !A || !b || !G || !h || !l || !nsoc || !q)
+        return QOCO_GPU_ERR_INVALID_ARG;
+    *out = nullptr;
+    const double t0 = now_s();
+    Stacked T;
+    std::string msg;
+    int rc;
+    try {
+        rc = stack_batch(nb, n, m, p, P, c, A, b, G, h, l, nsoc, q, &T, &msg);
+    } catch (const std::bad_alloc&) {
+        rc = QOCO_GPU_ERR_OOM;
+    }
+    if (rc) return rc;
+    if (T.m == 0) return QOCO_GPU_ERR_NOT_IMPLEMENTED;  // a batch needs cone rows
+    qoco_csc Pc{T.n, T.n, (int)T.Pi.size(), T.Pp.data(), T.Pi.data(), T.Pv.data()};
+    qoco_csc Ac{T.p, T.n, (int)T.Ai.size(), T.Ap.data(), T.Ai.data(), T.Av.data()};
+    qoco_csc Gc{T.m, T.n, (int)T.Gi.size(), T.Gp.data(), T.Gi.data(), T.Gv.data()};
+    qoco_gpu_solver* S = nullptr;
+    rc = qoco_gpu_setup(&S, T.n, T.m, T.p, T.Pi.empty() ? nullptr : &Pc, T.c.data(), T.p ? &Ac : nullptr,
+                        T.p ? T.b.data() : nullptr, &Gc, T.h.data(), T.l, T.nsoc, T.q.empty() ? nullptr : T.q.data(),
+                        settings);
+    if (rc) return rc;
+    try {
+        rc = batch_init(S, nb, T);
+    } catch (const std::bad_alloc&) {
+        rc = QOCO_GPU_ERR_OOM;
+    }
+    if (rc) {
+        qoco_gpu_cleanup(S);
+        return rc;
+    }
+    S->info.setup_time_s = now_s() - t0;
+    *out = S;
+    return 0;
+}
+
+int qoco_gpu_batch_size(const qoco_gpu_solver* S) { return S && S->batch ? S->bv.nb : 0; }
+
+int qoco_gpu_batch_offsets(const qoco_gpu_solver* S, int* xo, int* yo, int* lo, int* ko, int* so) {
+    if (!S || !S->batch) return QOCO_GPU_ERR_INVALID_ARG;
+    const size_t k = S->h_xo.size();
+    if (xo) memcpy(xo, S->h_xo.data(), sizeof(int) * k);
+    if (yo) memcpy(yo, S->h_yo.data(), sizeof(int) * k);
+    if (lo) memcpy(lo, S->h_lo.data(), sizeof(int) * k);
+    if (ko) memcpy(ko, S->h_ko.data(), sizeof(int) * k);
+    if (so) memcpy(so, S->h_so.data(), sizeof(int) * k);
+    return 0;
+}
+
+int qoco_gpu_batch_info(const qoco_gpu_solver* S, int* status, int* iters, double* pobj, double* dobj,
+                        double* gap) {
+    if (!S || !S->batch) return QOCO_GPU_ERR_INVALID_ARG;
+    const int nb = S->bv.nb;
+    std::vector<int> cv(nb), ci(nb), nf(nb), it(nb);
+    QOCO_CUDA_TRY(cudaDeviceSynchronize());
+    QOCO_CUDA_TRY(cudaMemcpy(cv.data(), S->bv.conv, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+    QOCO_CUDA_TRY(cudaMemcpy(ci.data(), S->bv.conv_inacc, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+    QOCO_CUDA_TRY(cudaMemcpy(nf.data(), S->bv.nonfinite, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+    QOCO_CUDA_TRY(cudaMemcpy(it.data(), S->bv.iters, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+    if (status)
+        for (int i = 0; i < nb; ++i)
+            status[i] = cv[i] ? QOCO_GPU_SOLVED
+                              : nf[i] ? QOCO_GPU_ERR_NUMERICAL
+                                      : ci[i] ? QOCO_GPU_SOLVED_INACCURATE : QOCO_GPU_MAX_ITER;
+    if (iters)
+        for (int i = 0; i < nb; ++i) iters[i] = cv[i] ? it[i] : S->info.iters;
+    if (pobj) QOCO_CUDA_TRY(cudaMemcpy(pobj, S->bv.pobj, sizeof(double) * nb, cudaMemcpyDeviceToHost));
+    if (dobj) QOCO_CUDA_TRY(cudaMemcpy(dobj, S->bv.dobj, sizeof(double) * nb, cudaMemcpyDeviceToHost));
+    if (gap) QOCO_CUDA_TRY(cudaMemcpy(gap, S->bv.gap, sizeof(double) * nb, cudaMemcpyDeviceToHost));
     return 0;
 }
 
