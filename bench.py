@@ -34,6 +34,8 @@ WORKLOAD = "trajectory_socp_N20000"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Nominal FP64 rate of GB300 (non-tensor and tensor alike); see the design doc for the derivation.
 FP64_NOMINAL_GFLOPS = 1250.0
+# Nominal FP32 CUDA-core rate: 152 SMs × 128 lanes × 2 flops × 2.07 GHz.
+FP32_NOMINAL_GFLOPS = 80540.0
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -46,6 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--stages", type=int, default=20000, help="trajectory stages (default: the benchmark size)")
+    ap.add_argument("--workload", default="trajectory", choices=["trajectory", "lasso", "mpc_batch"],
+                    help="trajectory (default, the headline line); lasso: the lasso QP scaled by 1/10 "
+                         "(F 5000x10000, FP64 or --mixed); mpc_batch: 4096 MPC instances, solves/s")
+    ap.add_argument("--mixed", action="store_true", help="FP32 large fronts with FP64 refinement")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -426,6 +432,115 @@ def run_e2e(q, prob, args, stream, dev):
             "note": "setup incl. host ordering + symbolic analysis, solve, solution copy-back"}
 
 
+# --------------------------------------------------------------------------- other workloads
+def other_workload(args):
+    from workloads import lasso_qp, mpc_batch
+    if args.workload == "lasso":
+        return [lasso_qp(rows=5000, cols=10000, density=5e-3, seed=0)]
+    return mpc_batch(count=4096, seed=0)
+
+
+def run_other(args, ws, rank, local):
+    """The lasso QP (time to the 1e-7 gap, FP64 or mixed) or the MPC batch (solves/s),
+    timed like the headline workload: W warm-up solves, K timed solves with CUDA events,
+    L2 flushed between them; e2e includes set-up from host data and the copy-back."""
+    import numpy as np
+    import torch
+    import paper_2603_29197_gb300 as q
+    from paper_2603_29197_gb300 import build as qbuild
+    if not os.path.exists(qbuild.LIB):
+        qbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    probs = other_workload(args)
+    batch = args.workload == "mpc_batch"
+    kw = dict(mixed_precision=1 if args.mixed else 0)
+    make = (lambda: q.BatchSolver(probs, **kw)) if batch else (lambda: q.Solver(probs[0], **kw))
+    S = make()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        st = S.solve(stream.cuda_stream)
+        if st != 0:
+            raise RuntimeError(f"warm-up solve returned {st}")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(None)
+    clocks.start()
+    S.set_profiling(True)
+    times, launches = [], 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = S.solve(stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        if st != 0:
+            raise RuntimeError(f"solve returned {st}")
+        times.append(e0.elapsed_time(e1))
+        launches += int(S.info()["kernel_launches"])
+    clk = clocks.stop()
+    prof = S.profile()
+    info = S.info()
+    S.set_profiling(False)
+    ms = statistics.mean(times)
+    fcalls = max(1, prof["factor"]["calls"])
+    f_ms = prof["factor"]["ms"] / fcalls
+    gflops = info["factor_flops"] / (f_ms * 1e-3) / 1e9
+    peak = FP32_NOMINAL_GFLOPS if args.mixed else FP64_NOMINAL_GFLOPS
+    rl = {"kernel": "factorisation (large-front panel kernels + supernodal kernels)", "bound": "alu",
+          "achieved": gflops, "peak": peak, "unit": "GFLOP/s", "frac": gflops / peak, "traffic": None,
+          "per_launch_unit": f"{info['factor_flops']:.4g} algorithmic flops per factorisation",
+          "peak_source": ("nominal FP32 CUDA-core rate" if args.mixed else "nominal FP64 rate") +
+                         " (unit counts × clock), not a measured peak", "avg_ms": f_ms}
+    # e2e: set-up from host data, solve, copy-back
+    t0 = time.perf_counter()
+    E = make()
+    st = E.solve(stream.cuda_stream)
+    sol = E.solution()
+    e2e_s = time.perf_counter() - t0
+    E.close()
+    # CPU oracle on a bounded sample
+    from oracle import ipm
+    t0 = time.perf_counter()
+    if batch:
+        sample = probs[:16]
+        for pr in sample:
+            ipm.solve(pr)
+        cpu_s = (time.perf_counter() - t0) / len(sample) * len(probs)
+        cpu = {"value": len(probs) / cpu_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle IPM on 16 of the {len(probs)} instances, scaled"}
+    else:
+        ipm.solve(probs[0], ipm.Settings(max_iter=0))
+        t_init = time.perf_counter() - t0
+        cpu = {"value": t_init * (info["iters"] + 1), "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle initial point (one sparse LU of the KKT, {t_init:.1f} s) × "
+                         f"{info['iters'] + 1} factorisations"}
+    if batch:
+        metric, value, unit, hib = "batched_solves_per_s", len(probs) / (ms * 1e-3), "solves/s", True
+        e2e = {"value": len(probs) / e2e_s, "unit": unit}
+    else:
+        metric, value, unit, hib = "time_to_1e-7_gap", ms * 1e-3, "s", False
+        e2e = {"value": e2e_s, "unit": unit}
+    e2e.update({"h2d_bytes_per_step": int(sol["info"]["h2d_bytes"]),
+                "d2h_bytes_per_step": int(sol["info"]["d2h_bytes"]) + 8 * (S.n + 2 * S.m + S.p)})
+    cfg = {"workload": ("mpc_batch_4096: horizons U{10..60}, state 4, control 2, Q^3 input cone, "
+                        "box bounds" if batch else "lasso_qp_r5000_c10000: F 5000x10000, 50 nnz/row"),
+           "kkt_dim": info["kkt_dim"], "kkt_nnz": info["kkt_nnz"], "factor_flops": info["factor_flops"],
+           "iterations": info["iters"], "max_front": info["max_front"], "large_fronts": info["large_fronts"],
+           "precision": "mixed (FP32 large fronts, FP64 refinement)" if args.mixed else "fp64",
+           "fp32_factors": info["fp32_factors"], "fp64_escalations": info["fp64_escalations"],
+           "l2": "flushed between timed steps (256 MiB write)"}
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64" if args.mixed else "f64", "data": "synthetic (seeded generator)",
+           "config": cfg, "gpu_launches": launches, "refactor_gflops": gflops,
+           "phase_ms_per_solve": {k: v["ms"] / args.steps for k, v in prof.items()},
+           "roofline": rl, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    S.close()
+
+
 def main():
     args = parse()
     if args.cpu_baseline_child:
@@ -434,6 +549,8 @@ def main():
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload != "trajectory":
+        run_other(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
