@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "common.cuh"
 #include "factor.h"
@@ -87,9 +88,12 @@ __global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorV
     constexpr int kOwn = (kBigNB * (kBigNB + 1) / 2 + 255) / 256;  // entries per thread
     __shared__ T D[kBigNB][kBigNB + 1];
     __shared__ T s_inv[kBigNB];
+    __shared__ signed char s_sign[kBigNB];
     const int f = a.nrow[s], first = a.first[s];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int ntri = nb * (nb + 1) / 2;
+    // pivot signs staged once, off the pivot chain
+    for (int k = tid; k < nb; k += nt) s_sign[k] = a.dsign[first + k0 + k] > 0 ? 1 : -1;
     for (int t = tid; t < nb * nb; t += nt) {
         const int j = t / nb, i = t - j * nb;
         if (i >= j) D[i][j] = F[(int64_t)(k0 + j) * f + k0 + i];
@@ -112,25 +116,34 @@ __global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorV
     }
     __syncthreads();
     int nreg = 0;
+    const T thr = (T)a.dyn_thresh, dval = (T)a.dyn_value;
     auto pivot = [&](int k) {
-        double d = (double)D[k][k];
-        const bool pos = a.dsign[first + k0 + k] > 0;
-        const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
-        if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
-        const T dt = (T)d;
-        D[k][k] = dt;
-        s_inv[k] = rcp_t<T>(dt);
+        T d = D[k][k];
+        const bool pos = s_sign[k] > 0;
+        const bool ok = pos ? (d >= thr) : (d <= -thr);
+        if (!ok) { d = pos ? dval : -dval; ++nreg; }
+        D[k][k] = d;
+        s_inv[k] = rcp_t<T>(d);
     };
-    if (tid == 0) pivot(0);
+    // which diagonal entries this thread owns (entry (d, d) has index d(d+3)/2)
+    uint64_t own_diag = 0;
+#pragma unroll
+    for (int u = 0; u < kOwn; ++u)
+        if (oi[u] >= 0 && oi[u] == oj[u]) own_diag |= 1ull << oi[u];
+    if (own_diag & 1ull) pivot(0);
     __syncthreads();
     for (int k = 0; k < nb; ++k) {
         const T inv = s_inv[k];
+        // the next pivot first: its owner updates it and computes it before anything else
+        if (k + 1 < nb && ((own_diag >> (k + 1)) & 1ull)) {
+            D[k + 1][k + 1] -= D[k + 1][k] * D[k + 1][k] * inv;
+            pivot(k + 1);
+        }
 #pragma unroll
         for (int u = 0; u < kOwn; ++u) {
             const int i = oi[u], j = oj[u];
-            if (j <= k) continue;
+            if (j <= k || (i == k + 1 && j == k + 1)) continue;
             D[i][j] -= D[i][k] * D[j][k] * inv;
-            if (i == k + 1 && j == k + 1) pivot(k + 1);
         }
         __syncthreads();
     }
@@ -170,10 +183,11 @@ __global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorV
     if (nreg) atomicAdd(a.nreg, nreg);
 }
 
-// rows i ≥ k0+nb: w = a_i· L11⁻ᵀ, l_i· = w D⁻¹ (into F), w into W[i·kBigNB + k]
+// rows i ≥ k0+nb: w = a_i· L11⁻ᵀ, l_i· = w D⁻¹ (into F and, if Lr, row-major into
+// Lr[i·ldw + k]), w into W[i·ldw + k]
 template <class T>
 __global__ void __launch_bounds__(128) k_big_l21(int s, int k0, int nb, FactorView a, T* __restrict__ F,
-                                                 T* __restrict__ W) {
+                                                 T* __restrict__ W, T* __restrict__ Lr, int ldw) {
     __shared__ T L11[kBigNB][kBigNB + 1];
     __shared__ T dv[kBigNB];
     const int f = a.nrow[s], first = a.first[s];
@@ -185,7 +199,7 @@ __global__ void __launch_bounds__(128) k_big_l21(int s, int k0, int nb, FactorVi
     __syncthreads();
     const int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= f) return;
-    T* wr = W + (int64_t)i * kBigNB;
+    T* wr = W + (int64_t)i * ldw;
     // two halves of 32 columns keep the row in registers without spills: the second
     // half first takes the first half's contribution (re-read from W, written by this
     // same thread), then both halves run the forward substitution with their diagonal
@@ -210,7 +224,9 @@ __global__ void __launch_bounds__(128) k_big_l21(int s, int k0, int nb, FactorVi
         for (int k = 0; k < 32; ++k)
             if (kb + k < nb) {
                 wr[kb + k] = w[k];
-                F[(int64_t)(k0 + kb + k) * f + i] = w[k] * dv[kb + k];
+                const T l = w[k] * dv[kb + k];
+                F[(int64_t)(k0 + kb + k) * f + i] = l;
+                if (Lr) Lr[(int64_t)i * ldw + kb + k] = l;
             }
     }
 }
@@ -219,18 +235,27 @@ __global__ void __launch_bounds__(128) k_big_l21(int s, int k0, int nb, FactorVi
 // tile of the lower triangle (tile index → (ti, tj), ti ≥ tj), 256 threads, 4×4 each
 template <class T>
 __global__ void __launch_bounds__(256) k_big_trailing(int s, int k0, int nb, FactorView a, T* __restrict__ F,
-                                                      const T* __restrict__ W) {
+                                                      const T* __restrict__ W, int ldw, int cend) {
     constexpr int KC = 32;  // panel columns staged per step (keeps the tiles ≤ 33 KB)
     __shared__ T Ls[KC][kBT + 1];
     __shared__ T Ws[KC][kBT + 1];
     const int f = a.nrow[s];
     const int base = k0 + nb;
-    // triangular tile index
     const int t = blockIdx.x;
-    int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-    while (ti * (ti + 1) / 2 > t) --ti;
-    const int tj = t - ti * (ti + 1) / 2;
+    int ti, tj;
+    if (cend >= f) {
+        // the whole trailing lower triangle: triangular tile index
+        ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        while (ti * (ti + 1) / 2 > t) --ti;
+        tj = t - ti * (ti + 1) / 2;
+    } else {
+        // only columns [base, cend): rectangular tile grid, tiles above the diagonal idle
+        const int ntj = (cend - base + kBT - 1) / kBT;
+        ti = t / ntj;
+        tj = t - ti * ntj;
+        if (ti < tj) return;
+    }
     const int r0 = base + ti * kBT, c0 = base + tj * kBT;
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
@@ -247,7 +272,7 @@ __global__ void __launch_bounds__(256) k_big_trailing(int s, int k0, int nb, Fac
         }
         for (int e = tid; e < kn * kBT; e += 256) {
             const int cc = e / kn, k = e - cc * kn;
-            Ws[k][cc] = c0 + cc < f ? W[(int64_t)(c0 + cc) * kBigNB + kc + k] : T(0);
+            Ws[k][cc] = c0 + cc < f ? W[(int64_t)(c0 + cc) * ldw + kc + k] : T(0);
         }
         __syncthreads();
         for (int k = 0; k < kn; ++k) {
@@ -266,7 +291,7 @@ __global__ void __launch_bounds__(256) k_big_trailing(int s, int k0, int nb, Fac
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const int j = c0 + ty * 4 + v;
-        if (j >= f) continue;
+        if (j >= f || j >= cend) continue;
         T* Fj = F + (int64_t)j * f;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -274,6 +299,161 @@ __global__ void __launch_bounds__(256) k_big_trailing(int s, int k0, int nb, Fac
             if (i < f && i >= j) Fj[i] -= acc[u][v];
         }
     }
+}
+
+// ---- tensor-core trailing update (FP32 fronts) ---------------------------------------
+// A22 −= L21·Wᵀ on 128×128 tiles of the lower triangle with tcgen05.mma kind::tf32: each
+// FP32 operand is split into a TF32 head and the FP32 remainder (a = a_hi + a_lo), and
+// D = A_hi·B_hiᵀ + A_hi·B_loᵀ + A_lo·B_hiᵀ accumulates in FP32 in tensor memory, which
+// keeps the update at FP32 accuracy (three TF32 products).  Operands are staged by the
+// CTA's threads into shared memory in the canonical K-major layout without swizzle:
+// core matrices of 8 rows × 16 bytes, adjacent along K 128 bytes apart (leading byte
+// offset) and along M/N 2048 bytes apart (stride byte offset).  One thread issues the
+// MMAs; completion is signalled through an mbarrier whose wait is bounded (on a timeout
+// the tile is left unchanged and *err is set, so the refinement rejects the factor).
+constexpr int kTcM = 128;                        // tile rows (L21) and columns (W)
+constexpr int kTcTile = kTcM * kBigNB * 4;      // bytes of one 128×64 FP32 operand
+constexpr int kTcSmem = 4 * kTcTile + 1024;     // four operands + alignment slack
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int kmaj_off(int r, int k) {
+    return (((r >> 3) * (kBigNB / 4) + (k >> 2)) << 7) + ((r & 7) << 4) + ((k & 3) << 2);
+}
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;                   // leading byte offset (K)
+    d |= (uint64_t)((8 * kBigNB * 4) >> 4) << 32;      // stride byte offset (8-row groups)
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    return d;                                          // layout: no swizzle
+}
+
+__global__ void __launch_bounds__(512) k_big_trailing_tc(int s, int k0, int kb, FactorView a, float* __restrict__ F,
+                                                         const float* __restrict__ Lr, const float* __restrict__ W,
+                                                         int ldw, int* err) {
+    extern __shared__ unsigned char tc_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* Ahi = sm;
+    unsigned char* Alo = sm + kTcTile;
+    unsigned char* Bhi = sm + 2 * kTcTile;
+    unsigned char* Blo = sm + 3 * kTcTile;
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int f = a.nrow[s];
+    const int base = k0 + kb;
+    const int t = blockIdx.x;
+    int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    while (ti * (ti + 1) / 2 > t) --ti;
+    const int tj = t - ti * (ti + 1) / 2;
+    const int r0 = base + ti * kTcM, c0 = base + tj * kTcM;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kTcM));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // D format F32, A and B TF32, both K-major, N = 128, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcM >> 3) << 17) |
+                           ((uint32_t)(kTcM >> 4) << 24);
+    uint32_t tmem = 0;
+    bool ok = true;
+    // the panel's K = kb columns in chunks of kBigNB: stage, multiply, wait, next chunk
+    for (int kc = 0, round = 0; kc < kb; kc += kBigNB, ++round) {
+        const int kn = min(kBigNB, kb - kc);
+        // operands, split into TF32 head and remainder, zero outside the front / chunk; one
+        // 16-byte row segment per thread, eight consecutive threads filling one 128-byte
+        // core matrix (conflict-free shared stores)
+        for (int e = tid; e < kTcM * (kBigNB / 4); e += blockDim.x) {
+            const int rin = e & 7, kq = (e >> 3) & (kBigNB / 4 - 1), rg = e >> 7;
+            const int r = rg * 8 + rin, k = kq * 4;
+            float4 av = make_float4(0.f, 0.f, 0.f, 0.f), bv = av;
+            if (k < kn && r0 + r < f) av = *(const float4*)(Lr + (int64_t)(r0 + r) * ldw + kc + k);
+            if (k < kn && c0 + r < f) bv = *(const float4*)(W + (int64_t)(c0 + r) * ldw + kc + k);
+            const float* ap = &av.x;
+            const float* bp = &bv.x;
+            float4 ah, al, bh, bl;
+            float* ahp = &ah.x; float* alp = &al.x; float* bhp = &bh.x; float* blp = &bl.x;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool in = k + u < kn;
+                const float x = in ? ap[u] : 0.0f, y = in ? bp[u] : 0.0f;
+                ahp[u] = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+                alp[u] = x - ahp[u];
+                bhp[u] = __uint_as_float(__float_as_uint(y) & 0xffffe000u);
+                blp[u] = y - bhp[u];
+            }
+            const int o = ((rg * (kBigNB / 4) + kq) << 7) + (rin << 4);
+            *(float4*)(Ahi + o) = ah;
+            *(float4*)(Alo + o) = al;
+            *(float4*)(Bhi + o) = bh;
+            *(float4*)(Blo + o) = bl;
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        tmem = tmem_base;
+        if (tid == 0) {
+            const unsigned char* As[3] = {Ahi, Ahi, Alo};
+            const unsigned char* Bs[3] = {Bhi, Blo, Bhi};
+            for (int kk = 0; kk < kn; kk += 8)
+                for (int q = 0; q < 3; ++q) {
+                    const uint64_t ad = umma_sdesc(smem_u32(As[q]) + (kk / 4) * 128);
+                    const uint64_t bd = umma_sdesc(smem_u32(Bs[q]) + (kk / 4) * 128);
+                    const uint32_t acc = (kc > 0 || kk > 0 || q > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar)));
+        }
+        // bounded wait for this chunk's MMAs (mbarrier phase = round parity); the staged
+        // operands may only be overwritten after it
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 24) && !done; ++it)
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(smem_u32(&mbar)), "r"((uint32_t)(round & 1)));
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        ok = __syncthreads_and(done) != 0;
+        if (!ok) break;
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    if (ok) {
+        // warp w reads the tensor-memory lanes of its quarter (w mod 4) and the 32 columns
+        // of chunk w / 4
+        const int quarter = warp & 3, cb = (warp >> 2) * 32;
+        const int i = r0 + quarter * 32 + lane;
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (i < f) {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = c0 + cb + jj;
+                if (j < f && i >= j) F[(int64_t)j * f + i] -= __uint_as_float(v[jj]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTcM));
 }
 
 // FP32 working front → the FP64 front storage (lower triangle)
@@ -431,6 +611,8 @@ unsigned gridfor(int64_t n, int threads) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)nsm() * 16));
 }
 
+constexpr int kOuterNB = 4 * kBigNB;  // FP32 fronts: outer panel width (tensor-core K)
+
 template <class T>
 int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, int idx, T* F, T* W,
                  cudaStream_t st) {
@@ -442,22 +624,63 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
     k_big_extend_add<T><<<(unsigned)((f + 7) / 8), 256, 0, st>>>(s, a, P.d_ea_ptr + P.big_ea_off[idx],
                                                                   P.d_ea_child, P.d_ea_pos, F);
     launches += 3;
-    for (int k0 = 0; k0 < c; k0 += kBigNB) {
-        const int nb = std::min(kBigNB, c - k0);
-        k_big_diag<T><<<1, 256, 0, st>>>(s, k0, nb, a, F, P.big_linv + P.big_linv_off[idx] +
-                                                              (int64_t)(k0 / kBigNB) * kBigNB * kBigNB);
-        const int rows = f - k0 - nb;
-        ++launches;
-        if (rows <= 0) continue;
-        k_big_l21<T><<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(s, k0, nb, a, F, W);
-        const int nt = (rows + kBT - 1) / kBT;
-        k_big_trailing<T><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(s, k0, nb, a, F, W);
-        launches += 2;
+    double* linv = P.big_linv + P.big_linv_off[idx];
+    if constexpr (sizeof(T) == 8) {
+        // FP64: 64-column panels, each followed by the full trailing update
+        for (int k0 = 0; k0 < c; k0 += kBigNB) {
+            const int nb = std::min(kBigNB, c - k0);
+            k_big_diag<T><<<1, 256, 0, st>>>(s, k0, nb, a, F, linv + (int64_t)(k0 / kBigNB) * kBigNB * kBigNB);
+            const int rows = f - k0 - nb;
+            ++launches;
+            if (rows <= 0) continue;
+            k_big_l21<T><<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(s, k0, nb, a, F, W, nullptr, kBigNB);
+            const int nt = (rows + kBT - 1) / kBT;
+            k_big_trailing<T><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(s, k0, nb, a, F, W, kBigNB, f);
+            launches += 2;
+        }
+    } else {
+        // FP32: outer panels of kOuterNB columns made of 64-column inner panels; an inner
+        // panel updates only the rest of its outer panel (CUDA cores), and the trailing
+        // matrix takes one rank-kOuterNB update on the tensor cores (3×TF32)
+        T* Lr = W + (int64_t)P.max_big_f * kOuterNB;
+        for (int k0 = 0; k0 < c; k0 += kOuterNB) {
+            const int nbo = std::min(kOuterNB, c - k0);
+            for (int k1 = k0; k1 < k0 + nbo; k1 += kBigNB) {
+                const int nb = std::min(kBigNB, k0 + nbo - k1);
+                k_big_diag<T><<<1, 256, 0, st>>>(s, k1, nb, a, F, linv + (int64_t)(k1 / kBigNB) * kBigNB * kBigNB);
+                const int rows = f - k1 - nb;
+                ++launches;
+                if (rows <= 0) continue;
+                k_big_l21<T><<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(s, k1, nb, a, F, W + (k1 - k0),
+                                                                             Lr + (k1 - k0), kOuterNB);
+                ++launches;
+                const int cend = k0 + nbo;
+                if (k1 + nb < cend) {
+                    const int ntr = (rows + kBT - 1) / kBT, ntc = (cend - k1 - nb + kBT - 1) / kBT;
+                    k_big_trailing<T><<<(unsigned)(ntr * ntc), 256, 0, st>>>(s, k1, nb, a, F, W + (k1 - k0),
+                                                                             kOuterNB, cend);
+                    ++launches;
+                }
+            }
+            const int rows = f - k0 - nbo;
+            if (rows > 0) {
+                const int nt = (rows + kTcM - 1) / kTcM;
+                k_big_trailing_tc<<<(unsigned)(nt * (nt + 1) / 2), 512, kTcSmem, st>>>(s, k0, nbo, a, F, Lr, W,
+                                                                                      kOuterNB, P.big_err);
+                ++launches;
+            }
+        }
     }
     return launches;
 }
 
 }  // namespace
+
+int big_set_attributes() {
+    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_big_trailing_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    nsm();  // queried here, outside any stream capture of the launch sequences
+    return 0;
+}
 
 int launch_big_factor(const FactorPlan& P, const FactorView& a, const double* kval, int idx, cudaStream_t st) {
     const int f = P.big_f[idx];

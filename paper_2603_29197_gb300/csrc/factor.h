@@ -85,13 +85,14 @@ struct FactorPlan {
     // block b of front idx at big_linv + big_linv_off[idx] + b·64·64), for the solves
     std::vector<int64_t> big_linv_off;
     double* big_linv = nullptr;
+    int* big_err = nullptr;        // set when a tensor-core tile's completion wait ran out
     int64_t* d_ea_ptr = nullptr;
     int* d_ea_child = nullptr;
     int* d_ea_pos = nullptr;
     int max_big_f = 0;
     bool big_fp32 = false;         // factor large fronts in FP32 (mixed precision)
     float* big_work32 = nullptr;   // max_big_f² FP32 working front
-    void* big_w = nullptr;         // max_big_f × kBigNB (FP64 or FP32) panel rows W
+    void* big_w = nullptr;         // max_big_f × 4·kBigNB doubles: panel rows W (FP64), or W and L (FP32)
     double* big_v = nullptr;       // max_big_f solve work vector
     double* big_y = nullptr;       // max_big_f solved block values
 };
@@ -122,6 +123,7 @@ int launch_solve_persistent(const FactorPlan& P, const FactorView& a, const doub
                             cudaStream_t st);
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
 // One large front (P.big_*[idx]): partial LDLᵀ, or the forward / backward solve step.
+int big_set_attributes();
 int launch_big_factor(const FactorPlan& P, const FactorView& a, const double* kval, int idx, cudaStream_t st);
 int launch_big_fwd(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, int idx,
                    cudaStream_t st);

@@ -236,6 +236,13 @@ struct qoco_gpu_solver {
     // polls a grid-barrier wait may take before it gives up (each poll sleeps ~64 ns)
     long long barrier_spins = 20000000;
     bool have_solution = false;  // a solve completed (adjoint available)
+    // CUDA graphs of the level-launch factorisation (per large-front precision) and of the
+    // level-launch solves (per right-hand side / solution / accumulate triple); captured
+    // on a private stream once, replayed on the caller's stream
+    struct Graph { const void* r = nullptr; void* x = nullptr; int acc = 0; cudaGraphExec_t exec = nullptr; int launches = 0; };
+    Graph fgraph[2];
+    std::vector<Graph> sgraphs;
+    cudaStream_t cap_stream = nullptr;
     // batch of independent instances (qoco_gpu_setup_batch)
     bool batch = false;
     BatchView bv;
@@ -455,12 +462,16 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
             nlinv += (int64_t)((P.big_c[idx] + kBigNB - 1) / kBigNB) * kBigNB * kBigNB;
         }
         if ((rc = dalloc(S, &P.big_linv, std::max<int64_t>(nlinv, 1)))) return rc;
+        // panel rows W (and, for FP32 fronts, row-major L) of up to 4·kBigNB columns
         double* pw;
-        if ((rc = dalloc(S, &pw, (size_t)P.max_big_f * kBigNB))) return rc;
+        if ((rc = dalloc(S, &pw, (size_t)P.max_big_f * 4 * kBigNB))) return rc;
         P.big_w = pw;
         if ((rc = dalloc(S, &P.big_v, P.max_big_f))) return rc;
         if ((rc = dalloc(S, &P.big_y, P.max_big_f))) return rc;
         if (S->st.mixed_precision && (rc = dalloc(S, &P.big_work32, (size_t)P.max_big_f * P.max_big_f))) return rc;
+        if ((rc = dalloc(S, &P.big_err, 1))) return rc;
+        QOCO_CUDA_TRY(cudaMemset(P.big_err, 0, sizeof(int)));
+        if ((rc = big_set_attributes())) return rc;
     }
     S->info.large_fronts = (int)ph.big.size();
     P.ntasks = (int)ph.task.size() / 2;
@@ -555,6 +566,26 @@ int sync_scalars(qoco_gpu_solver* S, cudaStream_t st) {
     return 0;
 }
 
+// Captures `launch` (which returns its kernel count) into a graph on the private
+// capture stream and instantiates it.
+template <class F>
+int capture_graph(qoco_gpu_solver* S, qoco_gpu_solver::Graph* g, F launch) {
+    if (!S->cap_stream) QOCO_CUDA_TRY(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    QOCO_CUDA_TRY(cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int n = launch(S->cap_stream);
+    const cudaError_t e = cudaStreamEndCapture(S->cap_stream, &graph);
+    if (e != cudaSuccess || n < 0) {
+        if (graph) cudaGraphDestroy(graph);
+        return n < 0 ? n : cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaGraphInstantiate", __FILE__, __LINE__);
+    g->launches = n;
+    return 0;
+}
+
 int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
     {
         Phase ph(S, QOCO_GPU_PHASE_ROW, st);
@@ -573,7 +604,15 @@ int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
             if (rc < 0) return rc;
             S->launches += rc;
         } else {
-            S->launches += launch_factor(S->plan, S->fv, S->d_val, st);
+            // the level launches (and large-front kernel sequences) are the same every
+            // time: replayed from a graph
+            qoco_gpu_solver::Graph& g = S->fgraph[S->plan.big_fp32 ? 1 : 0];
+            if (!g.exec) {
+                const int rc = capture_graph(S, &g, [&](cudaStream_t cs) { return launch_factor(S->plan, S->fv, S->d_val, cs); });
+                if (rc) return rc;
+            }
+            QOCO_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+            S->launches += g.launches;
         }
     }
     QOCO_CUDA_TRY(cudaGetLastError());
@@ -603,7 +642,24 @@ int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStre
         if (rc < 0) return rc;
         S->launches += rc;
     } else {
-        S->launches += launch_solve(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, st);
+        // level launches: one graph per (r, x, acc) triple (a handful per solver)
+        qoco_gpu_solver::Graph* g = nullptr;
+        for (auto& c : S->sgraphs)
+            if (c.r == r && c.x == x && c.acc == (acc ? 1 : 0)) g = &c;
+        if (!g) {
+            qoco_gpu_solver::Graph ng;
+            ng.r = r;
+            ng.x = x;
+            ng.acc = acc ? 1 : 0;
+            const int rc = capture_graph(S, &ng, [&](cudaStream_t cs) {
+                return launch_solve(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, cs);
+            });
+            if (rc) return rc;
+            S->sgraphs.push_back(ng);
+            g = &S->sgraphs.back();
+        }
+        QOCO_CUDA_TRY(cudaGraphLaunch(g->exec, st));
+        S->launches += g->launches;
     }
     return 0;
 }
@@ -1341,6 +1397,9 @@ int qoco_gpu_get_profile(const qoco_gpu_solver* S, qoco_gpu_profile* out) {
 
 int qoco_gpu_cleanup(qoco_gpu_solver* S) {
     if (!S) return 0;
+    for (auto& g : S->fgraph) if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& g : S->sgraphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
     for (void* p : S->allocs) cudaFree(p);
     if (S->h_S) cudaFreeHost(S->h_S);
     delete S;
