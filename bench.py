@@ -493,16 +493,20 @@ def run_other(args, ws, rank, local):
           "peak_source": ("nominal FP32 CUDA-core rate" if args.mixed else "nominal FP64 rate") +
                          " (unit counts × clock), not a measured peak", "avg_ms": f_ms}
     # e2e: set-up from host data, solve, copy-back
-    t0 = time.perf_counter()
-    E = make()
-    st = E.solve(stream.cuda_stream)
-    sol = E.solution()
-    e2e_s = time.perf_counter() - t0
-    E.close()
+    e2e_s, sol = None, None
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        E = make()
+        st = E.solve(stream.cuda_stream)
+        sol = E.solution()
+        e2e_s = time.perf_counter() - t0
+        E.close()
     # CPU oracle on a bounded sample
     from oracle import ipm
     t0 = time.perf_counter()
-    if batch:
+    if args.no_cpu_baseline:
+        cpu = None
+    elif batch:
         sample = probs[:16]
         for pr in sample:
             ipm.solve(pr)
@@ -517,12 +521,13 @@ def run_other(args, ws, rank, local):
                          f"{info['iters'] + 1} factorisations"}
     if batch:
         metric, value, unit, hib = "batched_solves_per_s", len(probs) / (ms * 1e-3), "solves/s", True
-        e2e = {"value": len(probs) / e2e_s, "unit": unit}
+        e2e = {"value": len(probs) / e2e_s, "unit": unit} if e2e_s else None
     else:
         metric, value, unit, hib = "time_to_1e-7_gap", ms * 1e-3, "s", False
-        e2e = {"value": e2e_s, "unit": unit}
-    e2e.update({"h2d_bytes_per_step": int(sol["info"]["h2d_bytes"]),
-                "d2h_bytes_per_step": int(sol["info"]["d2h_bytes"]) + 8 * (S.n + 2 * S.m + S.p)})
+        e2e = {"value": e2e_s, "unit": unit} if e2e_s else None
+    if e2e:
+        e2e.update({"h2d_bytes_per_step": int(sol["info"]["h2d_bytes"]),
+                    "d2h_bytes_per_step": int(sol["info"]["d2h_bytes"]) + 8 * (S.n + 2 * S.m + S.p)})
     cfg = {"workload": ("mpc_batch_4096: horizons U{10..60}, state 4, control 2, Q^3 input cone, "
                         "box bounds" if batch else "lasso_qp_r5000_c10000: F 5000x10000, 50 nnz/row"),
            "kkt_dim": info["kkt_dim"], "kkt_nnz": info["kkt_nnz"], "factor_flops": info["factor_flops"],
