@@ -8,7 +8,7 @@
 namespace qoco {
 
 constexpr int kRowThreads = 256;
-constexpr int kMaxRowBlocks = 152 * 2;  // grid cap: 2 blocks (16 warps) per SM
+constexpr int kMaxRowBlocks = 152 * 8;  // grid cap: 8 blocks (64 warps, a full SM) per SM
 
 template <int NV>
 __device__ __forceinline__ void store_partials(double (&v)[NV], const bool (&is_max)[NV], double* partial) {
@@ -230,7 +230,7 @@ int launch_residual(const KKTView& K, int lpr, const double* xyz, const double* 
     if ((int64_t)rows_blocks(K.N, lpr) * kResNV > cap) return -1;
     int nb = 0;
     QOCO_LPR_SWITCH(lpr, k_residual, K, xyz, s, c, b, h, r, partial)
-    k_finalize_residual<<<1, 512, 0, st>>>(partial, nb, S);
+    k_finalize_residual<<<1, 1024, 0, st>>>(partial, nb, S);
     return 0;
 }
 int launch_spmv_res(const KKTView& K, int lpr, const double* x, const double* r, double* res,
@@ -238,7 +238,7 @@ int launch_spmv_res(const KKTView& K, int lpr, const double* x, const double* r,
     if ((int64_t)rows_blocks(K.N, lpr) * 3 > cap) return -1;
     int nb = 0;
     QOCO_LPR_SWITCH(lpr, k_spmv_res, K, x, r, res, partial)
-    k_finalize_refine<<<1, 512, 0, st>>>(partial, nb, S);
+    k_finalize_refine<<<1, 1024, 0, st>>>(partial, nb, S);
     return 0;
 }
 int launch_norm_inf(const KKTView& K, int lpr, double* partial, int64_t cap, IPMScalars* S,
@@ -246,7 +246,7 @@ int launch_norm_inf(const KKTView& K, int lpr, double* partial, int64_t cap, IPM
     if ((int64_t)rows_blocks(K.N, lpr) > cap) return -1;
     int nb = 0;
     QOCO_LPR_SWITCH(lpr, k_norm_inf, K, partial)
-    k_finalize_norm<<<1, 512, 0, st>>>(partial, nb, S);
+    k_finalize_norm<<<1, 1024, 0, st>>>(partial, nb, S);
     return 0;
 }
 

@@ -196,6 +196,7 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S) {
         if (parent[last] >= 0) fparent[s] = col2f[parent[last]];
     }
     // relaxed amalgamation: merge the immediately preceding supernode (the last child)
+    constexpr int kAmalgSmallFront = 48, kAmalgSmallCap = 40;
     struct SN { int first, ncol, f; double truenz; int fparent; };
     std::vector<SN> stack;
     stack.reserve(nf);
@@ -215,8 +216,12 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S) {
             double dense = (double)ncol * f - 0.5 * (double)ncol * (ncol - 1);
             double tnz = c.truenz + cur.truenz;
             double zf = 1.0 - tnz / dense;
-            bool ok = (ncol <= 4) || (ncol <= 16 && zf <= 0.8) || (ncol <= 48 && zf <= 0.1) ||
-                      (zf <= 0.05);
+            // Merging trades explicit zeros (FP64 work) for fewer supernodes and a shallower
+            // tree (a shorter dependent chain of fronts).  A parent that is still a small
+            // front stays at order ≤ kAmalgSmallCap, so that it remains on the one-warp /
+            // one-thread kernels and their occupancy; larger fronts merge by zeros alone.
+            bool ok = (ncol <= 4) || (ncol <= 16 && zf <= 0.8) || (ncol <= 48 && zf <= 0.7) || (zf <= 0.3);
+            if (cur.f <= kAmalgSmallFront && f > kAmalgSmallCap) ok = false;
             if (!ok) break;
             cur.first = c.first;
             cur.ncol = ncol;

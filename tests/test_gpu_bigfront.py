@@ -1,7 +1,7 @@
 """Large fronts (order ≥ 256): the grid-wide panel kernels, in FP64 and in mixed
 precision (FP32 fronts, FP64 solves and refinement), through the C ABI.
 
-* FP64: the factor of a natural-order dense QP (fronts of 448–600 rows, several 64-column
+* FP64: the factor of a natural-order dense QP (large fronts of several 64-column
   panels) equals the textbook LDLᵀ of the regularised KKT matrix (oracle/kkt.py).
 * Mixed: the same factor agrees to FP32 accuracy, and refinement still reaches the
   1e-10 backward error on the unregularised K.
@@ -43,7 +43,8 @@ def test_large_front_factor_matches_textbook_ldlt(mixed):
     prob = dense_qp(seed=0)
     s, z, _, _ = random_cone_iterate(prob.l, prob.q, seed=4)
     S = q.Solver(prob, ordering=q.ORDER_NATURAL, mixed_precision=mixed)
-    assert S.info()["large_fronts"] >= 2
+    info = S.info()
+    assert info["large_fronts"] >= 1 and info["max_front"] >= 4 * 64  # several 64-column panels
     S.kkt_factor_at(T(s), T(z))
     perm, L, D = S.factor_dense()
     sg = ok.reg_signs(prob)
