@@ -218,6 +218,8 @@ int row_partials(int N) { return rows_blocks(N, 32) * kResNV; }
 
 #define QOCO_LPR_SWITCH(lpr, KERNEL, ...)                                          \
     switch (lpr) {                                                                 \
+        case 1: KERNEL<1><<<rows_blocks(K.N, 1), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 1); break;   \
+        case 2: KERNEL<2><<<rows_blocks(K.N, 2), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 2); break;   \
         case 4: KERNEL<4><<<rows_blocks(K.N, 4), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 4); break;   \
         case 8: KERNEL<8><<<rows_blocks(K.N, 8), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 8); break;   \
         case 16: KERNEL<16><<<rows_blocks(K.N, 16), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 16); break; \

@@ -353,7 +353,9 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     S->kv.N = N; S->kv.n = K.n; S->kv.p = K.p; S->kv.m = K.m;
     S->kv.rowptr = S->d_rowptr; S->kv.colidx = S->d_colidx; S->kv.val = S->d_val;
     const double avg = N ? (double)K.nnz() / N : 1.0;
-    S->lpr = avg <= 8 ? 4 : avg <= 24 ? 8 : avg <= 64 ? 16 : 32;
+    // lanes per KKT row in the row kernels: one thread per row for the very sparse rows
+    // of stage-structured problems (no shuffles, one row-pointer load per row)
+    S->lpr = avg <= 6 ? 1 : avg <= 12 ? 2 : avg <= 24 ? 4 : avg <= 48 ? 8 : avg <= 96 ? 16 : 32;
 
     // symbolic structure
     FactorView& f = S->fv;
