@@ -73,7 +73,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_info: bool = False) 
                 logs.append(out)
     if todo or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
+        _run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"])
         os.replace(tmp, LIB)
     if verbose:
         print("\n".join(l for l in logs if l.strip()))

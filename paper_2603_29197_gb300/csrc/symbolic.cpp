@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 #include "symbolic.h"
 
@@ -138,9 +139,16 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S) {
     } else {
         // AUTO: cost model = factor flops at an effective FP64 rate plus a per-level
         // latency for the level-scheduled factor and solves
-        std::vector<int> pa = order_amd(g);
-        std::vector<int> pn = order_nd(g, st.nd_leaf);
-        OrderingCost ca = ordering_cost(K, pa), cn = ordering_cost(K, pn);
+        // the two candidates are independent: ordered and costed on two host threads
+        std::vector<int> pa, pn;
+        OrderingCost ca, cn;
+        std::thread tn([&]() {
+            pn = order_nd(g, st.nd_leaf);
+            cn = ordering_cost(K, pn);
+        });
+        pa = order_amd(g);
+        ca = ordering_cost(K, pa);
+        tn.join();
         auto cost = [](const OrderingCost& c) { return c.flops / 2e11 + c.height * 4e-5; };
         if (cost(cn) < cost(ca)) { perm0 = std::move(pn); used = QOCO_GPU_ORDER_ND; }
         else { perm0 = std::move(pa); used = QOCO_GPU_ORDER_AMD; }
