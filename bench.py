@@ -244,6 +244,18 @@ def roofline(profile, info, stages):
             "launches_per_call": rec["launches"] / max(1, rec["calls"])}
 
 
+def reduce_max(value, device=None):
+    """Max of a float over the ranks (identity without a process group); the tensor lives
+    on `device` (CUDA for NCCL, CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -347,19 +359,13 @@ def run_ours(args, ws, rank, local):
     info = S.info()
     info["m_cone"] = prob.m
     ms = statistics.mean(times)
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_local.item())
+    ms_max = reduce_max(ms, dev)
     rl = roofline(prof, info, args.stages)
 
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(q, prob, args, stream, dev)
-        if ws > 1:
-            tt = torch.tensor([e2e["value"]], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e2e["value"] = float(tt.item())
+        e2e["value"] = reduce_max(e2e["value"], dev)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(args.stages)
