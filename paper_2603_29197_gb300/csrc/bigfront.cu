@@ -83,8 +83,7 @@ __global__ void k_big_extend_add(int s, FactorView a, const int64_t* __restrict_
 // soon as it has applied the current column to it, so each column costs one barrier.
 // Entry (i, j) of the lower triangle belongs to thread (i·(i+1)/2 + j) mod blockDim.
 template <class T>
-__global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorView a, T* __restrict__ F,
-                                                  double* __restrict__ Xinv) {
+__global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorView a, T* __restrict__ F) {
     constexpr int kOwn = (kBigNB * (kBigNB + 1) / 2 + 255) / 256;  // entries per thread
     __shared__ T D[kBigNB][kBigNB + 1];
     __shared__ T s_inv[kBigNB];
@@ -149,38 +148,48 @@ __global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorV
     }
     // FP64 reciprocal pivots for the solves (off the pivot chain)
     for (int k = tid; k < nb; k += nt) a.dinv[first + k0 + k] = recip((double)D[k][k]);
-    // L (scaled columns) and D back to the front; the strictly lower part of D becomes L
+    // L (scaled columns) and D back to the front
     for (int t = tid; t < nb * nb; t += nt) {
         const int j = t / nb, i = t - j * nb;
-        if (i > j) {
-            const T l = D[i][j] * s_inv[j];
-            F[(int64_t)(k0 + j) * f + k0 + i] = l;
-            D[i][j] = l;
-        } else if (i == j) {
-            F[(int64_t)(k0 + j) * f + k0 + i] = D[i][j];
-        }
+        if (i > j) F[(int64_t)(k0 + j) * f + k0 + i] = D[i][j] * s_inv[j];
+        else if (i == j) F[(int64_t)(k0 + j) * f + k0 + i] = D[i][j];
+    }
+    if (nreg) atomicAdd(a.nreg, nreg);
+}
+
+// Inverses of the front's 64×64 unit-lower diagonal blocks (for the solves), one CTA per
+// block, after the whole front is factored (off the factorisation's pivot chain).  In
+// place in shared memory: after step k, rows ≤ k hold L⁻¹'s rows; row i > k takes
+// X_ij ← X_ij − L_ik·X_kj for j < k and X_ik ← −L_ik (L_ik read before column k is
+// overwritten).  Stored row-major: Xinv[b][i·64 + j] (unit diagonal, zero above).
+template <class T>
+__global__ void __launch_bounds__(256) k_big_block_inverse(int s, FactorView a, const T* __restrict__ F,
+                                                           double* __restrict__ Xinv) {
+    __shared__ double X[kBigNB][kBigNB + 1];
+    const int f = a.nrow[s], c = a.ncol[s];
+    const int k0 = blockIdx.x * kBigNB, nb = min(kBigNB, c - k0);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int t = tid; t < nb * nb; t += nt) {
+        const int j = t / nb, i = t - j * nb;
+        X[i][j] = i > j ? (double)F[(int64_t)(k0 + j) * f + k0 + i] : 0.0;
     }
     __syncthreads();
-    // in-place inverse of the unit lower triangle (in the working precision): after step
-    // k, rows ≤ k hold L⁻¹'s rows; row i > k takes X_ij ← X_ij − L_ik·X_kj for j < k and
-    // X_ik ← −L_ik (L_ik is read from column k before that column is overwritten)
     for (int k = 0; k < nb - 1; ++k) {
-        const int m = nb - 1 - k;  // rows k+1 .. nb−1
+        const int m = nb - 1 - k;
         for (int t = tid; t < m * k; t += nt) {
             const int ii = t / k, j = t - ii * k;
             const int i = k + 1 + ii;
-            D[i][j] -= D[i][k] * D[k][j];
+            X[i][j] -= X[i][k] * X[k][j];
         }
         __syncthreads();
-        for (int i = k + 1 + tid; i < nb; i += nt) D[i][k] = -D[i][k];
+        for (int i = k + 1 + tid; i < nb; i += nt) X[i][k] = -X[i][k];
         __syncthreads();
     }
-    // store row-major: Xinv[i·kBigNB + j] = (L_bb⁻¹)_ij (unit diagonal, zero above)
+    double* out = Xinv + (int64_t)blockIdx.x * kBigNB * kBigNB;
     for (int t = tid; t < nb * nb; t += nt) {
         const int i = t / nb, j = t - i * nb;
-        Xinv[i * kBigNB + j] = j < i ? (double)D[i][j] : (j == i ? 1.0 : 0.0);
+        out[i * kBigNB + j] = j < i ? X[i][j] : (j == i ? 1.0 : 0.0);
     }
-    if (nreg) atomicAdd(a.nreg, nreg);
 }
 
 // rows i ≥ k0+nb: w = a_i· L11⁻ᵀ, l_i· = w D⁻¹ (into F and, if Lr, row-major into
@@ -316,9 +325,6 @@ constexpr int kTcTile = kTcM * kBigNB * 4;      // bytes of one 128×64 FP32 ope
 constexpr int kTcSmem = 4 * kTcTile + 1024;     // four operands + alignment slack
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ int kmaj_off(int r, int k) {
-    return (((r >> 3) * (kBigNB / 4) + (k >> 2)) << 7) + ((r & 7) << 4) + ((k & 3) << 2);
-}
 __device__ __forceinline__ uint64_t umma_sdesc(uint32_t addr) {
     uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
     d |= (uint64_t)(128 >> 4) << 16;                   // leading byte offset (K)
@@ -629,7 +635,7 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
         // FP64: 64-column panels, each followed by the full trailing update
         for (int k0 = 0; k0 < c; k0 += kBigNB) {
             const int nb = std::min(kBigNB, c - k0);
-            k_big_diag<T><<<1, 256, 0, st>>>(s, k0, nb, a, F, linv + (int64_t)(k0 / kBigNB) * kBigNB * kBigNB);
+            k_big_diag<T><<<1, 256, 0, st>>>(s, k0, nb, a, F);
             const int rows = f - k0 - nb;
             ++launches;
             if (rows <= 0) continue;
@@ -647,7 +653,7 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
             const int nbo = std::min(kOuterNB, c - k0);
             for (int k1 = k0; k1 < k0 + nbo; k1 += kBigNB) {
                 const int nb = std::min(kBigNB, k0 + nbo - k1);
-                k_big_diag<T><<<1, 256, 0, st>>>(s, k1, nb, a, F, linv + (int64_t)(k1 / kBigNB) * kBigNB * kBigNB);
+                k_big_diag<T><<<1, 256, 0, st>>>(s, k1, nb, a, F);
                 const int rows = f - k1 - nb;
                 ++launches;
                 if (rows <= 0) continue;
@@ -671,7 +677,9 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
             }
         }
     }
-    return launches;
+    // the diagonal blocks' inverses for the solves, all blocks in parallel
+    k_big_block_inverse<T><<<(unsigned)((c + kBigNB - 1) / kBigNB), 256, 0, st>>>(s, a, F, linv);
+    return launches + 1;
 }
 
 }  // namespace

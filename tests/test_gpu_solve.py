@@ -111,3 +111,28 @@ def test_orderings_agree(q):
     for s in sols[1:]:
         assert rel_inf(s["x"], sols[0]["x"]) <= 1e-6
         assert abs(s["info"]["pobj"] - sols[0]["info"]["pobj"]) <= 1e-7 * abs(sols[0]["info"]["pobj"])
+
+
+def test_one_variable_problem(q):
+    # min x² + x  s.t.  x ≥ 0  (G = −1, h = 0): the bound is active, x = 0
+    prob = Problem(n=1, m=1, p=0, P=sp.csc_matrix([[2.0]]), c=np.array([1.0]), A=sp.csc_matrix((0, 1)),
+                   b=np.zeros(0), G=sp.csc_matrix([[-1.0]]), h=np.zeros(1), l=1, q=[], name="one_var")
+    ref = ipm.solve(prob)
+    S = q.Solver(prob)
+    assert S.solve() == 0
+    sol = S.solution()
+    assert abs(sol["x"][0] - ref.x[0]) <= 1e-6 and abs(sol["x"][0]) <= 1e-6
+    assert abs(sol["z"][0] - 1.0) <= 1e-5  # the multiplier equals the gradient at 0
+    S.close()
+
+
+def test_infeasible_problem_is_not_reported_solved(q):
+    # x ≥ 1 and x ≤ −1: no feasible point; the loop must stop at max_iter (or on a
+    # numerical failure) without claiming a solution
+    prob = Problem(n=1, m=2, p=0, P=sp.csc_matrix((1, 1)), c=np.array([1.0]), A=sp.csc_matrix((0, 1)),
+                   b=np.zeros(0), G=sp.csc_matrix([[-1.0], [1.0]]), h=np.array([-1.0, -1.0]), l=2, q=[],
+                   name="infeasible")
+    S = q.Solver(prob, max_iter=40)
+    status = S.solve()
+    assert status in (2, -5), status  # MAX_ITER or ERR_NUMERICAL
+    S.close()
