@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--stages", type=int, default=20000, help="trajectory stages (default: the benchmark size)")
-    ap.add_argument("--workload", default="trajectory", choices=["trajectory", "lasso", "mpc_batch"],
+    ap.add_argument("--workload", default="trajectory", choices=["trajectory", "lasso", "mpc_batch", "portfolio"],
                     help="trajectory (default, the headline line); lasso: the lasso QP scaled by 1/10 "
-                         "(F 5000x10000, FP64 or --mixed); mpc_batch: 4096 MPC instances, solves/s")
+                         "(F 5000x10000, FP64 or --mixed); mpc_batch: 4096 MPC instances, solves/s; "
+                         "portfolio: n = 20000 assets, solve plus the adjoint of ||x - 1/n||^2")
     ap.add_argument("--mixed", action="store_true", help="FP32 large fronts with FP64 refinement")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -440,10 +441,29 @@ def run_e2e(q, prob, args, stream, dev):
 
 # --------------------------------------------------------------------------- other workloads
 def other_workload(args):
-    from workloads import lasso_qp, mpc_batch
+    from workloads import lasso_qp, mpc_batch, portfolio_socp
     if args.workload == "lasso":
         return [lasso_qp(rows=5000, cols=10000, density=5e-3, seed=0)]
+    if args.workload == "portfolio":
+        return [portfolio_socp(n=20000, k=200, seed=0)]
     return mpc_batch(count=4096, seed=0)
+
+
+def golden_error(name, sol, pobj):
+    """Deviation of the solution from the stored oracle values (tests/golden), if any."""
+    path = os.path.join(ROOT, "tests", "golden", name + ".json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        g = json.load(f)
+    out = {"pobj_rel": abs(pobj - g["pobj"]) / max(1.0, abs(g["pobj"]))}
+    for key in ("x", "y", "z"):
+        if f"{key}_idx" in g:
+            got = [float(sol[key][i]) for i in g[f"{key}_idx"]]
+            d = max(abs(a - b) for a, b in zip(got, g[f"{key}_val"]))
+            out[f"{key}_rel_sampled"] = d / max(1.0, g[f"{key}_inf"])
+    out["reference"] = f"oracle values stored in tests/golden/{name}.json"
+    return out
 
 
 def run_other(args, ws, rank, local):
@@ -489,6 +509,23 @@ def run_other(args, ws, rank, local):
     info = S.info()
     S.set_profiling(False)
     ms = statistics.mean(times)
+    adj = None
+    if args.workload == "portfolio":
+        # the adjoint of L = ||x - 1/n||^2 after the last timed solve (reuses its factor)
+        x = S.solution_tensors()[0]
+        gx = 2.0 * (x - 1.0 / x.numel())
+        bts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S.backward(dx=gx)
+            e1.record(stream)
+            e1.synchronize()
+            bts.append(e0.elapsed_time(e1))
+        bi = S.backward_info()
+        adj = {"backward_ms": statistics.mean(bts), "refine_steps": bi["refine_steps"],
+               "backward_error": bi["backward_error"], "refactored": bi["refactored"],
+               "solve_plus_backward_ms": ms + statistics.mean(bts)}
     fcalls = max(1, prof["factor"]["calls"])
     f_ms = prof["factor"]["ms"] / fcalls
     gflops = info["factor_flops"] / (f_ms * 1e-3) / 1e9
@@ -534,8 +571,10 @@ def run_other(args, ws, rank, local):
     if e2e:
         e2e.update({"h2d_bytes_per_step": int(sol["info"]["h2d_bytes"]),
                     "d2h_bytes_per_step": int(sol["info"]["d2h_bytes"]) + 8 * (S.n + 2 * S.m + S.p)})
-    cfg = {"workload": ("mpc_batch_4096: horizons U{10..60}, state 4, control 2, Q^3 input cone, "
-                        "box bounds" if batch else "lasso_qp_r5000_c10000: F 5000x10000, 50 nnz/row"),
+    wl = {"mpc_batch": "mpc_batch_4096: horizons U{10..60}, state 4, control 2, Q^3 input cone, box bounds",
+          "lasso": "lasso_qp_r5000_c10000: F 5000x10000, 50 nnz/row",
+          "portfolio": "portfolio_socp_n20000: 20000 assets, factor model k=200, Q^201 risk cone"}
+    cfg = {"workload": wl[args.workload],
            "kkt_dim": info["kkt_dim"], "kkt_nnz": info["kkt_nnz"], "factor_flops": info["factor_flops"],
            "iterations": info["iters"], "max_front": info["max_front"], "large_fronts": info["large_fronts"],
            "precision": "mixed (FP32 large fronts, FP64 refinement)" if args.mixed else "fp64",
@@ -547,6 +586,11 @@ def run_other(args, ws, rank, local):
            "config": cfg, "gpu_launches": launches, "refactor_gflops": gflops,
            "phase_ms_per_solve": {k: v["ms"] / args.steps for k, v in prof.items()},
            "roofline": rl, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    if not batch:
+        gname = {"lasso": "lasso_qp_r5000_c10000", "portfolio": "portfolio_socp_n20000"}[args.workload]
+        out["error_vs_oracle"] = golden_error(gname, S.solution(), info["pobj"])
+    if adj:
+        out["adjoint"] = adj
     if rank == 0:
         print(json.dumps(out), flush=True)
     S.close()

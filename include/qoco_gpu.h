@@ -84,7 +84,7 @@ typedef struct {
                                            subtree tasks below the level launches; ≤ 0 = none,
                                            every supernode in level launches (default 0) */
     int verbose;                        /* 0: silent; 1: one line per iteration on stdout */
-    int mixed_precision;                /* 1: fronts of order ≥ 256 factored in FP32 (FP32
+    int mixed_precision;                /* 1: fronts of order ≥ 160 factored in FP32 (FP32
                                            accumulation), solves and refinement in FP64; a
                                            solve whose refinement misses refine_tol within
                                            max_refine steps refactors in FP64, and the rest

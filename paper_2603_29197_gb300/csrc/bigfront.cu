@@ -462,6 +462,142 @@ __global__ void __launch_bounds__(512) k_big_trailing_tc(int s, int k0, int kb, 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTcM));
 }
 
+// ---- leaf groups ----------------------------------------------------------------------
+// Member pivots: one warp per member front (childless, c ≤ 8 pivot columns): its f×c
+// columns are assembled from the KKT values, the c×c block factored (dynamic
+// regularisation as everywhere), the columns scaled to L; the update block is never
+// formed (its sum over the group reaches the parent through k_group_syrk_*).
+__global__ void k_leaf_members(const int* __restrict__ members, int nmem, FactorView a,
+                               const double* __restrict__ kval) {
+    const int lane = threadIdx.x & 31;
+    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (w >= nmem) return;
+    const int s = members[w];
+    const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
+    double* Fm = a.front + a.front_off[s];
+    for (int e = lane; e < f * c; e += 32) Fm[e] = 0.0;
+    __syncwarp();
+    for (int64_t e = a.amap_ptr[s] + lane; e < a.amap_ptr[s + 1]; e += 32) {
+        const int off = a.amap_off[e];
+        double v = kval[a.amap_slot[e]];
+        const int col = off / f, row = off - col * f;
+        if (row == col) v += a.dsign[first + col] > 0 ? a.eps : -a.eps;
+        Fm[off] = v;
+    }
+    __syncwarp();
+    int nreg = 0;
+    for (int k = 0; k < c; ++k) {
+        double d = Fm[k * f + k];
+        const bool pos = a.dsign[first + k] > 0;
+        const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
+        if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
+        const double inv = recip(d);
+        __syncwarp();
+        if (lane == 0) {
+            Fm[k * f + k] = d;
+            a.dinv[first + k] = inv;
+        }
+        // later pivot columns with the unscaled column k, then scale column k
+        for (int j = k + 1; j < c; ++j) {
+            const double wj = Fm[k * f + j] * inv;
+            for (int i = j + lane; i < f; i += 32) Fm[j * f + i] -= Fm[k * f + i] * wj;
+        }
+        __syncwarp();
+        for (int i = k + 1 + lane; i < f; i += 32) Fm[k * f + i] *= inv;
+        __syncwarp();
+    }
+    if (lane == 0 && nreg) atomicAdd(a.nreg, nreg);
+}
+
+// Group operands: Lg[i·K + kofs + p] = L21 entries of member column p, Wg = Lg·d_p
+__global__ void k_group_gather(const int* __restrict__ members, const int* __restrict__ kofs, int nmem, int r, int K,
+                               FactorView a, double* __restrict__ Lg, double* __restrict__ Wg) {
+    const int lane = threadIdx.x & 31;
+    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (w >= nmem) return;
+    const int s = members[w];
+    const int f = a.nrow[s], c = a.ncol[s];
+    const double* Fm = a.front + a.front_off[s];
+    for (int p = 0; p < c; ++p) {
+        const double d = Fm[p * f + p];
+        for (int i = lane; i < r; i += 32) {
+            const double l = Fm[p * f + c + i];
+            Lg[(int64_t)i * K + kofs[w] + p] = l;
+            Wg[(int64_t)i * K + kofs[w] + p] = l * d;
+        }
+    }
+}
+
+// Split-K partial products of the group's update −Lg·Wgᵀ: CTA (tile, split) computes one
+// 64×64 lower tile of Lg·Wgᵀ over its K-chunk into part[(split·ntile + tile)·4096]
+__global__ void __launch_bounds__(256) k_group_syrk_part(const double* __restrict__ Lg, const double* __restrict__ Wg,
+                                                         int r, int K, int nsplit, double* __restrict__ part) {
+    constexpr int KC = 32;
+    __shared__ double Ls[KC][kBT + 1];
+    __shared__ double Ws[KC][kBT + 1];
+    const int nt = (r + kBT - 1) / kBT, ntile = nt * (nt + 1) / 2;
+    const int tile = blockIdx.x % ntile, split = blockIdx.x / ntile;
+    int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    while (ti * (ti + 1) / 2 > tile) --ti;
+    const int tj = tile - ti * (ti + 1) / 2;
+    const int r0 = ti * kBT, c0 = tj * kBT;
+    const int kchunk = (K + nsplit - 1) / nsplit;
+    const int kb = split * kchunk, ke = min(K, kb + kchunk);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int k0 = kb; k0 < ke; k0 += KC) {
+        const int kn = min(KC, ke - k0);
+        for (int e = tid; e < KC * kBT; e += 256) {
+            const int rr = e / KC, k = e - rr * KC;
+            Ls[k][rr] = (k < kn && r0 + rr < r) ? Lg[(int64_t)(r0 + rr) * K + k0 + k] : 0.0;
+            Ws[k][rr] = (k < kn && c0 + rr < r) ? Wg[(int64_t)(c0 + rr) * K + k0 + k] : 0.0;
+        }
+        __syncthreads();
+        for (int k = 0; k < kn; ++k) {
+            double lr[4], wc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) lr[u] = Ls[k][tx + 16 * u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) wc[v] = Ws[k][ty * 4 + v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += lr[u] * wc[v];
+        }
+        __syncthreads();
+    }
+    double* out = part + ((int64_t)split * ntile + tile) * (kBT * kBT);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) out[(tx + 16 * u) * kBT + ty * 4 + v] = acc[u][v];
+}
+
+// Sum of the split-K partials in split order, subtracted into the parent front at the
+// members' relative positions (lower triangle)
+template <class T>
+__global__ void k_group_syrk_reduce(const double* __restrict__ part, int r, int nsplit, const int* __restrict__ rel,
+                                    int f, T* __restrict__ F) {
+    const int nt = (r + kBT - 1) / kBT, ntile = nt * (nt + 1) / 2;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)ntile * kBT * kBT) return;
+    const int tile = (int)(e / (kBT * kBT)), q = (int)(e - (int64_t)tile * kBT * kBT);
+    int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+    while (ti * (ti + 1) / 2 > tile) --ti;
+    const int tj = tile - ti * (ti + 1) / 2;
+    const int i = ti * kBT + q / kBT, j = tj * kBT + q % kBT;
+    if (i >= r || j >= r || i < j) return;
+    double sum = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) sum += part[((int64_t)sp * ntile + tile) * (kBT * kBT) + q];
+    F[(int64_t)rel[j] * f + rel[i]] -= (T)sum;
+}
+
 // FP32 working front → the FP64 front storage (lower triangle)
 __global__ void k_big_writeback(const float* __restrict__ Fw, double* __restrict__ G, int f) {
     const int64_t n = (int64_t)f * f;
@@ -483,6 +619,29 @@ __global__ void k_big_fwd_gather(int s, FactorView a, const int64_t* __restrict_
         for (int64_t e = ea_ptr[i]; e < ea_ptr[i + 1]; ++e) acc += a.upd[a.cinfo[ea_child[e]].rel_off + ea_pos[e]];
         v[i] = acc;
     }
+}
+
+// Leaf-group members' update vectors, summed in two deterministic stages: CTA b sums
+// members [b·kGrpChunk, …) row by row into part[b·r + i]; then the chunks are summed in
+// order into the parent's gathered vector at the members' relative rows.
+constexpr int kGrpChunk = 256;
+__global__ void k_group_upd_part(const int64_t* __restrict__ updoff, int nmem, int r, FactorView a,
+                                 double* __restrict__ part) {
+    const int b = blockIdx.x;
+    const int m0 = b * kGrpChunk, m1 = min(nmem, m0 + kGrpChunk);
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+        double acc = 0.0;
+        for (int m = m0; m < m1; ++m) acc += a.upd[updoff[m] + i];
+        part[(int64_t)b * r + i] = acc;
+    }
+}
+__global__ void k_group_upd_reduce(const double* __restrict__ part, int nchunk, int r, const int* __restrict__ rel,
+                                   double* __restrict__ v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= r) return;
+    double acc = 0.0;
+    for (int b = 0; b < nchunk; ++b) acc += part[(int64_t)b * r + i];
+    v[rel[i]] += acc;
 }
 
 // one forward block: y_b = L_bb⁻¹ v_b with the inverse stored by the factorisation
@@ -630,6 +789,18 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
     k_big_extend_add<T><<<(unsigned)((f + 7) / 8), 256, 0, st>>>(s, a, P.d_ea_ptr + P.big_ea_off[idx],
                                                                   P.d_ea_child, P.d_ea_pos, F);
     launches += 3;
+    for (const FactorPlan::LeafGroup& g : P.groups) {
+        if (g.big_idx != idx) continue;
+        k_group_gather<<<(unsigned)((g.nmem + 7) / 8), 256, 0, st>>>(g.d_members, g.d_kofs, g.nmem, g.r, g.K, a,
+                                                                     P.grp_L, P.grp_W);
+        const int nt = (g.r + kBT - 1) / kBT, ntile = nt * (nt + 1) / 2;
+        k_group_syrk_part<<<(unsigned)(ntile * P.grp_split), 256, 0, st>>>(P.grp_L, P.grp_W, g.r, g.K, P.grp_split,
+                                                                          P.grp_part);
+        const int64_t ne = (int64_t)ntile * kBT * kBT;
+        k_group_syrk_reduce<T><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(P.grp_part, g.r, P.grp_split,
+                                                                            a.rel + g.rel_off, f, F);
+        launches += 3;
+    }
     double* linv = P.big_linv + P.big_linv_off[idx];
     if constexpr (sizeof(T) == 8) {
         // FP64: 64-column panels, each followed by the full trailing update
@@ -684,6 +855,15 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
 
 }  // namespace
 
+int launch_leaf_groups(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st) {
+    int launches = 0;
+    for (const FactorPlan::LeafGroup& g : P.groups) {
+        k_leaf_members<<<(unsigned)((g.nmem + 7) / 8), 256, 0, st>>>(g.d_members, g.nmem, a, kval);
+        ++launches;
+    }
+    return launches;
+}
+
 int big_set_attributes() {
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_big_trailing_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
     nsm();  // queried here, outside any stream capture of the launch sequences
@@ -712,6 +892,14 @@ int launch_big_fwd(const FactorPlan& P, const FactorView& a, const double* rhs, 
     int launches = 0;
     k_big_fwd_gather<<<gridfor(f, 256), 256, 0, st>>>(s, a, P.d_ea_ptr + P.big_ea_off[idx], P.d_ea_child,
                                                        P.d_ea_pos, rhs, P.big_v);
+    for (const FactorPlan::LeafGroup& g : P.groups) {
+        if (g.big_idx != idx) continue;
+        const int nchunk = (g.nmem + kGrpChunk - 1) / kGrpChunk;
+        k_group_upd_part<<<(unsigned)nchunk, 256, 0, st>>>(g.d_updoff, g.nmem, g.r, a, P.grp_part);
+        k_group_upd_reduce<<<(unsigned)((g.r + 255) / 256), 256, 0, st>>>(P.grp_part, nchunk, g.r, a.rel + g.rel_off,
+                                                                          P.big_v);
+        launches += 2;
+    }
     ++launches;
     for (int k0 = 0; k0 < c; k0 += kBigNB) {
         const int nb = std::min(kBigNB, c - k0);

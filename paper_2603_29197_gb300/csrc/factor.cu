@@ -310,7 +310,7 @@ __device__ __forceinline__ bool thread_bwd_front(int s, const FactorView& a, con
 __global__ void __launch_bounds__(128) k_thread_factor(const int* __restrict__ list, int n, FactorView a,
                                                        const double* __restrict__ kval) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) thread_factor_front(list[t], a, kval, NoWait());
+    if (t < n && !(a.skip && a.skip[list[t]])) thread_factor_front(list[t], a, kval, NoWait());
 }
 __global__ void __launch_bounds__(128) k_thread_fwd(const int* __restrict__ list, int n, FactorView a,
                                                     const double* __restrict__ rhs, double* __restrict__ w) {
@@ -375,6 +375,7 @@ __global__ void __launch_bounds__(256) k_front_factor(const int* __restrict__ li
                                                       const double* __restrict__ kval) {
     extern __shared__ double smem[];
     const int s = list[blockIdx.x];
+    if (a.skip && a.skip[s]) return;  // a leaf-group member (whole CTA)
     const int f = a.nrow[s];
     double* F = SMEM ? smem : a.front + a.front_off[s];
     double* lk = SMEM ? smem + (size_t)f * f : smem;
@@ -650,7 +651,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_factor(const int* 
     extern __shared__ double smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * kWarpsPerBlock + wid;
-    if (t >= n) return;
+    if (t >= n || (a.skip && a.skip[list[t]])) return;
     double* F = smem + (size_t)wid * wfactor_stride(fmax);
     warp_factor_front(list[t], a, kval, F, F + fmax * fmax, lane, NoWait());
 }
@@ -1035,6 +1036,7 @@ static size_t wfactor_smem(int fmax) { return (size_t)kWarpsPerBlock * wfactor_s
 
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st) {
     int launches = 0;
+    if (!P.groups.empty()) launches += launch_leaf_groups(P, a, kval, st);
     if (P.ntasks) {
         const int fm = P.task_max_f;
         k_task_factor<<<wblocks(P.ntasks), kWarpsPerBlock * 32, wfactor_smem(fm), st>>>(

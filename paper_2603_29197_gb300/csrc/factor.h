@@ -41,6 +41,9 @@ struct FactorView {
     double* upd = nullptr;           // Σ r_s doubles (solve update vectors)
     double* dinv = nullptr;          // N: reciprocal pivots 1/d_j (permuted order)
     int* nreg = nullptr;             // dynamic-regularisation counter
+    // per supernode: 1 = factored by the leaf-group kernel (a one-level leaf whose update
+    // reaches its large parent through the group's rank-K product), skipped elsewhere
+    const signed char* skip = nullptr;
     double eps = 1e-8, dyn_thresh = 1e-13, dyn_value = 1e-7;
 };
 
@@ -86,6 +89,25 @@ struct FactorPlan {
     std::vector<int64_t> big_linv_off;
     double* big_linv = nullptr;
     int* big_err = nullptr;        // set when a tensor-core tile's completion wait ran out
+    // leaf groups: many childless children of one large front with the same update rows
+    // (an arrowhead border).  Their pivots are factored one warp per member; the parent
+    // receives −Σ L21·D·L21ᵀ as one split-K rank-K product instead of one update matrix
+    // per member.  Host lists; per group: parent's index into big_*, members, r, K.
+    struct LeafGroup {
+        int big_idx = 0;
+        int r = 0;                 // update rows (common to the members)
+        int K = 0;                 // Σ c over the members
+        int nmem = 0;
+        int64_t rel_off = 0;       // one member's relative indices (all equal)
+        int* d_members = nullptr;  // member supernodes
+        int* d_kofs = nullptr;     // nmem + 1: each member's first column in the group's K
+        int64_t* d_updoff = nullptr;  // each member's update vector in FactorView::upd
+    };
+    std::vector<LeafGroup> groups;
+    double* grp_L = nullptr;       // r × K (row-major) of the group being assembled
+    double* grp_W = nullptr;       // r × K: L21·D
+    double* grp_part = nullptr;    // split-K partial tiles (also the solve's member-sum partials)
+    int grp_split = 0;
     int64_t* d_ea_ptr = nullptr;
     int* d_ea_child = nullptr;
     int* d_ea_pos = nullptr;
@@ -124,6 +146,8 @@ int launch_solve_persistent(const FactorPlan& P, const FactorView& a, const doub
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
 // One large front (P.big_*[idx]): partial LDLᵀ, or the forward / backward solve step.
 int big_set_attributes();
+// The leaf-group members' pivot columns (all groups), one warp per member.
+int launch_leaf_groups(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
 int launch_big_factor(const FactorPlan& P, const FactorView& a, const double* kval, int idx, cudaStream_t st);
 int launch_big_fwd(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, int idx,
                    cudaStream_t st);

@@ -17,7 +17,7 @@ constexpr int kWideLevel = 2432;     // levels with at least this many fronts (1
 // Fronts at least this large are factored and solved by grid-wide kernel sequences
 // (panels of kBigNB columns), one front after the other, when their level holds at most
 // kBigPerLevel of them; fronts of at least kHugeFront always are.
-constexpr int kBigFront = 256;
+constexpr int kBigFront = 160;
 constexpr int kHugeFront = 1024;
 constexpr int kBigPerLevel = 64;
 constexpr int kBigNB = 64;

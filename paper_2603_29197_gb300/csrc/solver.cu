@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -427,6 +428,55 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         P.max_big_f = std::max(P.max_big_f, Y.sn_nrow[s]);
     }
     if (P.max_big_f) {
+        // leaf groups: childless children of a large front (c ≤ 8) sharing their update
+        // rows, at least kMinGroup of them
+        constexpr int kMinGroup = 32, kMaxLeafCols = 8;
+        std::vector<signed char> skip(Y.ns, 0);
+        int64_t max_rK = 0, max_tiles = 0, max_upd = 0;
+        for (size_t idx = 0; idx < P.big_s.size(); ++idx) {
+            const int s = P.big_s[idx];
+            std::map<std::pair<int, uint64_t>, std::vector<int>> by_rows;
+            for (int k = Y.child_ptr[s]; k < Y.child_ptr[s + 1]; ++k) {
+                const int ch = Y.child[k];
+                if (Y.child_ptr[ch + 1] > Y.child_ptr[ch]) continue;
+                const int c = Y.sn_ncol[ch], r = Y.sn_nrow[ch] - c;
+                if (c > kMaxLeafCols || r <= 0) continue;
+                uint64_t hsh = 1469598103934665603ull;
+                for (int i = 0; i < r; ++i) hsh = (hsh ^ (uint64_t)Y.rel[Y.upd_off[ch] + i]) * 1099511628211ull;
+                by_rows[{r, hsh}].push_back(ch);
+            }
+            for (auto& kv : by_rows) {
+                std::vector<int>& mem = kv.second;
+                const int r = kv.first.first;
+                // keep the members whose relative indices equal the first member's exactly
+                const int* rel0 = &Y.rel[Y.upd_off[mem[0]]];
+                std::vector<int> same;
+                for (int ch : mem)
+                    if (std::equal(rel0, rel0 + r, &Y.rel[Y.upd_off[ch]])) same.push_back(ch);
+                if ((int)same.size() < kMinGroup) continue;
+                FactorPlan::LeafGroup g;
+                g.big_idx = (int)idx;
+                g.r = r;
+                g.nmem = (int)same.size();
+                g.rel_off = Y.upd_off[same[0]];
+                std::vector<int> kofs(1, 0);
+                for (int ch : same) {
+                    kofs.push_back(kofs.back() + Y.sn_ncol[ch]);
+                    skip[ch] = 1;
+                }
+                g.K = kofs.back();
+                std::vector<int64_t> uo;
+                for (int ch : same) uo.push_back(Y.upd_off[ch]);
+                if ((rc = dcopy(S, &g.d_updoff, uo))) return rc;
+                if ((rc = dcopy(S, &g.d_members, same))) return rc;
+                if ((rc = dcopy(S, &g.d_kofs, kofs))) return rc;
+                max_rK = std::max(max_rK, (int64_t)r * g.K);
+                max_upd = std::max(max_upd, (int64_t)((g.nmem + 255) / 256) * r);  // solve partials
+                const int64_t nt = (r + 63) / 64;
+                max_tiles = std::max(max_tiles, nt * (nt + 1) / 2);
+                P.groups.push_back(g);
+            }
+        }
         // row-ownership lists of the large fronts' children (extend-add and solve gather)
         std::vector<int64_t> ea_ptr;
         std::vector<int> ea_child, ea_pos;
@@ -436,6 +486,7 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
             std::vector<int64_t> cnt(f + 1, 0);
             for (int k = Y.child_ptr[s]; k < Y.child_ptr[s + 1]; ++k) {
                 const int ch = Y.child[k], r = Y.sn_nrow[ch] - Y.sn_ncol[ch];
+                if (skip[ch]) continue;  // a leaf-group member: reaches the parent through its group
                 for (int jj = 0; jj < r; ++jj) cnt[Y.rel[Y.upd_off[ch] + jj] + 1]++;
             }
             for (int q = 0; q < f; ++q) cnt[q + 1] += cnt[q];
@@ -446,6 +497,7 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
             std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
             for (int k = Y.child_ptr[s]; k < Y.child_ptr[s + 1]; ++k) {
                 const int ch = Y.child[k], r = Y.sn_nrow[ch] - Y.sn_ncol[ch];
+                if (skip[ch]) continue;
                 for (int jj = 0; jj < r; ++jj) {
                     const int64_t e = base + fill[Y.rel[Y.upd_off[ch] + jj]]++;
                     ea_child[e] = k;
@@ -454,6 +506,16 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
             }
         }
         if ((rc = dcopy(S, &P.d_ea_ptr, ea_ptr))) return rc;
+        if (!P.groups.empty()) {
+            P.grp_split = 128;
+            if ((rc = dalloc(S, &P.grp_L, (size_t)max_rK))) return rc;
+            if ((rc = dalloc(S, &P.grp_W, (size_t)max_rK))) return rc;
+            if ((rc = dalloc(S, &P.grp_part, (size_t)std::max<int64_t>(P.grp_split * max_tiles * 64 * 64, max_upd))))
+                return rc;
+            signed char* pskip;
+            if ((rc = dcopy(S, &pskip, skip))) return rc;
+            S->fv.skip = pskip;
+        }
         if (!ea_child.empty()) {
             if ((rc = dcopy(S, &P.d_ea_child, ea_child))) return rc;
             if ((rc = dcopy(S, &P.d_ea_pos, ea_pos))) return rc;

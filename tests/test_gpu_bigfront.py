@@ -1,4 +1,4 @@
-"""Large fronts (order ≥ 256): the grid-wide panel kernels, in FP64 and in mixed
+"""Large fronts (order ≥ 160): the grid-wide panel kernels, in FP64 and in mixed
 precision (FP32 fronts, FP64 solves and refinement), through the C ABI.
 
 * FP64: the factor of a natural-order dense QP (large fronts of several 64-column
