@@ -89,6 +89,15 @@ typedef struct {
                                            solve whose refinement misses refine_tol within
                                            max_refine steps refactors in FP64, and the rest
                                            of that qoco_gpu_solve stays FP64 (default 0) */
+    int batch_schedule;                 /* factor/solve schedule of a batch (qoco_gpu_setup_batch)
+                                           whose fronts all fit one warp: 1–4 = per-instance
+                                           kernels, one CTA per instance at a time (1: 4 warps
+                                           per CTA, fronts of order ≤ 8 one per thread; 2: 8
+                                           warps, same split; 3: 4 warps, every front one warp;
+                                           4: 8 warps, every front one warp); 5 = the shared
+                                           kernels of single problems; 0 = the fastest of the
+                                           five, timed on the first factorisation (default 0).
+                                           Other batches always use 5. */
 } qoco_gpu_settings;
 
 typedef struct {
@@ -113,7 +122,8 @@ typedef struct {
     int large_fronts;           /* fronts factored by the grid-wide large-front kernels */
     int fp32_factors;           /* factorisations of the last solve with FP32 large fronts */
     int fp64_escalations;       /* refinements that missed the target on an FP32 factor */
-    int pad_info;
+    int batch_schedule_used;    /* batches: the schedule in use (1–5 as in the settings; 0
+                                   while the autotuning waits for the first factorisation) */
     char message[160];
 } qoco_gpu_info;
 

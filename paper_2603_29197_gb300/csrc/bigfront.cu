@@ -29,7 +29,7 @@ namespace qoco {
 
 namespace {
 
-constexpr int kBT = 64;  // trailing-update tile (rows and columns)
+int nsm();               // SM count of the current device (queried once, outside captures)
 
 template <class T>
 __device__ __forceinline__ T rcp_t(T d);
@@ -157,97 +157,85 @@ __global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorV
     if (nreg) atomicAdd(a.nreg, nreg);
 }
 
-// Inverses of the front's 64×64 unit-lower diagonal blocks (for the solves), one CTA per
-// block, after the whole front is factored (off the factorisation's pivot chain).  In
-// place in shared memory: after step k, rows ≤ k hold L⁻¹'s rows; row i > k takes
-// X_ij ← X_ij − L_ik·X_kj for j < k and X_ik ← −L_ik (L_ik read before column k is
-// overwritten).  Stored row-major: Xinv[b][i·64 + j] (unit diagonal, zero above).
+// X = L11⁻¹ of a panel's unit-lower diagonal block, row-major X[i·kBigNB + j], stored
+// in the solves' block-inverse slot; one warp per column j of X (x = e_j, then for
+// k = j … nb−1 the rows i > k take x_i −= L_ik·x_k).  The panel's rows below use it
+// right away (k_big_l21x): their triangular solves become one parallel product.
 template <class T>
-__global__ void __launch_bounds__(256) k_big_block_inverse(int s, FactorView a, const T* __restrict__ F,
-                                                           double* __restrict__ Xinv) {
-    __shared__ double X[kBigNB][kBigNB + 1];
-    const int f = a.nrow[s], c = a.ncol[s];
-    const int k0 = blockIdx.x * kBigNB, nb = min(kBigNB, c - k0);
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int t = tid; t < nb * nb; t += nt) {
+__global__ void __launch_bounds__(256) k_big_panel_inverse(int s, int k0, int nb, FactorView a,
+                                                           const T* __restrict__ F, double* __restrict__ X) {
+    __shared__ double L[kBigNB][kBigNB + 1];
+    __shared__ double xs[8][kBigNB];
+    const int f = a.nrow[s];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
         const int j = t / nb, i = t - j * nb;
-        X[i][j] = i > j ? (double)F[(int64_t)(k0 + j) * f + k0 + i] : 0.0;
+        L[i][j] = i > j ? (double)F[(int64_t)(k0 + j) * f + k0 + i] : 0.0;
     }
     __syncthreads();
-    for (int k = 0; k < nb - 1; ++k) {
-        const int m = nb - 1 - k;
-        for (int t = tid; t < m * k; t += nt) {
-            const int ii = t / k, j = t - ii * k;
-            const int i = k + 1 + ii;
-            X[i][j] -= X[i][k] * X[k][j];
-        }
-        __syncthreads();
-        for (int i = k + 1 + tid; i < nb; i += nt) X[i][k] = -X[i][k];
-        __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 8 + w;
+    if (j >= kBigNB) return;
+    double* x = xs[w];
+    for (int i = lane; i < kBigNB; i += 32) x[i] = i == j ? 1.0 : 0.0;
+    __syncwarp();
+    for (int k = j; k < nb - 1; ++k) {
+        const double xk = x[k];
+        for (int i = k + 1 + lane; i < nb; i += 32) x[i] -= L[i][k] * xk;
+        __syncwarp();
     }
-    double* out = Xinv + (int64_t)blockIdx.x * kBigNB * kBigNB;
-    for (int t = tid; t < nb * nb; t += nt) {
-        const int i = t / nb, j = t - i * nb;
-        out[i * kBigNB + j] = j < i ? X[i][j] : (j == i ? 1.0 : 0.0);
-    }
+    for (int i = lane; i < kBigNB; i += 32) X[(int64_t)i * kBigNB + j] = x[i];
 }
 
-// rows i ≥ k0+nb: w = a_i· L11⁻ᵀ, l_i· = w D⁻¹ (into F and, if Lr, row-major into
-// Lr[i·ldw + k]), w into W[i·ldw + k]
+// rows i ≥ k0+nb: w_i = a_i·L11⁻ᵀ = Σ_{j ≤ k} a_ij X_kj, l_i = w_i D⁻¹ into F (and, if Lr,
+// row-major into Lr[i·ldw + k]), w_i into W[i·ldw + k].  CTA: 8 rows; thread (r, g) takes
+// row r and columns 4g … 4g+3.
 template <class T>
-__global__ void __launch_bounds__(128) k_big_l21(int s, int k0, int nb, FactorView a, T* __restrict__ F,
-                                                 T* __restrict__ W, T* __restrict__ Lr, int ldw) {
-    __shared__ T L11[kBigNB][kBigNB + 1];
+__global__ void __launch_bounds__(128) k_big_l21x(int s, int k0, int nb, FactorView a, T* __restrict__ F,
+                                                  T* __restrict__ W, T* __restrict__ Lr, int ldw,
+                                                  const double* __restrict__ X) {
+    __shared__ T Xs[kBigNB][kBigNB + 1];
+    __shared__ T As[8][kBigNB + 1];
     __shared__ T dv[kBigNB];
     const int f = a.nrow[s], first = a.first[s];
-    for (int t = threadIdx.x; t < kBigNB * kBigNB; t += blockDim.x) {
-        const int j = t / kBigNB, i = t - j * kBigNB;
-        L11[i][j] = (i > j && i < nb) ? F[(int64_t)(k0 + j) * f + k0 + i] : T(0);
+    const int row0 = k0 + nb + blockIdx.x * 8;
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int k = t / nb, j = t - k * nb;
+        Xs[k][j] = (T)X[k * kBigNB + j];
+    }
+    for (int t = threadIdx.x; t < 8 * nb; t += blockDim.x) {
+        const int j = t >> 3, r = t & 7;
+        As[r][j] = row0 + r < f ? F[(int64_t)(k0 + j) * f + row0 + r] : T(0);
     }
     for (int k = threadIdx.x; k < nb; k += blockDim.x) dv[k] = (T)a.dinv[first + k0 + k];
     __syncthreads();
-    const int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = threadIdx.x & 7, g = threadIdx.x >> 3;
+    const int i = row0 + r;
     if (i >= f) return;
-    T* wr = W + (int64_t)i * ldw;
-    // two halves of 32 columns keep the row in registers without spills: the second
-    // half first takes the first half's contribution (re-read from W, written by this
-    // same thread), then both halves run the forward substitution with their diagonal
-    // block of L11
-    for (int kb = 0; kb < nb; kb += 32) {
-        T w[32];
 #pragma unroll
-        for (int k = 0; k < 32; ++k) w[k] = kb + k < nb ? F[(int64_t)(k0 + kb + k) * f + i] : T(0);
-        for (int j = 0; j < kb; ++j) {
-            const T wj = wr[j];
-#pragma unroll
-            for (int k = 0; k < 32; ++k) w[k] -= wj * L11[kb + k][j];
-        }
-#pragma unroll
-        for (int k = 1; k < 32; ++k) {
-            T acc = w[k];
-#pragma unroll
-            for (int j = 0; j < k; ++j) acc -= w[j] * L11[kb + k][kb + j];
-            w[k] = acc;
-        }
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-            if (kb + k < nb) {
-                wr[kb + k] = w[k];
-                const T l = w[k] * dv[kb + k];
-                F[(int64_t)(k0 + kb + k) * f + i] = l;
-                if (Lr) Lr[(int64_t)i * ldw + kb + k] = l;
-            }
+    for (int v = 0; v < 4; ++v) {
+        const int k = 4 * g + v;
+        if (k >= nb) break;
+        T acc = T(0);
+        for (int j = 0; j <= k; ++j) acc += As[r][j] * Xs[k][j];
+        W[(int64_t)i * ldw + k] = acc;
+        const T l = acc * dv[k];
+        F[(int64_t)(k0 + k) * f + i] = l;
+        if (Lr) Lr[(int64_t)i * ldw + k] = l;
     }
 }
 
-// A22 −= L21·Wᵀ on the lower triangle of rows/columns [base, f); one CTA per 64×64
-// tile of the lower triangle (tile index → (ti, tj), ti ≥ tj), 256 threads, 4×4 each
-template <class T>
-__global__ void __launch_bounds__(256) k_big_trailing(int s, int k0, int nb, FactorView a, T* __restrict__ F,
-                                                      const T* __restrict__ W, int ldw, int cend) {
+// A22 −= L21·Wᵀ on the lower triangle of rows/columns [base, f); one CTA per BT×BT tile
+// of the lower triangle (tile index → (ti, tj), ti ≥ tj), (BT/R)² threads, R×R entries
+// each.  Large fronts take 64-row tiles; small trailing matrices take smaller tiles so
+// that the update spreads over more SMs (an SM's FP64 rate bounds a tile's time).
+template <class T, int BT, int R>
+__global__ void __launch_bounds__((BT / R) * (BT / R)) k_big_trailing(int s, int k0, int nb, FactorView a,
+                                                                      T* __restrict__ F, const T* __restrict__ W,
+                                                                      int ldw, int cend) {
     constexpr int KC = 32;  // panel columns staged per step (keeps the tiles ≤ 33 KB)
-    __shared__ T Ls[KC][kBT + 1];
-    __shared__ T Ws[KC][kBT + 1];
+    constexpr int TX = BT / R, NTH = TX * TX;
+    __shared__ T Ls[KC][BT + 1];
+    __shared__ T Ws[KC][BT + 1];
     const int f = a.nrow[s];
     const int base = k0 + nb;
     const int t = blockIdx.x;
@@ -260,54 +248,75 @@ __global__ void __launch_bounds__(256) k_big_trailing(int s, int k0, int nb, Fac
         tj = t - ti * (ti + 1) / 2;
     } else {
         // only columns [base, cend): rectangular tile grid, tiles above the diagonal idle
-        const int ntj = (cend - base + kBT - 1) / kBT;
+        const int ntj = (cend - base + BT - 1) / BT;
         ti = t / ntj;
         tj = t - ti * ntj;
         if (ti < tj) return;
     }
-    const int r0 = base + ti * kBT, c0 = base + tj * kBT;
+    const int r0 = base + ti * BT, c0 = base + tj * BT;
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
-    T acc[4][4];
+    const int tx = tid % TX, ty = tid / TX;
+    T acc[R][R];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+        for (int v = 0; v < R; ++v) acc[u][v] = T(0);
     for (int kc = 0; kc < nb; kc += KC) {
         const int kn = min(KC, nb - kc);
-        for (int e = tid; e < kn * kBT; e += 256) {
-            const int k = e / kBT, r = e - k * kBT;
+        for (int e = tid; e < kn * BT; e += NTH) {
+            const int k = e / BT, r = e - k * BT;
             Ls[k][r] = r0 + r < f ? F[(int64_t)(k0 + kc + k) * f + r0 + r] : T(0);
         }
-        for (int e = tid; e < kn * kBT; e += 256) {
+        for (int e = tid; e < kn * BT; e += NTH) {
             const int cc = e / kn, k = e - cc * kn;
             Ws[k][cc] = c0 + cc < f ? W[(int64_t)(c0 + cc) * ldw + kc + k] : T(0);
         }
         __syncthreads();
         for (int k = 0; k < kn; ++k) {
-            T lr[4], wc[4];
+            T lr[R], wc[R];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) lr[u] = Ls[k][tx + 16 * u];
+            for (int u = 0; u < R; ++u) lr[u] = Ls[k][tx + TX * u];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) wc[v] = Ws[k][ty * 4 + v];
+            for (int v = 0; v < R; ++v) wc[v] = Ws[k][ty * R + v];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < R; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += lr[u] * wc[v];
+                for (int v = 0; v < R; ++v) acc[u][v] += lr[u] * wc[v];
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-        const int j = c0 + ty * 4 + v;
+    for (int v = 0; v < R; ++v) {
+        const int j = c0 + ty * R + v;
         if (j >= f || j >= cend) continue;
         T* Fj = F + (int64_t)j * f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = r0 + tx + 16 * u;
+        for (int u = 0; u < R; ++u) {
+            const int i = r0 + tx + TX * u;
             if (i < f && i >= j) Fj[i] -= acc[u][v];
         }
     }
+}
+
+// Trailing update after the panel (k0, nb) on rows [k0+nb, f) and columns [k0+nb, cend):
+// the largest tile that still gives at least two CTAs per SM
+template <class T>
+int launch_trailing(int s, int k0, int nb, int rows, int cend, const FactorView& a, T* F, const T* W, int ldw,
+                    int f, cudaStream_t st) {
+    const int base = k0 + nb;
+    auto ntiles = [&](int bt) -> int64_t {
+        const int64_t nr = (rows + bt - 1) / bt;
+        if (cend >= f) return nr * (nr + 1) / 2;
+        return nr * ((cend - base + bt - 1) / bt);
+    };
+    const int64_t want = 2 * (int64_t)nsm();
+    if (ntiles(64) >= want)
+        k_big_trailing<T, 64, 4><<<(unsigned)ntiles(64), 256, 0, st>>>(s, k0, nb, a, F, W, ldw, cend);
+    else if (ntiles(32) >= want)
+        k_big_trailing<T, 32, 2><<<(unsigned)ntiles(32), 256, 0, st>>>(s, k0, nb, a, F, W, ldw, cend);
+    else
+        k_big_trailing<T, 16, 2><<<(unsigned)ntiles(16), 64, 0, st>>>(s, k0, nb, a, F, W, ldw, cend);
+    return 1;
 }
 
 // ---- tensor-core trailing update (FP32 fronts) ---------------------------------------
@@ -509,73 +518,74 @@ __global__ void k_leaf_members(const int* __restrict__ members, int nmem, Factor
     if (lane == 0 && nreg) atomicAdd(a.nreg, nreg);
 }
 
-// Group operands: Lg[i·K + kofs + p] = L21 entries of member column p, Wg = Lg·d_p
-__global__ void k_group_gather(const int* __restrict__ members, const int* __restrict__ kofs, int nmem, int r, int K,
-                               FactorView a, double* __restrict__ Lg, double* __restrict__ Wg) {
+// Group operands, one warp per gathered column k (member column p of member m):
+// Lg[k·r + i] = L21(i, p), Wg[k·r + i] = L21(i, p)·d_p
+__global__ void k_group_gather(const int* __restrict__ members, const int* __restrict__ gmem,
+                               const int* __restrict__ gloc, int K, int r, FactorView a, double* __restrict__ Lg,
+                               double* __restrict__ Wg) {
     const int lane = threadIdx.x & 31;
-    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (w >= nmem) return;
-    const int s = members[w];
+    const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (k >= K) return;
+    const int s = members[gmem[k]], p = gloc[k];
     const int f = a.nrow[s], c = a.ncol[s];
-    const double* Fm = a.front + a.front_off[s];
-    for (int p = 0; p < c; ++p) {
-        const double d = Fm[p * f + p];
-        for (int i = lane; i < r; i += 32) {
-            const double l = Fm[p * f + c + i];
-            Lg[(int64_t)i * K + kofs[w] + p] = l;
-            Wg[(int64_t)i * K + kofs[w] + p] = l * d;
-        }
+    const double* col = a.front + a.front_off[s] + (int64_t)p * f;
+    const double d = col[p];
+    for (int i = lane; i < r; i += 32) {
+        const double l = col[c + i];
+        Lg[(int64_t)k * r + i] = l;
+        Wg[(int64_t)k * r + i] = l * d;
     }
 }
 
-// Split-K partial products of the group's update −Lg·Wgᵀ: CTA (tile, split) computes one
-// 64×64 lower tile of Lg·Wgᵀ over its K-chunk into part[(split·ntile + tile)·4096]
-__global__ void __launch_bounds__(256) k_group_syrk_part(const double* __restrict__ Lg, const double* __restrict__ Wg,
-                                                         int r, int K, int nsplit, double* __restrict__ part) {
-    constexpr int KC = 32;
-    __shared__ double Ls[KC][kBT + 1];
-    __shared__ double Ws[KC][kBT + 1];
-    const int nt = (r + kBT - 1) / kBT, ntile = nt * (nt + 1) / 2;
-    const int tile = blockIdx.x % ntile, split = blockIdx.x / ntile;
-    int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+// Split-K partial products of the group's update −Lg·Wgᵀ (a contraction over the K
+// gathered columns, FP64 FMA-bound): CTA (tile, split) computes one kGT×kGT lower tile
+// of Lgᵀ·Wg over its K-chunk into part[(split·ntile + tile)·kGT²].  Small tiles keep the
+// work spent on the upper halves of diagonal tiles and on the ragged last tile row low.
+constexpr int kGT = kGroupTile;
+__device__ __forceinline__ void lower_tile(int tile, int& ti, int& tj) {
+    ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
     while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
     while (ti * (ti + 1) / 2 > tile) --ti;
-    const int tj = tile - ti * (ti + 1) / 2;
-    const int r0 = ti * kBT, c0 = tj * kBT;
+    tj = tile - ti * (ti + 1) / 2;
+}
+__global__ void __launch_bounds__(64) k_group_syrk_part(const double* __restrict__ Lg, const double* __restrict__ Wg,
+                                                        int r, int K, int nsplit, double* __restrict__ part) {
+    constexpr int KC = 32;
+    __shared__ double Ls[KC][kGT + 1];
+    __shared__ double Ws[KC][kGT + 1];
+    const int nt = (r + kGT - 1) / kGT, ntile = nt * (nt + 1) / 2;
+    const int tile = blockIdx.x % ntile, split = blockIdx.x / ntile;
+    int ti, tj;
+    lower_tile(tile, ti, tj);
+    const int r0 = ti * kGT, c0 = tj * kGT;
     const int kchunk = (K + nsplit - 1) / nsplit;
     const int kb = split * kchunk, ke = min(K, kb + kchunk);
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    double acc[4][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;  // rows tx, tx+8; columns 2ty, 2ty+1
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     for (int k0 = kb; k0 < ke; k0 += KC) {
         const int kn = min(KC, ke - k0);
-        for (int e = tid; e < KC * kBT; e += 256) {
-            const int rr = e / KC, k = e - rr * KC;
-            Ls[k][rr] = (k < kn && r0 + rr < r) ? Lg[(int64_t)(r0 + rr) * K + k0 + k] : 0.0;
-            Ws[k][rr] = (k < kn && c0 + rr < r) ? Wg[(int64_t)(c0 + rr) * K + k0 + k] : 0.0;
+        for (int e = tid; e < KC * kGT; e += 64) {
+            const int k = e / kGT, rr = e - k * kGT;
+            const bool in = k < kn;
+            Ls[k][rr] = (in && r0 + rr < r) ? Lg[(int64_t)(k0 + k) * r + r0 + rr] : 0.0;
+            Ws[k][rr] = (in && c0 + rr < r) ? Wg[(int64_t)(k0 + k) * r + c0 + rr] : 0.0;
         }
         __syncthreads();
         for (int k = 0; k < kn; ++k) {
-            double lr[4], wc[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) lr[u] = Ls[k][tx + 16 * u];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) wc[v] = Ws[k][ty * 4 + v];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] += lr[u] * wc[v];
+            const double l0 = Ls[k][tx], l1 = Ls[k][tx + 8];
+            const double w0 = Ws[k][2 * ty], w1 = Ws[k][2 * ty + 1];
+            acc[0][0] += l0 * w0;
+            acc[0][1] += l0 * w1;
+            acc[1][0] += l1 * w0;
+            acc[1][1] += l1 * w1;
         }
         __syncthreads();
     }
-    double* out = part + ((int64_t)split * ntile + tile) * (kBT * kBT);
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) out[(tx + 16 * u) * kBT + ty * 4 + v] = acc[u][v];
+    double* out = part + ((int64_t)split * ntile + tile) * (kGT * kGT);
+    out[tx * kGT + 2 * ty] = acc[0][0];
+    out[tx * kGT + 2 * ty + 1] = acc[0][1];
+    out[(tx + 8) * kGT + 2 * ty] = acc[1][0];
+    out[(tx + 8) * kGT + 2 * ty + 1] = acc[1][1];
 }
 
 // Sum of the split-K partials in split order, subtracted into the parent front at the
@@ -583,18 +593,16 @@ __global__ void __launch_bounds__(256) k_group_syrk_part(const double* __restric
 template <class T>
 __global__ void k_group_syrk_reduce(const double* __restrict__ part, int r, int nsplit, const int* __restrict__ rel,
                                     int f, T* __restrict__ F) {
-    const int nt = (r + kBT - 1) / kBT, ntile = nt * (nt + 1) / 2;
+    const int nt = (r + kGT - 1) / kGT, ntile = nt * (nt + 1) / 2;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)ntile * kBT * kBT) return;
-    const int tile = (int)(e / (kBT * kBT)), q = (int)(e - (int64_t)tile * kBT * kBT);
-    int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
-    while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-    while (ti * (ti + 1) / 2 > tile) --ti;
-    const int tj = tile - ti * (ti + 1) / 2;
-    const int i = ti * kBT + q / kBT, j = tj * kBT + q % kBT;
+    if (e >= (int64_t)ntile * kGT * kGT) return;
+    const int tile = (int)(e / (kGT * kGT)), q = (int)(e - (int64_t)tile * kGT * kGT);
+    int ti, tj;
+    lower_tile(tile, ti, tj);
+    const int i = ti * kGT + q / kGT, j = tj * kGT + q % kGT;
     if (i >= r || j >= r || i < j) return;
     double sum = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) sum += part[((int64_t)sp * ntile + tile) * (kBT * kBT) + q];
+    for (int sp = 0; sp < nsplit; ++sp) sum += part[((int64_t)sp * ntile + tile) * (kGT * kGT) + q];
     F[(int64_t)rel[j] * f + rel[i]] -= (T)sum;
 }
 
@@ -791,12 +799,13 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
     launches += 3;
     for (const FactorPlan::LeafGroup& g : P.groups) {
         if (g.big_idx != idx) continue;
-        k_group_gather<<<(unsigned)((g.nmem + 7) / 8), 256, 0, st>>>(g.d_members, g.d_kofs, g.nmem, g.r, g.K, a,
-                                                                     P.grp_L, P.grp_W);
-        const int nt = (g.r + kBT - 1) / kBT, ntile = nt * (nt + 1) / 2;
-        k_group_syrk_part<<<(unsigned)(ntile * P.grp_split), 256, 0, st>>>(P.grp_L, P.grp_W, g.r, g.K, P.grp_split,
-                                                                          P.grp_part);
-        const int64_t ne = (int64_t)ntile * kBT * kBT;
+        if (g.K == 0) continue;
+        k_group_gather<<<(unsigned)((g.K + 7) / 8), 256, 0, st>>>(g.d_members, g.d_gmem, g.d_gloc, g.K, g.r, a,
+                                                                  P.grp_L, P.grp_W);
+        const int nt = (g.r + kGT - 1) / kGT, ntile = nt * (nt + 1) / 2;
+        k_group_syrk_part<<<(unsigned)(ntile * P.grp_split), 64, 0, st>>>(P.grp_L, P.grp_W, g.r, g.K, P.grp_split,
+                                                                         P.grp_part);
+        const int64_t ne = (int64_t)ntile * kGT * kGT;
         k_group_syrk_reduce<T><<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(P.grp_part, g.r, P.grp_split,
                                                                             a.rel + g.rel_off, f, F);
         launches += 3;
@@ -807,13 +816,13 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
         for (int k0 = 0; k0 < c; k0 += kBigNB) {
             const int nb = std::min(kBigNB, c - k0);
             k_big_diag<T><<<1, 256, 0, st>>>(s, k0, nb, a, F);
+            double* X = linv + (int64_t)(k0 / kBigNB) * kBigNB * kBigNB;
+            k_big_panel_inverse<T><<<kBigNB / 8, 256, 0, st>>>(s, k0, nb, a, F, X);
             const int rows = f - k0 - nb;
-            ++launches;
-            if (rows <= 0) continue;
-            k_big_l21<T><<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(s, k0, nb, a, F, W, nullptr, kBigNB);
-            const int nt = (rows + kBT - 1) / kBT;
-            k_big_trailing<T><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, st>>>(s, k0, nb, a, F, W, kBigNB, f);
             launches += 2;
+            if (rows <= 0) continue;
+            k_big_l21x<T><<<(unsigned)((rows + 7) / 8), 128, 0, st>>>(s, k0, nb, a, F, W, nullptr, kBigNB, X);
+            launches += 1 + launch_trailing<T>(s, k0, nb, rows, f, a, F, W, kBigNB, f, st);
         }
     } else {
         // FP32: outer panels of kOuterNB columns made of 64-column inner panels; an inner
@@ -825,19 +834,17 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
             for (int k1 = k0; k1 < k0 + nbo; k1 += kBigNB) {
                 const int nb = std::min(kBigNB, k0 + nbo - k1);
                 k_big_diag<T><<<1, 256, 0, st>>>(s, k1, nb, a, F);
+                double* X = linv + (int64_t)(k1 / kBigNB) * kBigNB * kBigNB;
+                k_big_panel_inverse<T><<<kBigNB / 8, 256, 0, st>>>(s, k1, nb, a, F, X);
                 const int rows = f - k1 - nb;
-                ++launches;
+                launches += 2;
                 if (rows <= 0) continue;
-                k_big_l21<T><<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(s, k1, nb, a, F, W + (k1 - k0),
-                                                                             Lr + (k1 - k0), kOuterNB);
+                k_big_l21x<T><<<(unsigned)((rows + 7) / 8), 128, 0, st>>>(s, k1, nb, a, F, W + (k1 - k0),
+                                                                           Lr + (k1 - k0), kOuterNB, X);
                 ++launches;
                 const int cend = k0 + nbo;
-                if (k1 + nb < cend) {
-                    const int ntr = (rows + kBT - 1) / kBT, ntc = (cend - k1 - nb + kBT - 1) / kBT;
-                    k_big_trailing<T><<<(unsigned)(ntr * ntc), 256, 0, st>>>(s, k1, nb, a, F, W + (k1 - k0),
-                                                                             kOuterNB, cend);
-                    ++launches;
-                }
+                if (k1 + nb < cend)
+                    launches += launch_trailing<T>(s, k1, nb, rows, cend, a, F, W + (k1 - k0), kOuterNB, f, st);
             }
             const int rows = f - k0 - nbo;
             if (rows > 0) {
@@ -848,9 +855,7 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
             }
         }
     }
-    // the diagonal blocks' inverses for the solves, all blocks in parallel
-    k_big_block_inverse<T><<<(unsigned)((c + kBigNB - 1) / kBigNB), 256, 0, st>>>(s, a, F, linv);
-    return launches + 1;
+    return launches;
 }
 
 }  // namespace

@@ -2,6 +2,8 @@
 // entry points of the C ABI.
 #include "cone_kernels.h"
 
+#include <algorithm>
+
 #include <mutex>
 
 #include "qoco_gpu.h"
@@ -26,9 +28,32 @@ __global__ void k_nt_scaling(ConeView c, ConeGrid g, const double* __restrict__ 
         return;
     }
     const int k = it.idx, o = c.off[k], d = c.dim[k];
-    const int64_t* slots = kval ? w2slot + c.l + w2ptr[k] : nullptr;
-    if (it.kind == 1) soc_nt<1>(k, o, d, 0, s, z, wbar, eta, lam, kval, slots);
-    else soc_nt<32>(k, o, d, it.lane, s, z, wbar, eta, lam, kval, slots);
+    double* kv = d > kWideCone ? nullptr : kval;  // wide cones: k_w2_wide writes the block
+    const int64_t* slots = kv ? w2slot + c.l + w2ptr[k] : nullptr;
+    if (it.kind == 1) soc_nt<1>(k, o, d, 0, s, z, wbar, eta, lam, kv, slots);
+    else soc_nt<32>(k, o, d, it.lane, s, z, wbar, eta, lam, kv, slots);
+}
+
+// The −W² blocks of the wide SOCs, one thread per entry (coalesced slot reads):
+// −η²(2 w̄_a w̄_b − J_ab), or −I for the initial point (identity != 0)
+__global__ void k_w2_wide(ConeView c, const double* __restrict__ wbar, const double* __restrict__ eta,
+                          double* __restrict__ kval, const int64_t* __restrict__ w2slot,
+                          const int64_t* __restrict__ w2ptr, int identity) {
+    for (int j = blockIdx.y; j < c.nwide; j += gridDim.y) {
+        const int k = c.wide[j], d = c.dim[k], o = c.off[k];
+        const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (e >= (int64_t)d * d) continue;
+        const int a = (int)(e / d), b = (int)(e - (int64_t)a * d);
+        const double J = (a == b) ? (a == 0 ? 1.0 : -1.0) : 0.0;
+        double v;
+        if (identity) {
+            v = (a == b) ? -1.0 : 0.0;
+        } else {
+            const double e2 = eta[k] * eta[k];
+            v = -e2 * (2.0 * wbar[o + a] * wbar[o + b] - J);
+        }
+        kval[w2slot[c.l + w2ptr[k] + e]] = v;
+    }
 }
 
 // W = I in the KKT value array (initial point)
@@ -38,6 +63,7 @@ __global__ void k_w2_identity(ConeView c, ConeGrid g, double* kval, const int64_
     if (!cone_item(c, g, &it)) return;
     if (it.kind == 0) { kval[w2slot[it.idx]] = -1.0; return; }
     const int k = it.idx, d = c.dim[k];
+    if (d > kWideCone) return;  // k_w2_wide
     const int64_t* slots = w2slot + c.l + w2ptr[k];
     const int G = it.kind == 1 ? 1 : 32;
     for (int a = it.lane; a < d; a += G)
@@ -258,16 +284,28 @@ __global__ void k_min_partials(const double* __restrict__ partial, int n, double
 }
 
 // ---- launchers ----------------------------------------------------------------
-void launch_nt_scaling(const ConeView& c, const double* s, const double* z, double* wbar, double* eta,
-                       double* lam, double* kval, const int64_t* w2slot, const int64_t* w2ptr,
+static int launch_w2_wide(const ConeView& c, const double* wbar, const double* eta, double* kval,
+                          const int64_t* w2slot, const int64_t* w2ptr, int identity, cudaStream_t st) {
+    if (!c.nwide || !kval) return 0;
+    const int64_t dd = (int64_t)c.wide_maxd * c.wide_maxd;
+    const dim3 grid((unsigned)((dd + 255) / 256), (unsigned)std::min(c.nwide, 65535));
+    k_w2_wide<<<grid, 256, 0, st>>>(c, wbar, eta, kval, w2slot, w2ptr, identity);
+    return 1;
+}
+int launch_nt_scaling(const ConeView& c, const double* s, const double* z, double* wbar, double* eta,
+                      double* lam, double* kval, const int64_t* w2slot, const int64_t* w2ptr,
+                      cudaStream_t st) {
+    ConeGrid g = cone_grid(c);
+    if (!g.blocks()) return 0;
+    k_nt_scaling<<<g.blocks(), kConeThreads, 0, st>>>(c, g, s, z, wbar, eta, lam, kval, w2slot, w2ptr);
+    return 1 + launch_w2_wide(c, wbar, eta, kval, w2slot, w2ptr, 0, st);
+}
+int launch_w2_identity(const ConeView& c, double* kval, const int64_t* w2slot, const int64_t* w2ptr,
                        cudaStream_t st) {
     ConeGrid g = cone_grid(c);
-    if (g.blocks()) k_nt_scaling<<<g.blocks(), kConeThreads, 0, st>>>(c, g, s, z, wbar, eta, lam, kval, w2slot, w2ptr);
-}
-void launch_w2_identity(const ConeView& c, double* kval, const int64_t* w2slot, const int64_t* w2ptr,
-                        cudaStream_t st) {
-    ConeGrid g = cone_grid(c);
-    if (g.blocks()) k_w2_identity<<<g.blocks(), kConeThreads, 0, st>>>(c, g, kval, w2slot, w2ptr);
+    if (!g.blocks()) return 0;
+    k_w2_identity<<<g.blocks(), kConeThreads, 0, st>>>(c, g, kval, w2slot, w2ptr);
+    return 1 + launch_w2_wide(c, nullptr, nullptr, kval, w2slot, w2ptr, 1, st);
 }
 void launch_rhs_z(const ConeView& c, const double* lam, const double* wbar, const double* eta,
                   const double* rz, const double* dsa, const double* dza, const double* smu,

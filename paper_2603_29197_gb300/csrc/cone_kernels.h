@@ -5,11 +5,12 @@
 
 namespace qoco {
 
-void launch_nt_scaling(const ConeView& c, const double* s, const double* z, double* wbar, double* eta,
-                       double* lam, double* kval, const int64_t* w2slot, const int64_t* w2ptr,
+// Both return the number of kernels launched.
+int launch_nt_scaling(const ConeView& c, const double* s, const double* z, double* wbar, double* eta,
+                      double* lam, double* kval, const int64_t* w2slot, const int64_t* w2ptr,
+                      cudaStream_t st);
+int launch_w2_identity(const ConeView& c, double* kval, const int64_t* w2slot, const int64_t* w2ptr,
                        cudaStream_t st);
-void launch_w2_identity(const ConeView& c, double* kval, const int64_t* w2slot, const int64_t* w2ptr,
-                        cudaStream_t st);
 void launch_rhs_z(const ConeView& c, const double* lam, const double* wbar, const double* eta,
                   const double* rz, const double* dsa, const double* dza, const double* smu,
                   bool combined, double* t, double* t1, double* t2, double* rhs, cudaStream_t st);

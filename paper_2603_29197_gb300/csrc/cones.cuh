@@ -18,6 +18,10 @@ struct ConeView {
     const int* small = nullptr;  // ids of SOCs with dim ≤ kSmallCone
     const int* large = nullptr;  // ids of SOCs with dim > kSmallCone
     int nsmall = 0, nlarge = 0;
+    // SOCs with dim > kWideCone: their dim² block of −W² is written by a grid-wide kernel
+    // (one thread per entry) instead of the cone's warp
+    const int* wide = nullptr;
+    int nwide = 0, wide_maxd = 0;
     // batched problems: instance of each orthant entry (l) and of each SOC (nsoc); null
     // for a single problem (everything is instance 0)
     const int* inst_orth = nullptr;
@@ -25,6 +29,7 @@ struct ConeView {
 };
 
 constexpr int kConeThreads = 256;
+constexpr int kWideCone = 64;
 
 struct ConeGrid {
     int b_orth = 0, b_small = 0, b_large = 0;

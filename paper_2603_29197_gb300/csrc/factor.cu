@@ -1028,6 +1028,132 @@ int launch_factor_dataflow(const FactorPlan& P, const FactorView& a, const doubl
     return 1;
 }
 
+// ---------------------------------------------------------------------------
+// Batches: one CTA per instance.  A persistent grid takes instances from a queue that
+// holds the largest first; the CTA walks the instance's tree level by level (thread
+// fronts and warp fronts of a level side by side, a block barrier between levels), so
+// no flag or cross-CTA wait is involved and a front's children are complete, and
+// visible to the whole CTA, when it starts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int inst_take(unsigned int* next) {
+    __shared__ int s_i;
+    if (threadIdx.x == 0) s_i = (int)atomicAdd(next, 1u);
+    __syncthreads();
+    const int i = s_i;
+    __syncthreads();
+    return i;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_inst_factor(const int* __restrict__ order, int ninst,
+                                                         const int* __restrict__ lv_ptr, const int* __restrict__ ent,
+                                                         const int* __restrict__ sched, FactorView a,
+                                                         const double* __restrict__ kval, int fmax,
+                                                         unsigned int* next) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* F = smem + (size_t)wid * wfactor_stride(fmax);
+    for (;;) {
+        const int i = inst_take(next);
+        if (i >= ninst) return;
+        const int inst = order[i];
+        for (int k = lv_ptr[inst]; k < lv_ptr[inst + 1]; ++k) {
+            const int t0 = ent[3 * k], w0 = ent[3 * k + 1], e1 = ent[3 * k + 2];
+            for (int t = t0 + (int)threadIdx.x; t < w0; t += NW * 32) thread_factor_front(sched[t], a, kval, NoWait());
+            for (int t = w0 + wid; t < e1; t += NW) warp_factor_front(sched[t], a, kval, F, F + fmax * fmax, lane, NoWait());
+            __syncthreads();
+        }
+    }
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_inst_solve(const int* __restrict__ order, int ninst,
+                                                        const int* __restrict__ lv_ptr, const int* __restrict__ ent,
+                                                        const int* __restrict__ sched, FactorView a,
+                                                        const double* __restrict__ rhs, double* w, double* xp,
+                                                        double* x, int accumulate, int fmax, unsigned int* next) {
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double* v = smem + (size_t)wid * fmax * (fmax + 1);
+    double* P = v + fmax;
+    for (;;) {
+        const int i = inst_take(next);
+        if (i >= ninst) return;
+        const int inst = order[i], k0 = lv_ptr[inst], k1 = lv_ptr[inst + 1];
+        for (int k = k0; k < k1; ++k) {
+            const int t0 = ent[3 * k], w0 = ent[3 * k + 1], e1 = ent[3 * k + 2];
+            for (int t = t0 + (int)threadIdx.x; t < w0; t += NW * 32) thread_fwd_front(sched[t], a, rhs, w, NoWait());
+            for (int t = w0 + wid; t < e1; t += NW) warp_fwd_front(sched[t], a, rhs, w, v, P, lane, NoWait());
+            __syncthreads();
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            const int t0 = ent[3 * k], w0 = ent[3 * k + 1], e1 = ent[3 * k + 2];
+            for (int t = t0 + (int)threadIdx.x; t < w0; t += NW * 32)
+                thread_bwd_front(sched[t], a, w, xp, x, accumulate, NoWait());
+            for (int t = w0 + wid; t < e1; t += NW) warp_bwd_front(sched[t], a, w, xp, x, accumulate, v, P, lane, NoWait());
+            __syncthreads();
+        }
+    }
+}
+
+static size_t inst_factor_smem(int nw, int fmax) { return (size_t)nw * wfactor_stride(fmax) * sizeof(double); }
+static size_t inst_solve_smem(int nw, int fmax) { return (size_t)nw * fmax * (fmax + 1) * sizeof(double); }
+
+int plan_instances(FactorPlan& P, int fmax) {
+    fmax = max(fmax, 1);
+    int dev = 0, nsm = 0;
+    QOCO_CUDA_TRY(cudaGetDevice(&dev));
+    QOCO_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const void* fk[2] = {(const void*)k_inst_factor<4>, (const void*)k_inst_factor<8>};
+    const void* sk[2] = {(const void*)k_inst_solve<4>, (const void*)k_inst_solve<8>};
+    for (int v = 0; v < 2; ++v) {
+        const int nw = v ? 8 : 4;
+        const size_t fs = inst_factor_smem(nw, fmax), ss = inst_solve_smem(nw, fmax);
+        QOCO_CUDA_TRY(cudaFuncSetAttribute(fk[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fs));
+        QOCO_CUDA_TRY(cudaFuncSetAttribute(sk[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss));
+        int of = 0, os = 0;
+        QOCO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, fk[v], nw * 32, fs));
+        QOCO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&os, sk[v], nw * 32, ss));
+        if (of < 1 || os < 1) return 0;
+        P.inst_fgrid[v] = min(nsm * of, P.ninst);
+        P.inst_sgrid[v] = min(nsm * os, P.ninst);
+    }
+    P.inst_fmax = fmax;
+    P.inst = true;
+    return 0;
+}
+
+// variant 1–4: bit 0 of (variant − 1) = 8 warps, bit 1 = every front one warp
+int launch_inst_factor(const FactorPlan& P, const FactorView& a, const double* kval, int variant,
+                       cudaStream_t st) {
+    const int v8 = (variant - 1) & 1;
+    const FactorPlan::InstSched& I = P.isched[((variant - 1) >> 1) & 1];
+    QOCO_CUDA_TRY(cudaMemsetAsync(P.d_inst_next, 0, sizeof(unsigned int), st));
+    if (v8)
+        k_inst_factor<8><<<P.inst_fgrid[1], 256, inst_factor_smem(8, P.inst_fmax), st>>>(
+            P.d_inst_order, P.ninst, I.d_lv_ptr, I.d_ent, I.d_sched, a, kval, P.inst_fmax, P.d_inst_next);
+    else
+        k_inst_factor<4><<<P.inst_fgrid[0], 128, inst_factor_smem(4, P.inst_fmax), st>>>(
+            P.d_inst_order, P.ninst, I.d_lv_ptr, I.d_ent, I.d_sched, a, kval, P.inst_fmax, P.d_inst_next);
+    return 1;
+}
+
+int launch_inst_solve(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
+                      double* x, bool accumulate, int variant, cudaStream_t st) {
+    const int v8 = (variant - 1) & 1;
+    const FactorPlan::InstSched& I = P.isched[((variant - 1) >> 1) & 1];
+    unsigned int* next = P.d_inst_next + 1;
+    QOCO_CUDA_TRY(cudaMemsetAsync(next, 0, sizeof(unsigned int), st));
+    const int acc = accumulate ? 1 : 0;
+    if (v8)
+        k_inst_solve<8><<<P.inst_sgrid[1], 256, inst_solve_smem(8, P.inst_fmax), st>>>(
+            P.d_inst_order, P.ninst, I.d_lv_ptr, I.d_ent, I.d_sched, a, rhs, w, xp, x, acc, P.inst_fmax, next);
+    else
+        k_inst_solve<4><<<P.inst_sgrid[0], 128, inst_solve_smem(4, P.inst_fmax), st>>>(
+            P.d_inst_order, P.ninst, I.d_lv_ptr, I.d_ent, I.d_sched, a, rhs, w, xp, x, acc, P.inst_fmax, next);
+    return 1;
+}
+
 // ---- launchers ----------------------------------------------------------------
 static int wblocks(int n) { return (n + kWarpsPerBlock - 1) / kWarpsPerBlock; }
 // per warp: the front vector (fmax) and the panel (≤ fmax·fmax)

@@ -76,6 +76,21 @@ struct FactorPlan {
     int* d_ftb_ptr = nullptr;
     int* d_fwg_ptr = nullptr;
     int* d_cdone = nullptr;  // per supernode: epoch of its finished factorisation
+    // batches of independent instances: one CTA takes one whole instance at a time from a
+    // queue (largest instances first) and runs its factorisation / solve level by level
+    // with block barriers.  Two schedules (fronts of order ≤ kThreadFront one per thread,
+    // or every front one warp), each runnable with 4 or 8 warps per CTA: candidates 1–4.
+    struct InstSched {
+        int* d_lv_ptr = nullptr;  // ninst + 1: the instance's level entries
+        int* d_ent = nullptr;     // 3 per entry: thread fronts [t0, w0), warp fronts [w0, end) of sched
+        int* d_sched = nullptr;
+    };
+    bool inst = false;
+    int ninst = 0, inst_fmax = 0, inst_variant = 0;
+    int inst_fgrid[2] = {0, 0}, inst_sgrid[2] = {0, 0};  // persistent grids for 4 / 8 warps
+    int* d_inst_order = nullptr;
+    InstSched isched[2];
+    unsigned int* d_inst_next = nullptr;
     // large fronts (grid-wide kernel sequences, bigfront.cu); host lists indexed by the
     // levels' off_big/n_big
     std::vector<int> big_s, big_f, big_c;
@@ -96,16 +111,17 @@ struct FactorPlan {
     struct LeafGroup {
         int big_idx = 0;
         int r = 0;                 // update rows (common to the members)
-        int K = 0;                 // Σ c over the members
+        int K = 0;                 // member columns with entries in the update rows
         int nmem = 0;
         int64_t rel_off = 0;       // one member's relative indices (all equal)
         int* d_members = nullptr;  // member supernodes
-        int* d_kofs = nullptr;     // nmem + 1: each member's first column in the group's K
+        int* d_gmem = nullptr;     // K: member (index into d_members) of each gathered column
+        int* d_gloc = nullptr;     // K: its column inside the member front
         int64_t* d_updoff = nullptr;  // each member's update vector in FactorView::upd
     };
     std::vector<LeafGroup> groups;
-    double* grp_L = nullptr;       // r × K (row-major) of the group being assembled
-    double* grp_W = nullptr;       // r × K: L21·D
+    double* grp_L = nullptr;       // K × r (column k of L21ᵀ contiguous) of the group being assembled
+    double* grp_W = nullptr;       // K × r: (L21·D)ᵀ
     double* grp_part = nullptr;    // split-K partial tiles (also the solve's member-sum partials)
     int grp_split = 0;
     int64_t* d_ea_ptr = nullptr;
@@ -128,6 +144,11 @@ struct DataflowState {
 };
 
 int factor_set_attributes();
+// Per-instance kernels of a batch: grid sizes for the fronts' largest order fmax (≤ kWarpFront).
+int plan_instances(FactorPlan& P, int fmax);
+int launch_inst_factor(const FactorPlan& P, const FactorView& a, const double* kval, int variant, cudaStream_t st);
+int launch_inst_solve(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
+                      double* x, bool accumulate, int variant, cudaStream_t st);
 // Decides whether the persistent solve applies and sizes its cooperative grid.
 int plan_persistent_solve(FactorPlan& P, int max_warp_f, bool any_cta_front);
 // Launches a 4-block cooperative kernel whose block 0 never reaches the barrier; returns

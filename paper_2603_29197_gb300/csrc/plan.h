@@ -21,6 +21,7 @@ constexpr int kBigFront = 160;
 constexpr int kHugeFront = 1024;
 constexpr int kBigPerLevel = 64;
 constexpr int kBigNB = 64;
+constexpr int kGroupTile = 16;  // tile of a leaf group's split-K rank-K product
 
 // Launch plan of one factorisation / solve.  Supernodes are split into
 //  * subtree tasks: a task is a whole subtree of small fronts whose supernodes occupy a

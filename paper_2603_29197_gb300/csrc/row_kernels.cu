@@ -24,7 +24,44 @@ __device__ __forceinline__ void store_partials(double (&v)[NV], const bool (&is_
 // group_sum always see full warps.  The grid is capped (kMaxRowBlocks) so that the
 // single-block finalisation reduces few partials.
 
+constexpr int kLongThreads = 512;
+
 // residuals: r_x = Px + c + Aᵀy + Gᵀz, r_y = Ax − b, r_z = Gx + s − h
+// One row's outputs from its three partial products a0 = K_row,x·x, a1 = K_row,y·y,
+// a2 = K_row,z·z, accumulated into the block's sums and maxima v.
+__device__ __forceinline__ void residual_row(int row, int n, int p, double a0, double a1, double a2,
+                                             const double* __restrict__ xyz, const double* __restrict__ s,
+                                             const double* __restrict__ c, const double* __restrict__ b,
+                                             const double* __restrict__ h, double* __restrict__ r,
+                                             double (&v)[kResNV]) {
+    if (row < n) {
+        const double rx = a0 + c[row] + a1 + a2;
+        r[row] = rx;
+        v[0] += xyz[row] * a0;  // xᵀPx
+        v[1] += c[row] * xyz[row];
+        v[5] = amax(v[5], a0);   // |Px|
+        v[6] = amax(v[6], a1);   // |Aᵀy|
+        v[7] = amax(v[7], a2);   // |Gᵀz|
+        v[10] = amax(v[10], rx);
+    } else if (row < n + p) {
+        const int i = row - n;
+        const double ry = a0 - b[i];
+        r[row] = ry;
+        v[2] += b[i] * xyz[row];
+        v[8] = amax(v[8], a0);   // |Ax|
+        v[11] = amax(v[11], ry);
+    } else {
+        const int i = row - n - p;
+        const double rz = a0 + s[i] - h[i];
+        r[row] = rz;
+        v[3] += h[i] * xyz[row];
+        v[4] += s[i] * xyz[row];
+        v[9] = amax(v[9], a0);   // |Gx|
+        v[12] = amax(v[12], rz);
+        v[13] = amax(v[13], s[i]);
+    }
+}
+
 // sums: xᵀPx, cᵀx, bᵀy, hᵀz, sᵀz   maxes: |Px|,|Aᵀy|,|Gᵀz|,|Ax|,|Gx|,|r_x|,|r_y|,|r_z|,|s|
 template <int LPR>
 __global__ void __launch_bounds__(kRowThreads) k_residual(KKTView K, const double* __restrict__ xyz,
@@ -43,49 +80,61 @@ __global__ void __launch_bounds__(kRowThreads) k_residual(KKTView K, const doubl
     for (int base = blockIdx.x * GPB; base < K.N; base += gridDim.x * GPB) {
         const int row = base + grp;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-        if (row < K.N) {
+        bool mine = row < K.N;
+        if (mine) {
             const int64_t beg = K.rowptr[row], end = K.rowptr[row + 1];
-            for (int64_t t = beg + lane; t < end; t += LPR) {
-                const int j = K.colidx[t];
-                const double kv = K.val[t] * xyz[j];
-                if (j < n) a0 += kv;
-                else if (j < n + p) a1 += kv;
-                else a2 += kv;
-            }
+            mine = end - beg <= kLongRow;
+            if (mine)
+                for (int64_t t = beg + lane; t < end; t += LPR) {
+                    const int j = K.colidx[t];
+                    const double kv = K.val[t] * xyz[j];
+                    if (j < n) a0 += kv;
+                    else if (j < n + p) a1 += kv;
+                    else a2 += kv;
+                }
         }
         a0 = group_sum<LPR>(a0);
         a1 = group_sum<LPR>(a1);
         a2 = group_sum<LPR>(a2);
-        if (row < K.N && lane == 0) {
-            if (row < n) {
-                const double rx = a0 + c[row] + a1 + a2;
-                r[row] = rx;
-                v[0] += xyz[row] * a0;  // xᵀPx
-                v[1] += c[row] * xyz[row];
-                v[5] = amax(v[5], a0);   // |Px|
-                v[6] = amax(v[6], a1);   // |Aᵀy|
-                v[7] = amax(v[7], a2);   // |Gᵀz|
-                v[10] = amax(v[10], rx);
-            } else if (row < n + p) {
-                const int i = row - n;
-                const double ry = a0 - b[i];
-                r[row] = ry;
-                v[2] += b[i] * xyz[row];
-                v[8] = amax(v[8], a0);   // |Ax|
-                v[11] = amax(v[11], ry);
-            } else {
-                const int i = row - n - p;
-                const double rz = a0 + s[i] - h[i];
-                r[row] = rz;
-                v[3] += h[i] * xyz[row];
-                v[4] += s[i] * xyz[row];
-                v[9] = amax(v[9], a0);   // |Gx|
-                v[12] = amax(v[12], rz);
-                v[13] = amax(v[13], s[i]);
-            }
-        }
+        if (mine && lane == 0) residual_row(row, n, p, a0, a1, a2, xyz, s, c, b, h, r, v);
     }
     store_partials<kResNV>(v, is_max, partial);
+}
+
+// Sum of NV values over the whole block, in a fixed order; valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    __shared__ double sm[NV * 32];
+    bool is_sum[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) is_sum[k] = false;
+    block_reduce<NV>(v, is_sum, sm);
+}
+
+// The long rows of the residual pass: block b takes row long_rows[b] and writes its
+// contributions as partial block nb + b.
+__global__ void __launch_bounds__(kLongThreads) k_residual_long(KKTView K, const double* __restrict__ xyz,
+                                                               const double* __restrict__ s,
+                                                               const double* __restrict__ c,
+                                                               const double* __restrict__ b,
+                                                               const double* __restrict__ h,
+                                                               double* __restrict__ r, double* partial, int nb) {
+    const int row = K.long_rows[blockIdx.x], n = K.n, p = K.p;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int64_t t = K.rowptr[row] + threadIdx.x; t < K.rowptr[row + 1]; t += kLongThreads) {
+        const int j = K.colidx[t];
+        const double kv = K.val[t] * xyz[j];
+        if (j < n) a[0] += kv;
+        else if (j < n + p) a[1] += kv;
+        else a[2] += kv;
+    }
+    block_sum<3>(a);
+    if (threadIdx.x != 0) return;
+    double v[kResNV];
+#pragma unroll
+    for (int k = 0; k < kResNV; ++k) v[k] = 0.0;
+    residual_row(row, n, p, a[0], a[1], a[2], xyz, s, c, b, h, r, v);
+    for (int k = 0; k < kResNV; ++k) partial[(int64_t)(nb + blockIdx.x) * kResNV + k] = v[k];
 }
 
 // res = r − K x (unregularised K), maxes |res|, |x|, |r|
@@ -100,11 +149,15 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_res(KKTView K, const doubl
     for (int base = blockIdx.x * GPB; base < K.N; base += gridDim.x * GPB) {
         const int row = base + grp;
         double acc = 0.0;
-        if (row < K.N)
-            for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR)
-                acc += K.val[t] * x[K.colidx[t]];
+        bool mine = row < K.N;
+        if (mine) {
+            const int64_t beg = K.rowptr[row], end = K.rowptr[row + 1];
+            mine = end - beg <= kLongRow;
+            if (mine)
+                for (int64_t t = beg + lane; t < end; t += LPR) acc += K.val[t] * x[K.colidx[t]];
+        }
         acc = group_sum<LPR>(acc);
-        if (row < K.N && lane == 0) {
+        if (mine && lane == 0) {
             const double e = r[row] - acc;
             res[row] = e;
             v[0] = amax(v[0], e);
@@ -113,6 +166,24 @@ __global__ void __launch_bounds__(kRowThreads) k_spmv_res(KKTView K, const doubl
         }
     }
     store_partials<3>(v, is_max, partial);
+}
+
+__global__ void __launch_bounds__(kLongThreads) k_spmv_res_long(KKTView K, const double* __restrict__ x,
+                                                               const double* __restrict__ r,
+                                                               double* __restrict__ res, double* partial,
+                                                               int nb) {
+    const int row = K.long_rows[blockIdx.x];
+    double a[1] = {0.0};
+    for (int64_t t = K.rowptr[row] + threadIdx.x; t < K.rowptr[row + 1]; t += kLongThreads)
+        a[0] += K.val[t] * x[K.colidx[t]];
+    block_sum<1>(a);
+    if (threadIdx.x != 0) return;
+    const double e = r[row] - a[0];
+    res[row] = e;
+    double* out = partial + (int64_t)(nb + blockIdx.x) * 3;
+    out[0] = fabs(e);
+    out[1] = fabs(x[row]);
+    out[2] = fabs(r[row]);
 }
 
 // max_i Σ_j |K_ij|
@@ -125,12 +196,23 @@ __global__ void __launch_bounds__(kRowThreads) k_norm_inf(KKTView K, double* par
     for (int base = blockIdx.x * GPB; base < K.N; base += gridDim.x * GPB) {
         const int row = base + grp;
         double acc = 0.0;
-        if (row < K.N)
-            for (int64_t t = K.rowptr[row] + lane; t < K.rowptr[row + 1]; t += LPR) acc += fabs(K.val[t]);
+        if (row < K.N) {
+            const int64_t beg = K.rowptr[row], end = K.rowptr[row + 1];
+            if (end - beg <= kLongRow)
+                for (int64_t t = beg + lane; t < end; t += LPR) acc += fabs(K.val[t]);
+        }
         acc = group_sum<LPR>(acc);
         v[0] = amax(v[0], acc);
     }
     store_partials<1>(v, is_max, partial);
+}
+
+__global__ void __launch_bounds__(kLongThreads) k_norm_inf_long(KKTView K, double* partial, int nb) {
+    const int row = K.long_rows[blockIdx.x];
+    double a[1] = {0.0};
+    for (int64_t t = K.rowptr[row] + threadIdx.x; t < K.rowptr[row + 1]; t += kLongThreads) a[0] += fabs(K.val[t]);
+    block_sum<1>(a);
+    if (threadIdx.x == 0) partial[nb + blockIdx.x] = a[0];
 }
 
 // one block: reduce NV columns of partial[nb][NV] in a fixed order into out[NV]
@@ -214,7 +296,7 @@ static int rows_blocks(int N, int lpr) {
 }
 // partial-buffer size in doubles: the most blocks (32 lanes per row) times the most
 // values per block (the residual pass)
-int row_partials(int N) { return rows_blocks(N, 32) * kResNV; }
+int row_partials(int N, int n_long) { return (rows_blocks(N, 32) + n_long) * kResNV; }
 
 #define QOCO_LPR_SWITCH(lpr, KERNEL, ...)                                          \
     switch (lpr) {                                                                 \
@@ -229,27 +311,30 @@ int row_partials(int N) { return rows_blocks(N, 32) * kResNV; }
 int launch_residual(const KKTView& K, int lpr, const double* xyz, const double* s, const double* c,
                     const double* b, const double* h, double* r, double* partial, int64_t cap,
                     IPMScalars* S, cudaStream_t st) {
-    if ((int64_t)rows_blocks(K.N, lpr) * kResNV > cap) return -1;
+    if ((int64_t)(rows_blocks(K.N, lpr) + K.n_long) * kResNV > cap) return -1;
     int nb = 0;
     QOCO_LPR_SWITCH(lpr, k_residual, K, xyz, s, c, b, h, r, partial)
-    k_finalize_residual<<<1, 1024, 0, st>>>(partial, nb, S);
-    return 0;
+    if (K.n_long) k_residual_long<<<K.n_long, kLongThreads, 0, st>>>(K, xyz, s, c, b, h, r, partial, nb);
+    k_finalize_residual<<<1, 1024, 0, st>>>(partial, nb + K.n_long, S);
+    return K.n_long ? 3 : 2;
 }
 int launch_spmv_res(const KKTView& K, int lpr, const double* x, const double* r, double* res,
                     double* partial, int64_t cap, IPMScalars* S, cudaStream_t st) {
-    if ((int64_t)rows_blocks(K.N, lpr) * 3 > cap) return -1;
+    if ((int64_t)(rows_blocks(K.N, lpr) + K.n_long) * 3 > cap) return -1;
     int nb = 0;
     QOCO_LPR_SWITCH(lpr, k_spmv_res, K, x, r, res, partial)
-    k_finalize_refine<<<1, 1024, 0, st>>>(partial, nb, S);
-    return 0;
+    if (K.n_long) k_spmv_res_long<<<K.n_long, kLongThreads, 0, st>>>(K, x, r, res, partial, nb);
+    k_finalize_refine<<<1, 1024, 0, st>>>(partial, nb + K.n_long, S);
+    return K.n_long ? 3 : 2;
 }
 int launch_norm_inf(const KKTView& K, int lpr, double* partial, int64_t cap, IPMScalars* S,
                     cudaStream_t st) {
-    if ((int64_t)rows_blocks(K.N, lpr) > cap) return -1;
+    if ((int64_t)(rows_blocks(K.N, lpr) + K.n_long) > cap) return -1;
     int nb = 0;
     QOCO_LPR_SWITCH(lpr, k_norm_inf, K, partial)
-    k_finalize_norm<<<1, 1024, 0, st>>>(partial, nb, S);
-    return 0;
+    if (K.n_long) k_norm_inf_long<<<K.n_long, kLongThreads, 0, st>>>(K, partial, nb);
+    k_finalize_norm<<<1, 1024, 0, st>>>(partial, nb + K.n_long, S);
+    return K.n_long ? 3 : 2;
 }
 
 }  // namespace qoco

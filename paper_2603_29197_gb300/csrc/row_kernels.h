@@ -12,7 +12,12 @@ struct KKTView {
     const int64_t* rowptr = nullptr;
     const int* colidx = nullptr;
     const double* val = nullptr;
+    // rows with more than kLongRow entries (the dense rows of a factor model or a budget
+    // constraint): the row kernels skip them and one block per listed row takes them
+    const int* long_rows = nullptr;
+    int n_long = 0;
 };
+constexpr int kLongRow = 2048;
 
 // Device-resident scalars of one solve (read back to the host once per iteration).
 struct IPMScalars {
@@ -40,9 +45,9 @@ constexpr int kResNSum = 5;
 constexpr int kResNV = 14;
 
 // Size (doubles) of the per-block partial buffer the row kernels need for any LPR.
-int row_partials(int N);
+int row_partials(int N, int n_long);
 // Each launcher returns −1 without launching when `cap` (the partial buffer's size in
-// doubles) is too small for its grid, else 0.
+// doubles) is too small for its grid, else the number of kernels it launched.
 int launch_residual(const KKTView& K, int lpr, const double* xyz, const double* s, const double* c,
                     const double* b, const double* h, double* r, double* partial, int64_t cap,
                     IPMScalars* S, cudaStream_t st);

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <new>
 #include <string>
@@ -210,6 +211,7 @@ struct qoco_gpu_solver {
     std::vector<void*> allocs;
     // device data
     int64_t* d_rowptr = nullptr;
+    int* d_long_rows = nullptr;
     int* d_colidx = nullptr;
     double* d_val = nullptr;
     int64_t* d_w2slot = nullptr;
@@ -331,6 +333,17 @@ int build_cone_view(qoco_gpu_solver* S, const KKTPattern& K) {
     c.large = p;
     c.nsmall = (int)sm.size();
     c.nlarge = (int)lg.size();
+    std::vector<int> wide;
+    for (int k = 0; k < K.nsoc; ++k)
+        if (K.q[k] > kWideCone) {
+            wide.push_back(k);
+            c.wide_maxd = std::max(c.wide_maxd, K.q[k]);
+        }
+    if (!wide.empty()) {
+        if ((rc = dcopy(S, &p, wide))) return rc;
+        c.wide = p;
+        c.nwide = (int)wide.size();
+    }
     return 0;
 }
 
@@ -353,7 +366,20 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     if ((rc = build_cone_view(S, K))) return rc;
     S->kv.N = N; S->kv.n = K.n; S->kv.p = K.p; S->kv.m = K.m;
     S->kv.rowptr = S->d_rowptr; S->kv.colidx = S->d_colidx; S->kv.val = S->d_val;
-    const double avg = N ? (double)K.nnz() / N : 1.0;
+    std::vector<int> long_rows;
+    int64_t long_nnz = 0;
+    for (int i = 0; i < N; ++i)
+        if (K.rowptr[i + 1] - K.rowptr[i] > kLongRow) {
+            long_rows.push_back(i);
+            long_nnz += K.rowptr[i + 1] - K.rowptr[i];
+        }
+    if (!long_rows.empty()) {
+        if ((rc = dcopy(S, &S->d_long_rows, long_rows))) return rc;
+        S->kv.long_rows = S->d_long_rows;
+        S->kv.n_long = (int)long_rows.size();
+    }
+    const int n_short = N - (int)long_rows.size();
+    const double avg = n_short ? (double)(K.nnz() - long_nnz) / n_short : 1.0;
     // lanes per KKT row in the row kernels: one thread per row for the very sparse rows
     // of stage-structured problems (no shuffles, one row-pointer load per row)
     S->lpr = avg <= 6 ? 1 : avg <= 12 ? 2 : avg <= 24 ? 4 : avg <= 48 ? 8 : avg <= 96 ? 16 : 32;
@@ -459,20 +485,35 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
                 g.r = r;
                 g.nmem = (int)same.size();
                 g.rel_off = Y.upd_off[same[0]];
-                std::vector<int> kofs(1, 0);
-                for (int ch : same) {
-                    kofs.push_back(kofs.back() + Y.sn_ncol[ch]);
+                // member columns that reach the update rows: a member is a leaf, so its
+                // columns' patterns are its KKT entries plus the fill among its own pivots
+                std::vector<int> gmem, gloc;
+                std::vector<unsigned char> pat;
+                for (int w = 0; w < g.nmem; ++w) {
+                    const int ch = same[w], f = Y.sn_nrow[ch], c = Y.sn_ncol[ch];
+                    pat.assign((size_t)c * f, 0);
+                    for (int64_t e = Y.amap_ptr[ch]; e < Y.amap_ptr[ch + 1]; ++e) pat[Y.amap_off[e]] = 1;
+                    for (int t = 0; t < c; ++t)
+                        for (int i = t + 1; i < c; ++i)
+                            if (pat[(size_t)t * f + i])
+                                for (int q2 = i + 1; q2 < f; ++q2) pat[(size_t)i * f + q2] |= pat[(size_t)t * f + q2];
+                    for (int t = 0; t < c; ++t) {
+                        bool border = false;
+                        for (int q2 = c; q2 < f && !border; ++q2) border = pat[(size_t)t * f + q2] != 0;
+                        if (border) { gmem.push_back(w); gloc.push_back(t); }
+                    }
                     skip[ch] = 1;
                 }
-                g.K = kofs.back();
+                g.K = (int)gmem.size();
                 std::vector<int64_t> uo;
                 for (int ch : same) uo.push_back(Y.upd_off[ch]);
                 if ((rc = dcopy(S, &g.d_updoff, uo))) return rc;
                 if ((rc = dcopy(S, &g.d_members, same))) return rc;
-                if ((rc = dcopy(S, &g.d_kofs, kofs))) return rc;
+                if ((rc = dcopy(S, &g.d_gmem, gmem))) return rc;
+                if ((rc = dcopy(S, &g.d_gloc, gloc))) return rc;
                 max_rK = std::max(max_rK, (int64_t)r * g.K);
                 max_upd = std::max(max_upd, (int64_t)((g.nmem + 255) / 256) * r);  // solve partials
-                const int64_t nt = (r + 63) / 64;
+                const int64_t nt = (r + kGroupTile - 1) / kGroupTile;
                 max_tiles = std::max(max_tiles, nt * (nt + 1) / 2);
                 P.groups.push_back(g);
             }
@@ -510,7 +551,8 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
             P.grp_split = 128;
             if ((rc = dalloc(S, &P.grp_L, (size_t)max_rK))) return rc;
             if ((rc = dalloc(S, &P.grp_W, (size_t)max_rK))) return rc;
-            if ((rc = dalloc(S, &P.grp_part, (size_t)std::max<int64_t>(P.grp_split * max_tiles * 64 * 64, max_upd))))
+            if ((rc = dalloc(S, &P.grp_part,
+                             (size_t)std::max<int64_t>(P.grp_split * max_tiles * kGroupTile * kGroupTile, max_upd))))
                 return rc;
             signed char* pskip;
             if ((rc = dcopy(S, &pskip, skip))) return rc;
@@ -596,7 +638,7 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     double** vecM[] = {&S->s, &S->ds_aff, &S->ds_cmb, &S->wbar, &S->lam, &S->t, &S->t1, &S->t2};
     for (double** v : vecM) if ((rc = dalloc(S, v, m))) return rc;
     if ((rc = dalloc(S, &S->eta, K.nsoc))) return rc;
-    const int np = std::max(row_partials(N), 2 * std::max(1, max_step_partials(S->cv)));
+    const int np = std::max(row_partials(N, S->kv.n_long), 2 * std::max(1, max_step_partials(S->cv)));
     if ((rc = dalloc(S, &S->partial, np))) return rc;
     S->partial_cap = np;
     if ((rc = dalloc(S, &S->d_S, 1))) return rc;
@@ -650,43 +692,35 @@ int capture_graph(qoco_gpu_solver* S, qoco_gpu_solver::Graph* g, F launch) {
     return 0;
 }
 
-int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
-    {
-        Phase ph(S, QOCO_GPU_PHASE_ROW, st);
-        if (launch_norm_inf(S->kv, S->lpr, S->partial, S->partial_cap, S->d_S, st)) return QOCO_GPU_ERR_INVALID_ARG;
-        S->launches += 2;
+// Batch schedules: 1–4 are the per-instance kernels (launch_inst_factor), 5 the shared
+// kernels every problem uses (dataflow launches, or level launches from graphs).
+constexpr int kSharedSchedule = 5;
+
+int factor_shared(qoco_gpu_solver* S, cudaStream_t st) {
+    if (S->plan.fdataflow) {
+        DataflowState ds;
+        ds.next = &S->d_S->sched_next;
+        ds.err = &S->d_S->bar_err;
+        ds.epoch = ++S->factor_epoch;
+        ds.max_spins = S->barrier_spins;
+        const int rc = launch_factor_dataflow(S->plan, S->fv, S->d_val, ds, st);
+        if (rc < 0) return rc;
+        S->launches += rc;
+        return 0;
     }
-    {
-        Phase ph(S, QOCO_GPU_PHASE_FACTOR, st);
-        if (S->plan.fdataflow) {
-            DataflowState ds;
-            ds.next = &S->d_S->sched_next;
-            ds.err = &S->d_S->bar_err;
-            ds.epoch = ++S->factor_epoch;
-            ds.max_spins = S->barrier_spins;
-            const int rc = launch_factor_dataflow(S->plan, S->fv, S->d_val, ds, st);
-            if (rc < 0) return rc;
-            S->launches += rc;
-        } else {
-            // the level launches (and large-front kernel sequences) are the same every
-            // time: replayed from a graph
-            qoco_gpu_solver::Graph& g = S->fgraph[S->plan.big_fp32 ? 1 : 0];
-            if (!g.exec) {
-                const int rc = capture_graph(S, &g, [&](cudaStream_t cs) { return launch_factor(S->plan, S->fv, S->d_val, cs); });
-                if (rc) return rc;
-            }
-            QOCO_CUDA_TRY(cudaGraphLaunch(g.exec, st));
-            S->launches += g.launches;
-        }
+    // the level launches (and large-front kernel sequences) are the same every time:
+    // replayed from a graph
+    qoco_gpu_solver::Graph& g = S->fgraph[S->plan.big_fp32 ? 1 : 0];
+    if (!g.exec) {
+        const int rc = capture_graph(S, &g, [&](cudaStream_t cs) { return launch_factor(S->plan, S->fv, S->d_val, cs); });
+        if (rc) return rc;
     }
-    QOCO_CUDA_TRY(cudaGetLastError());
-    if (S->plan.big_fp32) ++S->fp32_factors;
-    S->have_factor = true;
+    QOCO_CUDA_TRY(cudaGraphLaunch(g.exec, st));
+    S->launches += g.launches;
     return 0;
 }
 
-int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStream_t st) {
-    Phase ph(S, QOCO_GPU_PHASE_SOLVE, st);
+int solve_shared(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStream_t st) {
     if (S->plan.dataflow) {
         DataflowState ds;
         ds.next = &S->d_S->sched_next;
@@ -728,6 +762,85 @@ int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStre
     return 0;
 }
 
+int factor_with(qoco_gpu_solver* S, int v, cudaStream_t st) {
+    if (v >= 1 && v <= 4) {
+        const int rc = launch_inst_factor(S->plan, S->fv, S->d_val, v, st);
+        if (rc < 0) return rc;
+        S->launches += rc;
+        return 0;
+    }
+    return factor_shared(S, st);
+}
+
+int solve_with(qoco_gpu_solver* S, int v, const double* r, double* x, bool acc, cudaStream_t st) {
+    if (v >= 1 && v <= 4) {
+        const int rc = launch_inst_solve(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, v, st);
+        if (rc < 0) return rc;
+        S->launches += rc;
+        return 0;
+    }
+    return solve_shared(S, r, x, acc, st);
+}
+
+// Autotuning of a batch's factor/solve schedule: each candidate (the four per-instance
+// layouts and the shared kernels) factors the current KKT values and runs one solve (on
+// the combined-direction and residual buffers, dead whenever a factorisation starts),
+// twice; the candidate with the fastest second run is kept for the solver's lifetime.
+int tune_instances(qoco_gpu_solver* S, cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    QOCO_CUDA_TRY(cudaEventCreate(&e0));
+    QOCO_CUDA_TRY(cudaEventCreate(&e1));
+    int best = kSharedSchedule;
+    float best_ms = 0.0f;
+    int rc = 0;
+    for (int v = 1; v <= kSharedSchedule && !rc; ++v) {
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            QOCO_CUDA_TRY(cudaEventRecord(e0, st));
+            if ((rc = factor_with(S, v, st))) break;
+            if ((rc = solve_with(S, v, S->d_cmb, S->res, false, st))) break;
+            QOCO_CUDA_TRY(cudaEventRecord(e1, st));
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = QOCO_GPU_ERR_CUDA;
+            else cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (!rc && (v == 1 || ms < best_ms)) { best = v; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    QOCO_CUDA_TRY(cudaGetLastError());
+    S->plan.inst_variant = best;
+    S->info.batch_schedule_used = best;
+    return 0;
+}
+
+int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
+    {
+        Phase ph(S, QOCO_GPU_PHASE_ROW, st);
+        const int nl = launch_norm_inf(S->kv, S->lpr, S->partial, S->partial_cap, S->d_S, st);
+        if (nl < 0) return QOCO_GPU_ERR_INVALID_ARG;
+        S->launches += nl;
+    }
+    {
+        Phase ph(S, QOCO_GPU_PHASE_FACTOR, st);
+        if (S->plan.inst && S->plan.inst_variant == 0) {
+            const int rc = tune_instances(S, st);
+            if (rc) return rc;
+        }
+        const int rc = factor_with(S, S->plan.inst ? S->plan.inst_variant : kSharedSchedule, st);
+        if (rc) return rc;
+    }
+    QOCO_CUDA_TRY(cudaGetLastError());
+    if (S->plan.big_fp32) ++S->fp32_factors;
+    S->have_factor = true;
+    return 0;
+}
+
+int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStream_t st) {
+    Phase ph(S, QOCO_GPU_PHASE_SOLVE, st);
+    return solve_with(S, S->plan.inst ? S->plan.inst_variant : kSharedSchedule, r, x, acc, st);
+}
+
 // x = K_ε⁻¹ r refined against K until the backward error target (r, x device, N).  On a
 // factor with FP32 large fronts, a refinement that misses the target refactors in FP64
 // (for the rest of the current solve) and starts over.
@@ -739,9 +852,9 @@ int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
         for (;;) {
             {
                 Phase ph(S, QOCO_GPU_PHASE_ROW, st);
-                if (launch_spmv_res(S->kv, S->lpr, x, r, S->res, S->partial, S->partial_cap, S->d_S, st))
-                    return QOCO_GPU_ERR_INVALID_ARG;
-                S->launches += 2;
+                const int nl = launch_spmv_res(S->kv, S->lpr, x, r, S->res, S->partial, S->partial_cap, S->d_S, st);
+                if (nl < 0) return QOCO_GPU_ERR_INVALID_ARG;
+                S->launches += nl;
             }
             QOCO_CUDA_TRY(cudaGetLastError());
             int rc = sync_scalars(S, st);
@@ -780,8 +893,7 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
     S->plan.big_fp32 = S->st.mixed_precision != 0 && S->plan.max_big_f > 0 && S->plan.big_work32;
     if ((rc = reset_barrier(S, st))) return rc;
     // initial point: K(W = I) [x; y; z] = [−c; b; h], s = −z, shift s and z into the cone
-    launch_w2_identity(cv, S->d_val, S->d_w2slot, S->d_w2ptr, st);
-    S->launches += cl;
+    S->launches += launch_w2_identity(cv, S->d_val, S->d_w2slot, S->d_w2ptr, st);
     if ((rc = factor_now(S, st))) return rc;
     k_init_rhs<<<grid(N), 256, 0, st>>>(S->rhs, S->d_c, S->d_b, S->d_h, n, p, m);
     S->launches += 1;
@@ -818,10 +930,10 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
                 S->launches += launch_batch_residual(S->kv, S->bv, S->batch_L, S->xyz, S->s, S->d_c, S->d_b,
                                                      S->d_h, S->r, S->b_aux, it, tol, S->d_S, st);
             } else {
-                if (launch_residual(S->kv, S->lpr, S->xyz, S->s, S->d_c, S->d_b, S->d_h, S->r, S->partial,
-                                    S->partial_cap, S->d_S, st))
-                    return QOCO_GPU_ERR_INVALID_ARG;
-                S->launches += 2;
+                const int nl = launch_residual(S->kv, S->lpr, S->xyz, S->s, S->d_c, S->d_b, S->d_h, S->r,
+                                               S->partial, S->partial_cap, S->d_S, st);
+                if (nl < 0) return QOCO_GPU_ERR_INVALID_ARG;
+                S->launches += nl;
             }
         }
         QOCO_CUDA_TRY(cudaGetLastError());
@@ -845,8 +957,8 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
         // NT scaling, −W² into the KKT values, factor
         {
             Phase ph(S, QOCO_GPU_PHASE_CONE, st);
-            launch_nt_scaling(cv, S->s, z, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot, S->d_w2ptr, st);
-            S->launches += cl;
+            S->launches += launch_nt_scaling(cv, S->s, z, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot,
+                                             S->d_w2ptr, st);
         }
         if ((rc = factor_now(S, st))) return rc;
         // predictor
@@ -1023,6 +1135,71 @@ int stack_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc
     return 0;
 }
 
+// Per-instance schedules of a batch's factorisation and solves (see launch_inst_factor):
+// when every front fits one warp, each instance's supernodes are listed level by level,
+// thread fronts (order ≤ kThreadFront, schedule 0 only) before warp fronts, and the
+// instances are queued by decreasing work Σ f²(c + 1).
+int plan_batch_instances(qoco_gpu_solver* S, int nb, const std::vector<int>& row) {
+    const Symbolic& Y = S->S;
+    FactorPlan& P = S->plan;
+    if (Y.ns == 0 || Y.max_front > kWarpFront || !P.groups.empty() || !P.big_s.empty()) return 0;
+    std::vector<int> inst(Y.ns);
+    int maxlev = 0;
+    std::vector<double> work(nb, 0.0);
+    for (int s = 0; s < Y.ns; ++s) {
+        inst[s] = row[Y.perm[Y.sn_first[s]]];
+        for (int j = Y.sn_first[s]; j < Y.sn_first[s + 1]; ++j)
+            if (row[Y.perm[j]] != inst[s]) return 0;  // a front spanning instances: keep the shared kernels
+        maxlev = std::max(maxlev, Y.level[s]);
+        const double f = Y.sn_nrow[s], c = Y.sn_ncol[s];
+        work[inst[s]] += f * f * (c + 1.0);
+    }
+    // supernodes bucketed by (instance, level), postorder kept inside a bucket
+    const int64_t nkey = (int64_t)nb * (maxlev + 1);
+    std::vector<int64_t> cnt(nkey + 1, 0);
+    for (int s = 0; s < Y.ns; ++s) cnt[(int64_t)inst[s] * (maxlev + 1) + Y.level[s] + 1]++;
+    for (int64_t k = 0; k < nkey; ++k) cnt[k + 1] += cnt[k];
+    std::vector<int> bucket(Y.ns);
+    {
+        std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int s = 0; s < Y.ns; ++s) bucket[fill[(int64_t)inst[s] * (maxlev + 1) + Y.level[s]]++] = s;
+    }
+    P.ninst = nb;
+    int rc;
+    for (int v = 0; v < 2; ++v) {
+        const int thr = v == 0 ? kThreadFront : 0;
+        std::vector<int> lv_ptr(1, 0), ent, sched;
+        sched.reserve(Y.ns);
+        for (int i = 0; i < nb; ++i) {
+            for (int L = 0; L <= maxlev; ++L) {
+                const int64_t b0 = cnt[(int64_t)i * (maxlev + 1) + L], b1 = cnt[(int64_t)i * (maxlev + 1) + L + 1];
+                if (b0 == b1) continue;
+                const int t0 = (int)sched.size();
+                for (int64_t e = b0; e < b1; ++e)
+                    if (Y.sn_nrow[bucket[e]] <= thr) sched.push_back(bucket[e]);
+                const int w0 = (int)sched.size();
+                for (int64_t e = b0; e < b1; ++e)
+                    if (Y.sn_nrow[bucket[e]] > thr) sched.push_back(bucket[e]);
+                ent.push_back(t0);
+                ent.push_back(w0);
+                ent.push_back((int)sched.size());
+            }
+            lv_ptr.push_back((int)ent.size() / 3);
+        }
+        if ((rc = dcopy(S, &P.isched[v].d_lv_ptr, lv_ptr))) return rc;
+        if ((rc = dcopy(S, &P.isched[v].d_ent, ent))) return rc;
+        if ((rc = dcopy(S, &P.isched[v].d_sched, sched))) return rc;
+    }
+    std::vector<int> order(nb);
+    for (int i = 0; i < nb; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    if ((rc = dcopy(S, &P.d_inst_order, order))) return rc;
+    if ((rc = dalloc(S, &P.d_inst_next, 2))) return rc;
+    if ((rc = plan_instances(P, Y.max_front))) return rc;
+    P.inst_variant = S->st.batch_schedule;  // 0: chosen on the first factorisation
+    return 0;
+}
+
 int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
     int rc;
     BatchView& B = S->bv;
@@ -1049,6 +1226,10 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
         for (int k = T.ko[i]; k < T.ko[i + 1]; ++k) soc[k] = i;
     }
     if ((rc = dcopy(S, &pi, row))) return rc; B.inst_row = pi;
+    if (S->st.batch_schedule >= 0 && S->st.batch_schedule < kSharedSchedule &&
+        (rc = plan_batch_instances(S, nb, row)))
+        return rc;
+    S->info.batch_schedule_used = S->plan.inst ? S->st.batch_schedule : kSharedSchedule;
     if (L) { if ((rc = dcopy(S, &pi, orth))) return rc; S->cv.inst_orth = pi; }
     if (T.nsoc) { if ((rc = dcopy(S, &pi, soc))) return rc; S->cv.inst_soc = pi; }
     double** vd[] = {&B.pobj, &B.dobj, &B.gap, &B.mu, &B.alpha_max, &B.sigma_mu, &B.alpha};
@@ -1087,6 +1268,7 @@ void qoco_gpu_default_settings(qoco_gpu_settings* s) {
     s->subtree_tasks = 0;
     s->verbose = 0;
     s->mixed_precision = 0;
+    s->batch_schedule = 0;
 }
 
 int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A, const qoco_csc* G, int l,
@@ -1325,9 +1507,9 @@ int adjoint_refine(qoco_gpu_solver* S, const double* g, double* v, bool* ok, cud
         }
         k_adj_rhs<<<grid(N), 256, 0, st>>>(rp, g, m ? S->t2 : nullptr, n + p, N);
         ++S->launches;
-        if (launch_spmv_res(S->kv, S->lpr, v, rp, S->res, S->partial, S->partial_cap, S->d_S, st))
-            return QOCO_GPU_ERR_INVALID_ARG;
-        S->launches += 2;
+        const int nl = launch_spmv_res(S->kv, S->lpr, v, rp, S->res, S->partial, S->partial_cap, S->d_S, st);
+        if (nl < 0) return QOCO_GPU_ERR_INVALID_ARG;
+        S->launches += nl;
         QOCO_CUDA_TRY(cudaGetLastError());
         if ((rc = sync_scalars(S, st))) return rc;
         if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
@@ -1364,9 +1546,8 @@ int qoco_gpu_backward(qoco_gpu_solver* S, const double* dx, const double* dy, co
     if ((rc = adjoint_refine(S, g, v, &ok, st))) return rc;
     if (!ok && m) {
         // refactor once at the final iterate's NT scaling, then refine again
-        launch_nt_scaling(S->cv, S->s, S->xyz + n + p, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot,
-                          S->d_w2ptr, st);
-        S->launches += cone_launch_count(S->cv);
+        S->launches += launch_nt_scaling(S->cv, S->s, S->xyz + n + p, S->wbar, S->eta, S->lam, S->d_val,
+                                         S->d_w2slot, S->d_w2ptr, st);
         if ((rc = factor_now(S, st))) return rc;
         S->adj_refactored = 1;
         if ((rc = adjoint_refine(S, g, v, &ok, st))) return rc;
@@ -1473,7 +1654,7 @@ int qoco_gpu_cleanup(qoco_gpu_solver* S) {
 int qoco_gpu_kkt_factor_at(qoco_gpu_solver* S, const double* s, const double* z, void* stream) {
     if (!S || (S->m && (!s || !z))) return QOCO_GPU_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    launch_nt_scaling(S->cv, s, z, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot, S->d_w2ptr, st);
+    S->launches += launch_nt_scaling(S->cv, s, z, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot, S->d_w2ptr, st);
     S->plan.big_fp32 = S->st.mixed_precision != 0 && S->plan.max_big_f > 0 && S->plan.big_work32;
     int rc = factor_now(S, st);
     if (rc) return rc;

@@ -92,3 +92,49 @@ def test_mpc_batch_4096(q):
         assert ref.status == "solved"
         _check_instance(probs[i], sols[i], ref)
     S.close()
+
+
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5])
+def test_batch_schedules_match_the_oracle(q, schedule):
+    """Every layout of the per-instance factor/solve kernels (4 or 8 warps per CTA,
+    tiny fronts one per thread or every front one warp) and the shared kernels solve the
+    same instances to the oracle's tolerances."""
+    probs = mpc_batch(count=48, tmin=10, tmax=60, seed=21)
+    S = q.BatchSolver(probs, batch_schedule=schedule)
+    assert S.solve() == 0
+    assert S.info()["batch_schedule_used"] == schedule
+    info = S.batch_info()
+    assert np.all(info["status"] == 0)
+    sols = S.instance_solutions()
+    for i in (0, 7, 19, 33, 47):
+        ref = ipm.solve(probs[i])
+        assert ref.status == "solved"
+        assert abs(int(info["iters"][i]) - ref.iters) <= 3
+        _check_instance(probs[i], sols[i], ref)
+    S.close()
+
+
+def test_batch_schedule_autotune_picks_a_candidate(q):
+    probs = mpc_batch(count=32, tmin=10, tmax=60, seed=22)
+    S = q.BatchSolver(probs)
+    assert S.info()["batch_schedule_used"] == 0  # chosen on the first factorisation
+    assert S.solve() == 0
+    used = S.info()["batch_schedule_used"]
+    assert used in (1, 2, 3, 4, 5)
+    sols = S.instance_solutions()
+    T = q.BatchSolver(probs, batch_schedule=used)
+    assert T.solve() == 0
+    for a, b in zip(sols, T.instance_solutions()):
+        for k in ("x", "y", "z", "s"):
+            assert np.array_equal(a[k], b[k])  # the tuned run is the fixed candidate's run
+    S.close()
+    T.close()
+
+
+def test_batch_with_a_front_beyond_one_warp_uses_the_shared_kernels(q):
+    probs = mpc_batch(count=4, tmin=10, tmax=20, seed=23) + [dense_qp(n=60, p=10, m=90, rank=8, density=0.1, seed=4)]
+    S = q.BatchSolver(probs)
+    assert S.info()["max_front"] > 48
+    assert S.info()["batch_schedule_used"] == 5
+    assert S.solve() == 0
+    S.close()

@@ -43,9 +43,10 @@ def _oracle_K(prob, s, z):
     return ok.assemble(prob, ok.z_block(W, prob.m))
 
 
-@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("name", list(SMALL) + ["portfolio_n400_wide_cone"])
 def test_w2_update_of_kkt_values(name):
-    prob = SMALL[name]()
+    # a Q^91 risk cone (> 64): its −W² block is written by the one-thread-per-entry kernel
+    prob = SMALL[name]() if name in SMALL else portfolio_socp(n=400, k=90, seed=8)
     s, z, _, _ = random_cone_iterate(prob.l, prob.q, seed=3, scale_spread=2.0)
     S = _setup(prob)
     S.kkt_factor_at(T(s), T(z))
@@ -91,10 +92,12 @@ def test_factor_reconstructs_permuted_matrix(name):
 
 @pytest.mark.parametrize("name,spread", [("dense_qp_c1", 0.0), ("trajectory_N12", 3.0),
                                          ("portfolio_n300", 2.0), ("trajectory_N2000", 2.0),
-                                         ("portfolio_n2000", 1.0)])
+                                         ("portfolio_n2000", 1.0), ("portfolio_n2500", 1.0)])
 def test_refined_solve_matches_oracle(name, spread):
     makers = dict(SMALL, trajectory_N2000=lambda: trajectory_socp(N=2000, seed=5),
-                  portfolio_n2000=lambda: portfolio_socp(n=2000, k=60, seed=6))
+                  portfolio_n2000=lambda: portfolio_socp(n=2000, k=60, seed=6),
+                  # budget and risk-cone rows of 2500 entries: the row kernels' long-row blocks
+                  portfolio_n2500=lambda: portfolio_socp(n=2500, k=30, seed=7))
     prob = makers[name]()
     s, z, _, _ = random_cone_iterate(prob.l, prob.q, seed=6, scale_spread=spread)
     S = _setup(prob)
