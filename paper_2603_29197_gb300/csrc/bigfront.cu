@@ -652,45 +652,199 @@ __global__ void k_group_upd_reduce(const double* __restrict__ part, int nchunk, 
     v[rel[i]] += acc;
 }
 
-// one forward block: y_b = L_bb⁻¹ v_b with the inverse stored by the factorisation
-// (every CTA, redundantly: a 64×64 matrix-vector product, no dependent chain), CTA 0
-// stores y_b; each CTA updates its rows i ≥ k0+nb: v_i −= Σ_k L_{i,k0+k} y_k
-__global__ void __launch_bounds__(256) k_big_fwd_step(int s, int k0, int nb, FactorView a,
-                                                      const double* __restrict__ Xb, double* __restrict__ v,
-                                                      double* __restrict__ y) {
-    __shared__ double vb[kBigNB], yb[kBigNB];
-    const int f = a.nrow[s];
-    const double* L = a.front + a.front_off[s];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = tid; k < nb; k += blockDim.x) vb[k] = v[k0 + k];
-    __syncthreads();
-    for (int i = wid; i < nb; i += blockDim.x >> 5) {
-        const double* xr = Xb + i * kBigNB;
-        double acc = 0.0;
-        for (int j = lane; j < i; j += 32) acc += xr[j] * vb[j];
-        acc = warp_sum(acc);
-        if (lane == 0) yb[i] = vb[i] + acc;
+// ---- dataflow solves of one large front ----------------------------------------------
+// Forward: row blocks are the pivot blocks [k0, k0+nb) (nb ≤ 64) followed by 64-row blocks
+// of the border rows ≥ c, taken in that order from a counter (ctl[0]).  Block b subtracts
+// L_{rows, k}·y_k for each pivot block k < b (k < nblk for a border block) as soon as y_k
+// is published (flag ctl[1+k], bounded wait); a pivot block then computes
+// y_b = X_b·(v_b − Σ) with its stored block inverse and publishes it, a border block
+// leaves v − Σ (the front's update vector).  A block waits only on blocks taken before
+// it, so the launch cannot deadlock whatever the number of resident CTAs.
+constexpr int kDfThreads = 256;
+
+__device__ __forceinline__ bool df_wait(const int* flag, int* err, long long max_spins) {
+    const volatile int* vf = flag;
+    const volatile int* ve = err;
+    long long spins = 0;
+    while (*vf == 0) {
+        if (*ve) return false;
+        if (++spins > max_spins) {
+            atomicExch(err, 1);
+            return false;
+        }
+        __nanosleep(32);
     }
+    return true;
+}
+
+__device__ __forceinline__ int df_take(int* ctl) {
+    __shared__ int s_b;
+    if (threadIdx.x == 0) s_b = atomicAdd(ctl, 1);
     __syncthreads();
-    if (blockIdx.x == 0)
-        for (int k = tid; k < nb; k += blockDim.x) y[k0 + k] = yb[k];
-    // rows below: four threads per row (lane bits 0–1 pick a quarter of the block's
-    // columns), reduced with two shuffles
-    const int q = tid & 3;
-    const int64_t nrow = f - (k0 + nb);
-    for (int64_t r0 = (int64_t)blockIdx.x * (blockDim.x >> 2); r0 < nrow; r0 += (int64_t)gridDim.x * (blockDim.x >> 2)) {
-        const int64_t r = r0 + (tid >> 2);
-        const int i = k0 + nb + (int)r;
-        double acc0 = 0.0, acc1 = 0.0;
-        if (r < nrow)
-            for (int k = q; k < nb; k += 8) {
-                acc0 += L[(int64_t)(k0 + k) * f + i] * yb[k];
-                if (k + 4 < nb) acc1 += L[(int64_t)(k0 + k + 4) * f + i] * yb[k + 4];
+    const int b = s_b;
+    __syncthreads();
+    return b;
+}
+
+__global__ void __launch_bounds__(kDfThreads) k_big_fwd_df(int s, FactorView a, const double* __restrict__ Xall,
+                                                           double* __restrict__ v, double* __restrict__ y,
+                                                           int* __restrict__ ctl, int* err, long long max_spins) {
+    __shared__ double part[4][kBigNB];
+    __shared__ double ys[kBigNB];
+    const int f = a.nrow[s], c = a.ncol[s];
+    const double* L = a.front + a.front_off[s];
+    const int nblk = (c + kBigNB - 1) / kBigNB, nrb = nblk + (f - c + kBigNB - 1) / kBigNB;
+    const int tid = threadIdx.x, r = tid & (kBigNB - 1), q = tid >> 6;
+    for (;;) {
+        const int b = df_take(ctl);
+        if (b >= nrb) return;
+        const bool pivot = b < nblk;
+        const int row0 = pivot ? b * kBigNB : c + (b - nblk) * kBigNB;
+        const int nrow = pivot ? min(kBigNB, c - row0) : min(kBigNB, f - row0);
+        const int i = row0 + r;
+        const bool mine = r < nrow;
+        // this thread's entries of the block inverse (final since the factorisation),
+        // loaded before any wait: X_{r,j}, j = q + 4m ≤ r
+        const double* X = Xall + (int64_t)(pivot ? b : 0) * kBigNB * kBigNB;
+        double xv[kBigNB / 4];
+#pragma unroll
+        for (int m = 0; m < kBigNB / 4; ++m) {
+            const int j = q + 4 * m;
+            xv[m] = (pivot && mine && j <= r) ? X[r * kBigNB + j] : 0.0;
+        }
+        const double vi = mine ? v[i] : 0.0;  // final before the launch (pivot rows are read only)
+        double acc = 0.0;
+        const int kend = pivot ? b : nblk;
+        for (int k = 0; k < kend; ++k) {
+            const int k0 = k * kBigNB, nb = min(kBigNB, c - k0);
+            // L's block (rows of b, columns of k) is final: its loads go out before the wait
+            double l[kBigNB / 4];
+#pragma unroll
+            for (int m = 0; m < kBigNB / 4; ++m) {
+                const int kk = q + 4 * m;
+                l[m] = (mine && kk < nb) ? L[(int64_t)(k0 + kk) * f + i] : 0.0;
             }
-        double acc = acc0 + acc1;
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        if (r < nrow && q == 0) v[i] -= acc;
+            bool ok = true;
+            if (tid == 0) {
+                ok = df_wait(ctl + 1 + k, err, max_spins);
+                __threadfence();
+            }
+            if (!__syncthreads_and(ok)) return;
+            if (tid < kBigNB) ys[tid] = tid < nb ? __ldcg(y + k0 + tid) : 0.0;
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < kBigNB / 4; ++m) acc += l[m] * ys[q + 4 * m];
+            __syncthreads();
+        }
+        part[q][r] = acc;
+        __syncthreads();
+        if (!pivot) {
+            if (q == 0 && mine) v[i] = vi - ((part[0][r] + part[1][r]) + (part[2][r] + part[3][r]));
+            __syncthreads();
+            continue;
+        }
+        if (q == 0) ys[r] = mine ? vi - ((part[0][r] + part[1][r]) + (part[2][r] + part[3][r])) : 0.0;
+        __syncthreads();
+        // y_b = X_b u (X unit lower, row-major): row r, quarter q of its columns j ≤ r
+        double t = 0.0;
+#pragma unroll
+        for (int m = 0; m < kBigNB / 4; ++m) t += xv[m] * ys[q + 4 * m];
+        part[q][r] = t;
+        __syncthreads();
+        if (q == 0 && mine) y[i] = (part[0][r] + part[1][r]) + (part[2][r] + part[3][r]);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();  // cumulative: orders the block's stores (seen through the barrier) before the flag
+            atomicExch(ctl + 1 + b, 1);
+        }
+    }
+}
+
+// Backward, pivot blocks from the last: block b (taken as nblk−1−counter) waits for every
+// later block k > b, last first (the order in which they are published), and subtracts
+// Σ_j L_{j,i}·x_j (column i of L, rows of block k) from v_i, then x_b = X_bᵀ·(v_b − Σ) and
+// publishes it.  v holds w − (border contributions) from k_big_bwd_below.
+__global__ void __launch_bounds__(kDfThreads) k_big_bwd_df(int s, FactorView a, const double* __restrict__ Xall,
+                                                           const double* __restrict__ v, double* __restrict__ x,
+                                                           int* __restrict__ ctl, int* err, long long max_spins) {
+    __shared__ double part[8][kBigNB + 1];
+    __shared__ double xs[kBigNB];
+    __shared__ double us[kBigNB];
+    __shared__ double red[4][kBigNB];
+    const int f = a.nrow[s], c = a.ncol[s];
+    const double* L = a.front + a.front_off[s];
+    const int nblk = (c + kBigNB - 1) / kBigNB;
+    const int tid = threadIdx.x, q8 = tid & 7, rr = tid >> 3;  // 32 rows × 8 per pass
+    for (;;) {
+        const int t = df_take(ctl);
+        if (t >= nblk) return;
+        const int b = nblk - 1 - t;
+        const int row0 = b * kBigNB, nrow = min(kBigNB, c - row0);
+        // this thread's entries of the block inverse, loaded before any wait:
+        // X_{i,j} for column j = tid & 63 and rows i = j + q + 4m < nrow
+        const int j = tid & (kBigNB - 1), q = tid >> 6;
+        const double* X = Xall + (int64_t)b * kBigNB * kBigNB;
+        double xv[kBigNB / 4];
+#pragma unroll
+        for (int m = 0; m < kBigNB / 4; ++m) {
+            const int i = j + q + 4 * m;
+            xv[m] = (j < nrow && i < nrow) ? X[i * kBigNB + j] : 0.0;
+        }
+        const double vj = (tid < kBigNB && tid < nrow) ? v[row0 + tid] : 0.0;  // read only here
+        double acc0 = 0.0, acc1 = 0.0;  // rows rr and rr + 32
+        // later blocks in the order they are published (the last first)
+        for (int k = nblk - 1; k > b; --k) {
+            const int k0 = k * kBigNB, nb = min(kBigNB, c - k0);
+            // L's block is final: its loads go out before the wait
+            double l0[kBigNB / 8], l1[kBigNB / 8];
+            const double* col0 = L + (int64_t)(row0 + rr) * f + k0;
+            const double* col1 = col0 + (int64_t)32 * f;
+#pragma unroll
+            for (int m = 0; m < kBigNB / 8; ++m) {
+                const int j = q8 + 8 * m;
+                l0[m] = (rr < nrow && j < nb) ? col0[j] : 0.0;
+                l1[m] = (rr + 32 < nrow && j < nb) ? col1[j] : 0.0;
+            }
+            bool ok = true;
+            if (tid == 0) {
+                ok = df_wait(ctl + 1 + k, err, max_spins);
+                __threadfence();
+            }
+            if (!__syncthreads_and(ok)) return;
+            if (tid < kBigNB) xs[tid] = tid < nb ? __ldcg(x + k0 + tid) : 0.0;
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < kBigNB / 8; ++m) {
+                acc0 += l0[m] * xs[q8 + 8 * m];
+                acc1 += l1[m] * xs[q8 + 8 * m];
+            }
+            __syncthreads();
+        }
+        part[q8][rr] = acc0;
+        part[q8][rr + 32] = acc1;
+        __syncthreads();
+        if (tid < kBigNB) {
+            double sum = 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) sum += part[u][tid];
+            us[tid] = tid < nrow ? vj - sum : 0.0;
+        }
+        __syncthreads();
+        // x_j = Σ_{i ≥ j} X_ij u_i (X unit lower, row-major): column j, quarter q of the rows
+        double tsum = 0.0;
+#pragma unroll
+        for (int m = 0; m < kBigNB / 4; ++m) {
+            const int i = j + q + 4 * m;
+            if (i < nrow) tsum += xv[m] * us[i];
+        }
+        red[q][j] = tsum;
+        __syncthreads();
+        if (q == 0 && j < nrow) x[row0 + j] = (red[0][j] + red[1][j]) + (red[2][j] + red[3][j]);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicExch(ctl + 1 + b, 1);
+        }
     }
 }
 
@@ -718,43 +872,6 @@ __global__ void k_big_bwd_below(int s, FactorView a, const double* __restrict__ 
     for (int i = c + lane; i < f; i += 32) acc += colk[i] * xp[R[i]];
     acc = warp_sum(acc);
     if (lane == 0) v[k] = w[first + k] - acc;
-}
-
-// one backward block (from the last): x_b = L_bb⁻ᵀ v_b with the stored inverse (every
-// CTA, redundantly), CTA 0 stores x_b; each CTA updates its rows k < k0:
-// v_k −= Σ_j L_{k0+j,k} x_j
-__global__ void __launch_bounds__(256) k_big_bwd_step(int s, int k0, int nb, FactorView a,
-                                                      const double* __restrict__ Xb, double* __restrict__ v,
-                                                      double* __restrict__ x) {
-    __shared__ double vb[kBigNB], xb[kBigNB];
-    const int f = a.nrow[s];
-    const double* L = a.front + a.front_off[s];
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int k = tid; k < nb; k += blockDim.x) vb[k] = v[k0 + k];
-    __syncthreads();
-    for (int j = wid; j < nb; j += blockDim.x >> 5) {
-        double acc = 0.0;
-        for (int i = j + 1 + lane; i < nb; i += 32) acc += Xb[i * kBigNB + j] * vb[i];
-        acc = warp_sum(acc);
-        if (lane == 0) xb[j] = vb[j] + acc;
-    }
-    __syncthreads();
-    if (blockIdx.x == 0)
-        for (int k = tid; k < nb; k += blockDim.x) x[k0 + k] = xb[k];
-    // earlier rows: eight threads per row k read consecutive entries of its column
-    const int q = tid & 7;
-    for (int r0 = blockIdx.x * (blockDim.x >> 3); r0 < k0; r0 += gridDim.x * (blockDim.x >> 3)) {
-        const int k = r0 + (tid >> 3);
-        double acc = 0.0;
-        if (k < k0) {
-            const double* colk = L + (int64_t)k * f + k0;
-            for (int j = q; j < nb; j += 8) acc += colk[j] * xb[j];
-        }
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-        if (k < k0 && q == 0) v[k] -= acc;
-    }
 }
 
 __global__ void k_big_bwd_finish(int s, FactorView a, const double* __restrict__ xs, double* __restrict__ xp,
@@ -906,15 +1023,12 @@ int launch_big_fwd(const FactorPlan& P, const FactorView& a, const double* rhs, 
         launches += 2;
     }
     ++launches;
-    for (int k0 = 0; k0 < c; k0 += kBigNB) {
-        const int nb = std::min(kBigNB, c - k0);
-        const double* Xb = P.big_linv + P.big_linv_off[idx] + (int64_t)(k0 / kBigNB) * kBigNB * kBigNB;
-        k_big_fwd_step<<<gridfor(4 * (int64_t)std::max(1, f - k0 - nb), 256), 256, 0, st>>>(s, k0, nb, a, Xb,
-                                                                                          P.big_v, P.big_y);
-        ++launches;
-    }
+    const int nblk = (c + kBigNB - 1) / kBigNB, nrb = nblk + (f - c + kBigNB - 1) / kBigNB;
+    QOCO_CUDA_TRY(cudaMemsetAsync(P.big_ctl, 0, sizeof(int) * (1 + nblk), st));
+    k_big_fwd_df<<<(unsigned)std::min(nrb, 2 * nsm()), kDfThreads, 0, st>>>(
+        s, a, P.big_linv + P.big_linv_off[idx], P.big_v, P.big_y, P.big_ctl, P.df_err, P.df_spins);
     k_big_fwd_finish<<<gridfor(f, 256), 256, 0, st>>>(s, a, P.big_v, P.big_y, w);
-    return launches + 1;
+    return launches + 2;
 }
 
 int launch_big_bwd(const FactorPlan& P, const FactorView& a, const double* w, double* xp, double* x,
@@ -924,15 +1038,11 @@ int launch_big_bwd(const FactorPlan& P, const FactorView& a, const double* w, do
     k_big_bwd_below<<<(unsigned)((c + 7) / 8), 256, 0, st>>>(s, a, w, xp, P.big_v);
     ++launches;
     const int nblk = (c + kBigNB - 1) / kBigNB;
-    for (int b = nblk - 1; b >= 0; --b) {
-        const int k0 = b * kBigNB, nb = std::min(kBigNB, c - k0);
-        const double* Xb = P.big_linv + P.big_linv_off[idx] + (int64_t)b * kBigNB * kBigNB;
-        k_big_bwd_step<<<gridfor(8 * (int64_t)std::max(1, k0), 256), 256, 0, st>>>(s, k0, nb, a, Xb, P.big_v,
-                                                                                 P.big_y);
-        ++launches;
-    }
+    QOCO_CUDA_TRY(cudaMemsetAsync(P.big_ctl, 0, sizeof(int) * (1 + nblk), st));
+    k_big_bwd_df<<<(unsigned)std::min(nblk, 2 * nsm()), kDfThreads, 0, st>>>(
+        s, a, P.big_linv + P.big_linv_off[idx], P.big_v, P.big_y, P.big_ctl, P.df_err, P.df_spins);
     k_big_bwd_finish<<<gridfor(c, 256), 256, 0, st>>>(s, a, P.big_y, xp, x, accumulate ? 1 : 0);
-    return launches + 1;
+    return launches + 2;
 }
 
 }  // namespace qoco

@@ -133,6 +133,11 @@ struct FactorPlan {
     void* big_w = nullptr;         // max_big_f × 4·kBigNB doubles: panel rows W (FP64), or W and L (FP32)
     double* big_v = nullptr;       // max_big_f solve work vector
     double* big_y = nullptr;       // max_big_f solved block values
+    // dataflow solves of the large fronts: block counter and per-block flags (reset before
+    // each launch), the solver's error flag and its poll bound
+    int* big_ctl = nullptr;
+    int* df_err = nullptr;
+    long long df_spins = 0;
 };
 
 // Shared state of one dataflow solve launch.

@@ -576,6 +576,10 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         if ((rc = dalloc(S, &P.big_y, P.max_big_f))) return rc;
         if (S->st.mixed_precision && (rc = dalloc(S, &P.big_work32, (size_t)P.max_big_f * P.max_big_f))) return rc;
         if ((rc = dalloc(S, &P.big_err, 1))) return rc;
+        int64_t max_blk = 0;
+        for (size_t idx = 0; idx < P.big_s.size(); ++idx)
+            max_blk = std::max<int64_t>(max_blk, (P.big_c[idx] + kBigNB - 1) / kBigNB);
+        if ((rc = dalloc(S, &P.big_ctl, (size_t)(1 + max_blk)))) return rc;
         QOCO_CUDA_TRY(cudaMemset(P.big_err, 0, sizeof(int)));
         if ((rc = big_set_attributes())) return rc;
     }
@@ -642,6 +646,8 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     if ((rc = dalloc(S, &S->partial, np))) return rc;
     S->partial_cap = np;
     if ((rc = dalloc(S, &S->d_S, 1))) return rc;
+    S->plan.df_err = &S->d_S->bar_err;
+    S->plan.df_spins = S->barrier_spins;
     QOCO_CUDA_TRY(cudaMallocHost((void**)&S->h_S, sizeof(IPMScalars)));
 
     IPMScalars hs;
