@@ -37,6 +37,36 @@ def test_default_settings(lib):
     assert st.abstol == 1e-7 and st.reltol == 1e-7
     assert st.max_iter == 200 and st.static_reg == 1e-8 and st.step_fraction == 0.99
     assert st.max_refine == 10 and st.refine_tol == 1e-10
+    assert st.mixed_precision == 0 and st.batch_schedule == 0
+
+
+def _header_struct(name):
+    txt = open(os.path.join(ROOT, "include", "qoco_gpu.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", txt).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        m = re.match(r"(double|int64_t|int|char)\s+(.*)$", decl, flags=re.S)
+        ctype, names = m.group(1), m.group(2)
+        for nm in names.split(","):
+            nm = nm.strip()
+            arr = re.match(r"(\w+)\[(\w+)\]", nm)
+            fields.append((arr.group(1), ctype, int(arr.group(2))) if arr else (nm, ctype, 1))
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("qoco_gpu_settings", "Settings"), ("qoco_gpu_info", "Info")])
+def test_binding_structs_mirror_the_header(cname, pyname):
+    import ctypes as C
+    want = {"double": C.c_double, "int": C.c_int, "int64_t": C.c_int64, "char": C.c_char}
+    hdr = _header_struct(cname)
+    py = getattr(_lib, pyname)._fields_
+    assert [f[0] for f in hdr] == [f[0] for f in py]
+    for (nm, ctype, n), (_, pytype) in zip(hdr, py):
+        assert C.sizeof(pytype) == C.sizeof(want[ctype]) * n, nm
 
 
 def _tiny(**kw):
