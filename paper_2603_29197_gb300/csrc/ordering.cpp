@@ -14,10 +14,13 @@
 //    by AMD.  Gives the O(log N)-deep elimination trees that level-scheduled GPU
 //    factorisation needs on banded / stage-structured problems.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <functional>
+#include <memory>
 #include <numeric>
+#include <thread>
 
 #include "symbolic.h"
 
@@ -210,43 +213,64 @@ std::vector<int> order_amd(const Graph& g, double dense_factor) {
 
 namespace {
 
-// AMD on the subgraph induced by `nodes`; appends the ordered nodes to `out`.
-void amd_subset(const Graph& g, const std::vector<int>& nodes, std::vector<int>& local,
-                std::vector<int>* out) {
+// Shared marks of the dissection.  Subproblems that run concurrently own disjoint node
+// sets; a node's tag is written only by the subproblem that owns it, but a BFS reads the
+// tags of its nodes' neighbours, which may belong to a concurrent subproblem, so tags are
+// atomics (relaxed: a foreign tag is never equal to the reader's own).  Levels and local
+// indices are read and written only for a subproblem's own nodes.
+struct Marks {
+    explicit Marks(int n) : tag(new std::atomic<int>[n]), lev(n, -1), local(n, -1) {
+        for (int i = 0; i < n; ++i) tag[i].store(0, std::memory_order_relaxed);
+    }
+    std::unique_ptr<std::atomic<int>[]> tag;
+    std::vector<int> lev, local;
+    std::atomic<int> next_tag{1};
+    int get(int v) const { return tag[v].load(std::memory_order_relaxed); }
+    void set(int v, int t) { tag[v].store(t, std::memory_order_relaxed); }
+};
+
+// AMD on the subgraph induced by `nodes` (all tagged t); appends the ordered nodes to `out`.
+void amd_subset(const Graph& g, Marks& mk, int t, const std::vector<int>& nodes, std::vector<int>* out) {
     const int n = (int)nodes.size();
     if (n <= 2) {
         out->insert(out->end(), nodes.begin(), nodes.end());
         return;
     }
-    for (int i = 0; i < n; ++i) local[nodes[i]] = i;
+    for (int i = 0; i < n; ++i) mk.local[nodes[i]] = i;
     Graph sg;
     sg.N = n;
     sg.ptr.assign(n + 1, 0);
     for (int i = 0; i < n; ++i) {
         int v = nodes[i];
-        for (int64_t t = g.ptr[v]; t < g.ptr[v + 1]; ++t) {
-            int u = g.adj[t];
-            if (local[u] >= 0) sg.adj.push_back(local[u]);
+        for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; ++e) {
+            int u = g.adj[e];
+            if (mk.get(u) == t) sg.adj.push_back(mk.local[u]);
         }
         sg.ptr[i + 1] = (int64_t)sg.adj.size();
     }
     std::vector<int> o = order_amd(sg);
     for (int i : o) out->push_back(nodes[i]);
-    for (int i = 0; i < n; ++i) local[nodes[i]] = -1;
+    for (int i = 0; i < n; ++i) mk.local[nodes[i]] = -1;
 }
+
+// Subproblems at least this large are split across two host threads (the first part on
+// a new thread) while fewer than kNdMaxDepth splits are in flight above them; the
+// order produced is the serial one (each part's order is computed independently and
+// the parts are concatenated in the serial order).
+constexpr int kNdParallelMin = 20000;
+constexpr int kNdMaxDepth = 4;
 
 struct ND {
     const Graph& g;
+    Marks& mk;
     int leaf;
-    std::vector<int> tag, local, lev, q;
-    int next_tag = 1;
-    std::vector<int>* out;
+    std::vector<int> q;  // BFS queue (per ND object: one per host thread)
 
-    ND(const Graph& gg, int leaf_size, std::vector<int>* o)
-        : g(gg), leaf(leaf_size), tag(gg.N, 0), local(gg.N, -1), lev(gg.N, -1), q(), out(o) {}
+    ND(const Graph& gg, Marks& m, int leaf_size) : g(gg), mk(m), leaf(leaf_size) {}
 
     // BFS within the nodes carrying tag t; returns levels (as offsets into q).
     int bfs(int root, int t, std::vector<int>& lptr) {
+        std::vector<int>& lev = mk.lev;
         q.clear();
         lptr.clear();
         q.push_back(root);
@@ -260,29 +284,39 @@ struct ND {
             ++h;
             for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; ++e) {
                 int u = g.adj[e];
-                if (tag[u] == t && lev[u] < 0) { lev[u] = lev[v] + 1; q.push_back(u); }
+                if (mk.get(u) == t && lev[u] < 0) { lev[u] = lev[v] + 1; q.push_back(u); }
             }
         }
         lptr.push_back((int)q.size());
         return (int)lptr.size() - 1;  // number of levels
     }
-    void clear_lev() { for (int v : q) lev[v] = -1; }
+    void clear_lev() { for (int v : q) mk.lev[v] = -1; }
 
     int local_degree(int v, int t) const {
         int d = 0;
-        for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; ++e) d += tag[g.adj[e]] == t;
+        for (int64_t e = g.ptr[v]; e < g.ptr[v + 1]; ++e) d += mk.get(g.adj[e]) == t;
         return d;
     }
 
-    void run(std::vector<int> nodes) {
-        if ((int)nodes.size() <= leaf) { amd_subset(g, nodes, local, out); return; }
-        const int t = next_tag++;
-        for (int v : nodes) tag[v] = t;
-        // connected components
+    void leaf_amd(const std::vector<int>& nodes, std::vector<int>* out) {
+        const int t = mk.next_tag.fetch_add(1, std::memory_order_relaxed);
+        for (int v : nodes) mk.set(v, t);
+        amd_subset(g, mk, t, nodes, out);
+    }
+
+    void run(std::vector<int> nodes, std::vector<int>* out, int depth) {
+        std::vector<int>& lev = mk.lev;
+        if ((int)nodes.size() <= leaf) { leaf_amd(nodes, out); return; }
+        const int t = mk.next_tag.fetch_add(1, std::memory_order_relaxed);
+        for (int v : nodes) mk.set(v, t);
+        // connected components; the first BFS (from nodes[0]) is also the first level
+        // structure of the pseudo-peripheral search when the subgraph is connected
         std::vector<int> lptr;
-        std::vector<std::vector<int>> comps;
-        {
-            std::vector<int> seen;
+        int nl = bfs(nodes[0], t, lptr);
+        if ((int)q.size() < (int)nodes.size()) {
+            std::vector<std::vector<int>> comps;
+            std::vector<int> seen(q.begin(), q.end());
+            comps.emplace_back(q.begin(), q.end());
             for (int v : nodes) {
                 if (lev[v] >= 0) continue;
                 bfs(v, t, lptr);
@@ -291,28 +325,35 @@ struct ND {
                 seen.insert(seen.end(), q.begin(), q.end());
             }
             for (int v : seen) lev[v] = -1;
-        }
-        if (comps.size() > 1) {
-            for (auto& c : comps) run(std::move(c));
+            for (auto& c : comps) run(std::move(c), out, depth);
             return;
         }
-        // pseudo-peripheral root
-        int root = nodes[0];
-        int nl = bfs(root, t, lptr);
+        // pseudo-peripheral root: BFS from the least-degree node of the last level while
+        // that deepens the level structure; the kept structure is restored from its
+        // saved queue instead of a repeated BFS
+        std::vector<int> keep_q, keep_l;
         for (int it = 0; it < 8; ++it) {
             int best = -1, bd = 1 << 30;
             for (int k = lptr[nl - 1]; k < lptr[nl]; ++k) {
                 int d = local_degree(q[k], t);
                 if (d < bd) { bd = d; best = q[k]; }
             }
-            clear_lev();
+            keep_q.swap(q);
+            keep_l.swap(lptr);
+            for (int v : keep_q) lev[v] = -1;
             int nl2 = bfs(best, t, lptr);
-            if (nl2 <= nl) { clear_lev(); nl = bfs(root, t, lptr); break; }
-            root = best;
+            if (nl2 <= nl) {
+                clear_lev();
+                q.swap(keep_q);
+                lptr.swap(keep_l);
+                for (int k = 0; k < nl; ++k)
+                    for (int j = lptr[k]; j < lptr[k + 1]; ++j) lev[q[j]] = k;
+                break;
+            }
             nl = nl2;
         }
         const int S = (int)nodes.size();
-        if (nl < 3) { clear_lev(); amd_subset(g, nodes, local, out); return; }
+        if (nl < 3) { clear_lev(); amd_subset(g, mk, t, nodes, out); return; }
         // separator level: smallest level whose both sides hold ≥ 20% of the nodes,
         // else the median level
         int pick = -1, psize = 1 << 30, median = -1;
@@ -325,6 +366,8 @@ struct ND {
         if (pick < 0) pick = median < 0 ? nl / 2 : median;
         // thin the separator: keep only level nodes touching the next level
         std::vector<int> part1, part2, sep;
+        part1.reserve(lptr[pick + 1]);
+        part2.reserve(S - lptr[pick + 1]);
         for (int k = 0; k < lptr[pick]; ++k) part1.push_back(q[k]);
         for (int k = lptr[pick + 1]; k < S; ++k) part2.push_back(q[k]);
         for (int k = lptr[pick]; k < lptr[pick + 1]; ++k) {
@@ -332,18 +375,33 @@ struct ND {
             bool touches = false;
             for (int64_t e = g.ptr[v]; e < g.ptr[v + 1] && !touches; ++e) {
                 int u = g.adj[e];
-                touches = tag[u] == t && lev[u] == pick + 1;
+                touches = mk.get(u) == t && lev[u] == pick + 1;
             }
             (touches ? sep : part1).push_back(v);
         }
         clear_lev();
         if ((double)sep.size() > 0.4 * S || part1.empty() || part2.empty()) {
-            amd_subset(g, nodes, local, out);
+            amd_subset(g, mk, t, nodes, out);
             return;
         }
-        run(std::move(part1));
-        run(std::move(part2));
-        amd_subset(g, sep, local, out);
+        // the separator's nodes keep tag t while the parts are dissected (the parts take
+        // new tags), so that the separator is ordered by AMD on exactly its own nodes
+        if (S >= kNdParallelMin && depth < kNdMaxDepth) {
+            std::vector<int> out1;
+            std::thread th([this, &part1, &out1, depth]() {
+                ND sub(g, mk, leaf);
+                sub.run(std::move(part1), &out1, depth + 1);
+            });
+            std::vector<int> out2;
+            run(std::move(part2), &out2, depth + 1);
+            th.join();
+            out->insert(out->end(), out1.begin(), out1.end());
+            out->insert(out->end(), out2.begin(), out2.end());
+        } else {
+            run(std::move(part1), out, depth + 1);
+            run(std::move(part2), out, depth + 1);
+        }
+        amd_subset(g, mk, t, sep, out);
     }
 };
 
@@ -352,10 +410,11 @@ struct ND {
 std::vector<int> order_nd(const Graph& g, int leaf_size) {
     std::vector<int> out;
     out.reserve(g.N);
-    ND nd(g, std::max(leaf_size, 4), &out);
+    Marks mk(g.N);
+    ND nd(g, mk, std::max(leaf_size, 4));
     std::vector<int> all(g.N);
     std::iota(all.begin(), all.end(), 0);
-    nd.run(std::move(all));
+    nd.run(std::move(all), &out, 0);
     return out;
 }
 

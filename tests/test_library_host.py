@@ -169,3 +169,12 @@ def test_amd_orders_dense_rows_last(lib):
     core = {n} | set(range(n + p + prob.l + 1, n + p + prob.m))
     assert set(perm[-len(core):].tolist()) == core
     assert info["n_levels"] <= 4
+
+
+def test_nested_dissection_is_reproducible_across_host_threads(lib):
+    # 135k KKT nodes: the top separators' parts are dissected on concurrent host threads;
+    # the order must not depend on their timing
+    pr = trajectory_socp(N=5000, seed=4)
+    perms = [q.analyze(pr, ordering=2)[1] for _ in range(3)]
+    assert all(np.array_equal(perms[0], p) for p in perms[1:])
+    assert sorted(perms[0].tolist()) == list(range(len(perms[0])))
