@@ -47,7 +47,7 @@ extern "C" {
 #define QOCO_GPU_ERR_NUMERICAL       -5  /* NaN/Inf in an iterate, or an iterate left the cone */
 #define QOCO_GPU_ERR_OOM             -6
 #define QOCO_GPU_ERR_CUDA            -7
-#define QOCO_GPU_ERR_DEVICE_TIMEOUT  -8
+#define QOCO_GPU_ERR_DEVICE_TIMEOUT  -8  /* a bounded device wait (dataflow flag, grid barrier) ran out */
 #define QOCO_GPU_ERR_NO_FACTOR       -9  /* a call needs a factorisation that does not exist */
 #define QOCO_GPU_ERR_INVALID_ARG    -10
 #define QOCO_GPU_ERR_NOT_IMPLEMENTED -11
@@ -167,7 +167,8 @@ int qoco_gpu_setup(qoco_gpu_solver** out, int n, int m, int p,
  * point until the stopping tests hold or max_iter is reached (paper §2: one
  * factorisation and two solves per iteration).  Blocks until the solve ends (one
  * 64-byte device→host read per iteration carries the stopping test).  Returns the
- * solve status (SOLVED, SOLVED_INACCURATE, MAX_ITER) or an error (NUMERICAL, CUDA). */
+ * solve status (SOLVED, SOLVED_INACCURATE, MAX_ITER) or an error (NUMERICAL, CUDA,
+ * DEVICE_TIMEOUT: one of the dataflow kernels' bounded waits gave up, the solve stops). */
 int qoco_gpu_solve(qoco_gpu_solver* solver, void* stream);
 
 /* Copies the last iterate to host buffers (any may be NULL): x[n], s[m], y[p], z[m];
