@@ -49,6 +49,7 @@ std::vector<int> order_amd(const Graph& g, double dense_factor) {
     std::vector<uint64_t> hsh(N, 0);
     for (int i = 0; i < N; ++i) {
         if (status[i] == DENSE) continue;
+        vars[i].reserve(g.ptr[i + 1] - g.ptr[i]);
         for (int64_t t = g.ptr[i]; t < g.ptr[i + 1]; ++t)
             if (status[g.adj[t]] != DENSE) vars[i].push_back(g.adj[t]);
         deg[i] = (int)vars[i].size();
@@ -110,25 +111,31 @@ std::vector<int> order_amd(const Graph& g, double dense_factor) {
         }
         // degree update, list pruning, aggressive absorption
         for (int i : Lp) {
-            tmpE.clear();
+            // both lists filtered in place (order kept), p appended to the elements
+            std::vector<int>& Ei = elems[i];
+            size_t ke = 0;
             int dext = 0;
-            for (int e : elems[i]) {
+            for (size_t x = 0; x < Ei.size(); ++x) {
+                const int e = Ei[x];
                 if (status[e] != ELEM) continue;
                 if (w[e] <= 0) {  // Le ⊆ Lp: absorb e into p
                     status[e] = DEAD;
                     std::vector<int>().swap(Le[e]);
                     continue;
                 }
-                tmpE.push_back(e);
+                Ei[ke++] = e;
                 dext += w[e];
             }
-            tmpE.push_back(p);
-            tmpV.clear();
+            Ei.resize(ke);
+            Ei.push_back(p);
+            std::vector<int>& Vi = vars[i];
+            size_t kv = 0;
             int dv = 0;
-            for (int j : vars[i])
-                if (status[j] == VAR && flag[j] != stamp) { tmpV.push_back(j); dv += nv[j]; }
-            elems[i].swap(tmpE);
-            vars[i].swap(tmpV);
+            for (size_t x = 0; x < Vi.size(); ++x) {
+                const int j = Vi[x];
+                if (status[j] == VAR && flag[j] != stamp) { Vi[kv++] = j; dv += nv[j]; }
+            }
+            Vi.resize(kv);
             long d1 = (long)dv + degLp - nv[i] + dext;
             long d2 = (long)deg[i] + degLp - nv[i];
             long d3 = (long)nleft - nv[i];
@@ -191,9 +198,15 @@ std::vector<int> order_amd(const Graph& g, double dense_factor) {
     }
 
     // expand supervariables: each eliminated principal is followed by its members
-    std::vector<std::vector<int>> members(N);
-    for (int j = 0; j < N; ++j)
-        if (merged_into[j] >= 0) members[merged_into[j]].push_back(j);
+    // (member lists in increasing index order, as singly linked lists with a tail)
+    std::vector<int> mhead(N, -1), mtail(N, -1), mnext(N, -1);
+    for (int j = 0; j < N; ++j) {
+        const int r = merged_into[j];
+        if (r < 0) continue;
+        if (mtail[r] < 0) mhead[r] = j;
+        else mnext[mtail[r]] = j;
+        mtail[r] = j;
+    }
     std::vector<int> out;
     out.reserve(N);
     std::vector<int> stack;
@@ -203,7 +216,7 @@ std::vector<int> order_amd(const Graph& g, double dense_factor) {
             int v = stack.back();
             stack.pop_back();
             out.push_back(v);
-            for (int u : members[v]) stack.push_back(u);
+            for (int u = mhead[v]; u >= 0; u = mnext[u]) stack.push_back(u);
         }
     }
     for (int i = 0; i < N; ++i)

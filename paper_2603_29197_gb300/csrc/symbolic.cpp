@@ -321,6 +321,8 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S) {
     S->amap_ptr.assign(ns + 1, 0);
     S->amap_slot.clear();
     S->amap_off.clear();
+    S->amap_slot.reserve((size_t)(K.nnz() + N) / 2);  // the lower triangle with the diagonal
+    S->amap_off.reserve((size_t)(K.nnz() + N) / 2);
     std::vector<int> pos(N, -1);
     for (int s = 0; s < ns; ++s) {
         for (int64_t t = S->row_ptr[s]; t < S->row_ptr[s + 1]; ++t) pos[S->rows[t]] = (int)(t - S->row_ptr[s]);
