@@ -4,6 +4,19 @@ Thin layer over the C ABI (include/qoco_gpu.h): it converts CSC matrices and num
 arrays to the ABI's plain pointers, passes torch CUDA tensors by data pointer and
 the current torch stream as the cudaStream_t.  Every step of the method runs in
 libqoco_gpu.so; nothing here computes.
+
+Use (a problem is any object with n, m, p, P, c, A, b, G, h, l, q; P upper CSC):
+
+    import paper_2603_29197_gb300 as q
+    S = q.Solver(prob)                      # validation, ordering, symbolic analysis, upload
+    status = S.solve()                      # 0 = solved to 1e-7
+    sol = S.solution()                      # x, s, y, z (numpy) and the info dict
+    grads = S.backward(dx=gx)               # gx = dL/dx as a CUDA float64 tensor → dP, dc, dA, db, dG, dh
+    S.update_data(c=new_c); S.solve()       # same pattern, new numbers: no new analysis
+    B = q.BatchSolver(list_of_problems)     # one interior-point loop over many instances
+    S.close(); B.close()
+
+`solve_function()` wraps solve + backward as a torch.autograd.Function.
 """
 from __future__ import annotations
 

@@ -621,6 +621,8 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         const int64_t nd = K.nnzP + K.nnzA + K.nnzG;
         std::vector<int> ca(nd, -1), cb(nd, -1);
         std::vector<int64_t> dslot, dsrc;
+        dslot.reserve(2 * nd);
+        dsrc.reserve(2 * nd);
         for (int i = 0; i < N; ++i)
             for (int64_t t = K.rowptr[i]; t < K.rowptr[i + 1]; ++t) {
                 const int64_t k = K.src[t];
