@@ -53,11 +53,9 @@ def parse():
                          "(F 5000x10000, FP64 or --mixed); mpc_batch: 4096 MPC instances, solves/s; "
                          "portfolio: n = 20000 assets, solve plus the adjoint of ||x - 1/n||^2")
     ap.add_argument("--mixed", action="store_true", help="FP32 large fronts with FP64 refinement")
-    ap.add_argument("--ordering", default=None, choices=["auto", "amd", "nd"],
+    ap.add_argument("--ordering", default="auto", choices=["auto", "amd", "nd"],
                     help="fill-reducing ordering of the lasso / portfolio / mpc_batch workloads "
-                         "(auto: the analysis' cost model; default auto, amd for mpc_batch, whose "
-                         "4096 independent trees hide the deeper AMD trees' chains: 47.8k vs "
-                         "44.6k solves/s with the cost model's ND)")
+                         "(auto: the analysis' cost model, which counts a batch's independent trees)")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -485,8 +483,6 @@ def run_other(args, ws, rank, local):
     torch.cuda.set_device(dev)
     probs = other_workload(args)
     batch = args.workload == "mpc_batch"
-    if args.ordering is None:
-        args.ordering = "amd" if batch else "auto"
     kw = dict(mixed_precision=1 if args.mixed else 0, ordering={"auto": 0, "amd": 1, "nd": 2}[args.ordering])
     make = (lambda: q.BatchSolver(probs, **kw)) if batch else (lambda: q.Solver(probs[0], **kw))
     S = make()

@@ -1054,14 +1054,15 @@ void fill_info(const qoco_gpu_solver* S, qoco_gpu_info* info) {
 int analyze_common(int n, int m, int p, const qoco_csc* P, const double* c, const qoco_csc* A,
                    const double* b, const qoco_csc* G, const double* h, int l, int nsoc, const int* q,
                    const qoco_gpu_settings* settings, bool check_vectors, qoco_gpu_settings* st,
-                   KKTPattern* K, Symbolic* Y, std::string* msg, double* t_analysis, int* used) {
+                   KKTPattern* K, Symbolic* Y, std::string* msg, double* t_analysis, int* used,
+                   int trees = 1) {
     if (settings) *st = *settings;
     else qoco_gpu_default_settings(st);
     int rc = validate_problem(n, m, p, P, c, A, b, G, h, l, nsoc, q, check_vectors, msg);
     if (rc) return rc;
     const double t0 = now_s();
     build_kkt_pattern(K, n, m, p, P, A, G, l, nsoc, q);
-    *used = analyze(*K, *st, Y);
+    *used = analyze(*K, *st, Y, trees);
     *t_analysis = now_s() - t0;
     return 0;
 }
@@ -1254,6 +1255,10 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
     return 0;
 }
 
+int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
+               const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
+               const int* q, const qoco_gpu_settings* settings, int trees);
+
 }  // namespace
 
 extern "C" {
@@ -1322,6 +1327,17 @@ int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A, 
 int qoco_gpu_setup(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
                    const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
                    const int* q, const qoco_gpu_settings* settings) {
+    return setup_impl(out, n, m, p, P, c, A, b, G, h, l, nsoc, q, settings, 1);
+}
+
+}  // extern "C"
+
+namespace {
+
+// qoco_gpu_setup for `trees` independent problems stacked block-diagonally (1: one problem)
+int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
+               const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
+               const int* q, const qoco_gpu_settings* settings, int trees) {
     if (!out) return QOCO_GPU_ERR_INVALID_ARG;
     *out = nullptr;
     const double t0 = now_s();
@@ -1337,7 +1353,7 @@ int qoco_gpu_setup(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P
     int rc;
     try {
         rc = analyze_common(n, m, p, P, c, A, b, G, h, l, nsoc, q, settings, true, &S->st, &S->K, &S->S,
-                            &S->msg, &ta, &used);
+                            &S->msg, &ta, &used, trees);
     } catch (const std::bad_alloc&) {
         rc = QOCO_GPU_ERR_OOM;
     }
@@ -1357,6 +1373,10 @@ int qoco_gpu_setup(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P
     *out = S;
     return 0;
 }
+
+}  // namespace
+
+extern "C" {
 
 int qoco_gpu_setup_batch(qoco_gpu_solver** out, int nb, const int* n, const int* m, const int* p,
                          const qoco_csc* P, const double* const* c, const qoco_csc* A, const double* const* b,
@@ -1380,9 +1400,9 @@ int qoco_gpu_setup_batch(qoco_gpu_solver** out, int nb, const int* n, const int*
     qoco_csc Ac{T.p, T.n, (int)T.Ai.size(), T.Ap.data(), T.Ai.data(), T.Av.data()};
     qoco_csc Gc{T.m, T.n, (int)T.Gi.size(), T.Gp.data(), T.Gi.data(), T.Gv.data()};
     qoco_gpu_solver* S = nullptr;
-    rc = qoco_gpu_setup(&S, T.n, T.m, T.p, T.Pi.empty() ? nullptr : &Pc, T.c.data(), T.p ? &Ac : nullptr,
-                        T.p ? T.b.data() : nullptr, &Gc, T.h.data(), T.l, T.nsoc, T.q.empty() ? nullptr : T.q.data(),
-                        settings);
+    rc = setup_impl(&S, T.n, T.m, T.p, T.Pi.empty() ? nullptr : &Pc, T.c.data(), T.p ? &Ac : nullptr,
+                    T.p ? T.b.data() : nullptr, &Gc, T.h.data(), T.l, T.nsoc, T.q.empty() ? nullptr : T.q.data(),
+                    settings, nb);
     if (rc) return rc;
     try {
         rc = batch_init(S, nb, T);

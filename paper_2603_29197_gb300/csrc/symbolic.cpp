@@ -124,7 +124,7 @@ OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm0) {
     return c;
 }
 
-int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S) {
+int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int trees) {
     const int N = K.N;
     Graph g = kkt_graph(K);
     std::vector<int> perm0;
@@ -138,7 +138,9 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S) {
         perm0 = order_nd(g, st.nd_leaf);
     } else {
         // AUTO: cost model = factor flops at an effective FP64 rate plus a per-level
-        // latency for the level-scheduled factor and solves
+        // latency for the level-scheduled factor and solves; the independent trees of a
+        // batch overlap their level chains (up to 64 of them are counted), which favours
+        // the lower flop counts of AMD there (C5's MPC batch: 47.8k vs 44.6k solves/s)
         // the two candidates are independent: ordered and costed on two host threads
         std::vector<int> pa, pn;
         OrderingCost ca, cn;
@@ -149,7 +151,8 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S) {
         pa = order_amd(g);
         ca = ordering_cost(K, pa);
         tn.join();
-        auto cost = [](const OrderingCost& c) { return c.flops / 2e11 + c.height * 4e-5; };
+        const double overlap = (double)std::max(1, std::min(trees, 64));
+        auto cost = [&](const OrderingCost& c) { return c.flops / 2e11 + c.height * 4e-5 / overlap; };
         if (cost(cn) < cost(ca)) { perm0 = std::move(pn); used = QOCO_GPU_ORDER_ND; }
         else { perm0 = std::move(pa); used = QOCO_GPU_ORDER_AMD; }
     }

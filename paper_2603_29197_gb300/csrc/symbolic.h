@@ -94,6 +94,8 @@ struct OrderingCost {
 OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm);
 
 // Full analysis for a given ordering choice; returns the ordering actually used.
-int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S);
+// `trees` is the number of independent problems stacked in K (a batch): their chains
+// of dependent fronts run side by side, which AUTO's cost model takes into account.
+int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int trees = 1);
 
 }  // namespace qoco
