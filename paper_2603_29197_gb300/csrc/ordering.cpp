@@ -317,6 +317,38 @@ struct ND {
         amd_subset(g, mk, t, nodes, out);
     }
 
+    // Independent components (a batch's instances) in their order; large sets of them
+    // are split into contiguous ranges of about equal node counts, one host thread per
+    // range, and the ranges' orders are concatenated in component order.
+    void run_components(std::vector<std::vector<int>>& comps, std::vector<int>* out, int depth) {
+        int64_t total = 0;
+        for (const auto& c : comps) total += (int64_t)c.size();
+        const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        const int nth = (int)std::min<int64_t>(hw, (int64_t)comps.size());
+        if (depth >= kNdMaxDepth || total < kNdParallelMin || nth < 2) {
+            for (auto& c : comps) run(std::move(c), out, depth);
+            return;
+        }
+        std::vector<size_t> cut(1, 0);
+        int64_t acc = 0;
+        for (size_t k = 0; k < comps.size(); ++k) {
+            acc += (int64_t)comps[k].size();
+            if ((int)cut.size() < nth && acc * nth >= total * (int64_t)cut.size()) cut.push_back(k + 1);
+        }
+        if (cut.back() != comps.size()) cut.push_back(comps.size());
+        const int nr = (int)cut.size() - 1;
+        std::vector<std::vector<int>> outs(nr);
+        std::vector<std::thread> ths;
+        for (int r = 1; r < nr; ++r)
+            ths.emplace_back([this, &comps, &outs, &cut, r]() {
+                ND sub(g, mk, leaf);
+                for (size_t k = cut[r]; k < cut[r + 1]; ++k) sub.run(std::move(comps[k]), &outs[r], kNdMaxDepth);
+            });
+        for (size_t k = cut[0]; k < cut[1]; ++k) run(std::move(comps[k]), &outs[0], kNdMaxDepth);
+        for (auto& t : ths) t.join();
+        for (const auto& o : outs) out->insert(out->end(), o.begin(), o.end());
+    }
+
     void run(std::vector<int> nodes, std::vector<int>* out, int depth) {
         std::vector<int>& lev = mk.lev;
         if ((int)nodes.size() <= leaf) { leaf_amd(nodes, out); return; }
@@ -338,7 +370,7 @@ struct ND {
                 seen.insert(seen.end(), q.begin(), q.end());
             }
             for (int v : seen) lev[v] = -1;
-            for (auto& c : comps) run(std::move(c), out, depth);
+            run_components(comps, out, depth);
             return;
         }
         // pseudo-peripheral root: BFS from the least-degree node of the last level while

@@ -11,7 +11,7 @@ import scipy.sparse as sp
 
 import paper_2603_29197_gb300 as q
 from paper_2603_29197_gb300 import _lib
-from workloads import Problem, dense_qp, portfolio_socp, trajectory_socp
+from workloads import Problem, dense_qp, mpc_batch, portfolio_socp, trajectory_socp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -175,6 +175,26 @@ def test_nested_dissection_is_reproducible_across_host_threads(lib):
     # 135k KKT nodes: the top separators' parts are dissected on concurrent host threads;
     # the order must not depend on their timing
     pr = trajectory_socp(N=5000, seed=4)
+    perms = [q.analyze(pr, ordering=2)[1] for _ in range(3)]
+    assert all(np.array_equal(perms[0], p) for p in perms[1:])
+    assert sorted(perms[0].tolist()) == list(range(len(perms[0])))
+
+
+def _stack(probs):
+    # block-diagonal stack with every orthant row first, then every SOC row
+    P = sp.block_diag([sp.csc_matrix(p.P) for p in probs], format="csc")
+    A = sp.block_diag([sp.csc_matrix(p.A) for p in probs], format="csc")
+    G = sp.vstack([sp.block_diag([sp.csc_matrix(p.G)[:p.l] for p in probs]),
+                   sp.block_diag([sp.csc_matrix(p.G)[p.l:] for p in probs])]).tocsc()
+    return Problem(n=P.shape[0], m=G.shape[0], p=A.shape[0], P=P, c=np.zeros(P.shape[0]), A=A,
+                   b=np.zeros(A.shape[0]), G=G, h=np.zeros(G.shape[0]), l=sum(p.l for p in probs),
+                   q=sum([list(p.q) for p in probs], []))
+
+
+def test_nested_dissection_of_many_components_is_reproducible(lib):
+    # 96 independent MPC instances (~70k KKT nodes): the components are dissected on
+    # concurrent host threads in contiguous ranges; the order is the component order
+    pr = _stack(mpc_batch(count=96, tmin=10, tmax=60, seed=5))
     perms = [q.analyze(pr, ordering=2)[1] for _ in range(3)]
     assert all(np.array_equal(perms[0], p) for p in perms[1:])
     assert sorted(perms[0].tolist()) == list(range(len(perms[0])))
