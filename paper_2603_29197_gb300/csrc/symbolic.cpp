@@ -103,84 +103,87 @@ int sn_height_fundamental(const std::vector<int>& parent, const std::vector<int>
 
 }  // namespace
 
-OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm0) {
-    Graph g = kkt_graph(K);
-    const int N = K.N;
-    std::vector<int> iperm(N);
-    for (int j = 0; j < N; ++j) iperm[perm0[j]] = j;
-    std::vector<int> parent = etree(g, perm0, iperm);
-    std::vector<int> post = postorder(parent);
-    std::vector<int> perm(N), ip2(N);
-    for (int k = 0; k < N; ++k) perm[k] = perm0[post[k]];
-    for (int j = 0; j < N; ++j) ip2[perm[j]] = j;
-    std::vector<int> par2 = etree(g, perm, ip2);
-    std::vector<int> cc = col_counts(g, perm, ip2, par2);
-    OrderingCost c;
-    for (int j = 0; j < N; ++j) {
-        c.l_nnz += cc[j];
-        c.flops += (double)cc[j] * cc[j] + 2.0 * cc[j];
+namespace {
+
+// An ordering made ready for the supernodal pass: its elimination tree postordered
+// (perm, iperm), that tree (parent) and L's column counts (cc), with the cost figures.
+struct Evaluated {
+    std::vector<int> perm, iperm, parent, cc;
+    OrderingCost cost;
+};
+
+void evaluate(const Graph& g, const std::vector<int>& perm0, bool keep_identity, Evaluated* E) {
+    const int N = g.N;
+    std::vector<int> ip0(N);
+    for (int j = 0; j < N; ++j) ip0[perm0[j]] = j;
+    std::vector<int> post;
+    if (keep_identity) {
+        // NATURAL keeps the identity: any order in which every column precedes its etree
+        // parent is valid for the supernodal pass
+        post.resize(N);
+        std::iota(post.begin(), post.end(), 0);
+    } else {
+        post = postorder(etree(g, perm0, ip0));
     }
-    c.height = sn_height_fundamental(par2, cc);
-    return c;
+    E->perm.resize(N);
+    E->iperm.resize(N);
+    for (int k = 0; k < N; ++k) E->perm[k] = perm0[post[k]];
+    for (int j = 0; j < N; ++j) E->iperm[E->perm[j]] = j;
+    E->parent = etree(g, E->perm, E->iperm);
+    E->cc = col_counts(g, E->perm, E->iperm, E->parent);
+    E->cost = OrderingCost();
+    for (int j = 0; j < N; ++j) {
+        E->cost.l_nnz += E->cc[j];
+        E->cost.flops += (double)E->cc[j] * E->cc[j] + 2.0 * E->cc[j];
+    }
+    E->cost.height = sn_height_fundamental(E->parent, E->cc);
+}
+
+}  // namespace
+
+OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm0) {
+    Evaluated E;
+    evaluate(kkt_graph(K), perm0, false, &E);
+    return E.cost;
 }
 
 int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int trees) {
     const int N = K.N;
     Graph g = kkt_graph(K);
-    std::vector<int> perm0;
     int used = st.ordering;
+    Evaluated E;
     if (st.ordering == QOCO_GPU_ORDER_NATURAL) {
-        perm0.resize(N);
+        std::vector<int> perm0(N);
         std::iota(perm0.begin(), perm0.end(), 0);
+        evaluate(g, perm0, true, &E);
     } else if (st.ordering == QOCO_GPU_ORDER_AMD) {
-        perm0 = order_amd(g);
+        evaluate(g, order_amd(g), false, &E);
     } else if (st.ordering == QOCO_GPU_ORDER_ND) {
-        perm0 = order_nd(g, st.nd_leaf);
+        evaluate(g, order_nd(g, st.nd_leaf), false, &E);
     } else {
         // AUTO: cost model = factor flops at an effective FP64 rate plus a per-level
         // latency for the level-scheduled factor and solves; the independent trees of a
         // batch overlap their level chains (up to 64 of them are counted), which favours
         // the lower flop counts of AMD there (C5's MPC batch: 47.8k vs 44.6k solves/s)
-        // the two candidates are independent: ordered and costed on two host threads
-        std::vector<int> pa, pn;
-        OrderingCost ca, cn;
-        std::thread tn([&]() {
-            pn = order_nd(g, st.nd_leaf);
-            cn = ordering_cost(K, pn);
-        });
-        pa = order_amd(g);
-        ca = ordering_cost(K, pa);
+        // the two candidates are independent: ordered and evaluated on two host threads
+        Evaluated En;
+        std::thread tn([&]() { evaluate(g, order_nd(g, st.nd_leaf), false, &En); });
+        evaluate(g, order_amd(g), false, &E);
         tn.join();
         const double overlap = (double)std::max(1, std::min(trees, 64));
         auto cost = [&](const OrderingCost& c) { return c.flops / 2e11 + c.height * 4e-5 / overlap; };
-        if (cost(cn) < cost(ca)) { perm0 = std::move(pn); used = QOCO_GPU_ORDER_ND; }
-        else { perm0 = std::move(pa); used = QOCO_GPU_ORDER_AMD; }
+        if (cost(En.cost) < cost(E.cost)) { E = std::move(En); used = QOCO_GPU_ORDER_ND; }
+        else used = QOCO_GPU_ORDER_AMD;
     }
 
-    // 1. etree + postorder
-    std::vector<int> iperm(N);
-    for (int j = 0; j < N; ++j) iperm[perm0[j]] = j;
-    std::vector<int> parent0 = etree(g, perm0, iperm);
-    // postorder (not for NATURAL, which keeps the identity: any order in which every
-    // column precedes its etree parent is valid for the supernodal pass below)
-    std::vector<int> post;
-    if (st.ordering == QOCO_GPU_ORDER_NATURAL) {
-        post.resize(N);
-        std::iota(post.begin(), post.end(), 0);
-    } else {
-        post = postorder(parent0);
-    }
+    // 1–2. postordered elimination tree and column counts of the chosen ordering
     S->N = N;
-    S->perm.resize(N);
-    S->iperm.resize(N);
-    for (int k = 0; k < N; ++k) S->perm[k] = perm0[post[k]];
-    for (int j = 0; j < N; ++j) S->iperm[S->perm[j]] = j;
+    S->perm = std::move(E.perm);
+    S->iperm = std::move(E.iperm);
     const std::vector<int>& perm = S->perm;
     const std::vector<int>& ip = S->iperm;
-    std::vector<int> parent = etree(g, perm, ip);
-
-    // 2. counts
-    std::vector<int> cc = col_counts(g, perm, ip, parent);
+    std::vector<int> parent = std::move(E.parent);
+    std::vector<int> cc = std::move(E.cc);
     S->l_nnz = 0;
     S->flops = 0.0;
     for (int j = 0; j < N; ++j) {
