@@ -191,6 +191,10 @@ int qoco_gpu_solution_device(const qoco_gpu_solver* solver, const double** x,
  * diagonal, its supernodal tree a forest).  The paper solves one problem at a time;
  * this is one of the forms grown beyond it.
  *
+ * With ordering AUTO the cost model counts the batch's independent trees (their
+ * dependent chains of fronts overlap), and the factor/solve schedule is picked by
+ * timing at the first factorisation unless settings->batch_schedule fixes it.
+ *
  * Arrays of length `batch` (host): n, m, p, l, nsoc; P, A, G are arrays of `batch` CSC
  * matrices (P[i] with colptr == NULL means P_i = 0; A[i] is ignored when p[i] = 0);
  * c, b, h, q are arrays of `batch` host pointers (b[i] may be NULL when p[i] = 0).
