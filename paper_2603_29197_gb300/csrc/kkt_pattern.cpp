@@ -192,10 +192,12 @@ void build_kkt_pattern(KKTPattern* K, int n, int m, int p, const qoco_csc* P,
             for (int b2 = 0; b2 < q[k]; ++b2)
                 put(n + p + K->cone_off[k] + a, n + p + K->cone_off[k] + b2, -1);
 
-    // sort each row by column (carry the source along)
+    // sort each row by column (carry the source along); most rows arrive sorted (the
+    // data's columns are visited in order), and those are left as they are
     std::vector<std::pair<int, int64_t>> tmp;
     for (int i = 0; i < N; ++i) {
         int64_t a = K->rowptr[i], b = K->rowptr[i + 1];
+        if (std::is_sorted(K->colidx.begin() + a, K->colidx.begin() + b)) continue;
         tmp.resize(b - a);
         for (int64_t t = a; t < b; ++t) tmp[t - a] = {K->colidx[t], K->src[t]};
         std::sort(tmp.begin(), tmp.end());
