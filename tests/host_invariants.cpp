@@ -1,6 +1,8 @@
 // Structural checks of the host symbolic analysis (ordering, supernodes, row structures,
-// relative indices, assembly map) that the device factorisation relies on.  Built and run
-// by tests/test_host_invariants.py on the CPU.
+// relative indices, assembly map) and of the launch plan (every front in exactly one
+// factor list and one solve list; dataflow items in topological order, the condition
+// under which their bounded waits always end) that the device kernels rely on.  Built and
+// run by tests/test_host_invariants.py on the CPU.
 //
 // usage: host_invariants <problem dir> <ordering> <trees> [plant_rel | plant_map]
 // The problem directory holds dims.bin (n, m, p, l, nsoc, q…) and for P (upper), A, G:
@@ -12,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "plan.h"
 #include "qoco_gpu.h"
 #include "symbolic.h"
 
@@ -189,10 +192,71 @@ int main(int argc, char** argv) {
         maxlev = std::max(maxlev, S.level[s]);
     }
     check(S.n_levels == maxlev + 1, "level count");
+    // launch plans, with and without subtree tasks
+    int df_solve_checked = 0, df_factor_checked = 0;
+    for (int tasks : {0, 64}) {
+        PlanHost P;
+        build_plan(S, tasks > 0, tasks, &P);
+        std::vector<int> fcount(ns, 0), scount(ns, 0);
+        for (size_t t = 0; t + 1 < P.task.size(); t += 2)
+            for (int x = P.task[t]; x <= P.task[t + 1]; ++x) { fcount[x]++; scount[x]++; }
+        for (const std::vector<int>* L : {&P.thread, &P.warp, &P.small, &P.large, &P.big})
+            for (int x : *L) fcount[x]++;
+        for (const std::vector<int>* L : {&P.sthread, &P.swarp, &P.cta, &P.big})
+            for (int x : *L) scount[x]++;
+        for (int x = 0; x < ns; ++x) {
+            check(fcount[x] == 1, "front in one factor list", x, fcount[x]);
+            check(scount[x] == 1, "front in one solve list", x, scount[x]);
+        }
+        for (size_t lv = 0; lv < P.levels.size(); ++lv) {
+            const LevelPlan& L = P.levels[lv];
+            for (int t = 0; t < L.n_sthread; ++t) check(S.level[P.sthread[L.off_sthread + t]] == (int)lv, "level list", (long)lv);
+            for (int t = 0; t < L.n_swarp; ++t) check(S.level[P.swarp[L.off_swarp + t]] == (int)lv, "level list", (long)lv);
+        }
+        // dataflow solve items: children strictly before parents
+        if (P.task.empty() && P.cta.empty() && P.big.empty()) {
+            ++df_solve_checked;
+            std::vector<int> item_of(ns, -1);
+            for (size_t it = 0; it < P.items.size(); ++it) {
+                const int item = P.items[it];
+                if (item >= 0) { check(item_of[item] < 0, "solve item once", item); item_of[item] = (int)it; continue; }
+                const int b = -item - 1;
+                for (int t = P.tb_ptr[b]; t < P.tb_ptr[b + 1]; ++t) {
+                    check(item_of[P.sthread[t]] < 0, "solve item once", P.sthread[t]);
+                    item_of[P.sthread[t]] = (int)it;
+                }
+            }
+            for (int x = 0; x < ns; ++x) {
+                check(item_of[x] >= 0, "solve item covers the front", x);
+                if (S.sn_parent[x] >= 0) check(item_of[x] < item_of[S.sn_parent[x]], "solve items topological", x);
+            }
+        }
+        // dataflow factorisation items
+        if (P.task.empty() && P.large.empty() && P.big.empty()) {
+            ++df_factor_checked;
+            std::vector<int> item_of(ns, -1);
+            for (size_t it = 0; it < P.fitems.size(); ++it) {
+                const int kind = P.fitems[it] & 3, idx = P.fitems[it] >> 2;
+                std::vector<int> members;
+                if (kind == 0) for (int t = P.ftb_ptr[idx]; t < P.ftb_ptr[idx + 1]; ++t) members.push_back(P.thread[t]);
+                else if (kind == 1) for (int t = P.fwg_ptr[idx]; t < P.fwg_ptr[idx + 1]; ++t) members.push_back(P.warp[t]);
+                else members.push_back(idx);
+                for (int x : members) {
+                    check(item_of[x] < 0, "factor item once", x);
+                    item_of[x] = (int)it;
+                }
+            }
+            for (int x = 0; x < ns; ++x) {
+                check(item_of[x] >= 0, "factor item covers the front", x);
+                if (S.sn_parent[x] >= 0) check(item_of[x] < item_of[S.sn_parent[x]], "factor items topological", x);
+            }
+        }
+    }
     if (fails) {
         std::printf("%d failures\n", fails);
         return 1;
     }
-    std::printf("ok N=%d supernodes=%d levels=%d\n", N, ns, S.n_levels);
+    std::printf("ok N=%d supernodes=%d levels=%d dataflow plans checked: solve %d factor %d\n", N, ns,
+                S.n_levels, df_solve_checked, df_factor_checked);
     return 0;
 }

@@ -4,8 +4,11 @@ sorted and symmetric with every diagonal; the ordering is a permutation; superno
 contiguous and postordered; each front lists its own columns first and its update rows
 sorted below them; every lower entry of the permuted matrix falls inside its column's
 front and is assembled exactly once at its front position; children's update rows are
-rows of the parent at their relative indices; levels grow towards the roots.  These are
-the facts the device factorisation and solves index by."""
+rows of the parent at their relative indices; levels grow towards the roots; the launch
+plan puts every front in exactly one factor list and one solve list, and its dataflow
+items list children strictly before parents (the condition under which the dataflow
+kernels' bounded waits always end).  These are the facts the device factorisation and
+solves index by."""
 import os
 import shutil
 import subprocess
@@ -26,7 +29,7 @@ def checker(tmp_path_factory):
         pytest.skip("no host C++ compiler")
     out = str(tmp_path_factory.mktemp("hostinv") / "host_invariants")
     srcs = [os.path.join(ROOT, "tests", "host_invariants.cpp")] + [
-        os.path.join(CSRC, f) for f in ("ordering.cpp", "symbolic.cpp", "kkt_pattern.cpp")]
+        os.path.join(CSRC, f) for f in ("ordering.cpp", "symbolic.cpp", "kkt_pattern.cpp", "plan.cpp")]
     cmd = ["g++", "-O1", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), *srcs, "-o", out,
            "-lpthread"]
     subprocess.run(cmd, check=True, capture_output=True)
@@ -79,6 +82,8 @@ def test_symbolic_analysis_invariants(checker, tmp_path, name):
         r = subprocess.run([checker, d, str(order), str(trees)], capture_output=True, text=True, timeout=300)
         assert r.returncode == 0, (order, r.stdout[-2000:], r.stderr[-2000:])
         assert r.stdout.startswith("ok"), r.stdout
+        if name == "mpc_stack":  # all fronts fit a warp: both dataflow plans were checked
+            assert "solve 1 factor 1" in r.stdout, r.stdout
 
 
 @pytest.mark.parametrize("plant", ["plant_rel", "plant_map"])
