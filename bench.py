@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="mpc_batch: skip timing the plain solver on a sample of the instances")
     ap.add_argument("--stages", type=int, default=20000, help="trajectory stages (default: the benchmark size)")
     ap.add_argument("--workload", default="trajectory", choices=["trajectory", "lasso", "mpc_batch", "portfolio"],
                     help="trajectory (default, the headline line); lasso: the lasso QP scaled by 1/10 "
@@ -529,6 +531,29 @@ def run_other(args, ws, rank, local):
         adj = {"backward_ms": statistics.mean(bts), "refine_steps": bi["refine_steps"],
                "backward_error": bi["backward_error"], "refactored": bi["refactored"],
                "solve_plus_backward_ms": ms + statistics.mean(bts)}
+    plain = None
+    if batch and not args.no_plain:
+        # the plain FP64 form on the same instances, one solver per instance, one at a
+        # time: a seeded sample of 16 instances (device-timed solves, set-up excluded)
+        idx = sorted(np.random.default_rng(0).choice(len(probs), size=16, replace=False).tolist())
+        pts = []
+        for i in idx:
+            one = q.Solver(probs[i])
+            if one.solve(stream.cuda_stream) != 0:
+                raise RuntimeError(f"plain solve of instance {i} failed")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st1 = one.solve(stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            if st1 != 0:
+                raise RuntimeError(f"plain solve of instance {i} failed")
+            pts.append(e0.elapsed_time(e1))
+            one.close()
+        per_s = 1e3 / statistics.mean(pts)
+        plain = {"value": per_s, "unit": "solves/s", "ms_per_solve": statistics.mean(pts),
+                 "sample": "16 seeded instances, each on its own solver, one after the other",
+                 "batched_over_plain": (len(probs) / (ms * 1e-3)) / per_s}
     fcalls = max(1, prof["factor"]["calls"])
     f_ms = prof["factor"]["ms"] / fcalls
     gflops = info["factor_flops"] / (f_ms * 1e-3) / 1e9
@@ -596,6 +621,8 @@ def run_other(args, ws, rank, local):
         out["error_vs_oracle"] = golden_error(gname, S.solution(), info["pobj"])
     if adj:
         out["adjoint"] = adj
+    if plain:
+        out["plain_fp64_one_at_a_time"] = plain
     if rank == 0:
         print(json.dumps(out), flush=True)
     S.close()
