@@ -100,7 +100,8 @@ struct FactorPlan {
     // child order: segment ea_ptr[big_ea_off[idx] + p .. + p + 1) of ea_child / ea_pos
     std::vector<int64_t> big_ea_off;
     // inverses of the 64×64 unit-lower diagonal blocks of each large front (row-major,
-    // block b of front idx at big_linv + big_linv_off[idx] + b·64·64), for the solves
+    // block b of front idx at big_linv + big_linv_off[idx] + b·64·64), written during the
+    // factorisation (used there for the panel's rows below, and by the solves)
     std::vector<int64_t> big_linv_off;
     double* big_linv = nullptr;
     int* big_err = nullptr;        // set when a tensor-core tile's completion wait ran out
