@@ -51,9 +51,9 @@ __global__ void k_big_assemble(int s, FactorView a, const double* __restrict__ k
     const int64_t e0 = a.amap_ptr[s], e1 = a.amap_ptr[s + 1];
     for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int off = a.amap_off[e];
+        const int64_t off = a.amap_off[e];
         double v = kval[a.amap_slot[e]];
-        const int col = off / f, row = off - col * f;
+        const int col = (int)(off / f), row = (int)(off - (int64_t)col * f);
         if (row == col) v += a.dsign[first + col] > 0 ? a.eps : -a.eps;
         F[off] = (T)v;
     }
@@ -487,7 +487,7 @@ __global__ void k_leaf_members(const int* __restrict__ members, int nmem, Factor
     for (int e = lane; e < f * c; e += 32) Fm[e] = 0.0;
     __syncwarp();
     for (int64_t e = a.amap_ptr[s] + lane; e < a.amap_ptr[s + 1]; e += 32) {
-        const int off = a.amap_off[e];
+        const int off = (int)a.amap_off[e];  // a member front: f·c < 2^31
         double v = kval[a.amap_slot[e]];
         const int col = off / f, row = off - col * f;
         if (row == col) v += a.dsign[first + col] > 0 ? a.eps : -a.eps;

@@ -218,7 +218,7 @@ __device__ __forceinline__ bool thread_factor_front(int s, const FactorView& a, 
     for (int j = 0; j < f; ++j)
         for (int i = j; i < f; ++i) F[j * LD + i] = 0.0;
     for (int64_t e = a.amap_ptr[s]; e < a.amap_ptr[s + 1]; ++e) {
-        const int off = a.amap_off[e];
+        const int off = (int)a.amap_off[e];
         const int col = off / f, row = off - col * f;
         double v = kval[a.amap_slot[e]];
         if (row == col) v += a.dsign[first + col] > 0 ? a.eps : -a.eps;
@@ -338,7 +338,7 @@ __device__ __forceinline__ bool cta_factor_front(int s, const FactorView& a, con
     for (int64_t i = tid; i < ff; i += nt) F[i] = 0.0;
     __syncthreads();
     for (int64_t e = a.amap_ptr[s] + tid; e < a.amap_ptr[s + 1]; e += nt) {
-        const int off = a.amap_off[e];
+        const int off = (int)a.amap_off[e];
         double v = kval[a.amap_slot[e]];
         const int col = off / f, row = off - col * f;
         if (row == col) v += a.dsign[first + col] > 0 ? a.eps : -a.eps;
@@ -481,7 +481,7 @@ __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, co
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int64_t eu = e + u * 32;
-                off[u] = eu < e1 ? a.amap_off[eu] : -1;
+                off[u] = eu < e1 ? (int)a.amap_off[eu] : -1;
                 v[u] = eu < e1 ? kval[a.amap_slot[eu]] : 0.0;
             }
 #pragma unroll

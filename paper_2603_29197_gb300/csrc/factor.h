@@ -33,7 +33,7 @@ struct FactorView {
     const ChildInfo* cinfo = nullptr;  // parallel to child
     const int64_t* amap_ptr = nullptr;
     const int64_t* amap_slot = nullptr;
-    const int* amap_off = nullptr;
+    const int64_t* amap_off = nullptr;  // col·f + row (64-bit: large fronts exceed 2^31 entries)
     const signed char* dsign = nullptr;
     const int* perm = nullptr;       // new → original
     const int* parent = nullptr;     // supernodal tree parent (−1 for roots)

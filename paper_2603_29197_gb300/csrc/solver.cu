@@ -415,7 +415,7 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     }
     if ((rc = dcopy(S, &pl, Y.amap_ptr))) return rc; f.amap_ptr = pl;
     if ((rc = dcopy(S, &pl, Y.amap_slot))) return rc; f.amap_slot = pl;
-    if ((rc = dcopy(S, &pi, Y.amap_off))) return rc; f.amap_off = pi;
+    if ((rc = dcopy(S, &pl, Y.amap_off))) return rc; f.amap_off = pl;
     signed char* pc;
     if ((rc = dcopy(S, &pc, Y.dsign))) return rc; f.dsign = pc;
     if ((rc = dcopy(S, &pi, Y.perm))) return rc; f.perm = pi;
@@ -438,7 +438,8 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         for (int s : ph.big) is_big[s] = 1;
         for (int s = 0; s < Y.ns; ++s)
             (is_big[s] ? max_big : max_small) = std::max(is_big[s] ? max_big : max_small, Y.sn_nrow[s]);
-        if (max_small > kMaxSolveFront || max_small > kMaxFactorFront || max_big > 46340) {
+        // large fronts index rows and columns with int and their entries with int64_t
+        if (max_small > kMaxSolveFront || max_small > kMaxFactorFront || max_big > (1 << 24)) {
             S->msg = "a supernode front exceeds the factor/solve kernels' limits";
             return QOCO_GPU_ERR_NOT_IMPLEMENTED;
         }

@@ -8,7 +8,8 @@
 //   3. fundamental supernodes (j+1 continues j's supernode when it is j's parent,
 //      has j as only child and count(j) = count(j+1) + 1), then relaxed
 //      amalgamation of a supernode with its last child when few explicit zeros
-//      are added;
+//      are added, then absorption of thin children with large updates into their
+//      (large) parents, with the columns re-emitted in a topological order;
 //   4. row structures R_s (own columns, then the rows below), the supernodal tree,
 //      levels (height above the leaves), front/update offsets, the extend-add
 //      relative indices and the map from KKT value slots to front positions.
@@ -116,6 +117,10 @@ void evaluate(const Graph& g, const std::vector<int>& perm0, bool keep_identity,
     const int N = g.N;
     std::vector<int> ip0(N);
     for (int j = 0; j < N; ++j) ip0[perm0[j]] = j;
+    // tree and counts of perm0; a postorder of that tree is a topological order of it, so
+    // the permuted matrix has the same tree and counts, relabelled (Liu 1990)
+    std::vector<int> parent0 = etree(g, perm0, ip0);
+    std::vector<int> cc0 = col_counts(g, perm0, ip0, parent0);
     std::vector<int> post;
     if (keep_identity) {
         // NATURAL keeps the identity: any order in which every column precedes its etree
@@ -123,14 +128,21 @@ void evaluate(const Graph& g, const std::vector<int>& perm0, bool keep_identity,
         post.resize(N);
         std::iota(post.begin(), post.end(), 0);
     } else {
-        post = postorder(etree(g, perm0, ip0));
+        post = postorder(parent0);
     }
+    std::vector<int> ipost(N);
+    for (int k = 0; k < N; ++k) ipost[post[k]] = k;
     E->perm.resize(N);
     E->iperm.resize(N);
-    for (int k = 0; k < N; ++k) E->perm[k] = perm0[post[k]];
+    E->parent.resize(N);
+    E->cc.resize(N);
+    for (int k = 0; k < N; ++k) {
+        E->perm[k] = perm0[post[k]];
+        const int p0 = parent0[post[k]];
+        E->parent[k] = p0 >= 0 ? ipost[p0] : -1;
+        E->cc[k] = cc0[post[k]];
+    }
     for (int j = 0; j < N; ++j) E->iperm[E->perm[j]] = j;
-    E->parent = etree(g, E->perm, E->iperm);
-    E->cc = col_counts(g, E->perm, E->iperm, E->parent);
     E->cost = OrderingCost();
     for (int j = 0; j < N; ++j) {
         E->cost.l_nnz += E->cc[j];
@@ -245,6 +257,104 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int t
         }
         stack.push_back(cur);
     }
+    // 3b. absorption into large fronts.  In a dense part of the factor (the lasso's
+    // Schur complement on the equality rows) a large front often has children that are
+    // thin (a few columns) but whose update blocks are themselves large dense matrices:
+    // only the last child is adjacent to the parent, so the pass above leaves the others
+    // as separate fronts, each storing an f×f block (mostly its update) and extend-adding
+    // it.  A child with at most kAbsorbCols columns and an update of at least
+    // kAbsorbRows rows is merged into its parent, as long as the columns merged into a
+    // front stay within max(kAbsorbCols, its own columns / 20) (each merged column costs
+    // a rank-1 update of the whole merged front).  The merged fronts' columns are then
+    // made contiguous by re-emitting the columns in a topological order of the merged
+    // tree (external children first, then every member's columns, children before
+    // parents).
+    {
+        constexpr int kAbsorbRows = 1024, kAbsorbCols = 256;
+        const int nsn = (int)stack.size();
+        std::vector<int> scol(N);
+        for (int t = 0; t < nsn; ++t)
+            for (int j = stack[t].first; j < stack[t].first + stack[t].ncol; ++j) scol[j] = t;
+        std::vector<int> sp(nsn, -1);
+        for (int t = 0; t < nsn; ++t) {
+            const int last = stack[t].first + stack[t].ncol - 1;
+            if (parent[last] >= 0) sp[t] = scol[parent[last]];
+        }
+        std::vector<std::vector<int>> kids(nsn);
+        for (int t = 0; t < nsn; ++t)
+            if (sp[t] >= 0 && stack[t].f - stack[t].ncol >= kAbsorbRows) kids[sp[t]].push_back(t);
+        std::vector<int> into(nsn, -1);
+        // group totals (members' columns, front order, true entries), built bottom-up
+        std::vector<int> gc(nsn), gf(nsn);
+        std::vector<double> gt(nsn);
+        for (int t = 0; t < nsn; ++t) { gc[t] = stack[t].ncol; gf[t] = stack[t].f; gt[t] = stack[t].truenz; }
+        bool any = false;
+        for (int t = 0; t < nsn; ++t) {
+            if (kids[t].empty()) continue;
+            std::vector<int>& k = kids[t];
+            std::stable_sort(k.begin(), k.end(), [&](int a, int b) { return gf[a] - gc[a] > gf[b] - gc[b]; });
+            const int cap = std::max(kAbsorbCols, stack[t].ncol / 20);
+            int took = 0;
+            for (int c : k) {
+                if (gc[c] > kAbsorbCols || took + gc[c] > cap) continue;
+                into[c] = t;
+                took += gc[c];
+                gc[t] += gc[c];
+                gf[t] += gc[c];
+                gt[t] += gt[c];
+                any = true;
+            }
+        }
+        if (any) {
+            // group root of every supernode (a parent comes after its children)
+            std::vector<int> root(nsn);
+            for (int t = nsn - 1; t >= 0; --t) root[t] = into[t] >= 0 ? root[into[t]] : t;
+            std::vector<std::vector<int>> members(nsn), gkids(nsn);
+            for (int t = 0; t < nsn; ++t) {
+                members[root[t]].push_back(t);
+                if (into[t] < 0 && sp[t] >= 0) gkids[root[sp[t]]].push_back(t);
+            }
+            std::vector<int> order;  // old column indices in the new order
+            order.reserve(N);
+            std::vector<SN> merged;
+            std::vector<std::pair<int, size_t>> st;  // (group, next child)
+            for (int t = 0; t < nsn; ++t) {
+                if (into[t] >= 0 || sp[t] >= 0) continue;
+                st.push_back({t, 0});
+                while (!st.empty()) {
+                    auto& top = st.back();
+                    if (top.second < gkids[top.first].size()) {
+                        const int ch = gkids[top.first][top.second++];
+                        st.push_back({ch, 0});
+                        continue;
+                    }
+                    const int g2 = top.first;
+                    st.pop_back();
+                    SN sn2 = stack[g2];
+                    sn2.first = (int)order.size();
+                    sn2.ncol = gc[g2];
+                    sn2.f = gf[g2];
+                    sn2.truenz = gt[g2];
+                    for (int mbr : members[g2])
+                        for (int j = stack[mbr].first; j < stack[mbr].first + stack[mbr].ncol; ++j) order.push_back(j);
+                    merged.push_back(sn2);
+                }
+            }
+            std::vector<int> newpos(N);
+            for (int k = 0; k < N; ++k) newpos[order[k]] = k;
+            std::vector<int> p2(N), c2(N), pm(N);
+            for (int j = 0; j < N; ++j) {
+                p2[newpos[j]] = parent[j] >= 0 ? newpos[parent[j]] : -1;
+                c2[newpos[j]] = cc[j];
+            }
+            for (int k = 0; k < N; ++k) pm[k] = S->perm[order[k]];
+            parent.swap(p2);
+            cc.swap(c2);
+            S->perm.swap(pm);
+            for (int j = 0; j < N; ++j) S->iperm[S->perm[j]] = j;
+            stack.swap(merged);
+        }
+    }
     const int ns = (int)stack.size();
     S->ns = ns;
     S->sn_first.resize(ns + 1);
@@ -347,7 +457,7 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int t
                 int i = ip[K.colidx[t]];
                 if (i < j) continue;
                 S->amap_slot.push_back(t);
-                S->amap_off.push_back((j - first) * f + pos[i]);
+                S->amap_off.push_back((int64_t)(j - first) * f + pos[i]);
             }
         }
         S->amap_ptr[s + 1] = (int64_t)S->amap_slot.size();

@@ -76,7 +76,7 @@ struct Symbolic {
     // assembly map: KKT lower entries (permuted) of each supernode's columns
     std::vector<int64_t> amap_ptr;      // ns + 1
     std::vector<int64_t> amap_slot;     // slot in the KKT value array
-    std::vector<int> amap_off;          // column-major offset inside the front (col·f + row)
+    std::vector<int64_t> amap_off;      // column-major offset inside the front (col·f + row)
     std::vector<signed char> dsign;     // sign of each permuted column
     // statistics
     int64_t l_nnz = 0;                  // Σ c_j (below-diagonal counts)

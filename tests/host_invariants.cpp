@@ -168,7 +168,8 @@ int main(int argc, char** argv) {
         const int f = S.sn_nrow[s], c = S.sn_ncol[s], first = S.sn_first[s];
         const int64_t r0 = S.row_ptr[s];
         for (int64_t e = S.amap_ptr[s]; e < S.amap_ptr[s + 1]; ++e) {
-            const int off = S.amap_off[e], col = off / f, row = off - col * f;
+            const int64_t off = S.amap_off[e];
+            const int col = (int)(off / f), row = (int)(off - (int64_t)col * f);
             const int64_t slot = S.amap_slot[e];
             check(col >= 0 && col < c && row >= col && row < f, "map offset in the front's lower part", s, off);
             if (!(col >= 0 && col < c && row >= col && row < f)) continue;

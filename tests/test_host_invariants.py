@@ -70,6 +70,9 @@ CASES = {
     "portfolio": (lambda: portfolio_socp(n=600, k=30, seed=4), 1, (0, 1, 2, 3)),
     "lasso": (lambda: lasso_qp(rows=300, cols=600, density=0.02, seed=5), 1, (0, 1, 2)),
     "mpc_stack": (lambda: _stack(mpc_batch(count=40, tmin=10, tmax=60, seed=6)), 40, (0, 1, 2)),
+    # a dense Schur complement on the equality rows: thin children with updates of more
+    # than 1024 rows are absorbed into the root front (columns re-emitted out of postorder)
+    "lasso_absorb": (lambda: lasso_qp(rows=5000, cols=10000, density=1e-2, seed=0), 1, (1,)),
 }
 
 
@@ -92,3 +95,17 @@ def test_checker_catches_a_planted_error(checker, tmp_path, plant):
     _write(trajectory_socp(N=200, seed=7), d)
     r = subprocess.run([checker, d, "2", "1", plant], capture_output=True, text=True, timeout=300)
     assert r.returncode == 1 and "FAIL" in r.stdout, r.stdout
+
+
+def test_thin_children_with_large_updates_are_absorbed_into_the_root():
+    """The scaled lasso's Schur complement on its 5000 equality rows is dense: its root
+    front has thin children (a few columns each) whose updates span 2500–4000 of the
+    root's rows.  After the absorption pass no front but the root has more than 1024
+    rows and the front storage is the root's plus small fronts."""
+    import paper_2603_29197_gb300 as q
+    prob = lasso_qp(rows=5000, cols=10000, density=1e-2, seed=0)
+    info, perm, sn, fs, lv = q.analyze(prob, structure=True, ordering=1)
+    big = np.sort(fs)[::-1]
+    assert big[0] >= 5000 and big[1] < 1024, big[:4]
+    # front storage: the root's f² plus small fronts (the separate children took 81e6 more)
+    assert info["front_entries"] < big[0] ** 2 + 30e6, info["front_entries"]
