@@ -32,11 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "time_to_1e-7_gap"
 WORKLOAD = "trajectory_socp_N20000"
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# Nominal FP64 rate of GB300 (non-tensor and tensor alike); see the design doc for the derivation.
-FP64_NOMINAL_GFLOPS = 1250.0
-# Nominal FP32 CUDA-core rate: 152 SMs × 128 lanes × 2 flops × 2.07 GHz.
-FP32_NOMINAL_GFLOPS = 80540.0
 HBM_FALLBACK_GBS = 6800.0
+BF16_FALLBACK_TFLOPS = 1900.0
+# TF32 : BF16 dense tensor-core rate of this part (1.1 : 2.25 PFLOP/s nominal, ~1/2)
+TF32_OVER_BF16 = 0.5
 
 
 def parse():
@@ -55,6 +54,10 @@ def parse():
                          "(F 5000x10000, FP64 or --mixed); mpc_batch: 4096 MPC instances, solves/s; "
                          "portfolio: n = 20000 assets, solve plus the adjoint of ||x - 1/n||^2")
     ap.add_argument("--mixed", action="store_true", help="FP32 large fronts with FP64 refinement")
+    ap.add_argument("--full", action="store_true",
+                    help="lasso: the full size, F 50000x100000 with density 1e-3 (one 50440-row dense front)")
+    ap.add_argument("--factor-only", action="store_true",
+                    help="lasso: time K factorisations at the initial scaling (W = I) instead of K solves")
     ap.add_argument("--ordering", default="auto", choices=["auto", "amd", "nd"],
                     help="fill-reducing ordering of the lasso / portfolio / mpc_batch workloads "
                          "(auto: the analysis' cost model, which counts a batch's independent trees)")
@@ -187,6 +190,27 @@ def peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def tf32_peak():
+    """TF32 dense tensor rate (GFLOP/s): the measured bf16 burst rate × the nominal
+    TF32:BF16 ratio of this part."""
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1e3 * TF32_OVER_BF16, "measured bf16 burst x 1/2 (nominal TF32:BF16)"
+    except Exception:
+        return BF16_FALLBACK_TFLOPS * 1e3 * TF32_OVER_BF16, "fallback bf16 x 1/2 (nominal TF32:BF16)"
+
+
+_FP64 = None
+
+
+def fp64_peaks(q):
+    """(DFMA, DMMA) GFLOP/s of this GPU, measured once by the library's own kernels."""
+    global _FP64
+    if _FP64 is None:
+        _FP64 = q.fp64_peaks()
+    return _FP64
+
+
 def kernel_source_digest():
     """Digest of the CUDA sources: DRAM traffic measured by ncu is only reported while
     the kernels are the ones it was measured on."""
@@ -216,9 +240,9 @@ def ncu_traffic(kernel, stages):
     return None
 
 
-def roofline(profile, info, stages):
+def roofline(profile, info, stages, fp64):
     """Roofline of the phase with the largest device time (CUDA events on the solver's
-    stream over the timed steps)."""
+    stream over the timed steps); fp64 = measured (DFMA, DMMA) GFLOP/s."""
     hbm, hbm_src = peaks()
     N = info["kkt_dim"]
     nnz = info["kkt_nnz"]
@@ -228,11 +252,13 @@ def roofline(profile, info, stages):
     if ph == "factor":
         flops = info["factor_flops"]
         ach = flops / (per_call_ms * 1e-3) / 1e9
+        peak = max(fp64)
         return {"kernel": "k_factor_dataflow (one launch per LDLᵀ factorisation)",
-                "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                "frac": ach / FP64_NOMINAL_GFLOPS, "traffic": ncu_traffic("k_factor_dataflow", stages),
+                "bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s",
+                "frac": ach / peak, "traffic": ncu_traffic("k_factor_dataflow", stages),
                 "per_launch_unit": f"{flops:.4g} algorithmic flops per factorisation",
-                "peak_source": "nominal FP64 rate (recipe table), not a measured peak",
+                "peak_source": (f"measured in this run by the library's FP64 kernels: DFMA {fp64[0]:.0f}, "
+                                f"DMMA m8n8k4 {fp64[1]:.0f} GFLOP/s (the larger)"),
                 "avg_ms": per_call_ms, "launches_per_call": rec["launches"] / max(1, rec["calls"])}
     if ph == "solve":
         by = 2.0 * info["l_nnz"] * 12.0 + N * 8.0 * 4.0
@@ -366,7 +392,7 @@ def run_ours(args, ws, rank, local):
     info["m_cone"] = prob.m
     ms = statistics.mean(times)
     ms_max = reduce_max(ms, dev)
-    rl = roofline(prof, info, args.stages)
+    rl = roofline(prof, info, args.stages, fp64_peaks(q))
 
     e2e = None
     if not args.no_e2e:
@@ -451,10 +477,30 @@ def other_workload(args, rank=0):
     job is ws × 4096 independent instances and no data crosses ranks)."""
     from workloads import lasso_qp, mpc_batch, portfolio_socp
     if args.workload == "lasso":
+        if args.full:
+            return [lasso_qp(rows=50000, cols=100000, density=1e-3, seed=0)]
         return [lasso_qp(rows=5000, cols=10000, density=5e-3, seed=0)]
     if args.workload == "portfolio":
         return [portfolio_socp(n=20000, k=200, seed=0)]
     return mpc_batch(count=4096, seed=rank)
+
+
+def lasso_certificate(prob, x_all, pobj):
+    """Optimality of the lasso part of a solution, from the data alone: with
+    g = Fᵀ(Fx − y), the subgradient condition is |g_j| ≤ λ everywhere and g_j = −λ·sign(x_j)
+    on the support.  Returned relative to λ (the 1e-7 stopping tolerance leaves ~1e-6)."""
+    import numpy as np
+    F, y, lam = prob.meta["F"], prob.meta["y"], prob.meta["lam"]
+    x = np.asarray(x_all[:F.shape[1]], float)
+    res = F @ x - y
+    g = F.T @ res
+    supp = np.abs(x) > 1e-6 * max(1.0, float(np.max(np.abs(x))))
+    obj = 0.5 * float(res @ res) + lam * float(np.abs(x).sum())
+    return {"max_abs_g_over_lambda_minus_1": float(np.max(np.abs(g)) / lam - 1.0),
+            "support": int(supp.sum()),
+            "support_sign_residual": float(np.max(np.abs(g[supp] + lam * np.sign(x[supp]))) / lam)
+            if supp.any() else 0.0,
+            "lasso_objective": obj, "objective_vs_pobj_rel": abs(obj - pobj) / max(1.0, abs(obj))}
 
 
 def golden_error(name, sol, pobj):
@@ -492,6 +538,9 @@ def run_other(args, ws, rank, local):
     make = (lambda: q.BatchSolver(probs, **kw)) if batch else (lambda: q.Solver(probs[0], **kw))
     S = make()
     stream = torch.cuda.current_stream(dev)
+    fp64 = fp64_peaks(q)
+    if args.factor_only:
+        return run_factor_only(args, S, probs[0], stream, dev, fp64)
     for _ in range(args.warmup):
         st = S.solve(stream.cuda_stream)
         if st != 0:
@@ -567,12 +616,7 @@ def run_other(args, ws, rank, local):
     fcalls = max(1, prof["factor"]["calls"])
     f_ms = prof["factor"]["ms"] / fcalls
     gflops = info["factor_flops"] / (f_ms * 1e-3) / 1e9
-    peak = FP32_NOMINAL_GFLOPS if args.mixed else FP64_NOMINAL_GFLOPS
-    rl = {"kernel": "factorisation (large-front panel kernels + supernodal kernels)", "bound": "alu",
-          "achieved": gflops, "peak": peak, "unit": "GFLOP/s", "frac": gflops / peak, "traffic": None,
-          "per_launch_unit": f"{info['factor_flops']:.4g} algorithmic flops per factorisation",
-          "peak_source": ("nominal FP32 CUDA-core rate" if args.mixed else "nominal FP64 rate") +
-                         " (unit counts × clock), not a measured peak", "avg_ms": f_ms}
+    rl = factor_roofline(args.mixed and info["fp32_factors"] > 0, gflops, f_ms, info, fp64)
     # e2e: set-up from host data, solve, copy-back
     e2e_s, sol = None, None
     if not args.no_e2e:
@@ -594,6 +638,10 @@ def run_other(args, ws, rank, local):
         cpu_s = (time.perf_counter() - t0) / len(sample) * len(probs)
         cpu = {"value": len(probs) / cpu_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle IPM on 16 of the {len(probs)} instances, scaled"}
+    elif args.full:
+        cpu = {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": "not run: one sparse LU of this KKT (a dense 50440-row Schur complement) takes hours "
+                         "on one core"}
     else:
         ipm.solve(probs[0], ipm.Settings(max_iter=0))
         t_init = time.perf_counter() - t0
@@ -611,7 +659,8 @@ def run_other(args, ws, rank, local):
         e2e.update({"h2d_bytes_per_step": int(sol["info"]["h2d_bytes"]),
                     "d2h_bytes_per_step": int(sol["info"]["d2h_bytes"]) + 8 * (S.n + 2 * S.m + S.p)})
     wl = {"mpc_batch": "mpc_batch_4096: horizons U{10..60}, state 4, control 2, Q^3 input cone, box bounds",
-          "lasso": "lasso_qp_r5000_c10000: F 5000x10000, 50 nnz/row",
+          "lasso": ("lasso_qp_r50000_c100000: F 50000x100000, density 1e-3 (100 nnz/row)" if args.full else
+                    "lasso_qp_r5000_c10000: F 5000x10000, 50 nnz/row"),
           "portfolio": "portfolio_socp_n20000: 20000 assets, factor model k=200, Q^201 risk cone"}
     cfg = {"workload": wl[args.workload],
            "kkt_dim": info["kkt_dim"], "kkt_nnz": info["kkt_nnz"], "factor_flops": info["factor_flops"],
@@ -631,14 +680,85 @@ def run_other(args, ws, rank, local):
            "phase_ms_per_solve": {k: v["ms"] / args.steps for k, v in prof.items()},
            "roofline": rl, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
     if not batch:
-        gname = {"lasso": "lasso_qp_r5000_c10000", "portfolio": "portfolio_socp_n20000"}[args.workload]
-        out["error_vs_oracle"] = golden_error(gname, S.solution(), info["pobj"])
+        final = S.solution()
+        if args.workload == "lasso" and args.full:
+            # no oracle run at this size: the solution is certified from the data alone
+            out["certificate"] = lasso_certificate(probs[0], final["x"], info["pobj"])
+        else:
+            gname = {"lasso": "lasso_qp_r5000_c10000", "portfolio": "portfolio_socp_n20000"}[args.workload]
+            out["error_vs_oracle"] = golden_error(gname, final, info["pobj"])
     if adj:
         out["adjoint"] = adj
     if plain:
         out["plain_fp64_one_at_a_time"] = plain
     if rank == 0:
         print(json.dumps(out), flush=True)
+    S.close()
+
+
+def factor_roofline(mixed, gflops, f_ms, info, fp64):
+    """Roofline of one factorisation: FP64 against the measured FP64 rate; mixed
+    precision (FP32 large fronts, their trailing updates as three TF32 tensor-core
+    products) against the TF32 tensor peak, with the products issued (3× the useful
+    flops of those updates) stated beside the useful rate."""
+    if mixed:
+        peak, src = tf32_peak()
+        return {"kernel": "factorisation (large fronts: FP32 panels + 3xTF32 tcgen05 trailing updates)",
+                "bound": "tensor", "achieved": gflops, "peak": peak, "unit": "GFLOP/s", "frac": gflops / peak,
+                "traffic": None, "issued_tf32_gflops_upper_bound": 3.0 * gflops,
+                "per_launch_unit": f"{info['factor_flops']:.4g} algorithmic flops per factorisation",
+                "peak_source": src, "avg_ms": f_ms}
+    peak = max(fp64)
+    return {"kernel": "factorisation (large-front panel kernels + supernodal kernels)", "bound": "alu",
+            "achieved": gflops, "peak": peak, "unit": "GFLOP/s", "frac": gflops / peak, "traffic": None,
+            "per_launch_unit": f"{info['factor_flops']:.4g} algorithmic flops per factorisation",
+            "peak_source": f"measured in this run: DFMA {fp64[0]:.0f}, DMMA m8n8k4 {fp64[1]:.0f} GFLOP/s (the larger)",
+            "avg_ms": f_ms}
+
+
+def run_factor_only(args, S, prob, stream, dev, fp64):
+    """K factorisations of the KKT matrix at the initial scaling s = z = e (W = I), each
+    timed with CUDA events on the solver's stream after W warm-up ones: the refactor
+    GFLOP/s of a size whose full solve is too long to repeat (FP64)."""
+    import numpy as np
+    import torch
+    e = torch.zeros(prob.m, dtype=torch.float64, device=dev)
+    o = 0
+    if prob.l:
+        e[:prob.l] = 1.0
+        o = prob.l
+    for qk in prob.q:
+        e[o] = 1.0
+        o += qk
+    for _ in range(args.warmup):
+        S.kkt_factor_at(e, e, stream.cuda_stream)
+    times = []
+    clocks = ClockSampler(None)
+    clocks.start()
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.kkt_factor_at(e, e, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    info = S.info()
+    f_ms = statistics.mean(times)
+    gflops = info["factor_flops"] / (f_ms * 1e-3) / 1e9
+    out = {"metric": "kkt_refactor_gflops", "value": gflops, "unit": "GFLOP/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": f_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.mixed else "f64",
+           "data": "synthetic (seeded generator)",
+           "config": {"workload": ("lasso_qp_r50000_c100000" if args.full else "lasso_qp_r5000_c10000") +
+                                  ": one factorisation at W = I (includes the NT-scaling kernel and the norm pass)",
+                      "kkt_dim": info["kkt_dim"], "factor_flops": info["factor_flops"],
+                      "max_front": info["max_front"], "front_entries": info["front_entries"],
+                      "setup_s": info["setup_time_s"], "analysis_s": info["analysis_time_s"],
+                      "precision": "mixed (FP32 large fronts)" if args.mixed else "fp64"},
+           "roofline": factor_roofline(args.mixed, gflops, f_ms, info, fp64), "clocks": clk,
+           "fp64_peaks_gflops": {"dfma": fp64[0], "dmma": fp64[1]}}
+    print(json.dumps(out), flush=True)
     S.close()
 
 

@@ -47,7 +47,7 @@ extern "C" {
 #define QOCO_GPU_ERR_NUMERICAL       -5  /* NaN/Inf in an iterate, or an iterate left the cone */
 #define QOCO_GPU_ERR_OOM             -6
 #define QOCO_GPU_ERR_CUDA            -7
-#define QOCO_GPU_ERR_DEVICE_TIMEOUT  -8  /* a bounded device wait (dataflow flag, grid barrier) ran out */
+#define QOCO_GPU_ERR_DEVICE_TIMEOUT  -8  /* a bounded device wait (dataflow dependency flag) ran out */
 #define QOCO_GPU_ERR_NO_FACTOR       -9  /* a call needs a factorisation that does not exist */
 #define QOCO_GPU_ERR_INVALID_ARG    -10
 #define QOCO_GPU_ERR_NOT_IMPLEMENTED -11
@@ -80,9 +80,11 @@ typedef struct {
     double step_fraction;               /* 0.99 */
     int ordering;                       /* QOCO_GPU_ORDER_* (AUTO) */
     int nd_leaf;                        /* ND stops splitting below this many nodes (64) */
-    int subtree_tasks;                  /* factor/solve scheduling: > 0 = target number of warp
-                                           subtree tasks below the level launches; ≤ 0 = none,
-                                           every supernode in level launches (default 0) */
+    int64_t wait_polls;                 /* polls (each sleeps ~32–64 ns) a device-side dependency
+                                           wait of the dataflow factor/solve kernels may take
+                                           before it gives up and the call returns
+                                           QOCO_GPU_ERR_DEVICE_TIMEOUT; ≤ 0 = 20000000, about a
+                                           second (default 0) */
     int verbose;                        /* 0: silent; 1: one line per iteration on stdout */
     int mixed_precision;                /* 1: fronts of order ≥ 160 factored in FP32 (FP32
                                            accumulation), solves and refinement in FP64; a
@@ -317,13 +319,22 @@ int qoco_gpu_get_factor_dense(const qoco_gpu_solver* solver, int* perm, double* 
  * from the hardware's approximate reciprocal).  Errors: NO_FACTOR. */
 int qoco_gpu_get_pivot_reciprocals(const qoco_gpu_solver* solver, double* dinv);
 
-/* Failure-detection self-test of the grid barrier used by the persistent solve kernel
- * (the paper has no counterpart): launches a small cooperative kernel in which one
- * block never arrives, so every other block's wait runs out after max_spins polls
- * (~64 ns each) and sets an error flag instead of hanging.  Returns
- * QOCO_GPU_ERR_DEVICE_TIMEOUT when that happened (the expected outcome), 0 if the
- * barrier completed, or a CUDA error.  Synchronous; the context stays usable. */
-int qoco_gpu_selftest_barrier_timeout(long long max_spins, void* stream);
+/* Failure-detection self-test of the dependency wait used by the dataflow factorisation
+ * and solve kernels (the paper has no counterpart): launches a probe whose wait is on a
+ * flag that nothing ever publishes, so the wait runs out after max_polls polls (≥ 1,
+ * ~32–64 ns each), raises the error flag and returns instead of hanging.  Returns
+ * QOCO_GPU_ERR_DEVICE_TIMEOUT when that happened (the expected outcome), 0 if the wait
+ * ended otherwise, INVALID_ARG for max_polls < 1, or a CUDA error.  Synchronous; the
+ * context stays usable. */
+int qoco_gpu_selftest_wait_timeout(long long max_polls, void* stream);
+
+/* FP64 throughput of the current device, measured by this library's own kernels (the
+ * paper has no counterpart; these are the FP64 roofline denominators of the factor
+ * kernels, §2.2): every warp of 8 blocks per SM issues long runs of independent FP64
+ * FMAs (dfma_gflops) or of FP64 tensor-core products mma.sync m8n8k4 (dmma_gflops);
+ * best of five timed launches (CUDA events on `stream`), GFLOP/s counting 2 flops per
+ * FMA and 512 per m8n8k4 product.  Host outputs.  Synchronous; allocates a few KB. */
+int qoco_gpu_fp64_peaks(double* dfma_gflops, double* dmma_gflops, void* stream);
 
 /* ---- stand-alone cone kernels (paper §2.1, §2.3) ---------------------------- */
 

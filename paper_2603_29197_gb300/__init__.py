@@ -128,6 +128,17 @@ def analyze(prob, settings=None, structure=False, **kw):
     return info.as_dict(), perm, sn
 
 
+def fp64_peaks(stream=None):
+    """(DFMA, DMMA) GFLOP/s of the current GPU, measured by the library's own kernels
+    (qoco_gpu_fp64_peaks)."""
+    lib = load()
+    a, b = C.c_double(), C.c_double()
+    rc = lib.qoco_gpu_fp64_peaks(C.byref(a), C.byref(b), _torch_stream(stream))
+    if rc != 0:
+        raise SolverError(rc, "fp64_peaks")
+    return a.value, b.value
+
+
 class SolverError(RuntimeError):
     def __init__(self, code, msg=""):
         super().__init__(f"{STATUS_NAMES.get(code, code)} ({code}) {msg}")

@@ -39,7 +39,7 @@ class Settings(C.Structure):
                 ("dyn_reg_thresh", C.c_double), ("dyn_reg_value", C.c_double),
                 ("max_refine", C.c_int), ("refine_tol", C.c_double),
                 ("step_fraction", C.c_double), ("ordering", C.c_int), ("nd_leaf", C.c_int),
-                ("subtree_tasks", C.c_int), ("verbose", C.c_int), ("mixed_precision", C.c_int),
+                ("wait_polls", C.c_int64), ("verbose", C.c_int), ("mixed_precision", C.c_int),
                 ("batch_schedule", C.c_int)]
 
 
@@ -108,7 +108,8 @@ SIGNATURES = {
     "qoco_gpu_get_kkt": (C.c_int, [_VP, C.POINTER(C.c_int64), _IP, _DP]),
     "qoco_gpu_get_factor_dense": (C.c_int, [_VP, _IP, _DP, _DP]),
     "qoco_gpu_get_pivot_reciprocals": (C.c_int, [_VP, _DP]),
-    "qoco_gpu_selftest_barrier_timeout": (C.c_int, [C.c_longlong, _VP]),
+    "qoco_gpu_selftest_wait_timeout": (C.c_int, [C.c_longlong, _VP]),
+    "qoco_gpu_fp64_peaks": (C.c_int, [_DP, _DP, _VP]),
     "qoco_gpu_cones_create": (C.c_int, [C.POINTER(_VP), C.c_int, C.c_int, _IP]),
     "qoco_gpu_cones_destroy": (C.c_int, [_VP]),
     "qoco_gpu_cone_nt_scaling": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),

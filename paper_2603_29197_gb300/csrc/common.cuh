@@ -69,54 +69,7 @@ __device__ __forceinline__ double recip(double d) {
     return fma(r, e, r);
 }
 
-// Grid-wide barrier for persistent kernels launched cooperatively (all blocks
-// co-resident).  Generation counting: each block's thread 0 reads the generation,
-// arrives on the counter; the last arrival resets the counter and advances the
-// generation, the others wait for the advance.  Every wait is bounded: after
-// `max_spins` polls the waiter sets *err, and every block returns false from this
-// and from every later barrier so that the kernel ends and the host can read the
-// error; no wait is unbounded.
-struct GridBarrier {
-    unsigned int* count;
-    unsigned int* gen;
-    int* err;
-    long long max_spins;
-};
 
-__device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        volatile int* verr = b.err;
-        volatile unsigned int* vgen = b.gen;
-        int ok = *verr == 0;
-        if (ok) {
-            const unsigned int g = *vgen;
-            const unsigned int arrived = atomicAdd(b.count, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(b.count, 0u);
-                __threadfence();
-                atomicAdd(b.gen, 1u);
-            } else {
-                long long spins = 0;
-                while (*vgen == g) {
-                    if (*verr) break;
-                    if (++spins > b.max_spins) {
-                        atomicExch(b.err, 1);
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            __threadfence();
-            ok = *verr == 0;
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 // sub-warp reductions over aligned groups of G lanes (G a power of two ≤ 32)
 template <int G>

@@ -609,41 +609,6 @@ __device__ __forceinline__ bool warp_bwd_front(int s, const FactorView& a, const
     return true;
 }
 
-// one warp per subtree task (children before parents)
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_factor(const int* __restrict__ task, int ntask,
-                                                                    FactorView a, const double* __restrict__ kval,
-                                                                    int fmax) {
-    extern __shared__ double smem[];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * kWarpsPerBlock + wid;
-    if (t >= ntask) return;
-    double* F = smem + (size_t)wid * wfactor_stride(fmax);
-    const int lo = task[2 * t], hi = task[2 * t + 1];
-    for (int s = lo; s <= hi; ++s) warp_factor_front(s, a, kval, F, F + fmax * fmax, lane, NoWait());
-}
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_fwd(const int* __restrict__ task, int ntask,
-                                                                 FactorView a, const double* __restrict__ rhs,
-                                                                 double* __restrict__ w, int fmax) {
-    extern __shared__ double smem[];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * kWarpsPerBlock + wid;
-    if (t >= ntask) return;
-    double* v = smem + (size_t)wid * fmax * (fmax + 1);
-    const int lo = task[2 * t], hi = task[2 * t + 1];
-    for (int s = lo; s <= hi; ++s) warp_fwd_front(s, a, rhs, w, v, v + fmax, lane, NoWait());
-}
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_task_bwd(const int* __restrict__ task, int ntask,
-                                                                 FactorView a, const double* __restrict__ w,
-                                                                 double* __restrict__ xp, double* __restrict__ x,
-                                                                 int accumulate, int fmax) {
-    extern __shared__ double smem[];
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t = blockIdx.x * kWarpsPerBlock + wid;
-    if (t >= ntask) return;
-    double* v = smem + (size_t)wid * fmax * (fmax + 1);
-    const int lo = task[2 * t], hi = task[2 * t + 1];
-    for (int s = hi; s >= lo; --s) warp_bwd_front(s, a, w, xp, x, accumulate, v, v + fmax, lane, NoWait());
-}
 // one warp per listed supernode of a level
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_factor(const int* __restrict__ list, int n,
                                                                     FactorView a, const double* __restrict__ kval,
@@ -678,112 +643,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_warp_bwd(const int* __r
 }
 
 // ---------------------------------------------------------------------------
-// Persistent level-synchronous solve: one cooperative launch walks the levels of the
-// tree (forward, then backward), each level's thread fronts spread over all threads
-// of the grid and its warp fronts over all warps, with a bounded grid barrier between
-// levels instead of a kernel launch.
-// ---------------------------------------------------------------------------
-constexpr int kPersistentThreads = 256;
-
-__global__ void __launch_bounds__(kPersistentThreads) k_solve_persistent(
-    const LevelPlan* __restrict__ lv, int nlev, const int* __restrict__ tlist, const int* __restrict__ wlist,
-    FactorView a, const double* __restrict__ rhs, double* __restrict__ w, double* __restrict__ xp,
-    double* __restrict__ x, int accumulate, int fmax, GridBarrier bar) {
-    extern __shared__ double smem[];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double* v = smem + (size_t)wid * fmax * (fmax + 1);
-    double* P = v + fmax;
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    const int gw = blockIdx.x * nw + wid, ngw = gridDim.x * nw;
-    for (int l = 0; l < nlev; ++l) {
-        const LevelPlan L = lv[l];
-        for (int t = gt; t < L.n_sthread; t += nt) thread_fwd_front(tlist[L.off_sthread + t], a, rhs, w, NoWait());
-        for (int t = gw; t < L.n_swarp; t += ngw)
-            warp_fwd_front(wlist[L.off_swarp + t], a, rhs, w, v, P, lane, NoWait());
-        if (!grid_sync(bar)) return;
-    }
-    for (int l = nlev - 1; l >= 0; --l) {
-        const LevelPlan L = lv[l];
-        for (int t = gt; t < L.n_sthread; t += nt)
-            thread_bwd_front(tlist[L.off_sthread + t], a, w, xp, x, accumulate, NoWait());
-        for (int t = gw; t < L.n_swarp; t += ngw)
-            warp_bwd_front(wlist[L.off_swarp + t], a, w, xp, x, accumulate, v, P, lane, NoWait());
-        if (l > 0 && !grid_sync(bar)) return;
-    }
-}
-
-// Self-test of the barrier's timeout path: block 0 leaves without arriving (the wait
-// of every other block is on an arrival that never comes), so the others give up after
-// max_spins polls and set the error flag.
-__global__ void k_barrier_timeout_probe(GridBarrier bar) {
-    if (blockIdx.x == 0) return;
-    grid_sync(bar);
-}
-
-int selftest_barrier_timeout(long long max_spins, cudaStream_t st) {
-    unsigned int* buf = nullptr;
-    QOCO_CUDA_TRY(cudaMalloc((void**)&buf, 4 * sizeof(unsigned int)));
-    int rc = 0;
-    cudaError_t e = cudaMemsetAsync(buf, 0, 4 * sizeof(unsigned int), st);
-    GridBarrier b;
-    b.count = buf;
-    b.gen = buf + 1;
-    b.err = (int*)(buf + 2);
-    b.max_spins = max_spins;
-    if (e == cudaSuccess) {
-        void* args[] = {(void*)&b};
-        e = cudaLaunchCooperativeKernel((const void*)k_barrier_timeout_probe, dim3(4), dim3(32), args, 0, st);
-    }
-    int err = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, buf + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) rc = cuda_fail(e, "barrier self-test", __FILE__, __LINE__);
-    else rc = err ? QOCO_GPU_ERR_DEVICE_TIMEOUT : 0;
-    cudaFree(buf);
-    return rc;
-}
-
-static size_t persistent_smem(int fmax) {
-    return (size_t)(kPersistentThreads / 32) * fmax * (fmax + 1) * sizeof(double);
-}
-
-int plan_persistent_solve(FactorPlan& P, int max_warp_f, bool any_cta_front) {
-    P.persistent = false;
-    if (any_cta_front || P.ntasks || P.levels.empty()) return 0;
-    const int fmax = max(1, max_warp_f);
-    const size_t sm = persistent_smem(fmax);
-    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_solve_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int dev = 0, nsm = 0, coop = 0, occ = 0;
-    QOCO_CUDA_TRY(cudaGetDevice(&dev));
-    QOCO_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    QOCO_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    QOCO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent, kPersistentThreads, sm));
-    if (!coop || occ < 1) return 0;
-    P.persistent = true;
-    P.persistent_grid = nsm * occ;
-    P.persistent_fmax = fmax;
-    return 0;
-}
-
-int launch_solve_persistent(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
-                            double* x, bool accumulate, const GridBarrier& bar, cudaStream_t st) {
-    const LevelPlan* lv = P.d_levels;
-    int nlev = (int)P.levels.size();
-    const int* tl = P.d_sthread;
-    const int* wl = P.d_swarp;
-    FactorView av = a;
-    const double* r = rhs;
-    double *ww = w, *xx = xp, *x0 = x;
-    int acc = accumulate ? 1 : 0, fm = P.persistent_fmax;
-    GridBarrier b = bar;
-    void* args[] = {(void*)&lv, (void*)&nlev, (void*)&tl, (void*)&wl, (void*)&av, (void*)&r, (void*)&ww,
-                    (void*)&xx, (void*)&x0, (void*)&acc, (void*)&fm, (void*)&b};
-    QOCO_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_solve_persistent, dim3(P.persistent_grid),
-                                              dim3(kPersistentThreads), args, persistent_smem(fm), st));
-    return 1;
-}
-
-// ---------------------------------------------------------------------------
 // Dataflow solve: one launch, no barriers.  Work items (warp fronts and batches of 32
 // one-thread fronts) are handed out by an atomic counter: first the forward items in
 // level order, then the backward items in reverse order.  A forward item waits until
@@ -810,6 +669,31 @@ __device__ __forceinline__ bool wait_epoch(const int* flag, int epoch, int* err,
         __nanosleep(32);
     }
     return true;
+}
+
+// Self-test of the dataflow wait's timeout path: warp 0 of the probe waits on a flag that
+// no item ever publishes, so its wait gives up after max_spins polls and raises the error
+// flag; warp 1 waits on the same flag and leaves as soon as it sees that error, as every
+// dataflow warp does.
+__global__ void k_wait_timeout_probe(const int* flag, int* err, long long max_spins) {
+    if ((threadIdx.x & 31) == 0) wait_epoch(flag, 1, err, max_spins);
+}
+
+int selftest_wait_timeout(long long max_spins, cudaStream_t st) {
+    int* buf = nullptr;
+    QOCO_CUDA_TRY(cudaMalloc((void**)&buf, 2 * sizeof(int)));
+    int rc = 0, err = 0;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) {
+        k_wait_timeout_probe<<<1, 64, 0, st>>>(buf, buf + 1, max_spins);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "wait self-test", __FILE__, __LINE__);
+    else rc = err ? QOCO_GPU_ERR_DEVICE_TIMEOUT : 0;
+    cudaFree(buf);
+    return rc;
 }
 
 __global__ void __launch_bounds__(kDataflowThreads) k_solve_dataflow(
@@ -890,7 +774,7 @@ static size_t dataflow_smem(int fmax) {
 
 int plan_dataflow_solve(FactorPlan& P, int max_warp_f, bool any_cta_front) {
     P.dataflow = false;
-    if (any_cta_front || P.ntasks || P.nitems == 0) return 0;
+    if (any_cta_front || P.nitems == 0) return 0;
     const int fmax = max(1, max_warp_f);
     const size_t sm = dataflow_smem(fmax);
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_solve_dataflow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -1004,7 +888,7 @@ static size_t fdataflow_smem(int fmax) {
 
 int plan_dataflow_factor(FactorPlan& P, int fmax, bool any_large) {
     P.fdataflow = false;
-    if (any_large || P.ntasks || P.nfitems == 0 || fmax > kWarpFront) return 0;
+    if (any_large || P.nfitems == 0 || fmax > kWarpFront) return 0;
     fmax = max(fmax, 1);
     const size_t sm = fdataflow_smem(fmax);
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_factor_dataflow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -1163,12 +1047,6 @@ static size_t wfactor_smem(int fmax) { return (size_t)kWarpsPerBlock * wfactor_s
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st) {
     int launches = 0;
     if (!P.groups.empty()) launches += launch_leaf_groups(P, a, kval, st);
-    if (P.ntasks) {
-        const int fm = P.task_max_f;
-        k_task_factor<<<wblocks(P.ntasks), kWarpsPerBlock * 32, wfactor_smem(fm), st>>>(
-            P.d_task, P.ntasks, a, kval, fm);
-        ++launches;
-    }
     for (int lv = 0; lv < (int)P.levels.size(); ++lv) {
         const LevelPlan& L = P.levels[lv];
         if (L.n_thread) {
@@ -1202,11 +1080,6 @@ int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, do
     int launches = 0;
     const int nl = (int)P.levels.size();
     const int acc = accumulate ? 1 : 0;
-    if (P.ntasks) {
-        k_task_fwd<<<wblocks(P.ntasks), kWarpsPerBlock * 32, wsolve_smem(P.task_max_f), st>>>(
-            P.d_task, P.ntasks, a, rhs, w, P.task_max_f);
-        ++launches;
-    }
     for (int lv = 0; lv < nl; ++lv) {
         const LevelPlan& L = P.levels[lv];
         if (L.n_sthread) {
@@ -1243,11 +1116,6 @@ int launch_solve(const FactorPlan& P, const FactorView& a, const double* rhs, do
         }
         for (int t = 0; t < L.n_big; ++t) launches += launch_big_bwd(P, a, w, xp, x, accumulate, L.off_big + t, st);
     }
-    if (P.ntasks) {
-        k_task_bwd<<<wblocks(P.ntasks), kWarpsPerBlock * 32, wsolve_smem(P.task_max_f), st>>>(
-            P.d_task, P.ntasks, a, w, xp, x, acc, P.task_max_f);
-        ++launches;
-    }
     return launches;
 }
 
@@ -1257,11 +1125,8 @@ int factor_set_attributes() {
                                        (kSmemFront * (kSmemFront + kPanel + 1) + kPanel + 1) * (int)sizeof(double)));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_front_factor<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        ((kPanel + 1) * kMaxFactorFront + kPanel + 1) * (int)sizeof(double)));
-    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_task_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_warp_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem));
     const int wsolve = kWarpsPerBlock * kWarpFront * (kWarpFront + 1) * (int)sizeof(double);
-    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_task_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, wsolve));
-    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_task_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, wsolve));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_warp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, wsolve));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_warp_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, wsolve));
     QOCO_CUDA_TRY(cudaFuncSetAttribute(k_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSolveFront * 8));

@@ -49,8 +49,6 @@ struct FactorView {
 
 struct FactorPlan {
     std::vector<LevelPlan> levels;
-    int ntasks = 0, task_max_f = 0, task_height = 0;
-    int* d_task = nullptr;   // 2·ntasks: lo, hi (inclusive) supernode ranges
     int* d_thread = nullptr; // level lists
     int* d_warp = nullptr;
     int* d_small = nullptr;
@@ -58,10 +56,6 @@ struct FactorPlan {
     int* d_cta = nullptr;
     int* d_sthread = nullptr;
     int* d_swarp = nullptr;
-    // persistent level-synchronous solve (used when every front is a thread or warp front)
-    LevelPlan* d_levels = nullptr;
-    bool persistent = false;
-    int persistent_grid = 0, persistent_fmax = 0;
     // dataflow solve (items in topological order, see PlanHost)
     bool dataflow = false;
     int nitems = 0, dataflow_grid = 0, dataflow_fmax = 0;
@@ -155,21 +149,15 @@ int plan_instances(FactorPlan& P, int fmax);
 int launch_inst_factor(const FactorPlan& P, const FactorView& a, const double* kval, int variant, cudaStream_t st);
 int launch_inst_solve(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
                       double* x, bool accumulate, int variant, cudaStream_t st);
-// Decides whether the persistent solve applies and sizes its cooperative grid.
-int plan_persistent_solve(FactorPlan& P, int max_warp_f, bool any_cta_front);
-// Launches a 4-block cooperative kernel whose block 0 never reaches the barrier; returns
-// QOCO_GPU_ERR_DEVICE_TIMEOUT when the other blocks' bounded waits ran out as designed.
-int selftest_barrier_timeout(long long max_spins, cudaStream_t st);
+// Launches a probe whose dataflow wait is on a flag nothing publishes; returns
+// QOCO_GPU_ERR_DEVICE_TIMEOUT when the bounded wait ran out as designed.
+int selftest_wait_timeout(long long max_spins, cudaStream_t st);
 int plan_dataflow_solve(FactorPlan& P, int max_warp_f, bool any_cta_front);
 int plan_dataflow_factor(FactorPlan& P, int fmax, bool any_large);
 int launch_factor_dataflow(const FactorPlan& P, const FactorView& a, const double* kval, const DataflowState& ds,
                            cudaStream_t st);
 int launch_solve_dataflow(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
                           double* x, bool accumulate, const DataflowState& ds, cudaStream_t st);
-// One cooperative launch for the forward, diagonal and backward solves.
-int launch_solve_persistent(const FactorPlan& P, const FactorView& a, const double* rhs, double* w,
-                            double* xp, double* x, bool accumulate, const GridBarrier& bar,
-                            cudaStream_t st);
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
 // One large front (P.big_*[idx]): partial LDLᵀ, or the forward / backward solve step.
 int big_set_attributes();

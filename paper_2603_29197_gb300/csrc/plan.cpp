@@ -1,4 +1,4 @@
-// Launch plan of the supernodal factorisation: subtree tasks + level lists.
+// Launch plan of the supernodal factorisation and solves: per-level lists and dataflow items.
 #include "plan.h"
 
 #include <algorithm>
@@ -6,66 +6,16 @@
 
 namespace qoco {
 
-void build_plan(const Symbolic& S, bool allow_tasks, int target_tasks, PlanHost* P) {
+void build_plan(const Symbolic& S, PlanHost* P) {
     const int ns = S.ns;
     *P = PlanHost();
-    std::vector<int> f(S.sn_nrow), par(S.sn_parent), lev(S.level);
+    std::vector<int> f(S.sn_nrow), lev(S.level);
     for (int s = 0; s < ns; ++s) P->max_f = std::max(P->max_f, f[s]);
-    // a subtree is eligible when every front in it is small; it is usable as a task only
-    // when its supernodes form a contiguous index range (true for postordered trees)
-    std::vector<char> elig(ns, 0);
-    std::vector<int> fd(ns), size(ns, 1);
-    for (int s = 0; s < ns; ++s) { elig[s] = f[s] <= kWarpFront; fd[s] = s; }
-    for (int s = 0; s < ns; ++s) {
-        const int p = par[s];
-        if (p < 0) continue;
-        if (!elig[s]) elig[p] = 0;
-        fd[p] = std::min(fd[p], fd[s]);
-        size[p] += size[s];
-    }
-    std::vector<char> contiguous(ns);
-    for (int s = 0; s < ns; ++s) contiguous[s] = size[s] == s - fd[s] + 1;
-    auto is_root = [&](int s, int H) {
-        if (!elig[s] || !contiguous[s] || lev[s] >= H) return false;
-        const int p = par[s];
-        return p < 0 || !elig[p] || !contiguous[p] || lev[p] >= H;
-    };
-    int H = 0;
-    if (allow_tasks && ns > 0) {
-        int best_h = 0, best_n = 0;
-        for (int h = 1; h <= S.n_levels; ++h) {
-            int cnt = 0;
-            for (int s = 0; s < ns; ++s) cnt += is_root(s, h);
-            if (cnt >= target_tasks) H = h;                       // largest h meeting the target
-            if (cnt > best_n || (cnt == best_n && cnt > 0)) { best_n = cnt; best_h = h; }
-        }
-        if (H == 0) H = best_h;
-    }
-    P->task_height = H;
-    std::vector<char> in_task(ns, 0);
-    std::vector<std::pair<double, int>> roots;
-    if (H > 0)
-        for (int s = 0; s < ns; ++s)
-            if (is_root(s, H)) {
-                double work = 0.0;
-                for (int t = fd[s]; t <= s; ++t) {
-                    in_task[t] = 1;
-                    work += (double)f[t] * f[t] * S.sn_ncol[t];
-                    P->task_max_f = std::max(P->task_max_f, f[t]);
-                }
-                roots.push_back({work, s});
-            }
-    // heaviest tasks first (they start in the first wave)
-    std::sort(roots.begin(), roots.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-    for (const auto& r : roots) {
-        P->task.push_back(fd[r.second]);
-        P->task.push_back(r.second);
-    }
-    // remaining supernodes by level
+    // supernodes by level
     P->levels.assign(S.n_levels, LevelPlan());
     std::vector<std::vector<int>> byl(S.n_levels);
     for (int s = 0; s < ns; ++s)
-        if (!in_task[s]) byl[lev[s]].push_back(s);
+        byl[lev[s]].push_back(s);
     for (int l = 0; l < S.n_levels; ++l) {
         LevelPlan& L = P->levels[l];
         // fronts sorted by decreasing order so that the lanes of a one-thread-per-front

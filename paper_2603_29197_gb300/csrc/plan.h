@@ -23,14 +23,10 @@ constexpr int kBigPerLevel = 64;
 constexpr int kBigNB = 64;
 constexpr int kGroupTile = 16;  // tile of a leaf group's split-K rank-K product
 
-// Launch plan of one factorisation / solve.  Supernodes are split into
-//  * subtree tasks: a task is a whole subtree of small fronts whose supernodes occupy a
-//    contiguous range [lo, hi] of the postorder; one warp processes it children-first
-//    (factor, forward) or parents-first (backward) with no grid-wide synchronisation;
-//  * the remaining (upper) supernodes, processed one tree level per launch: fronts up
-//    to kThreadFront by one thread each (so that every FP64 warp instruction serves 32
-//    fronts), up to kWarpFront by one warp each, up to kSmemFront by a CTA in shared
-//    memory, larger ones by a CTA in global memory.
+// Launch plan of one factorisation / solve: the supernodes of each tree level, fronts
+// up to kThreadFront by one thread each (so that every FP64 warp instruction serves 32
+// fronts), up to kWarpFront by one warp each, up to kSmemFront by a CTA in shared
+// memory, larger ones by a CTA in global memory or by the large-front kernels.
 struct LevelPlan {
     // factorisation lists
     int n_thread = 0, off_thread = 0;
@@ -48,7 +44,7 @@ struct LevelPlan {
 // Host-side lists from which the device plan is uploaded.
 struct PlanHost {
     std::vector<LevelPlan> levels;
-    std::vector<int> task, thread, warp, small, large;  // factorisation
+    std::vector<int> thread, warp, small, large;        // factorisation
     std::vector<int> sthread, swarp, cta;               // solves
     std::vector<int> big;                               // large fronts (factor and solves)
     // dataflow solve: work items in topological (level) order; item ≥ 0 is a warp
@@ -59,13 +55,10 @@ struct PlanHost {
     // batches of ≤ 128 one-thread fronts (thread[ftb_ptr[b] ..]), groups of ≤ 4 warp
     // fronts (warp[fwg_ptr[g] ..]) and single CTA fronts
     std::vector<int> fitems, ftb_ptr, fwg_ptr;
-    int task_max_f = 0, task_height = 0;
     int max_f = 0;
 };
 
-// Builds the plan: subtree tasks below the height that still leaves at least
-// `target_tasks` tasks (or, on small trees, the height with the most tasks), and the
-// per-level lists of the remaining supernodes.  No tasks when `allow_tasks` is false.
-void build_plan(const Symbolic& S, bool allow_tasks, int target_tasks, PlanHost* P);
+// Builds the plan: per-level lists of every supernode and the dataflow item lists.
+void build_plan(const Symbolic& S, PlanHost* P);
 
 }  // namespace qoco

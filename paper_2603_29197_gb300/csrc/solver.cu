@@ -236,8 +236,9 @@ struct qoco_gpu_solver {
     int64_t launches = 0;
     int refine_steps = 0;
     double last_berr = 0.0;
-    // polls a grid-barrier wait may take before it gives up (each poll sleeps ~64 ns)
-    long long barrier_spins = 20000000;
+    // polls a device-side dependency wait may take before it gives up (each poll sleeps
+    // ~32–64 ns): settings.wait_polls, or 20000000 (about a second)
+    long long wait_polls = 20000000;
     bool have_solution = false;  // a solve completed (adjoint available)
     // CUDA graphs of the level-launch factorisation (per large-front precision) and of the
     // level-launch solves (per right-hand side / solution / accumulate triple); captured
@@ -348,6 +349,7 @@ int build_cone_view(qoco_gpu_solver* S, const KKTPattern& K) {
 }
 
 int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h) {
+    if (S->st.wait_polls > 0) S->wait_polls = S->st.wait_polls;
     const KKTPattern& K = S->K;
     const Symbolic& Y = S->S;
     int rc;
@@ -431,7 +433,7 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
 
     // launch plan: subtree tasks + level lists
     PlanHost ph;
-    build_plan(Y, S->st.subtree_tasks > 0, S->st.subtree_tasks, &ph);
+    build_plan(Y, &ph);
     {
         int max_small = 0, max_big = 0;
         std::vector<char> is_big(Y.ns, 0);
@@ -585,10 +587,6 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         if ((rc = big_set_attributes())) return rc;
     }
     S->info.large_fronts = (int)ph.big.size();
-    P.ntasks = (int)ph.task.size() / 2;
-    P.task_max_f = ph.task_max_f;
-    P.task_height = ph.task_height;
-    if ((rc = dcopy(S, &P.d_task, ph.task))) return rc;
     if ((rc = dcopy(S, &P.d_thread, ph.thread))) return rc;
     if ((rc = dcopy(S, &P.d_warp, ph.warp))) return rc;
     if ((rc = dcopy(S, &P.d_small, ph.small))) return rc;
@@ -596,7 +594,6 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     if ((rc = dcopy(S, &P.d_cta, ph.cta))) return rc;
     if ((rc = dcopy(S, &P.d_sthread, ph.sthread))) return rc;
     if ((rc = dcopy(S, &P.d_swarp, ph.swarp))) return rc;
-    if ((rc = dcopy(S, &P.d_levels, ph.levels))) return rc;
     {
         int mwf = 0;
         for (const LevelPlan& L : ph.levels) mwf = std::max(mwf, L.max_swarp_f);
@@ -614,7 +611,6 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         if ((rc = dcopy(S, &P.d_fwg_ptr, ph.fwg_ptr))) return rc;
         if ((rc = dcopy(S, &P.d_cdone, zeros))) return rc;
         if ((rc = plan_dataflow_factor(P, ph.max_f, !ph.large.empty() || !ph.big.empty()))) return rc;
-        if (!P.dataflow && (rc = plan_persistent_solve(P, mwf, any_cta))) return rc;
     }
 
     // data-entry maps (adjoint coordinates, parametric-update scatter list)
@@ -650,7 +646,7 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     S->partial_cap = np;
     if ((rc = dalloc(S, &S->d_S, 1))) return rc;
     S->plan.df_err = &S->d_S->bar_err;
-    S->plan.df_spins = S->barrier_spins;
+    S->plan.df_spins = S->wait_polls;
     QOCO_CUDA_TRY(cudaMallocHost((void**)&S->h_S, sizeof(IPMScalars)));
 
     IPMScalars hs;
@@ -711,7 +707,7 @@ int factor_shared(qoco_gpu_solver* S, cudaStream_t st) {
         ds.next = &S->d_S->sched_next;
         ds.err = &S->d_S->bar_err;
         ds.epoch = ++S->factor_epoch;
-        ds.max_spins = S->barrier_spins;
+        ds.max_spins = S->wait_polls;
         const int rc = launch_factor_dataflow(S->plan, S->fv, S->d_val, ds, st);
         if (rc < 0) return rc;
         S->launches += rc;
@@ -735,17 +731,8 @@ int solve_shared(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaS
         ds.next = &S->d_S->sched_next;
         ds.err = &S->d_S->bar_err;
         ds.epoch = ++S->solve_epoch;
-        ds.max_spins = S->barrier_spins;
+        ds.max_spins = S->wait_polls;
         const int rc = launch_solve_dataflow(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, ds, st);
-        if (rc < 0) return rc;
-        S->launches += rc;
-    } else if (S->plan.persistent) {
-        GridBarrier bar;
-        bar.count = &S->d_S->bar_count;
-        bar.gen = &S->d_S->bar_gen;
-        bar.err = &S->d_S->bar_err;
-        bar.max_spins = S->barrier_spins;
-        const int rc = launch_solve_persistent(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, bar, st);
         if (rc < 0) return rc;
         S->launches += rc;
     } else {
@@ -1279,7 +1266,7 @@ void qoco_gpu_default_settings(qoco_gpu_settings* s) {
     s->step_fraction = 0.99;
     s->ordering = QOCO_GPU_ORDER_AUTO;
     s->nd_leaf = 64;
-    s->subtree_tasks = 0;
+    s->wait_polls = 0;
     s->verbose = 0;
     s->mixed_precision = 0;
     s->batch_schedule = 0;
@@ -1749,8 +1736,9 @@ int qoco_gpu_cone_max_step_noalloc(const qoco_gpu_cones* C, const double* u, con
     return launch_max_step_noalloc(C->v, u, du, cap, alpha, (cudaStream_t)stream);
 }
 
-int qoco_gpu_selftest_barrier_timeout(long long max_spins, void* stream) {
-    return selftest_barrier_timeout(max_spins, (cudaStream_t)stream);
+int qoco_gpu_selftest_wait_timeout(long long max_polls, void* stream) {
+    if (max_polls < 1) return QOCO_GPU_ERR_INVALID_ARG;
+    return selftest_wait_timeout(max_polls, (cudaStream_t)stream);
 }
 
 int qoco_gpu_get_pivot_reciprocals(const qoco_gpu_solver* S, double* dinv) {

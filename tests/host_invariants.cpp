@@ -193,14 +193,12 @@ int main(int argc, char** argv) {
         maxlev = std::max(maxlev, S.level[s]);
     }
     check(S.n_levels == maxlev + 1, "level count");
-    // launch plans, with and without subtree tasks
+    // launch plan
     int df_solve_checked = 0, df_factor_checked = 0;
-    for (int tasks : {0, 64}) {
+    {
         PlanHost P;
-        build_plan(S, tasks > 0, tasks, &P);
+        build_plan(S, &P);
         std::vector<int> fcount(ns, 0), scount(ns, 0);
-        for (size_t t = 0; t + 1 < P.task.size(); t += 2)
-            for (int x = P.task[t]; x <= P.task[t + 1]; ++x) { fcount[x]++; scount[x]++; }
         for (const std::vector<int>* L : {&P.thread, &P.warp, &P.small, &P.large, &P.big})
             for (int x : *L) fcount[x]++;
         for (const std::vector<int>* L : {&P.sthread, &P.swarp, &P.cta, &P.big})
@@ -215,7 +213,7 @@ int main(int argc, char** argv) {
             for (int t = 0; t < L.n_swarp; ++t) check(S.level[P.swarp[L.off_swarp + t]] == (int)lv, "level list", (long)lv);
         }
         // dataflow solve items: children strictly before parents
-        if (P.task.empty() && P.cta.empty() && P.big.empty()) {
+        if (P.cta.empty() && P.big.empty()) {
             ++df_solve_checked;
             std::vector<int> item_of(ns, -1);
             for (size_t it = 0; it < P.items.size(); ++it) {
@@ -233,7 +231,7 @@ int main(int argc, char** argv) {
             }
         }
         // dataflow factorisation items
-        if (P.task.empty() && P.large.empty() && P.big.empty()) {
+        if (P.large.empty() && P.big.empty()) {
             ++df_factor_checked;
             std::vector<int> item_of(ns, -1);
             for (size_t it = 0; it < P.fitems.size(); ++it) {

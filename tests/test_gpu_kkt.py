@@ -10,7 +10,7 @@ from oracle import cones as oc
 from oracle import kkt as ok
 from workloads import dense_qp, portfolio_socp, random_cone_iterate, trajectory_socp
 
-from _gpu_util import rel_inf
+from _gpu_util import assert_certificate, rel_inf
 
 pytestmark = pytest.mark.gpu
 
@@ -137,16 +137,36 @@ def test_pivot_reciprocals_within_two_ulp(name):
     assert np.all(np.abs(dinv - exact) <= 2 * ulp)
 
 
-def test_grid_barrier_wait_times_out_into_an_error_status():
-    """The persistent solve's grid barrier never waits without bound: with one block that
-    never arrives, the other blocks give up after a short poll budget and report
+def test_dataflow_wait_times_out_into_an_error_status():
+    """The dataflow kernels' dependency wait never waits without bound: a probe waiting
+    on a flag that nothing publishes gives up after a short poll budget and reports
     DEVICE_TIMEOUT; the context stays usable afterwards."""
     import torch
     import paper_2603_29197_gb300 as q
     from paper_2603_29197_gb300 import _lib
     lib = q.load()
-    rc = lib.qoco_gpu_selftest_barrier_timeout(200000, None)
+    assert lib.qoco_gpu_selftest_wait_timeout(0, None) == _lib.ERR_INVALID_ARG
+    rc = lib.qoco_gpu_selftest_wait_timeout(200000, None)
     assert rc == _lib.ERR_DEVICE_TIMEOUT
     # the device still works
     a = torch.ones(4, dtype=torch.float64, device="cuda")
     assert float((a * 2).sum().item()) == 8.0
+
+
+def test_solve_with_a_one_poll_wait_budget_stops_with_device_timeout():
+    """settings.wait_polls bounds every dependency wait of the real dataflow factor and
+    solve kernels: with a budget of one poll, a front whose children are still being
+    factored gives up at once, every block leaves, and qoco_gpu_solve returns
+    DEVICE_TIMEOUT instead of hanging.  A solver with the default budget then solves the
+    same problem in the same context."""
+    import paper_2603_29197_gb300 as q
+    from paper_2603_29197_gb300 import _lib
+    from workloads import trajectory_socp
+    prob = trajectory_socp(N=2000, seed=11)
+    S = q.Solver(prob, wait_polls=1)
+    assert S.solve() == _lib.ERR_DEVICE_TIMEOUT
+    S.close()
+    S = q.Solver(prob)
+    assert S.solve() == 0
+    assert_certificate(prob, S.solution())
+    S.close()
