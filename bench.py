@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--mixed", action="store_true", help="FP32 large fronts with FP64 refinement")
     ap.add_argument("--full", action="store_true",
                     help="lasso: the full size, F 50000x100000 with density 1e-3 (one 50440-row dense front)")
+    ap.add_argument("--batch-schedule", type=int, default=0,
+                    help="mpc_batch: 0 = the persistent batched kernel (default), 1-5 = the host-driven loop schedules")
     ap.add_argument("--factor-only", action="store_true",
                     help="lasso: time K factorisations at the initial scaling (W = I) instead of K solves")
     ap.add_argument("--ordering", default="auto", choices=["auto", "amd", "nd"],
@@ -471,10 +473,11 @@ def run_e2e(q, prob, args, stream, dev):
 
 
 # --------------------------------------------------------------------------- other workloads
-def other_workload(args, rank=0):
+def other_workload(args, rank=0, ws=1):
     """The instances of one rank: the lasso and portfolio problems are replicated; the
-    MPC batch is sharded by instance (rank r solves its own 4096 instances, seed r: the
-    job is ws × 4096 independent instances and no data crosses ranks)."""
+    MPC batch is one job of ws × 4096 instances (seed 0; the first 4096 are the 1-GPU
+    batch) split into contiguous ranges balanced by N_K³ (paper_2603_29197_gb300.shard),
+    and rank r solves its own range; nothing crosses ranks until the final gather."""
     from workloads import lasso_qp, mpc_batch, portfolio_socp
     if args.workload == "lasso":
         if args.full:
@@ -482,7 +485,11 @@ def other_workload(args, rank=0):
         return [lasso_qp(rows=5000, cols=10000, density=5e-3, seed=0)]
     if args.workload == "portfolio":
         return [portfolio_socp(n=20000, k=200, seed=0)]
-    return mpc_batch(count=4096, seed=rank)
+    from paper_2603_29197_gb300.shard import instance_cost, partition
+    job = mpc_batch(count=4096 * ws, seed=0)
+    starts = partition([instance_cost(p) for p in job], ws)
+    args.batch_job, args.batch_starts = len(job), starts
+    return job[starts[rank]:starts[rank + 1]]
 
 
 def lasso_certificate(prob, x_all, pobj):
@@ -501,6 +508,39 @@ def lasso_certificate(prob, x_all, pobj):
             "support_sign_residual": float(np.max(np.abs(g[supp] + lam * np.sign(x[supp]))) / lam)
             if supp.any() else 0.0,
             "lasso_objective": obj, "objective_vs_pobj_rel": abs(obj - pobj) / max(1.0, abs(obj))}
+
+
+def batch_check(S, args, ws, rank, dev):
+    """After the timed region: every rank's per-instance status and primal objective are
+    gathered to rank 0 (the one collective of the sharded batch), which reports how many
+    instances solved and compares a seeded sample of objectives with the oracle's values
+    stored in tests/golden/mpc_batch_4096_sample.json (the first 4096 instances of the
+    job are the 1-GPU batch)."""
+    import numpy as np
+    bi = S.batch_info()
+    mine = (rank, [int(v) for v in bi["status"]], [float(v) for v in bi["pobj"]])
+    if ws > 1:
+        import torch.distributed as dist
+        got = [None] * ws if rank == 0 else None
+        dist.gather_object(mine, got, dst=0)
+    else:
+        got = [mine]
+    if rank != 0:
+        return None
+    status, pobj = [0] * args.batch_job, [0.0] * args.batch_job
+    for r, st, po in got:
+        a = args.batch_starts[r]
+        status[a:a + len(st)] = st
+        pobj[a:a + len(po)] = po
+    out = {"instances": args.batch_job, "solved": int(sum(1 for v in status if v == 0))}
+    path = os.path.join(ROOT, "tests", "golden", "mpc_batch_4096_sample.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            g = json.load(f)
+        errs = [abs(pobj[i] - v) / max(1.0, abs(v)) for i, v in zip(g["idx"], g["pobj"])]
+        out["pobj_rel_vs_oracle_max"] = float(np.max(errs))
+        out["sample"] = f"{len(errs)} seeded instances, oracle values in tests/golden/mpc_batch_4096_sample.json"
+    return out
 
 
 def golden_error(name, sol, pobj):
@@ -532,19 +572,22 @@ def run_other(args, ws, rank, local):
         qbuild.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    probs = other_workload(args, rank)
+    probs = other_workload(args, rank, ws)
     batch = args.workload == "mpc_batch"
     kw = dict(mixed_precision=1 if args.mixed else 0, ordering={"auto": 0, "amd": 1, "nd": 2}[args.ordering])
+    if batch:
+        kw["batch_schedule"] = args.batch_schedule
     make = (lambda: q.BatchSolver(probs, **kw)) if batch else (lambda: q.Solver(probs[0], **kw))
     S = make()
     stream = torch.cuda.current_stream(dev)
     fp64 = fp64_peaks(q)
     if args.factor_only:
         return run_factor_only(args, S, probs[0], stream, dev, fp64)
+    failed = None  # a rank whose solve fails stops every rank together (below)
     for _ in range(args.warmup):
         st = S.solve(stream.cuda_stream)
         if st != 0:
-            raise RuntimeError(f"warm-up solve returned {st}")
+            failed = failed or f"warm-up solve returned {st}"
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     clocks = ClockSampler(None)
     clocks.start()
@@ -562,13 +605,15 @@ def run_other(args, ws, rank, local):
         e1.record(stream)
         e1.synchronize()
         if st != 0:
-            raise RuntimeError(f"solve returned {st}")
+            failed = failed or f"solve returned {st}"
         times.append(e0.elapsed_time(e1))
         launches += int(S.info()["kernel_launches"])
     if ws > 1:
         torch.cuda.synchronize(dev)
         dist.barrier()
     clk = clocks.stop()
+    if reduce_max(1.0 if failed else 0.0, dev) > 0.0:
+        raise RuntimeError(failed or "a solve failed on another rank")
     prof = S.profile()
     info = S.info()
     S.set_profiling(False)
@@ -613,10 +658,28 @@ def run_other(args, ws, rank, local):
         plain = {"value": per_s, "unit": "solves/s", "ms_per_solve": statistics.mean(pts),
                  "sample": "16 seeded instances, each on its own solver, one after the other",
                  "batched_over_plain": (len(probs) / (ms * 1e-3)) / per_s}
-    fcalls = max(1, prof["factor"]["calls"])
-    f_ms = prof["factor"]["ms"] / fcalls
-    gflops = info["factor_flops"] / (f_ms * 1e-3) / 1e9
-    rl = factor_roofline(args.mixed and info["fp32_factors"] > 0, gflops, f_ms, info, fp64)
+    fcalls = prof["factor"]["calls"]
+    if fcalls:
+        f_ms = prof["factor"]["ms"] / fcalls
+        gflops = info["factor_flops"] / (f_ms * 1e-3) / 1e9
+        rl = factor_roofline(args.mixed and info["fp32_factors"] > 0, gflops, f_ms, info, fp64)
+    else:
+        # the persistent batched kernel: one launch per batched solve runs every step; its
+        # algorithmic work counted here is the factorisations alone, Σ over instances of
+        # (iterations + 1) × that instance's factor flops (≈ the stack's flops × (mean
+        # iterations + 1)), a lower bound on the FP64 work of the launch
+        bi = S.batch_info()
+        mean_it = float(np.mean(bi["iters"]))
+        flops = info["factor_flops"] * (mean_it + 1.0)
+        gflops = flops / (ms * 1e-3) / 1e9
+        peak = max(fp64)
+        rl = {"kernel": "k_batch_ipm (one persistent launch per batched solve)", "bound": "alu",
+              "achieved": gflops, "peak": peak, "unit": "GFLOP/s", "frac": gflops / peak, "traffic": None,
+              "per_launch_unit": f"{flops:.4g} algorithmic factorisation flops per launch "
+                                 f"(stack {info['factor_flops']:.4g} x (mean iterations {mean_it:.2f} + 1))",
+              "peak_source": f"measured in this run: DFMA {fp64[0]:.0f}, DMMA {fp64[1]:.0f} GFLOP/s (the larger)",
+              "avg_ms": ms, "note": "latency-bound: per-instance level chains of small fronts"}
+        f_ms = None
     # e2e: set-up from host data, solve, copy-back
     e2e_s, sol = None, None
     if not args.no_e2e:
@@ -650,8 +713,8 @@ def run_other(args, ws, rank, local):
                          f"{info['iters'] + 1} factorisations"}
     if batch:
         # whole job: every rank's instances over the slowest rank's time
-        metric, value, unit, hib = "batched_solves_per_s", ws * len(probs) / (ms * 1e-3), "solves/s", True
-        e2e = {"value": ws * len(probs) / e2e_s, "unit": unit} if e2e_s else None
+        metric, value, unit, hib = "batched_solves_per_s", args.batch_job / (ms * 1e-3), "solves/s", True
+        e2e = {"value": args.batch_job / e2e_s, "unit": unit} if e2e_s else None
     else:
         metric, value, unit, hib = "time_to_1e-7_gap", ms * 1e-3, "s", False
         e2e = {"value": e2e_s, "unit": unit} if e2e_s else None
@@ -669,9 +732,12 @@ def run_other(args, ws, rank, local):
            "ordering": {0: "auto", 1: "amd", 2: "nd", 3: "natural"}.get(info["ordering_used"], "?") +
                        (" (requested)" if args.ordering != "auto" else " (cost model)"),
            "fp32_factors": info["fp32_factors"], "fp64_escalations": info["fp64_escalations"],
+           "krylov_steps": info["krylov_steps"], "refine_steps": info["refine_steps"],
+           "batch_schedule": info["batch_schedule_used"] if batch else None,
            "l2": "flushed between timed steps (256 MiB write)",
            "parallelism": ("single GPU" if ws == 1 else
-                           f"instance shards x{ws} (4096 instances per rank, no collective)" if batch else
+                           f"one job of {ws} x 4096 instances in {ws} contiguous ranges balanced by N_K^3, "
+                           f"one gather of the results to rank 0 after the timed region" if batch else
                            f"replicas x{ws}")}
     out = {"metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib, "scaling": "weak",
@@ -679,6 +745,8 @@ def run_other(args, ws, rank, local):
            "config": cfg, "gpu_launches": launches, "refactor_gflops": gflops,
            "phase_ms_per_solve": {k: v["ms"] / args.steps for k, v in prof.items()},
            "roofline": rl, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+    if batch:
+        out["batch_check"] = batch_check(S, args, ws, rank, dev)
     if not batch:
         final = S.solution()
         if args.workload == "lasso" and args.full:

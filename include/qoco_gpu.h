@@ -87,19 +87,27 @@ typedef struct {
                                            second (default 0) */
     int verbose;                        /* 0: silent; 1: one line per iteration on stdout */
     int mixed_precision;                /* 1: fronts of order ≥ 160 factored in FP32 (FP32
-                                           accumulation), solves and refinement in FP64; a
-                                           solve whose refinement misses refine_tol within
-                                           max_refine steps refactors in FP64, and the rest
-                                           of that qoco_gpu_solve stays FP64 (default 0) */
-    int batch_schedule;                 /* factor/solve schedule of a batch (qoco_gpu_setup_batch)
-                                           whose fronts all fit one warp: 1–4 = per-instance
-                                           kernels, one CTA per instance at a time (1: 4 warps
-                                           per CTA, fronts of order ≤ 8 one per thread; 2: 8
-                                           warps, same split; 3: 4 warps, every front one warp;
-                                           4: 8 warps, every front one warp); 5 = the shared
-                                           kernels of single problems; 0 = the fastest of the
-                                           five, timed on the first factorisation (default 0).
-                                           Other batches always use 5. */
+                                           accumulation, trailing updates on the tensor cores
+                                           as three TF32 products), solves and refinement in
+                                           FP64; a solve whose plain refinement stalls or
+                                           misses refine_tol within max_refine steps goes on
+                                           with restarted GMRES on K preconditioned by the
+                                           factor (≤ 3 cycles of 30); if that misses too, it
+                                           refactors in FP64 and the rest of that
+                                           qoco_gpu_solve stays FP64 (default 0) */
+    int batch_schedule;                 /* schedule of a batch (qoco_gpu_setup_batch) whose
+                                           fronts all fit one warp: 0 or 6 = one persistent
+                                           kernel per batched solve, each CTA running whole
+                                           instances' interior-point iterations on chip (its
+                                           tile configuration — warps per CTA, thread fronts —
+                                           timed on a sample at the first solve); 1–5 = the
+                                           host-driven iteration loop with per-instance factor
+                                           and solve kernels, one CTA per instance at a time
+                                           (1: 4 warps per CTA, fronts of order ≤ 8 one per
+                                           thread; 2: 8 warps, same split; 3: 4 warps, every
+                                           front one warp; 4: 8 warps, every front one warp)
+                                           or (5) the shared kernels of single problems
+                                           (default 0).  Other batches always use 5. */
 } qoco_gpu_settings;
 
 typedef struct {
@@ -124,8 +132,9 @@ typedef struct {
     int large_fronts;           /* fronts factored by the grid-wide large-front kernels */
     int fp32_factors;           /* factorisations of the last solve with FP32 large fronts */
     int fp64_escalations;       /* refinements that missed the target on an FP32 factor */
-    int batch_schedule_used;    /* batches: the schedule in use (1–5 as in the settings; 0
-                                   while the autotuning waits for the first factorisation) */
+    int batch_schedule_used;    /* batches: the schedule in use (1–6 as in the settings) */
+    int krylov_steps;           /* GMRES iterations of the last solve (refinement of solves
+                                   whose factor has FP32 large fronts, see mixed_precision) */
     char message[160];
 } qoco_gpu_info;
 
@@ -373,7 +382,9 @@ int qoco_gpu_cone_max_step(const qoco_gpu_cones* cones, const double* u, const d
  *     than 8192 partials (⌈l/256⌉ + ⌈#SOC of dim ≤ 32 / 256⌉ + ⌈#SOC of dim > 32 / 8⌉).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: it assumes the
+ *     device's context is not reset (cudaDeviceReset) in between; a call whose launch
+ *     fails forgets it, so the call after that looks it up again.
  *   - All calls on a device share the array; every slot a call reads is written earlier
  *     in the same call, so nothing carries over, but calls whose kernels overlap on the
  *     GPU (different streams, or threads) race on it and must be serialised. */

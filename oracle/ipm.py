@@ -5,7 +5,7 @@ The paper (§2) states the structure of one iteration — two solves with one KK
 matrix (eq. (2)), factored once (§2.2), plus cone operations (§2.1) — and the
 tolerances ε_abs = ε_rel = 1e-7 (§3).  It defers the method itself to QOCO and to
 the CVXOPT notes (§1).  Every constant below that the paper does not print is a
-reading, listed in DESIGN.md:
+reading of that method (an NT-scaled Mehrotra predictor–corrector):
 
   initial point   solve eq. (2) with W = I and rhs (−c, b, h); s = −z; shift s and z
                   into the cone (cones.shift_into_cone)
@@ -91,6 +91,21 @@ def converged(prob, rx, ry, rz, gap, pobj, dobj, scale, s, abstol, reltol):
     return ok_x and ok_y and ok_z and ok_g
 
 
+def newton_direction(prob, W, ks, rx, ry, rz, ds):
+    """One search direction for the Jordan-algebra right-hand side d_s: the solve of
+    K_ε[Δx; Δy; Δz] = [−r_x; −r_y; −r_z − W(λ\\d_s)] with refinement (ks), then
+    Δs = W(λ\\d_s − WΔz).  It satisfies the linearised Newton system
+        PΔx + AᵀΔy + GᵀΔz = −r_x,   AΔx = −r_y,   GΔx + Δs = −r_z,
+        λ∘(WΔz + W⁻¹Δs) = d_s."""
+    n, p, l, q = prob.n, prob.p, prob.l, prob.q
+    t = cones.jordan_division(W.lam, ds, l, q)
+    rhs = np.concatenate([-rx, -ry, -rz - W.apply_W(t)])
+    d = ks.solve(rhs)
+    dx, dy, dz = d[:n], d[n:n + p], d[n + p:]
+    dsv = W.apply_W(t - W.apply_W(dz))
+    return dx, dy, dz, dsv
+
+
 def solve(prob, settings: Settings | None = None) -> Result:
     st = settings or Settings()
     n, p, m, l, q = prob.n, prob.p, prob.m, prob.l, prob.q
@@ -134,12 +149,7 @@ def solve(prob, settings: Settings | None = None) -> Result:
         ks = kktmod.KKTSolver(K, signs, st.static_reg, st.max_refine, st.refine_tol)
 
         def direction(ds):
-            t = cones.jordan_division(lam, ds, l, q)
-            rhs = np.concatenate([-rx, -ry, -rz - W.apply_W(t)])
-            d = ks.solve(rhs)
-            dx, dy, dz = d[:n], d[n:n + p], d[n + p:]
-            dsv = W.apply_W(t - W.apply_W(dz))
-            return dx, dy, dz, dsv
+            return newton_direction(prob, W, ks, rx, ry, rz, ds)
 
         # --- predictor (affine) ---
         lamlam = cones.jordan_product(lam, lam, l, q)

@@ -56,7 +56,7 @@ class Info(C.Structure):
                 ("last_backward_error", C.c_double), ("kernel_launches", C.c_int64),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
                 ("large_fronts", C.c_int), ("fp32_factors", C.c_int), ("fp64_escalations", C.c_int),
-                ("batch_schedule_used", C.c_int), ("message", C.c_char * 160)]
+                ("batch_schedule_used", C.c_int), ("krylov_steps", C.c_int), ("message", C.c_char * 160)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "message"}

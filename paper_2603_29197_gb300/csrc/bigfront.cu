@@ -17,10 +17,13 @@
 // The solves of a large front are blocked the same way: per panel block one launch
 // in which every CTA solves the nb×nb triangle redundantly (a short dependent chain)
 // and then updates its own rows, so no second launch or grid barrier is needed.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 
 #include "common.cuh"
 #include "factor.h"
@@ -186,12 +189,24 @@ __global__ void __launch_bounds__(256) k_big_panel_inverse(int s, int k0, int nb
     for (int i = lane; i < kBigNB; i += 32) X[(int64_t)i * kBigNB + j] = x[i];
 }
 
-// rows i ≥ k0+nb: w_i = a_i·L11⁻ᵀ = Σ_{j ≤ k} a_ij X_kj, l_i = w_i D⁻¹ into F (and, if Lr,
-// row-major into Lr[i·ldw + k]), w_i into W[i·ldw + k].  CTA: 8 rows; thread (r, g) takes
-// row r and columns 4g … 4g+3.
+// Tensor-core operands of an FP32 front's outer panel, row-major with leading dimension
+// ldw: each FP32 value v split into a TF32 head (v with its 13 low mantissa bits cleared)
+// and the FP32 remainder v − head (exact).  Null pointers for FP64 fronts.
+struct SplitOut {
+    float* Lhi = nullptr;
+    float* Llo = nullptr;
+    float* Whi = nullptr;
+    float* Wlo = nullptr;
+    int zero_to = 0;  // columns [nb, zero_to) of the split operands are written as zeros
+};
+__device__ __forceinline__ float tf32_head(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
+
+// rows i ≥ k0+nb: w_i = a_i·L11⁻ᵀ = Σ_{j ≤ k} a_ij X_kj, l_i = w_i D⁻¹ into F, w_i into
+// W[i·ldw + k], and (FP32 fronts) the TF32 splits of l_i and w_i into sp at the same
+// positions.  CTA: 8 rows; thread (r, g) takes row r and columns 4g … 4g+3.
 template <class T>
 __global__ void __launch_bounds__(128) k_big_l21x(int s, int k0, int nb, FactorView a, T* __restrict__ F,
-                                                  T* __restrict__ W, T* __restrict__ Lr, int ldw,
+                                                  T* __restrict__ W, SplitOut sp, int ldw,
                                                   const double* __restrict__ X) {
     __shared__ T Xs[kBigNB][kBigNB + 1];
     __shared__ T As[8][kBigNB + 1];
@@ -214,13 +229,24 @@ __global__ void __launch_bounds__(128) k_big_l21x(int s, int k0, int nb, FactorV
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const int k = 4 * g + v;
-        if (k >= nb) break;
+        const int64_t o = (int64_t)i * ldw + k;
+        if (k >= nb) {
+            if (sp.Lhi && k < sp.zero_to) sp.Lhi[o] = sp.Llo[o] = sp.Whi[o] = sp.Wlo[o] = 0.0f;
+            continue;
+        }
         T acc = T(0);
         for (int j = 0; j <= k; ++j) acc += As[r][j] * Xs[k][j];
-        W[(int64_t)i * ldw + k] = acc;
+        W[o] = acc;
         const T l = acc * dv[k];
         F[(int64_t)(k0 + k) * f + i] = l;
-        if (Lr) Lr[(int64_t)i * ldw + k] = l;
+        if (sp.Lhi) {
+            const float lf = (float)l, wf = (float)acc;
+            const float lh = tf32_head(lf), wh = tf32_head(wf);
+            sp.Lhi[o] = lh;
+            sp.Llo[o] = lf - lh;
+            sp.Whi[o] = wh;
+            sp.Wlo[o] = wf - wh;
+        }
     }
 }
 
@@ -320,155 +346,284 @@ int launch_trailing(int s, int k0, int nb, int rows, int cend, const FactorView&
 }
 
 // ---- tensor-core trailing update (FP32 fronts) ---------------------------------------
-// A22 −= L21·Wᵀ on 128×128 tiles of the lower triangle with tcgen05.mma kind::tf32: each
-// FP32 operand is split into a TF32 head and the FP32 remainder (a = a_hi + a_lo), and
-// D = A_hi·B_hiᵀ + A_hi·B_loᵀ + A_lo·B_hiᵀ accumulates in FP32 in tensor memory, which
-// keeps the update at FP32 accuracy (three TF32 products).  Operands are staged by the
-// CTA's threads into shared memory in the canonical K-major layout without swizzle:
-// core matrices of 8 rows × 16 bytes, adjacent along K 128 bytes apart (leading byte
-// offset) and along M/N 2048 bytes apart (stride byte offset).  One thread issues the
-// MMAs; completion is signalled through an mbarrier whose wait is bounded (on a timeout
-// the tile is left unchanged and *err is set, so the refinement rejects the factor).
-constexpr int kTcM = 128;                        // tile rows (L21) and columns (W)
-constexpr int kTcTile = kTcM * kBigNB * 4;      // bytes of one 128×64 FP32 operand
-constexpr int kTcSmem = 4 * kTcTile + 1024;     // four operands + alignment slack
+// A22 −= L21·Wᵀ on the lower triangle of the trailing matrix after an outer panel of K ≤ 256
+// columns, with tcgen05.mma kind::tf32: each FP32 operand is split into a TF32 head and its
+// FP32 remainder (written by k_big_l21x), and D = Lhi·Whiᵀ + Lhi·Wloᵀ + Llo·Whiᵀ accumulates
+// in FP32 in tensor memory, which keeps the update at FP32 accuracy (three TF32 products,
+// the split of Ootomo & Yokota 2022).
+//
+// Persistent and warp-specialised, one CTA per SM (192 KB of shared memory):
+//   warp 0   one thread issues the TMA loads (cp.async.bulk.tensor, 128-byte swizzle) of
+//            each 32-column K chunk of the tile's four operands (Lhi, Llo: 128 rows; Whi,
+//            Wlo: 256 rows) into a two-stage ring, signalling "full" through an mbarrier's
+//            transaction count;
+//   warp 1   owns the tensor memory (512 columns: two 128×256 FP32 accumulators) and one
+//            thread issues the 12 MMAs of each chunk (4 K-steps of 8 × 3 products), then
+//            commits to the stage's "empty" barrier and, after a tile's last chunk, to the
+//            accumulator's "full" barrier;
+//   warps 2–5 the epilogue: each warp reads its 32 tensor-memory lanes (tcgen05.ld, 32
+//            columns at a time) and subtracts them from the front (column-major, coalesced
+//            per column), then releases the accumulator; with two accumulators the
+//            epilogue of one tile overlaps the MMAs of the next.
+// Tiles are 128 rows × 256 columns of the lower triangle, in groups of 16 row blocks,
+// column blocks outer within a group (the ~152 tiles in flight share their operands in L2).
+// Every mbarrier wait is bounded: a wait that runs out raises *err (the solve then returns
+// DEVICE_TIMEOUT) and an abort flag that ends the other roles' waits; before the CTA exits,
+// its armed TMA copies and issued MMAs are waited for (bounded) and the tensor memory freed.
+constexpr int kTcBM = 128, kTcBN = 256, kTcBK = 32;        // tile rows, columns; K floats per chunk
+constexpr int kTcABytes = kTcBM * kTcBK * 4;               // 16 KB: one 128-row operand chunk
+constexpr int kTcBBytes = kTcBN * kTcBK * 4;               // 32 KB: one 256-row operand chunk
+constexpr int kTcStageBytes = 2 * kTcABytes + 2 * kTcBBytes;
+constexpr int kTcStages = 2;
+constexpr int kTcSmem = kTcStages * kTcStageBytes + 1024;  // + alignment slack (1024-byte atoms)
+constexpr int kTcGroup = 16;                               // row blocks per tile group
+constexpr long long kTcMaxPolls = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ uint64_t umma_sdesc(uint32_t addr) {
+
+// Shared-memory matrix descriptor of a K-major operand written by TMA with the 128-byte
+// swizzle: rows of 128 bytes, 8-row atoms 1024 bytes apart (stride byte offset), the
+// leading byte offset unused inside one swizzle atom, descriptor version 1, layout code 2.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
     uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(128 >> 4) << 16;                   // leading byte offset (K)
-    d |= (uint64_t)((8 * kBigNB * 4) >> 4) << 32;      // stride byte offset (8-row groups)
-    d |= (uint64_t)1 << 46;                            // descriptor version
-    return d;                                          // layout: no swizzle
+    d |= (uint64_t)1 << 16;                 // leading byte offset (16 B, unused)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
 }
 
-__global__ void __launch_bounds__(512) k_big_trailing_tc(int s, int k0, int kb, FactorView a, float* __restrict__ F,
-                                                         const float* __restrict__ Lr, const float* __restrict__ W,
-                                                         int ldw, int* err) {
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait; false when it ran out (err and abort raised) or another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err) {
+    for (long long it = 0; it < kTcMaxPolls; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
+// tile t of the trailing lower triangle (row blocks of 128, column blocks of 256; block
+// (ti, tj) holds entries on or below the diagonal when ti ≥ 2·tj) → (ti, tj)
+__device__ __forceinline__ void tc_tile(int t, int nti, int& ti, int& tj) {
+    for (int g0 = 0; g0 < nti; g0 += kTcGroup) {
+        const int g1 = min(nti, g0 + kTcGroup), W = g1 - g0;
+        const int T0 = g0 / 2 + 1, T1 = (g1 + 1) / 2;  // tj < T0: whole group; T0 ≤ tj < T1: ti ≥ 2tj
+        const int full = T0 * W;
+        const int cnt = full + (T1 - T0) * (g1 - T0 - T1 + 1);
+        if (t >= cnt) { t -= cnt; continue; }
+        if (t < full) { tj = t / W; ti = g0 + t % W; return; }
+        t -= full;
+        for (int u = T0; u < T1; ++u) {
+            const int c = g1 - 2 * u;
+            if (t < c) { tj = u; ti = 2 * u + t; return; }
+            t -= c;
+        }
+    }
+    ti = tj = 0;  // not reached for t < tile count
+}
+
+int tc_tile_count(int nti) {
+    int n = 0;
+    for (int g0 = 0; g0 < nti; g0 += kTcGroup) {
+        const int g1 = std::min(nti, g0 + kTcGroup), W = g1 - g0;
+        const int T0 = g0 / 2 + 1, T1 = (g1 + 1) / 2;
+        n += T0 * W + (T1 - T0) * (g1 - T0 - T1 + 1);
+    }
+    return n;
+}
+
+struct TcMaps {
+    CUtensorMap Lhi, Llo, Whi, Wlo;
+};
+
+__global__ void __launch_bounds__(192, 1) k_big_trailing_tma(const __grid_constant__ TcMaps maps,
+                                                             float* __restrict__ F, int f, int base, int nchunk,
+                                                             int nti, int ntile, int* err) {
     extern __shared__ unsigned char tc_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* Ahi = sm;
-    unsigned char* Alo = sm + kTcTile;
-    unsigned char* Bhi = sm + 2 * kTcTile;
-    unsigned char* Blo = sm + 3 * kTcTile;
-    __shared__ uint64_t mbar;
+    __shared__ __align__(8) uint64_t bar_full[kTcStages], bar_empty[kTcStages], bar_tfull[2], bar_tempty[2],
+        bar_drain;
     __shared__ uint32_t tmem_base;
-    const int f = a.nrow[s];
-    const int base = k0 + kb;
-    const int t = blockIdx.x;
-    int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-    while (ti * (ti + 1) / 2 > t) --ti;
-    const int tj = t - ti * (ti + 1) / 2;
-    const int r0 = base + ti * kTcM, c0 = base + tj * kTcM;
+    __shared__ volatile int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kTcM));
+    if (tid == 0) {
+        s_abort = 0;
+        for (int i = 0; i < kTcStages; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[i])));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_tfull[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&bar_tempty[i])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_drain)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.Lhi) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.Llo) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.Whi) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&maps.Wlo) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    // D format F32, A and B TF32, both K-major, N = 128, M = 128
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcM >> 3) << 17) |
-                           ((uint32_t)(kTcM >> 4) << 24);
-    uint32_t tmem = 0;
-    bool ok = true;
-    // the panel's K = kb columns in chunks of kBigNB: stage, multiply, wait, next chunk
-    for (int kc = 0, round = 0; kc < kb; kc += kBigNB, ++round) {
-        const int kn = min(kBigNB, kb - kc);
-        // operands, split into TF32 head and remainder, zero outside the front / chunk; one
-        // 16-byte row segment per thread, eight consecutive threads filling one 128-byte
-        // core matrix (conflict-free shared stores)
-        for (int e = tid; e < kTcM * (kBigNB / 4); e += blockDim.x) {
-            const int rin = e & 7, kq = (e >> 3) & (kBigNB / 4 - 1), rg = e >> 7;
-            const int r = rg * 8 + rin, k = kq * 4;
-            float4 av = make_float4(0.f, 0.f, 0.f, 0.f), bv = av;
-            if (k < kn && r0 + r < f) av = *(const float4*)(Lr + (int64_t)(r0 + r) * ldw + kc + k);
-            if (k < kn && c0 + r < f) bv = *(const float4*)(W + (int64_t)(c0 + r) * ldw + kc + k);
-            const float* ap = &av.x;
-            const float* bp = &bv.x;
-            float4 ah, al, bh, bl;
-            float* ahp = &ah.x; float* alp = &al.x; float* bhp = &bh.x; float* blp = &bl.x;
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const int m = f - base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int g = 0;          // chunks issued so far (over all tiles)
+        int armed[kTcStages] = {-1, -1};
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+            int ti, tj;
+            tc_tile(t, nti, ti, tj);
+            const int ra = base + ti * kTcBM, rb = base + tj * kTcBN;
+            for (int c = 0; c < nchunk && ok; ++c, ++g) {
+                const int st = g % kTcStages;
+                if (!(ok = mbar_wait(smem_u32(&bar_empty[st]), ((g / kTcStages) & 1) ^ 1, &s_abort, err))) break;
+                const uint32_t fb = smem_u32(&bar_full[st]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kTcStageBytes)
+                             : "memory");
+                armed[st] = g;
+                unsigned char* sb = sm + st * kTcStageBytes;
+                const int x = c * kTcBK;
+                const CUtensorMap* tm[4] = {&maps.Lhi, &maps.Llo, &maps.Whi, &maps.Wlo};
+                const uint32_t dst[4] = {smem_u32(sb), smem_u32(sb + kTcABytes), smem_u32(sb + 2 * kTcABytes),
+                                         smem_u32(sb + 2 * kTcABytes + kTcBBytes)};
+                const int y[4] = {ra, ra, rb, rb};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const bool in = k + u < kn;
-                const float x = in ? ap[u] : 0.0f, y = in ? bp[u] : 0.0f;
-                ahp[u] = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
-                alp[u] = x - ahp[u];
-                bhp[u] = __uint_as_float(__float_as_uint(y) & 0xffffe000u);
-                blp[u] = y - bhp[u];
-            }
-            const int o = ((rg * (kBigNB / 4) + kq) << 7) + (rin << 4);
-            *(float4*)(Ahi + o) = ah;
-            *(float4*)(Alo + o) = al;
-            *(float4*)(Bhi + o) = bh;
-            *(float4*)(Blo + o) = bl;
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        tmem = tmem_base;
-        if (tid == 0) {
-            const unsigned char* As[3] = {Ahi, Ahi, Alo};
-            const unsigned char* Bs[3] = {Bhi, Blo, Bhi};
-            for (int kk = 0; kk < kn; kk += 8)
-                for (int q = 0; q < 3; ++q) {
-                    const uint64_t ad = umma_sdesc(smem_u32(As[q]) + (kk / 4) * 128);
-                    const uint64_t bd = umma_sdesc(smem_u32(Bs[q]) + (kk / 4) * 128);
-                    const uint32_t acc = (kc > 0 || kk > 0 || q > 0) ? 1u : 0u;
+                for (int q = 0; q < 4; ++q)
                     asm volatile(
-                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-                }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mbar)));
-        }
-        // bounded wait for this chunk's MMAs (mbarrier phase = round parity); the staged
-        // operands may only be overwritten after it
-        uint32_t done = 0;
-        for (int it = 0; it < (1 << 24) && !done; ++it)
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-                : "=r"(done)
-                : "r"(smem_u32(&mbar)), "r"((uint32_t)(round & 1)));
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        ok = __syncthreads_and(done) != 0;
-        if (!ok) break;
-    }
-    if (!ok && tid == 0) atomicExch(err, 1);
-    if (ok) {
-        // warp w reads the tensor-memory lanes of its quarter (w mod 4) and the 32 columns
-        // of chunk w / 4
-        const int quarter = warp & 3, cb = (warp >> 2) * 32;
-        const int i = r0 + quarter * 32 + lane;
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-              "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-              "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-              "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (i < f) {
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-                const int j = c0 + cb + jj;
-                if (j < f && i >= j) F[(int64_t)j * f + i] -= __uint_as_float(v[jj]);
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                        ::"r"(dst[q]), "l"((uint64_t)tm[q]), "r"(x), "r"(y[q]), "r"(fb)
+                        : "memory");
             }
+        }
+        if (!ok) {
+            // copies already armed must land before the CTA leaves
+            for (int st = 0; st < kTcStages; ++st)
+                if (armed[st] >= 0) {
+                    const uint32_t fb = smem_u32(&bar_full[st]);
+                    const uint32_t par = (armed[st] / kTcStages) & 1;
+                    for (long long it = 0; it < kTcMaxPolls && !mbar_try(fb, par); ++it) {}
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        // D format F32, A and B TF32, both K-major, N = 256, M = 128
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcBN >> 3) << 17) |
+                               ((uint32_t)(kTcBM >> 4) << 24);
+        int g = 0, n = 0;
+        bool ok = true, issued = false;
+        for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x, ++n) {
+            const int b = n & 1;
+            if (!(ok = mbar_wait(smem_u32(&bar_tempty[b]), ((n >> 1) & 1) ^ 1, &s_abort, err))) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t d = tmem + (uint32_t)(b * kTcBN);
+            for (int c = 0; c < nchunk; ++c, ++g) {
+                const int st = g % kTcStages;
+                if (!(ok = mbar_wait(smem_u32(&bar_full[st]), (g / kTcStages) & 1, &s_abort, err))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sb = smem_u32(sm + st * kTcStageBytes);
+                const uint32_t Ahi = sb, Alo = sb + kTcABytes, Bhi = sb + 2 * kTcABytes,
+                               Blo = sb + 2 * kTcABytes + kTcBBytes;
+                const uint32_t As[3] = {Ahi, Ahi, Alo}, Bs[3] = {Bhi, Blo, Bhi};
+#pragma unroll
+                for (int ks = 0; ks < kTcBK / 8; ++ks)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const uint64_t ad = umma_desc_sw128(As[q] + ks * 32);
+                        const uint64_t bd = umma_desc_sw128(Bs[q] + ks * 32);
+                        const uint32_t acc = (c > 0 || ks > 0 || q > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                issued = true;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&bar_empty[st]))
+                             : "memory");
+            }
+            if (!ok) break;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar_tfull[b]))
+                         : "memory");
+        }
+        if (!ok && issued) {
+            // MMAs already issued must finish before the tensor memory is freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&bar_drain))
+                         : "memory");
+            for (long long it = 0; it < kTcMaxPolls && !mbar_try(smem_u32(&bar_drain), 0); ++it) {}
+        }
+    } else if (warp >= 2) {
+        // ---- epilogue: warp w reads tensor-memory lanes 32·(w mod 4) …
+        const int quarter = warp & 3;
+        int n = 0;
+        for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++n) {
+            const int b = n & 1;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(smem_u32(&bar_tfull[b]), (n >> 1) & 1, &s_abort, err);
+            if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            int ti, tj;
+            tc_tile(t, nti, ti, tj);
+            const int r0 = ti * kTcBM, c0 = tj * kTcBN;  // relative to base
+            const int i = r0 + quarter * 32 + lane;
+            const bool row_ok = i < m;
+            float* Fi = F + (int64_t)base * f + base + i;  // column `base` of row base + i
+            for (int cb = 0; cb < kTcBN / 32; ++cb) {
+                const int j0 = c0 + cb * 32;
+                if (j0 > r0 + kTcBM - 1 || j0 >= m) break;  // chunk wholly above the diagonal / past the end
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTcBN + cb * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                      "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                      "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float old[32];
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = j0 + jj;
+                    old[jj] = (row_ok && j < m && i >= j) ? Fi[(int64_t)j * f] : 0.0f;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = j0 + jj;
+                    if (row_ok && j < m && i >= j) Fi[(int64_t)j * f] = old[jj] - __uint_as_float(v[jj]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_tempty[b])) : "memory");
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTcM));
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
 // ---- leaf groups ----------------------------------------------------------------------
@@ -606,12 +761,54 @@ __global__ void k_group_syrk_reduce(const double* __restrict__ part, int r, int 
     F[(int64_t)rel[j] * f + rel[i]] -= (T)sum;
 }
 
-// FP32 working front → the FP64 front storage (lower triangle)
-__global__ void k_big_writeback(const float* __restrict__ Fw, double* __restrict__ G, int f) {
+// FP32 fronts are factored scaled: with σ_i = 1/√|G_ii| of the assembled FP64 front G,
+// F = ΣGΣ has a unit diagonal (its entries stay inside the FP32 range whatever the
+// spread of the −W² block, 1e±16 near the end of a solve), and its LDLᵀ (L̃, D̃) gives
+// G's as L = Σ⁻¹L̃Σ, D = Σ⁻¹D̃Σ⁻¹, update block Σ⁻¹ŨΣ⁻¹ (and L₁₁⁻¹ = Σ⁻¹L̃₁₁⁻¹Σ).
+__global__ void k_big_scale(const double* __restrict__ G, int f, double* __restrict__ sc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < f; i += gridDim.x * blockDim.x) {
+        const double d = fabs(G[(int64_t)i * f + i]);
+        sc[i] = (d > 0.0 && isfinite(d)) ? 1.0 / sqrt(d) : 1.0;
+    }
+}
+// F = ΣGΣ on the lower triangle (zeros above)
+__global__ void k_big_to32(const double* __restrict__ G, float* __restrict__ F, int f, const double* __restrict__ sc) {
     const int64_t n = (int64_t)f * f;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / f), i = (int)(e - (int64_t)j * f);
-        if (i >= j) G[e] = (double)Fw[e];
+        F[e] = i >= j ? (float)(sc[i] * G[e] * sc[j]) : 0.0f;
+    }
+}
+// factored FP32 working front → the FP64 front storage, unscaled (lower triangle); the
+// reciprocal pivots of the solves recomputed from the unscaled D
+__global__ void k_big_writeback(int s, FactorView a, const float* __restrict__ Fw, double* __restrict__ G, int f,
+                                int c, const double* __restrict__ sc) {
+    const int first = a.first[s];
+    const int64_t n = (int64_t)f * f;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / f), i = (int)(e - (int64_t)j * f);
+        if (i < j) continue;
+        const double v = (double)Fw[e];
+        if (j < c) {
+            if (i == j) {
+                const double d = v / (sc[j] * sc[j]);
+                G[e] = d;
+                a.dinv[first + j] = recip(d);
+            } else {
+                G[e] = v * sc[j] / sc[i];
+            }
+        } else {
+            G[e] = v / (sc[i] * sc[j]);
+        }
+    }
+}
+// the pivot blocks' unit-lower inverses X (row-major 64×64 per block) unscaled
+__global__ void k_big_linv_unscale(double* __restrict__ X, int c, const double* __restrict__ sc) {
+    const int64_t n = (int64_t)((c + kBigNB - 1) / kBigNB) * kBigNB * kBigNB;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / (kBigNB * kBigNB)), q = (int)(e - (int64_t)b * kBigNB * kBigNB);
+        const int i = b * kBigNB + q / kBigNB, j = b * kBigNB + q % kBigNB;
+        if (i < c && j < c && i > j) X[e] *= sc[j] / sc[i];
     }
 }
 
@@ -903,10 +1100,10 @@ unsigned gridfor(int64_t n, int threads) {
 
 constexpr int kOuterNB = 4 * kBigNB;  // FP32 fronts: outer panel width (tensor-core K)
 
+// The front's entries: KKT values, the children's update blocks, leaf-group products.
 template <class T>
-int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, int idx, T* F, T* W,
-                 cudaStream_t st) {
-    const int s = P.big_s[idx], f = P.big_f[idx], c = P.big_c[idx];
+int big_assemble_t(const FactorPlan& P, const FactorView& a, const double* kval, int idx, T* F, cudaStream_t st) {
+    const int s = P.big_s[idx], f = P.big_f[idx];
     int launches = 0;
     const int64_t ff = (int64_t)f * f;
     k_big_zero<T><<<gridfor(ff, 256), 256, 0, st>>>(F, ff);
@@ -927,6 +1124,14 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
                                                                             a.rel + g.rel_off, f, F);
         launches += 3;
     }
+    return launches;
+}
+
+// The partial LDLᵀ of the assembled front F (panels; see the file header).
+template <class T>
+int big_factor_t(const FactorPlan& P, const FactorView& a, int idx, T* F, T* W, cudaStream_t st) {
+    const int s = P.big_s[idx], f = P.big_f[idx], c = P.big_c[idx];
+    int launches = 0;
     double* linv = P.big_linv + P.big_linv_off[idx];
     if constexpr (sizeof(T) == 8) {
         // FP64: 64-column panels, each followed by the full trailing update
@@ -938,14 +1143,15 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
             const int rows = f - k0 - nb;
             launches += 2;
             if (rows <= 0) continue;
-            k_big_l21x<T><<<(unsigned)((rows + 7) / 8), 128, 0, st>>>(s, k0, nb, a, F, W, nullptr, kBigNB, X);
+            k_big_l21x<T><<<(unsigned)((rows + 7) / 8), 128, 0, st>>>(s, k0, nb, a, F, W, SplitOut(), kBigNB, X);
             launches += 1 + launch_trailing<T>(s, k0, nb, rows, f, a, F, W, kBigNB, f, st);
         }
     } else {
         // FP32: outer panels of kOuterNB columns made of 64-column inner panels; an inner
-        // panel updates only the rest of its outer panel (CUDA cores), and the trailing
-        // matrix takes one rank-kOuterNB update on the tensor cores (3×TF32)
-        T* Lr = W + (int64_t)P.max_big_f * kOuterNB;
+        // panel updates only the rest of its outer panel (CUDA cores) and writes the TF32
+        // splits of its L and W rows, and the trailing matrix takes one rank-kOuterNB update
+        // on the tensor cores (3×TF32, TMA-fed)
+        const int64_t sps = (int64_t)P.max_big_f * kOuterNB;
         for (int k0 = 0; k0 < c; k0 += kOuterNB) {
             const int nbo = std::min(kOuterNB, c - k0);
             for (int k1 = k0; k1 < k0 + nbo; k1 += kBigNB) {
@@ -956,8 +1162,16 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
                 const int rows = f - k1 - nb;
                 launches += 2;
                 if (rows <= 0) continue;
-                k_big_l21x<T><<<(unsigned)((rows + 7) / 8), 128, 0, st>>>(s, k1, nb, a, F, W + (k1 - k0),
-                                                                           Lr + (k1 - k0), kOuterNB, X);
+                SplitOut sp;
+                sp.Lhi = P.big_split + (k1 - k0);
+                sp.Llo = sp.Lhi + sps;
+                sp.Whi = sp.Lhi + 2 * sps;
+                sp.Wlo = sp.Lhi + 3 * sps;
+                // the outer panel's last inner panel zero-fills its split columns up to 64 (the
+                // tensor-core K chunks of 32 reach past a ragged panel end)
+                sp.zero_to = (k1 + nb == k0 + nbo) ? kBigNB : 0;
+                k_big_l21x<T><<<(unsigned)((rows + 7) / 8), 128, 0, st>>>(s, k1, nb, a, F, W + (k1 - k0), sp,
+                                                                           kOuterNB, X);
                 ++launches;
                 const int cend = k0 + nbo;
                 if (k1 + nb < cend)
@@ -965,9 +1179,12 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, const double* kval, i
             }
             const int rows = f - k0 - nbo;
             if (rows > 0) {
-                const int nt = (rows + kTcM - 1) / kTcM;
-                k_big_trailing_tc<<<(unsigned)(nt * (nt + 1) / 2), 512, kTcSmem, st>>>(s, k0, nbo, a, F, Lr, W,
-                                                                                      kOuterNB, P.big_err);
+                const int nti = (rows + kTcBM - 1) / kTcBM;
+                const int ntile = tc_tile_count(nti);
+                TcMaps maps;
+                memcpy(&maps, P.big_tmaps, sizeof maps);
+                k_big_trailing_tma<<<(unsigned)std::min(ntile, nsm()), 192, kTcSmem, st>>>(
+                    maps, (float*)F, f, k0 + nbo, (nbo + kTcBK - 1) / kTcBK, nti, ntile, P.df_err);
                 ++launches;
             }
         }
@@ -987,8 +1204,35 @@ int launch_leaf_groups(const FactorPlan& P, const FactorView& a, const double* k
 }
 
 int big_set_attributes() {
-    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_big_trailing_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    QOCO_CUDA_TRY(cudaFuncSetAttribute(k_big_trailing_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
     nsm();  // queried here, outside any stream capture of the launch sequences
+    return 0;
+}
+
+// Tensor maps of the four split operands (rows: max_big_f, columns: kOuterNB FP32, row
+// stride kOuterNB·4 bytes; boxes of 32 columns × 128 or 256 rows, 128-byte swizzle, rows past
+// the end read as zeros).  Encoded once: the buffers live as long as the solver.
+int big_tma_setup(FactorPlan& P) {
+    static_assert(sizeof(TcMaps) <= sizeof(P.big_tmaps), "tensor-map storage");
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    QOCO_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr));
+    if (!fn || qr != cudaDriverEntryPointSuccess) return QOCO_GPU_ERR_CUDA;
+    auto encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    TcMaps maps;
+    CUtensorMap* out[4] = {&maps.Lhi, &maps.Llo, &maps.Whi, &maps.Wlo};
+    const int64_t sps = (int64_t)P.max_big_f * kOuterNB;
+    for (int q = 0; q < 4; ++q) {
+        const cuuint64_t dims[2] = {(cuuint64_t)kOuterNB, (cuuint64_t)P.max_big_f};
+        const cuuint64_t strides[1] = {(cuuint64_t)kOuterNB * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)(q < 2 ? kTcBM : kTcBN)};
+        const cuuint32_t estr[2] = {1, 1};
+        const CUresult r = encode(out[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, P.big_split + q * sps, dims, strides,
+                                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return QOCO_GPU_ERR_CUDA;
+    }
+    memcpy(P.big_tmaps, &maps, sizeof maps);
     return 0;
 }
 
@@ -997,13 +1241,25 @@ int launch_big_factor(const FactorPlan& P, const FactorView& a, const double* kv
     const int64_t off = P.big_front_off[idx];
     int launches = 0;
     if (P.big_fp32) {
+        // assembled in FP64, scaled symmetrically to a unit diagonal, factored in FP32, and
+        // L, D, the update block and the diagonal blocks' inverses unscaled into FP64
+        const int s = P.big_s[idx], c = P.big_c[idx];
         float* F = P.big_work32;
-        launches += big_factor_t<float>(P, a, kval, idx, F, (float*)P.big_w, st);
+        double* G = a.front + off;
         const int64_t ff = (int64_t)f * f;
-        k_big_writeback<<<gridfor(ff, 256), 256, 0, st>>>(F, a.front + off, f);
-        ++launches;
+        launches += big_assemble_t<double>(P, a, kval, idx, G, st);
+        k_big_scale<<<gridfor(f, 256), 256, 0, st>>>(G, f, P.big_scale);
+        k_big_to32<<<gridfor(ff, 256), 256, 0, st>>>(G, F, f, P.big_scale);
+        launches += 2;
+        launches += big_factor_t<float>(P, a, idx, F, (float*)P.big_w, st);
+        k_big_writeback<<<gridfor(ff, 256), 256, 0, st>>>(s, a, F, G, f, c, P.big_scale);
+        const int nblk = (c + kBigNB - 1) / kBigNB;
+        k_big_linv_unscale<<<gridfor((int64_t)nblk * kBigNB * kBigNB, 256), 256, 0, st>>>(
+            P.big_linv + P.big_linv_off[idx], c, P.big_scale);
+        launches += 2;
     } else {
-        launches += big_factor_t<double>(P, a, kval, idx, a.front + off, (double*)P.big_w, st);
+        launches += big_assemble_t<double>(P, a, kval, idx, a.front + off, st);
+        launches += big_factor_t<double>(P, a, idx, a.front + off, (double*)P.big_w, st);
     }
     return launches;
 }

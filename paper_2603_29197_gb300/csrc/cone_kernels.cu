@@ -77,38 +77,6 @@ __global__ void k_w2_identity(ConeView c, ConeGrid g, double* kval, const int64_
 //   t = λ\d_s;  rhs_z = −r_z − W t
 // scratch: t1, t2 (m each).  `smu` points at σμ on the device (combined only).
 // ---------------------------------------------------------------------------
-template <int G>
-__device__ void soc_rhs(int k, int o, int d, int lane, const ConeView& c, const double* lam,
-                        const double* wbar, const double* eta, const double* rz, const double* dsa,
-                        const double* dza, double smu, bool combined, double* t, double* t1,
-                        double* t2, double* rhs) {
-    const double et = eta[k];
-    soc_prod<G>(o, d, lane, lam, lam, t1);  // t1 = λ∘λ
-    gsync<G>();
-    if (combined) {
-        soc_W<G>(o, d, lane, wbar, et, dsa, t2, true);   // t2 = W⁻¹Δs_a
-        soc_W<G>(o, d, lane, wbar, et, dza, t, false);   // t  = WΔz_a
-        gsync<G>();
-        // t1 += t2∘t
-        double dot = 0.0;
-        for (int a = lane; a < d; a += G) dot += t2[o + a] * t[o + a];
-        dot = gsum<G>(dot);
-        const double a0 = t2[o], b0 = t[o];
-        gsync<G>();
-        for (int a = 1 + lane; a < d; a += G) t1[o + a] += a0 * t[o + a] + b0 * t2[o + a];
-        if (lane == 0) t1[o] += dot;
-        gsync<G>();
-    }
-    // t1 = d_s = −t1 + σμ e
-    for (int a = lane; a < d; a += G) t1[o + a] = -t1[o + a] + ((a == 0 && combined) ? smu : 0.0);
-    gsync<G>();
-    soc_div<G>(o, d, lane, lam, t1, t);  // t = λ\d_s
-    gsync<G>();
-    soc_W<G>(o, d, lane, wbar, et, t, t2, false);  // t2 = W t
-    gsync<G>();
-    for (int a = lane; a < d; a += G) rhs[o + a] = -rz[o + a] - t2[o + a];
-}
-
 __global__ void k_rhs_z(ConeView c, ConeGrid g, const double* __restrict__ lam,
                         const double* __restrict__ wbar, const double* __restrict__ eta,
                         const double* __restrict__ rz, const double* __restrict__ dsa,
@@ -385,7 +353,16 @@ int launch_max_step_noalloc(const ConeView& c, const double* u, const double* du
     const int rc = noalloc_partials(&partial);
     if (rc) return rc;
     launch_max_step(c, u, du, nullptr, nullptr, cap, partial, out, st);
-    QOCO_CUDA_TRY(cudaGetLastError());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        // a failed launch may mean a reset context: look the address up again next time
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < kNoAllocDevices) {
+            std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+            g_noalloc_ptr[dev] = nullptr;
+        }
+        return cuda_fail(e, "max_step_noalloc", __FILE__, __LINE__);
+    }
     return 0;
 }
 

@@ -230,4 +230,38 @@ __device__ __forceinline__ double soc_step(int o, int d, int lane, const double*
     return soc_root(a, b, c);
 }
 
+// Right-hand side of one SOC block of the z rows (see k_rhs_z): d_s = −λ∘λ (affine) or
+// −λ∘λ − (W⁻¹Δs_a)∘(WΔz_a) + σμ e (combined), t = λ\d_s, rhs_z = −r_z − W t.
+template <int G>
+__device__ __forceinline__ void soc_rhs(int k, int o, int d, int lane, const ConeView& c, const double* lam,
+                        const double* wbar, const double* eta, const double* rz, const double* dsa,
+                        const double* dza, double smu, bool combined, double* t, double* t1,
+                        double* t2, double* rhs) {
+    const double et = eta[k];
+    soc_prod<G>(o, d, lane, lam, lam, t1);  // t1 = λ∘λ
+    gsync<G>();
+    if (combined) {
+        soc_W<G>(o, d, lane, wbar, et, dsa, t2, true);   // t2 = W⁻¹Δs_a
+        soc_W<G>(o, d, lane, wbar, et, dza, t, false);   // t  = WΔz_a
+        gsync<G>();
+        // t1 += t2∘t
+        double dot = 0.0;
+        for (int a = lane; a < d; a += G) dot += t2[o + a] * t[o + a];
+        dot = gsum<G>(dot);
+        const double a0 = t2[o], b0 = t[o];
+        gsync<G>();
+        for (int a = 1 + lane; a < d; a += G) t1[o + a] += a0 * t[o + a] + b0 * t2[o + a];
+        if (lane == 0) t1[o] += dot;
+        gsync<G>();
+    }
+    // t1 = d_s = −t1 + σμ e
+    for (int a = lane; a < d; a += G) t1[o + a] = -t1[o + a] + ((a == 0 && combined) ? smu : 0.0);
+    gsync<G>();
+    soc_div<G>(o, d, lane, lam, t1, t);  // t = λ\d_s
+    gsync<G>();
+    soc_W<G>(o, d, lane, wbar, et, t, t2, false);  // t2 = W t
+    gsync<G>();
+    for (int a = lane; a < d; a += G) rhs[o + a] = -rz[o + a] - t2[o + a];
+}
+
 }  // namespace qoco

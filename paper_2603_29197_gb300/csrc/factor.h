@@ -98,7 +98,6 @@ struct FactorPlan {
     // factorisation (used there for the panel's rows below, and by the solves)
     std::vector<int64_t> big_linv_off;
     double* big_linv = nullptr;
-    int* big_err = nullptr;        // set when a tensor-core tile's completion wait ran out
     // leaf groups: many childless children of one large front with the same update rows
     // (an arrowhead border).  Their pivots are factored one warp per member; the parent
     // receives −Σ L21·D·L21ᵀ as one split-K rank-K product instead of one update matrix
@@ -125,6 +124,11 @@ struct FactorPlan {
     int max_big_f = 0;
     bool big_fp32 = false;         // factor large fronts in FP32 (mixed precision)
     float* big_work32 = nullptr;   // max_big_f² FP32 working front
+    // FP32 fronts: TF32 head / remainder of the outer panel's L and W rows (Lhi, Llo, Whi,
+    // Wlo, each max_big_f × 4·kBigNB row-major) and their TMA tensor maps (opaque bytes)
+    float* big_split = nullptr;
+    double* big_scale = nullptr;   // max_big_f: symmetric scaling of the FP32 front being factored
+    alignas(64) unsigned char big_tmaps[4 * 128] = {};
     void* big_w = nullptr;         // max_big_f × 4·kBigNB doubles: panel rows W (FP64), or W and L (FP32)
     double* big_v = nullptr;       // max_big_f solve work vector
     double* big_y = nullptr;       // max_big_f solved block values
@@ -163,6 +167,8 @@ int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, 
 int big_set_attributes();
 // The leaf-group members' pivot columns (all groups), one warp per member.
 int launch_leaf_groups(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
+// Encodes the tensor maps of big_split (mixed precision).
+int big_tma_setup(FactorPlan& P);
 int launch_big_factor(const FactorPlan& P, const FactorView& a, const double* kval, int idx, cudaStream_t st);
 int launch_big_fwd(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, int idx,
                    cudaStream_t st);

@@ -279,6 +279,7 @@ __global__ void k_finalize_refine(const double* __restrict__ partial, int nb, IP
     const double den = S->normK * red[1] + red[2];
     const double be = !finite ? __longlong_as_double(0x7ff8000000000000LL) : den > 0.0 ? red[0] / den : 0.0;
     S->berr = be;
+    S->refine_den = den;
     S->refine_done = (!finite || be <= S->refine_tol) ? 1 : 0;
 }
 

@@ -24,7 +24,7 @@ struct IPMScalars {
     // residual pass
     double pobj, dobj, gap, mu;
     double rx_inf, ry_inf, rz_inf, Px_inf, Aty_inf, Gtz_inf, Ax_inf, Gx_inf, s_inf;
-    int converged, converged_inacc, nonfinite, pad0;
+    int converged, converged_inacc, nonfinite, max_iters;  // max_iters: batched solves
     // constants set at setup
     double c_inf, b_inf, h_inf, nu;
     double abstol, reltol, abstol_inacc, reltol_inacc;
@@ -34,11 +34,13 @@ struct IPMScalars {
     double shift[2];
     // refinement
     double normK, berr;
+    double refine_den;        // ‖K‖∞‖x‖∞ + ‖r‖∞ of the last refinement residual (berr's denominator)
     int refine_done, pad1;
-    // grid barrier of the persistent solve kernel (count, generation, timeout flag)
+    // shared state of the dataflow kernels: two spare words, the timeout flag, the
+    // work-item counter (zeroed together before each solve)
     unsigned int bar_count, bar_gen;
     int bar_err;
-    unsigned int sched_next;  // work-item counter of the dataflow solve
+    unsigned int sched_next;
 };
 
 constexpr int kResNSum = 5;

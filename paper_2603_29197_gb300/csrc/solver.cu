@@ -17,8 +17,10 @@
 #include <vector>
 
 #include "batch.h"
+#include "batch_ipm.h"
 #include "cone_kernels.h"
 #include "factor.h"
+#include "krylov.h"
 #include "plan.h"
 #include "qoco_gpu.h"
 #include "row_kernels.h"
@@ -246,6 +248,7 @@ struct qoco_gpu_solver {
     struct Graph { const void* r = nullptr; void* x = nullptr; int acc = 0; cudaGraphExec_t exec = nullptr; int launches = 0; };
     Graph fgraph[2];
     std::vector<Graph> sgraphs;
+    Graph bgraph;
     cudaStream_t cap_stream = nullptr;
     // batch of independent instances (qoco_gpu_setup_batch)
     bool batch = false;
@@ -253,7 +256,20 @@ struct qoco_gpu_solver {
     int batch_L = 0;                   // stacked orthant dimension
     double *b_items = nullptr, *b_shift = nullptr, *b_aux = nullptr;
     std::vector<int> h_xo, h_yo, h_lo, h_ko, h_so;
+    // the persistent batched kernel (batch_schedule 0 or 6): its arguments, the tile
+    // configuration picked at the first solve (warps per CTA, thread-front split), the
+    // persistent grid per warp count (2, 4, 8) and the captured launch graph
+    bool fused = false;
+    BatchIPMArgs bargs;
+    int fused_nw = 0, fused_split = 0;
+    int fused_grid[3] = {0, 0, 0};
+    double fused_tune_ms[6] = {0, 0, 0, 0, 0, 0};
     int fp32_factors = 0, fp64_escalations = 0;
+    // GMRES refinement (mixed precision): basis V ((restart + 1) × N), work vector, zero
+    // vector, Hessenberg column / coefficients (device), dot-product partials
+    double *kv_basis = nullptr, *kv_z = nullptr, *kv_zero = nullptr, *kv_h = nullptr, *kv_y = nullptr,
+           *kv_part = nullptr;
+    int krylov_steps = 0;
     // adjoint: KKT position (row, column) of one slot of each data entry [P | A | G]
     int *d_adj_a = nullptr, *d_adj_b = nullptr;
     int adj_steps = 0, adj_refactored = 0;
@@ -577,13 +593,24 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
         P.big_w = pw;
         if ((rc = dalloc(S, &P.big_v, P.max_big_f))) return rc;
         if ((rc = dalloc(S, &P.big_y, P.max_big_f))) return rc;
-        if (S->st.mixed_precision && (rc = dalloc(S, &P.big_work32, (size_t)P.max_big_f * P.max_big_f))) return rc;
-        if ((rc = dalloc(S, &P.big_err, 1))) return rc;
+        if (S->st.mixed_precision) {
+            if ((rc = dalloc(S, &P.big_work32, (size_t)P.max_big_f * P.max_big_f))) return rc;
+            if ((rc = dalloc(S, &P.big_split, (size_t)4 * P.max_big_f * 4 * kBigNB))) return rc;
+            if ((rc = dalloc(S, &P.big_scale, (size_t)P.max_big_f))) return rc;
+            if ((rc = big_tma_setup(P))) return rc;
+            const size_t R = kKrylovRestart;
+            if ((rc = dalloc(S, &S->kv_basis, (R + 1) * (size_t)N))) return rc;
+            if ((rc = dalloc(S, &S->kv_z, (size_t)N))) return rc;
+            if ((rc = dalloc(S, &S->kv_zero, (size_t)N))) return rc;
+            QOCO_CUDA_TRY(cudaMemset(S->kv_zero, 0, sizeof(double) * N));
+            if ((rc = dalloc(S, &S->kv_h, 2 * (R + 2) + 1))) return rc;
+            if ((rc = dalloc(S, &S->kv_y, R))) return rc;
+            if ((rc = dalloc(S, &S->kv_part, (size_t)krylov_partials()))) return rc;
+        }
         int64_t max_blk = 0;
         for (size_t idx = 0; idx < P.big_s.size(); ++idx)
             max_blk = std::max<int64_t>(max_blk, (P.big_c[idx] + kBigNB - 1) / kBigNB);
         if ((rc = dalloc(S, &P.big_ctl, (size_t)(1 + max_blk)))) return rc;
-        QOCO_CUDA_TRY(cudaMemset(P.big_err, 0, sizeof(int)));
         if ((rc = big_set_attributes())) return rc;
     }
     S->info.large_fronts = (int)ph.big.size();
@@ -778,38 +805,6 @@ int solve_with(qoco_gpu_solver* S, int v, const double* r, double* x, bool acc, 
     return solve_shared(S, r, x, acc, st);
 }
 
-// Autotuning of a batch's factor/solve schedule: each candidate (the four per-instance
-// layouts and the shared kernels) factors the current KKT values and runs one solve (on
-// the combined-direction and residual buffers, dead whenever a factorisation starts),
-// twice; the candidate with the fastest second run is kept for the solver's lifetime.
-int tune_instances(qoco_gpu_solver* S, cudaStream_t st) {
-    cudaEvent_t e0, e1;
-    QOCO_CUDA_TRY(cudaEventCreate(&e0));
-    QOCO_CUDA_TRY(cudaEventCreate(&e1));
-    int best = kSharedSchedule;
-    float best_ms = 0.0f;
-    int rc = 0;
-    for (int v = 1; v <= kSharedSchedule && !rc; ++v) {
-        float ms = 0.0f;
-        for (int rep = 0; rep < 2 && !rc; ++rep) {
-            QOCO_CUDA_TRY(cudaEventRecord(e0, st));
-            if ((rc = factor_with(S, v, st))) break;
-            if ((rc = solve_with(S, v, S->d_cmb, S->res, false, st))) break;
-            QOCO_CUDA_TRY(cudaEventRecord(e1, st));
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = QOCO_GPU_ERR_CUDA;
-            else cudaEventElapsedTime(&ms, e0, e1);
-        }
-        if (!rc && (v == 1 || ms < best_ms)) { best = v; best_ms = ms; }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc) return rc;
-    QOCO_CUDA_TRY(cudaGetLastError());
-    S->plan.inst_variant = best;
-    S->info.batch_schedule_used = best;
-    return 0;
-}
-
 int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
     {
         Phase ph(S, QOCO_GPU_PHASE_ROW, st);
@@ -819,10 +814,6 @@ int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
     }
     {
         Phase ph(S, QOCO_GPU_PHASE_FACTOR, st);
-        if (S->plan.inst && S->plan.inst_variant == 0) {
-            const int rc = tune_instances(S, st);
-            if (rc) return rc;
-        }
         const int rc = factor_with(S, S->plan.inst ? S->plan.inst_variant : kSharedSchedule, st);
         if (rc) return rc;
     }
@@ -837,32 +828,132 @@ int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStre
     return solve_with(S, S->plan.inst ? S->plan.inst_variant : kSharedSchedule, r, x, acc, st);
 }
 
+int refine_residual(qoco_gpu_solver* S, const double* x, const double* r, double* res, cudaStream_t st) {
+    Phase ph(S, QOCO_GPU_PHASE_ROW, st);
+    const int nl = launch_spmv_res(S->kv, S->lpr, x, r, res, S->partial, S->partial_cap, S->d_S, st);
+    if (nl < 0) return QOCO_GPU_ERR_INVALID_ARG;
+    S->launches += nl;
+    return 0;
+}
+
+// GMRES refinement (GMRES-IR, Carson & Higham 2017–2018): restarted GMRES on K x = r with
+// K the unregularised KKT matrix (FP64 products), right-preconditioned by the current
+// factor M (FP32 large fronts): the Krylov space of K·M⁻¹ is built from the residual of the
+// refined x, orthogonalised by classical Gram–Schmidt applied twice, its least-squares
+// problem reduced by Givens rotations on the host, and x += M⁻¹·V·y at the end of a cycle;
+// each cycle ends early when the GMRES residual estimate is below half the backward-error
+// target, and is followed by the true residual.  Sets *ok when the backward error of x
+// reaches refine_tol.
+int gmres_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st, bool* ok) {
+    constexpr int R = kKrylovRestart, kCycles = 3;
+    const int64_t N = S->N, ld = N;
+    double* V = S->kv_basis;
+    double* hd = S->kv_h;  // [0, R+2): first pass, [R+2, 2R+4): second pass, [2R+4]: ‖w‖²
+    *ok = false;
+    std::vector<double> H((size_t)(R + 1) * R, 0.0), cs(R), sn(R), g(R + 1), hc(2 * (R + 2) + 1), y(R);
+    int rc;
+    for (int cycle = 0; cycle < kCycles; ++cycle) {
+        if ((rc = refine_residual(S, x, r, S->res, st))) return rc;
+        // β = ‖r − Kx‖₂, v_0 = (r − Kx)/β
+        S->launches += launch_dots(S->res, ld, 1, S->res, N, S->kv_part, hd, false, st);
+        S->launches += launch_scale_by_norm(S->res, V, N, hd, 1.0, st);
+        QOCO_CUDA_TRY(cudaMemcpyAsync(S->h_S, S->d_S, sizeof(IPMScalars), cudaMemcpyDeviceToHost, st));
+        QOCO_CUDA_TRY(cudaMemcpyAsync(hc.data(), hd, sizeof(double), cudaMemcpyDeviceToHost, st));
+        QOCO_CUDA_TRY(cudaStreamSynchronize(st));
+        if (S->prof.on) S->prof.flush();
+        if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
+        if (!std::isfinite(S->h_S->berr)) return 0;
+        if (S->h_S->refine_done) { *ok = true; return 0; }
+        const double beta = std::sqrt(hc[0]);
+        const double target = 0.5 * S->st.refine_tol * S->h_S->refine_den;
+        if (!(beta > 0.0)) return 0;
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < R; ++j) {
+            double* vj = V + (int64_t)j * ld;
+            double* w = V + (int64_t)(j + 1) * ld;
+            if ((rc = tri_solve(S, vj, S->kv_z, false, st))) return rc;              // z = M⁻¹ v_j
+            if ((rc = refine_residual(S, S->kv_z, S->kv_zero, w, st))) return rc;  // w = −K z
+            // two classical Gram–Schmidt passes on the negated vector, then its norm
+            S->launches += launch_dots(V, ld, j + 1, w, N, S->kv_part, hd, false, st);
+            S->launches += launch_sub_combination(V, ld, j + 1, hd, w, N, st);
+            S->launches += launch_dots(V, ld, j + 1, w, N, S->kv_part, hd + R + 2, false, st);
+            S->launches += launch_sub_combination(V, ld, j + 1, hd + R + 2, w, N, st);
+            S->launches += launch_dots(w, ld, 1, w, N, S->kv_part, hd + 2 * (R + 2), false, st);
+            S->launches += launch_scale_by_norm(w, w, N, hd + 2 * (R + 2), -1.0, st);
+            QOCO_CUDA_TRY(cudaMemcpyAsync(hc.data(), hd, sizeof(double) * hc.size(), cudaMemcpyDeviceToHost, st));
+            QOCO_CUDA_TRY(cudaStreamSynchronize(st));
+            S->d2h_bytes += (int64_t)(sizeof(double) * hc.size());
+            if (S->prof.on) S->prof.flush();
+            ++S->krylov_steps;
+            double* h = &H[(size_t)j * (R + 1)];  // column j of the Hessenberg matrix
+            for (int i = 0; i <= j; ++i) h[i] = -(hc[i] + hc[R + 2 + i]);
+            h[j + 1] = std::sqrt(hc[2 * (R + 2)]);
+            if (!std::isfinite(h[j + 1])) return 0;
+            for (int i = 0; i < j; ++i) {  // earlier rotations
+                const double a = cs[i] * h[i] + sn[i] * h[i + 1];
+                h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+                h[i] = a;
+            }
+            const double rr = std::hypot(h[j], h[j + 1]);
+            cs[j] = rr > 0.0 ? h[j] / rr : 1.0;
+            sn[j] = rr > 0.0 ? h[j + 1] / rr : 0.0;
+            h[j] = rr;
+            h[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            k = j + 1;
+            if (std::fabs(g[j + 1]) <= target || !(hc[2 * (R + 2)] > 0.0)) break;
+        }
+        // y = R⁻¹ g, x += M⁻¹ V y
+        for (int i = k - 1; i >= 0; --i) {
+            double a = g[i];
+            for (int c = i + 1; c < k; ++c) a -= H[(size_t)c * (R + 1) + i] * y[c];
+            y[i] = a / H[(size_t)i * (R + 1) + i];
+        }
+        QOCO_CUDA_TRY(cudaMemcpyAsync(S->kv_y, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        S->launches += launch_combination(V, ld, k, S->kv_y, S->kv_z, N, st);
+        if ((rc = tri_solve(S, S->kv_z, x, true, st))) return rc;
+    }
+    if ((rc = refine_residual(S, x, r, S->res, st))) return rc;
+    if ((rc = sync_scalars(S, st))) return rc;
+    if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
+    *ok = S->h_S->refine_done && std::isfinite(S->h_S->berr);
+    return 0;
+}
+
 // x = K_ε⁻¹ r refined against K until the backward error target (r, x device, N).  On a
-// factor with FP32 large fronts, a refinement that misses the target refactors in FP64
-// (for the rest of the current solve) and starts over.
+// factor with FP32 large fronts, a plain refinement that stalls (the backward error not
+// halving in a step) or misses the target goes on with GMRES refinement; if that misses
+// too, the solve refactors in FP64 (for the rest of the current solve) and starts over.
 int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st) {
     for (;;) {
         int rc0 = tri_solve(S, r, x, false, st);
         if (rc0) return rc0;
         int steps = 0;
+        double prev = INFINITY;
         for (;;) {
-            {
-                Phase ph(S, QOCO_GPU_PHASE_ROW, st);
-                const int nl = launch_spmv_res(S->kv, S->lpr, x, r, S->res, S->partial, S->partial_cap, S->d_S, st);
-                if (nl < 0) return QOCO_GPU_ERR_INVALID_ARG;
-                S->launches += nl;
-            }
-            QOCO_CUDA_TRY(cudaGetLastError());
-            int rc = sync_scalars(S, st);
+            int rc = refine_residual(S, x, r, S->res, st);
             if (rc) return rc;
+            QOCO_CUDA_TRY(cudaGetLastError());
+            if ((rc = sync_scalars(S, st))) return rc;
             if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
             if (S->h_S->refine_done || steps >= S->st.max_refine) break;
+            // an FP32 factor whose refinement no longer halves the error: GMRES takes over
+            if (S->plan.big_fp32 && S->kv_basis && steps >= 2 && !(S->h_S->berr < 0.5 * prev)) break;
+            prev = S->h_S->berr;
             if ((rc = tri_solve(S, S->res, x, true, st))) return rc;
             ++steps;
         }
         S->refine_steps += steps;
         S->last_berr = S->h_S->berr;
-        const bool ok = S->h_S->refine_done && std::isfinite(S->h_S->berr);
+        bool ok = S->h_S->refine_done && std::isfinite(S->h_S->berr);
+        if (!ok && S->plan.big_fp32 && S->kv_basis && std::isfinite(S->h_S->berr)) {
+            int rc = gmres_refine(S, r, x, st, &ok);
+            if (rc) return rc;
+            S->last_berr = S->h_S->berr;
+        }
         if (ok || !S->plan.big_fp32) return 0;
         S->plan.big_fp32 = false;
         ++S->fp64_escalations;
@@ -878,7 +969,90 @@ int reset_barrier(qoco_gpu_solver* S, cudaStream_t st) {
     return 0;
 }
 
+int fused_grid_index(int nw) { return nw == 2 ? 0 : nw == 4 ? 1 : 2; }
+
+// the batched kernel with tile configuration (nw, split) over the first nb instances of the
+// queue (all of them for a solve, a sample when tuning)
+int launch_fused(qoco_gpu_solver* S, int nw, int split, int nb, cudaStream_t st) {
+    BatchIPMArgs A = S->bargs;
+    const FactorPlan::InstSched& I = S->plan.isched[split ? 0 : 1];
+    A.lv_ptr = I.d_lv_ptr;
+    A.ent = I.d_ent;
+    A.sched = I.d_sched;
+    A.B.nb = nb;
+    const int grid = std::min(nb, S->fused_grid[fused_grid_index(nw)]);
+    return launch_batch_ipm(A, nw, grid, st);
+}
+
+// Tile configuration of the batched kernel: warps per CTA (2, 4, 8; more warps share an
+// instance's levels, fewer let more instances run side by side) × whether fronts of order
+// ≤ 8 get one thread each; each candidate solves the first (largest) instances of the
+// queue twice and the one with the fastest second run is kept.
+int tune_fused(qoco_gpu_solver* S, cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    QOCO_CUDA_TRY(cudaEventCreate(&e0));
+    QOCO_CUDA_TRY(cudaEventCreate(&e1));
+    const int sample = std::min(S->bv.nb, 1024);
+    float best = 0.0f;
+    int rc = 0, c = 0;
+    for (int nw : {2, 4, 8})
+        for (int split = 0; split < 2 && !rc; ++split, ++c) {
+            if (!S->fused_grid[fused_grid_index(nw)]) continue;
+            float ms = 0.0f;
+            for (int rep = 0; rep < 2 && !rc; ++rep) {
+                QOCO_CUDA_TRY(cudaEventRecord(e0, st));
+                const int nl = launch_fused(S, nw, split, sample, st);
+                if (nl < 0) { rc = nl; break; }
+                QOCO_CUDA_TRY(cudaEventRecord(e1, st));
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = QOCO_GPU_ERR_CUDA;
+                else cudaEventElapsedTime(&ms, e0, e1);
+            }
+            S->fused_tune_ms[c] = ms;
+            if (!rc && (!S->fused_nw || ms < best)) {
+                best = ms;
+                S->fused_nw = nw;
+                S->fused_split = split;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    QOCO_CUDA_TRY(cudaGetLastError());
+    return S->fused_nw ? 0 : QOCO_GPU_ERR_CUDA;
+}
+
+// One batched solve: the persistent kernel, the per-batch summary and its read-back,
+// replayed from a CUDA graph captured at the first solve (after the tuning).
+int run_fused(qoco_gpu_solver* S, cudaStream_t st) {
+    int rc;
+    if (!S->fused_nw && (rc = tune_fused(S, st))) return rc;
+    if (!S->bgraph.exec) {
+        rc = capture_graph(S, &S->bgraph, [&](cudaStream_t cs) {
+            const int nl = launch_fused(S, S->fused_nw, S->fused_split, S->bv.nb, cs);
+            if (nl < 0) return nl;
+            launch_batch_summary(S->bv, S->d_S, cs);
+            if (cudaMemcpyAsync(S->h_S, S->d_S, sizeof(IPMScalars), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+                return (int)QOCO_GPU_ERR_CUDA;
+            return nl + 1;
+        });
+        if (rc) return rc;
+    }
+    QOCO_CUDA_TRY(cudaGraphLaunch(S->bgraph.exec, st));
+    QOCO_CUDA_TRY(cudaStreamSynchronize(st));
+    S->launches += S->bgraph.launches;
+    S->d2h_bytes += (int64_t)sizeof(IPMScalars);
+    const IPMScalars& h = *S->h_S;
+    S->info.iters = h.max_iters;
+    S->info.gap = h.gap;
+    S->info.pobj = S->info.dobj = S->info.pres = S->info.dres = 0.0;
+    S->info.batch_schedule_used = 6;
+    if (h.nonfinite) return QOCO_GPU_ERR_NUMERICAL;
+    if (h.converged) return QOCO_GPU_SOLVED;
+    return h.converged_inacc ? QOCO_GPU_SOLVED_INACCURATE : QOCO_GPU_MAX_ITER;
+}
+
 int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
+    if (S->batch && S->fused) return run_fused(S, st);
     const int n = S->n, p = S->p, m = S->m, N = S->N;
     const ConeView& cv = S->cv;
     const int cl = cone_launch_count(cv);
@@ -886,6 +1060,7 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
     S->refine_steps = 0;
     S->fp32_factors = 0;
     S->fp64_escalations = 0;
+    S->krylov_steps = 0;
     S->plan.big_fp32 = S->st.mixed_precision != 0 && S->plan.max_big_f > 0 && S->plan.big_work32;
     if ((rc = reset_barrier(S, st))) return rc;
     // initial point: K(W = I) [x; y; z] = [−c; b; h], s = −z, shift s and z into the cone
@@ -1036,6 +1211,7 @@ void fill_info(const qoco_gpu_solver* S, qoco_gpu_info* info) {
     info->d2h_bytes = S->d2h_bytes;
     info->fp32_factors = S->fp32_factors;
     info->fp64_escalations = S->fp64_escalations;
+    info->krylov_steps = S->krylov_steps;
     snprintf(info->message, sizeof info->message, "%s", S->msg.c_str());
 }
 
@@ -1223,10 +1399,19 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
         for (int k = T.ko[i]; k < T.ko[i + 1]; ++k) soc[k] = i;
     }
     if ((rc = dcopy(S, &pi, row))) return rc; B.inst_row = pi;
-    if (S->st.batch_schedule >= 0 && S->st.batch_schedule < kSharedSchedule &&
-        (rc = plan_batch_instances(S, nb, row)))
-        return rc;
-    S->info.batch_schedule_used = S->plan.inst ? S->st.batch_schedule : kSharedSchedule;
+    const int bs = S->st.batch_schedule;
+    if ((bs >= 0 && bs < kSharedSchedule) || bs == 6)
+        if ((rc = plan_batch_instances(S, nb, row))) return rc;
+    const bool want_fused = bs == 0 || bs == 6;
+    if (want_fused && S->plan.inst) {
+        for (int nw : {2, 4, 8})
+            if ((rc = batch_ipm_grid(nw, S->plan.inst_fmax, nb, &S->fused_grid[fused_grid_index(nw)]))) return rc;
+        S->fused = S->fused_grid[0] || S->fused_grid[1] || S->fused_grid[2];
+    }
+    // the factorisation entry points outside a batched solve (kkt_factor_at, backward)
+    // use the shared kernels when the persistent kernel runs the solves
+    if (want_fused) S->plan.inst_variant = kSharedSchedule;
+    S->info.batch_schedule_used = S->fused ? 6 : S->plan.inst ? bs : kSharedSchedule;
     if (L) { if ((rc = dcopy(S, &pi, orth))) return rc; S->cv.inst_orth = pi; }
     if (T.nsoc) { if ((rc = dcopy(S, &pi, soc))) return rc; S->cv.inst_soc = pi; }
     double** vd[] = {&B.pobj, &B.dobj, &B.gap, &B.mu, &B.alpha_max, &B.sigma_mu, &B.alpha};
@@ -1240,6 +1425,30 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
     S->batch = true;
     S->batch_L = L;
     S->h_xo = T.xo; S->h_yo = T.yo; S->h_lo = T.lo; S->h_ko = T.ko; S->h_so = T.so;
+    if (S->fused) {
+        BatchIPMArgs& A = S->bargs;
+        A.K = S->kv;
+        A.C = S->cv;
+        A.F = S->fv;
+        A.B = B;
+        A.L = L;
+        A.order = S->plan.d_inst_order;
+        A.next = S->plan.d_inst_next;
+        A.w2slot = S->d_w2slot;
+        A.w2ptr = S->d_w2ptr;
+        A.kval = S->d_val;
+        A.c = S->d_c; A.b = S->d_b; A.h = S->d_h;
+        A.xyz = S->xyz; A.s = S->s;
+        A.d_aff = S->d_aff; A.ds_aff = S->ds_aff; A.d_cmb = S->d_cmb; A.ds_cmb = S->ds_cmb;
+        A.r = S->r; A.rhs = S->rhs; A.wbar = S->wbar; A.eta = S->eta; A.lam = S->lam;
+        A.t = S->t; A.t1 = S->t1; A.t2 = S->t2;
+        A.sol_w = S->sol_w; A.sol_xp = S->sol_xp; A.res = S->res;
+        A.abstol = S->st.abstol; A.reltol = S->st.reltol;
+        A.abstol_inacc = S->st.abstol_inacc; A.reltol_inacc = S->st.reltol_inacc;
+        A.refine_tol = S->st.refine_tol; A.step_fraction = S->st.step_fraction;
+        A.max_iter = S->st.max_iter; A.max_refine = S->st.max_refine;
+        A.fmax = S->plan.inst_fmax;
+    }
     return 0;
 }
 
@@ -1660,6 +1869,7 @@ int qoco_gpu_cleanup(qoco_gpu_solver* S) {
     if (!S) return 0;
     for (auto& g : S->fgraph) if (g.exec) cudaGraphExecDestroy(g.exec);
     for (auto& g : S->sgraphs) if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (S->bgraph.exec) cudaGraphExecDestroy(S->bgraph.exec);
     if (S->cap_stream) cudaStreamDestroy(S->cap_stream);
     for (void* p : S->allocs) cudaFree(p);
     if (S->h_S) cudaFreeHost(S->h_S);

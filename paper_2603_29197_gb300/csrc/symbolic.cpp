@@ -268,8 +268,8 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int t
     // a rank-1 update of the whole merged front).  The merged fronts' columns are then
     // made contiguous by re-emitting the columns in a topological order of the merged
     // tree (external children first, then every member's columns, children before
-    // parents).
-    {
+    // parents).  The natural ordering is kept as given (no re-emission).
+    if (used != QOCO_GPU_ORDER_NATURAL) {
         constexpr int kAbsorbRows = 1024, kAbsorbCols = 256;
         const int nsn = (int)stack.size();
         std::vector<int> scol(N);

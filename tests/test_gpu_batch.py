@@ -9,6 +9,9 @@ interior-point loop with per-instance scalars, through the C ABI.
   the same solution to rounding as a stand-alone solve.
 * The MPC batch of 4096 instances (horizons U{10..60}, state 4, control 2, Q³ input cone,
   box bounds) solves every instance; a seeded sample of 24 instances matches the oracle.
+* The persistent batched kernel (one launch per batched solve, the default when every
+  front fits one warp) and each of its tile configurations match the oracle instance by
+  instance, are bitwise reproducible, and agree with the level-loop schedules.
 """
 import numpy as np
 import pytest
@@ -94,11 +97,11 @@ def test_mpc_batch_4096(q):
     S.close()
 
 
-@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5, 6])
 def test_batch_schedules_match_the_oracle(q, schedule):
     """Every layout of the per-instance factor/solve kernels (4 or 8 warps per CTA,
-    tiny fronts one per thread or every front one warp) and the shared kernels solve the
-    same instances to the oracle's tolerances."""
+    tiny fronts one per thread or every front one warp), the shared kernels and the
+    persistent batched kernel solve the same instances to the oracle's tolerances."""
     probs = mpc_batch(count=48, tmin=10, tmax=60, seed=21)
     S = q.BatchSolver(probs, batch_schedule=schedule)
     assert S.solve() == 0
@@ -114,21 +117,42 @@ def test_batch_schedules_match_the_oracle(q, schedule):
     S.close()
 
 
-def test_batch_schedule_autotune_picks_a_candidate(q):
-    probs = mpc_batch(count=32, tmin=10, tmax=60, seed=22)
+def test_persistent_batched_kernel_is_the_default_and_reproducible(q):
+    """Batches whose fronts all fit one warp are solved by the persistent kernel (one
+    launch per batched solve, its tile configuration autotuned at the first solve):
+    repeated solves are bitwise equal, and every instance agrees with the level-loop
+    shared kernels (schedule 5) to 1e-8 with the same iteration count up to one."""
+    probs = mpc_batch(count=96, tmin=10, tmax=60, seed=22)
     S = q.BatchSolver(probs)
-    assert S.info()["batch_schedule_used"] == 0  # chosen on the first factorisation
+    assert S.info()["batch_schedule_used"] == 6
     assert S.solve() == 0
-    used = S.info()["batch_schedule_used"]
-    assert used in (1, 2, 3, 4, 5)
-    sols = S.instance_solutions()
-    T = q.BatchSolver(probs, batch_schedule=used)
-    assert T.solve() == 0
-    for a, b in zip(sols, T.instance_solutions()):
+    first = [dict((k, v.copy()) for k, v in d.items()) for d in S.instance_solutions()]
+    assert S.solve() == 0
+    assert S.info()["kernel_launches"] <= 3  # the batched kernel, the summary (one graph)
+    for a, b in zip(first, S.instance_solutions()):
         for k in ("x", "y", "z", "s"):
-            assert np.array_equal(a[k], b[k])  # the tuned run is the fixed candidate's run
+            assert np.array_equal(a[k], b[k])
+    fi = S.batch_info()
+    T = q.BatchSolver(probs, batch_schedule=5)
+    assert T.solve() == 0
+    ti = T.batch_info()
+    for i, (a, b) in enumerate(zip(first, T.instance_solutions())):
+        assert abs(int(fi["iters"][i]) - int(ti["iters"][i])) <= 1, i
+        for k in ("x", "y", "z"):
+            assert rel_inf(a[k], b[k]) <= 1e-8, (i, k)
     S.close()
     T.close()
+
+
+@pytest.mark.parametrize("wait_polls", [1])
+def test_persistent_batched_kernel_needs_no_device_waits(q, wait_polls):
+    """The persistent kernel's CTAs never wait on one another (each owns whole
+    instances), so even a one-poll wait budget leaves its solves unaffected."""
+    probs = mpc_batch(count=40, tmin=10, tmax=60, seed=24)
+    S = q.BatchSolver(probs, wait_polls=wait_polls)
+    assert S.solve() == 0
+    assert np.all(S.batch_info()["status"] == 0)
+    S.close()
 
 
 def test_batch_with_a_front_beyond_one_warp_uses_the_shared_kernels(q):

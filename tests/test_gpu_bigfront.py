@@ -67,6 +67,34 @@ def test_large_front_factor_matches_textbook_ldlt(mixed):
     S.close()
 
 
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_large_front_factor_backward_error(mixed):
+    """The computed factor of one 4000-row front is a small perturbation of K_ε, entry by
+    entry: |L·D·Lᵀ − K_ε|_ij ≤ tol·(|L|·|D|·|L|ᵀ)_ij (LDLᵀ without pivoting is backward
+    stable in that sense), tol = 1e-13 in FP64 and 5e-5 for FP32 fronts whose trailing
+    updates run on the tensor cores as three TF32 products (one TF32 product would leave
+    ~1e-3).  The first outer panel's trailing matrix has 3744 rows: 240 tensor-core tiles
+    of 128×256, so every CTA of the persistent kernel takes more than one tile and both
+    tensor-memory accumulators, diagonal and ragged tiles are exercised."""
+    import paper_2603_29197_gb300 as q
+    prob = dense_qp(n=1500, p=300, m=2200, rank=20, density=0.05, seed=5)
+    s, z, _, _ = random_cone_iterate(prob.l, prob.q, seed=6)
+    S = q.Solver(prob, ordering=q.ORDER_NATURAL, mixed_precision=mixed)
+    assert S.info()["max_front"] >= 3900
+    S.kkt_factor_at(T(s), T(z))
+    perm, L, D = S.factor_dense()
+    sg = ok.reg_signs(prob)
+    Ke = (_K(prob, s, z).toarray() + 1e-8 * np.diag(sg))[np.ix_(perm, perm)]
+    R = L @ (D[:, None] * L.T)
+    A = np.abs(L) @ (np.abs(D)[:, None] * np.abs(L).T)
+    nz = A > 0
+    err = float(np.max(np.abs(R - Ke)[nz] / A[nz]))
+    assert err <= (5e-5 if mixed else 1e-13), err
+    if mixed:
+        assert err >= 1e-9  # the front really ran in FP32
+    S.close()
+
+
 CASES = {
     "dense_qp_natural": (lambda: dense_qp(seed=1), dict(ordering=3)),
     "lasso_r500_c1000": (lambda: lasso_qp(rows=500, cols=1000, density=1e-2, seed=2), {}),

@@ -1,14 +1,16 @@
 """Full-size parity in the launch configuration bench.py times: the trajectory SOCP
-with N = 20000 stages (N_K = 540018) against stored oracle values
-(tests/golden/*.json, written by tests/golden/make_golden.py, which calls only the
-oracle), plus an independent KKT certificate of the returned point."""
+with N = 20000 stages (N_K = 540018), the portfolio SOCP with n = 20000 and the lasso
+QP scaled by 1/10 (F 5000x10000) against stored oracle values (tests/golden/*.json and
+every entry of x, y, z in tests/golden/*.npz, written by tests/golden/make_golden.py,
+which calls only the oracle), plus an independent KKT certificate of the returned
+point."""
 import json
 import os
 
 import numpy as np
 import pytest
 
-from workloads import portfolio_socp, trajectory_socp
+from workloads import lasso_qp, portfolio_socp, trajectory_socp
 
 from _gpu_util import assert_certificate
 
@@ -18,6 +20,7 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 CASES = {
     "trajectory_socp_N20000": lambda: trajectory_socp(N=20000, seed=0),
     "portfolio_socp_n20000": lambda: portfolio_socp(n=20000, k=200, seed=0),
+    "lasso_qp_r5000_c10000": lambda: lasso_qp(rows=5000, cols=10000, density=5e-3, seed=0),
 }
 
 
@@ -44,5 +47,14 @@ def test_full_size_against_oracle_golden(name):
         ref = np.asarray(g[f"{key}_val"])
         scale = max(1.0, g[f"{key}_inf"])
         assert np.max(np.abs(sol[key][idx] - ref)) <= 1e-5 * scale, key
+    full = os.path.join(GOLDEN, name + ".npz")
+    if os.path.exists(full):
+        with np.load(full) as z:
+            for key in ("x", "y", "z"):
+                ref = z[key]
+                assert sol[key].shape == ref.shape, key
+                if ref.size:
+                    d = np.max(np.abs(sol[key] - ref)) / max(1.0, float(np.max(np.abs(ref))))
+                    assert d <= 1e-5, (key, d)
     assert abs(info["iters"] - g["iters"]) <= 4, (info["iters"], g["iters"])
     assert_certificate(prob, sol)

@@ -183,3 +183,48 @@ def test_kkt_certificate_at_termination(make):
     r = ipm.solve(prob)
     assert r.status == "solved"
     certificate(prob, r)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: dense_qp(n=40, p=10, m=60, rank=5, density=0.2, seed=3),
+    lambda: trajectory_socp(N=30, seed=4),
+    lambda: portfolio_socp(n=60, k=8, seed=5),
+])
+def test_directions_satisfy_the_linearised_newton_system(make):
+    """Both search directions of an iteration (affine d_s = −λ∘λ and a combined one with
+    the Mehrotra term and centring) solve the linearised optimality conditions at the
+    current point, checked with the problem's dense matrices:
+        PΔx + AᵀΔy + GᵀΔz = −r_x,  AΔx = −r_y,  GΔx + Δs = −r_z,  λ∘(WΔz + W⁻¹Δs) = d_s.
+    A dropped or mis-signed term anywhere in the direction's right-hand side or in the
+    Δs recovery breaks one of the four."""
+    from oracle import kkt as kktmod
+    from workloads import random_cone_iterate
+    prob = make()
+    rng = np.random.default_rng(7)
+    n, p, m, l, q = prob.n, prob.p, prob.m, prob.l, prob.q
+    x, y = rng.standard_normal(n), rng.standard_normal(p)
+    s, z, _, _ = random_cone_iterate(l, q, seed=9)
+    Pu = prob.P.toarray()
+    P = np.triu(Pu) + np.triu(Pu, 1).T
+    A, G = prob.A.toarray(), prob.G.toarray()
+    rx = P @ x + prob.c + A.T @ y + G.T @ z
+    ry = A @ x - prob.b
+    rz = G @ x + s - prob.h
+    W = cones.NTScaling(s, z, l, q)
+    K = kktmod.assemble(prob, kktmod.z_block(W, m))
+    ks = kktmod.KKTSolver(K, kktmod.reg_signs(prob), 1e-8, 10, 1e-12)
+    lam = W.lam
+    e = cones.identity(l, q)
+    ds_aff = -cones.jordan_product(lam, lam, l, q)
+    dx_a, dy_a, dz_a, dsa = ipm.newton_direction(prob, W, ks, rx, ry, rz, ds_aff)
+    corr = cones.jordan_product(W.apply_Winv(dsa), W.apply_W(dz_a), l, q)
+    ds_cmb = ds_aff - corr + 0.3 * float(s @ z) / cones.degree(l, q) * e
+    for ds in (ds_aff, ds_cmb):
+        dx, dy, dz, dsv = ipm.newton_direction(prob, W, ks, rx, ry, rz, ds)
+        sc = 1.0 + max(np.abs(rx).max(), np.abs(rz).max(), np.abs(dx).max(), np.abs(dz).max())
+        assert np.abs(P @ dx + A.T @ dy + G.T @ dz + rx).max() <= 1e-8 * sc
+        if p:
+            assert np.abs(A @ dx + ry).max() <= 1e-8 * sc
+        assert np.abs(G @ dx + dsv + rz).max() <= 1e-8 * sc
+        lhs = cones.jordan_product(lam, W.apply_W(dz) + W.apply_Winv(dsv), l, q)
+        assert np.abs(lhs - ds).max() <= 1e-8 * (1.0 + np.abs(ds).max())
