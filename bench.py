@@ -501,7 +501,7 @@ def lasso_certificate(prob, x_all, pobj):
     x = np.asarray(x_all[:F.shape[1]], float)
     res = F @ x - y
     g = F.T @ res
-    supp = np.abs(x) > 1e-6 * max(1.0, float(np.max(np.abs(x))))
+    supp = np.abs(x) > 1e-3 * float(np.max(np.abs(x)))  # the clear support
     obj = 0.5 * float(res @ res) + lam * float(np.abs(x).sum())
     return {"max_abs_g_over_lambda_minus_1": float(np.max(np.abs(g)) / lam - 1.0),
             "support": int(supp.sum()),
@@ -734,6 +734,8 @@ def run_other(args, ws, rank, local):
            "fp32_factors": info["fp32_factors"], "fp64_escalations": info["fp64_escalations"],
            "krylov_steps": info["krylov_steps"], "refine_steps": info["refine_steps"],
            "batch_schedule": info["batch_schedule_used"] if batch else None,
+           "batch_tile": ({"warps_per_cta": info["batch_warps"], "thread_fronts": info["batch_thread_fronts"],
+                           "warps_per_sm": info["batch_warps_per_sm"]} if batch else None),
            "l2": "flushed between timed steps (256 MiB write)",
            "parallelism": ("single GPU" if ws == 1 else
                            f"one job of {ws} x 4096 instances in {ws} contiguous ranges balanced by N_K^3, "

@@ -85,22 +85,35 @@ typedef struct {
                                            before it gives up and the call returns
                                            QOCO_GPU_ERR_DEVICE_TIMEOUT; ≤ 0 = 20000000, about a
                                            second (default 0) */
-    int verbose;                        /* 0: silent; 1: one line per iteration on stdout */
-    int mixed_precision;                /* 1: fronts of order ≥ 160 factored in FP32 (FP32
-                                           accumulation, trailing updates on the tensor cores
-                                           as three TF32 products), solves and refinement in
-                                           FP64; a solve whose plain refinement stalls or
-                                           misses refine_tol within max_refine steps goes on
-                                           with restarted GMRES on K preconditioned by the
-                                           factor (≤ 3 cycles of 30); if that misses too, it
-                                           refactors in FP64 and the rest of that
-                                           qoco_gpu_solve stays FP64 (default 0) */
+    int verbose;                        /* 0: silent; 1: one line per iteration on stdout;
+                                           2: also one line per refinement of a solve */
+    int mixed_precision;                /* 1: fronts of order ≥ 160 factored in FP32 (scaled
+                                           to a unit diagonal, FP32 accumulation, trailing
+                                           updates on the tensor cores as three TF32 products,
+                                           pivots below 1e-5 of the scaled diagonal replaced),
+                                           solves and refinement in FP64; a solve whose plain
+                                           refinement stalls or misses refine_tol within
+                                           max_refine steps goes on with restarted GMRES on K
+                                           preconditioned by the factor (≤ 3 cycles of 30); if
+                                           that misses too, it refactors in FP64; the next
+                                           iteration factors in FP32 again unless the last two
+                                           FP32 factorisations failed.  Batches on the
+                                           persistent kernel factor every front in FP32 and
+                                           refactor an instance in FP64 when its refinement
+                                           misses (default 0) */
+    double mixed_reg;                   /* mixed precision: δ added to the diagonal of each
+                                           scaled FP32 front (unit diagonal), with the pivot's
+                                           sign (+ on x rows, − on y and z rows): a quasidefinite
+                                           shift that bounds the FP32 elimination's growth; the
+                                           refinement against the unregularised K removes it
+                                           (default 0) */
     int batch_schedule;                 /* schedule of a batch (qoco_gpu_setup_batch) whose
                                            fronts all fit one warp: 0 or 6 = one persistent
                                            kernel per batched solve, each CTA running whole
                                            instances' interior-point iterations on chip (its
-                                           tile configuration — warps per CTA, thread fronts —
-                                           timed on a sample at the first solve); 1–5 = the
+                                           tile configuration — warps per CTA, registers per
+                                           thread — timed on the whole batch at the first
+                                           solve); 1–5 = the
                                            host-driven iteration loop with per-instance factor
                                            and solve kernels, one CTA per instance at a time
                                            (1: 4 warps per CTA, fronts of order ≤ 8 one per
@@ -135,6 +148,9 @@ typedef struct {
     int batch_schedule_used;    /* batches: the schedule in use (1–6 as in the settings) */
     int krylov_steps;           /* GMRES iterations of the last solve (refinement of solves
                                    whose factor has FP32 large fronts, see mixed_precision) */
+    int batch_warps;            /* batches on the persistent kernel, as chosen by its tuning:   */
+    int batch_thread_fronts;    /* warps per CTA, whether fronts of order ≤ 8 get one thread, */
+    int batch_warps_per_sm;     /* and the resident warps per SM it was compiled for (16, 32)  */
     char message[160];
 } qoco_gpu_info;
 

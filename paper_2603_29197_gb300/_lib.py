@@ -40,6 +40,7 @@ class Settings(C.Structure):
                 ("max_refine", C.c_int), ("refine_tol", C.c_double),
                 ("step_fraction", C.c_double), ("ordering", C.c_int), ("nd_leaf", C.c_int),
                 ("wait_polls", C.c_int64), ("verbose", C.c_int), ("mixed_precision", C.c_int),
+                ("mixed_reg", C.c_double),
                 ("batch_schedule", C.c_int)]
 
 
@@ -56,7 +57,9 @@ class Info(C.Structure):
                 ("last_backward_error", C.c_double), ("kernel_launches", C.c_int64),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
                 ("large_fronts", C.c_int), ("fp32_factors", C.c_int), ("fp64_escalations", C.c_int),
-                ("batch_schedule_used", C.c_int), ("krylov_steps", C.c_int), ("message", C.c_char * 160)]
+                ("batch_schedule_used", C.c_int), ("krylov_steps", C.c_int),
+                ("batch_warps", C.c_int), ("batch_thread_fronts", C.c_int),
+                ("batch_warps_per_sm", C.c_int), ("message", C.c_char * 160)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "message"}

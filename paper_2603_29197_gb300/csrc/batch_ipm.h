@@ -30,14 +30,16 @@ struct BatchIPMArgs {
            *t2 = nullptr, *sol_w = nullptr, *sol_xp = nullptr, *res = nullptr;
     double abstol = 0, reltol = 0, abstol_inacc = 0, reltol_inacc = 0, refine_tol = 0, step_fraction = 0;
     int max_iter = 0, max_refine = 0, fmax = 1;
+    bool mixed = false;  // FP32 fronts, FP64 refinement, FP64 refactor of an instance on a miss
 };
 
-// Grid of the persistent kernel with nw ∈ {2, 4, 8} warps per CTA for fronts of order ≤
-// fmax (0 when it cannot run); sets the kernel's shared-memory attribute.
-int batch_ipm_grid(int nw, int fmax, int nb, int* grid);
+// Grid of the persistent kernel with nw ∈ {1, 2, 4} warps per CTA, compiled for 16 (dense
+// = 0) or 32 (dense = 1) resident warps per SM, for fronts of order ≤ fmax (0 when it cannot
+// run); sets the kernel's shared-memory attribute.
+int batch_ipm_grid(int nw, int dense, bool mixed, int fmax, int nb, int* grid);
 // One launch solving every instance (results in B: conv, conv_inacc, nonfinite, iters,
 // pobj, dobj, gap); resets the queue counter first.
-int launch_batch_ipm(const BatchIPMArgs& A, int nw, int grid, cudaStream_t st);
+int launch_batch_ipm(const BatchIPMArgs& A, int nw, int dense, int grid, cudaStream_t st);
 // Every-instance summary into S (converged, converged_inacc, nonfinite, max_iters, gap).
 int launch_batch_summary(const BatchView& B, IPMScalars* S, cudaStream_t st);
 

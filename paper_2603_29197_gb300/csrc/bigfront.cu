@@ -34,6 +34,10 @@ namespace {
 
 int nsm();               // SM count of the current device (queried once, outside captures)
 
+// smallest signed pivot accepted in a scaled FP32 front (its diagonal is ±1 before the
+// elimination); smaller ones are set to ±kFp32PivotFloor
+constexpr double kFp32PivotFloor = 1e-5;
+
 template <class T>
 __device__ __forceinline__ T rcp_t(T d);
 template <>
@@ -118,7 +122,10 @@ __global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorV
     }
     __syncthreads();
     int nreg = 0;
-    const T thr = (T)a.dyn_thresh, dval = (T)a.dyn_value;
+    // FP32 fronts are scaled to a unit diagonal: a pivot below kFp32PivotFloor there is
+    // rounding noise of the FP32 elimination, and is replaced like a breakdown
+    const T thr = sizeof(T) == 4 ? (T)fmax(a.dyn_thresh, kFp32PivotFloor) : (T)a.dyn_thresh;
+    const T dval = sizeof(T) == 4 ? (T)fmax(a.dyn_value, kFp32PivotFloor) : (T)a.dyn_value;
     auto pivot = [&](int k) {
         T d = D[k][k];
         const bool pos = s_sign[k] > 0;
@@ -165,8 +172,8 @@ __global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorV
 // k = j … nb−1 the rows i > k take x_i −= L_ik·x_k).  The panel's rows below use it
 // right away (k_big_l21x): their triangular solves become one parallel product.
 template <class T>
-__global__ void __launch_bounds__(256) k_big_panel_inverse(int s, int k0, int nb, FactorView a,
-                                                           const T* __restrict__ F, double* __restrict__ X) {
+__device__ __forceinline__ void panel_inverse_body(int s, int k0, int nb, const FactorView& a, const T* __restrict__ F,
+                                                   double* __restrict__ X, int jblock) {
     __shared__ double L[kBigNB][kBigNB + 1];
     __shared__ double xs[8][kBigNB];
     const int f = a.nrow[s];
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(256) k_big_panel_inverse(int s, int k0, int nb
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * 8 + w;
+    const int j = jblock * 8 + w;
     if (j >= kBigNB) return;
     double* x = xs[w];
     for (int i = lane; i < kBigNB; i += 32) x[i] = i == j ? 1.0 : 0.0;
@@ -187,6 +194,18 @@ __global__ void __launch_bounds__(256) k_big_panel_inverse(int s, int k0, int nb
         __syncwarp();
     }
     for (int i = lane; i < kBigNB; i += 32) X[(int64_t)i * kBigNB + j] = x[i];
+}
+template <class T>
+__global__ void __launch_bounds__(256) k_big_panel_inverse(int s, int k0, int nb, FactorView a,
+                                                           const T* __restrict__ F, double* __restrict__ X) {
+    panel_inverse_body<T>(s, k0, nb, a, F, X, blockIdx.x);
+}
+// every pivot block's inverse at once (blockIdx.y = block), from the finished FP64 front
+__global__ void __launch_bounds__(256) k_big_panel_inverse_all(int s, FactorView a, const double* __restrict__ F,
+                                                               double* __restrict__ Xall) {
+    const int c = a.ncol[s], k0 = blockIdx.y * kBigNB;
+    panel_inverse_body<double>(s, k0, min(kBigNB, c - k0), a, F, Xall + (int64_t)blockIdx.y * kBigNB * kBigNB,
+                               blockIdx.x);
 }
 
 // Tensor-core operands of an FP32 front's outer panel, row-major with leading dimension
@@ -246,6 +265,53 @@ __global__ void __launch_bounds__(128) k_big_l21x(int s, int k0, int nb, FactorV
             sp.Llo[o] = lf - lh;
             sp.Whi[o] = wh;
             sp.Wlo[o] = wf - wh;
+        }
+    }
+}
+
+// FP32 fronts: rows i ≥ k0+nb solved by forward substitution with the panel's unit-lower
+// diagonal block (w_i = a_i·L11⁻ᵀ, one thread per row, the block in shared memory, w in
+// registers), l_i = w_i D⁻¹ into F, w_i into W and the TF32 splits of both into sp.  No
+// explicit inverse of L11: with the scaled front's pivots down to the FP32 floor, such an
+// inverse can exceed the FP32 range where the substitution stays bounded.
+__global__ void __launch_bounds__(128) k_big_l21_subst(int s, int k0, int nb, FactorView a, float* __restrict__ F,
+                                                       float* __restrict__ W, SplitOut sp, int ldw) {
+    __shared__ float Ls[kBigNB][kBigNB + 1];
+    __shared__ float dv[kBigNB];
+    const int f = a.nrow[s], first = a.first[s];
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+        const int j = t / nb, i = t - j * nb;
+        Ls[i][j] = i > j ? F[(int64_t)(k0 + j) * f + k0 + i] : 0.0f;
+    }
+    for (int k = threadIdx.x; k < kBigNB; k += blockDim.x) dv[k] = k < nb ? (float)a.dinv[first + k0 + k] : 0.0f;
+    __syncthreads();
+    const int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f) return;
+    float w[kBigNB];
+#pragma unroll
+    for (int k = 0; k < kBigNB; ++k) w[k] = k < nb ? F[(int64_t)(k0 + k) * f + i] : 0.0f;
+#pragma unroll
+    for (int k = 1; k < kBigNB; ++k) {
+        float acc = w[k];
+#pragma unroll
+        for (int j = 0; j < k; ++j) acc -= Ls[k][j] * w[j];
+        w[k] = acc;
+    }
+    float* Wi = W + (int64_t)i * ldw;
+#pragma unroll
+    for (int k = 0; k < kBigNB; ++k) {
+        const int64_t o = (int64_t)i * ldw + k;
+        if (k < nb) {
+            const float l = w[k] * dv[k];
+            Wi[k] = w[k];
+            F[(int64_t)(k0 + k) * f + i] = l;
+            const float lh = tf32_head(l), wh = tf32_head(w[k]);
+            sp.Lhi[o] = lh;
+            sp.Llo[o] = l - lh;
+            sp.Whi[o] = wh;
+            sp.Wlo[o] = w[k] - wh;
+        } else if (k < sp.zero_to) {
+            sp.Lhi[o] = sp.Llo[o] = sp.Whi[o] = sp.Wlo[o] = 0.0f;
         }
     }
 }
@@ -764,19 +830,25 @@ __global__ void k_group_syrk_reduce(const double* __restrict__ part, int r, int 
 // FP32 fronts are factored scaled: with σ_i = 1/√|G_ii| of the assembled FP64 front G,
 // F = ΣGΣ has a unit diagonal (its entries stay inside the FP32 range whatever the
 // spread of the −W² block, 1e±16 near the end of a solve), and its LDLᵀ (L̃, D̃) gives
-// G's as L = Σ⁻¹L̃Σ, D = Σ⁻¹D̃Σ⁻¹, update block Σ⁻¹ŨΣ⁻¹ (and L₁₁⁻¹ = Σ⁻¹L̃₁₁⁻¹Σ).
+// G's as L = Σ⁻¹L̃Σ, D = Σ⁻¹D̃Σ⁻¹, update block Σ⁻¹ŨΣ⁻¹.
 __global__ void k_big_scale(const double* __restrict__ G, int f, double* __restrict__ sc) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < f; i += gridDim.x * blockDim.x) {
         const double d = fabs(G[(int64_t)i * f + i]);
         sc[i] = (d > 0.0 && isfinite(d)) ? 1.0 / sqrt(d) : 1.0;
     }
 }
-// F = ΣGΣ on the lower triangle (zeros above)
-__global__ void k_big_to32(const double* __restrict__ G, float* __restrict__ F, int f, const double* __restrict__ sc) {
+// F = ΣGΣ on the lower triangle (zeros above), plus the sign-aware shift δ on the
+// diagonal (mixed_reg)
+__global__ void k_big_to32(int s, FactorView a, const double* __restrict__ G, float* __restrict__ F, int f,
+                           const double* __restrict__ sc) {
+    const int first = a.first[s], c = a.ncol[s];
     const int64_t n = (int64_t)f * f;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / f), i = (int)(e - (int64_t)j * f);
-        F[e] = i >= j ? (float)(sc[i] * G[e] * sc[j]) : 0.0f;
+        double v = i >= j ? sc[i] * G[e] * sc[j] : 0.0;
+        // the shift only on the pivot columns: the update block goes to the parent exact
+        if (i == j && i < c && a.eps32 > 0.0) v += a.dsign[first + i] > 0 ? a.eps32 : -a.eps32;
+        F[e] = (float)v;
     }
 }
 // factored FP32 working front → the FP64 front storage, unscaled (lower triangle); the
@@ -800,15 +872,6 @@ __global__ void k_big_writeback(int s, FactorView a, const float* __restrict__ F
         } else {
             G[e] = v / (sc[i] * sc[j]);
         }
-    }
-}
-// the pivot blocks' unit-lower inverses X (row-major 64×64 per block) unscaled
-__global__ void k_big_linv_unscale(double* __restrict__ X, int c, const double* __restrict__ sc) {
-    const int64_t n = (int64_t)((c + kBigNB - 1) / kBigNB) * kBigNB * kBigNB;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(e / (kBigNB * kBigNB)), q = (int)(e - (int64_t)b * kBigNB * kBigNB);
-        const int i = b * kBigNB + q / kBigNB, j = b * kBigNB + q % kBigNB;
-        if (i < c && j < c && i > j) X[e] *= sc[j] / sc[i];
     }
 }
 
@@ -1157,10 +1220,8 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, int idx, T* F, T* W, 
             for (int k1 = k0; k1 < k0 + nbo; k1 += kBigNB) {
                 const int nb = std::min(kBigNB, k0 + nbo - k1);
                 k_big_diag<T><<<1, 256, 0, st>>>(s, k1, nb, a, F);
-                double* X = linv + (int64_t)(k1 / kBigNB) * kBigNB * kBigNB;
-                k_big_panel_inverse<T><<<kBigNB / 8, 256, 0, st>>>(s, k1, nb, a, F, X);
                 const int rows = f - k1 - nb;
-                launches += 2;
+                launches += 1;
                 if (rows <= 0) continue;
                 SplitOut sp;
                 sp.Lhi = P.big_split + (k1 - k0);
@@ -1170,8 +1231,8 @@ int big_factor_t(const FactorPlan& P, const FactorView& a, int idx, T* F, T* W, 
                 // the outer panel's last inner panel zero-fills its split columns up to 64 (the
                 // tensor-core K chunks of 32 reach past a ragged panel end)
                 sp.zero_to = (k1 + nb == k0 + nbo) ? kBigNB : 0;
-                k_big_l21x<T><<<(unsigned)((rows + 7) / 8), 128, 0, st>>>(s, k1, nb, a, F, W + (k1 - k0), sp,
-                                                                           kOuterNB, X);
+                k_big_l21_subst<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(s, k1, nb, a, (float*)F,
+                                                                                (float*)W + (k1 - k0), sp, kOuterNB);
                 ++launches;
                 const int cend = k0 + nbo;
                 if (k1 + nb < cend)
@@ -1249,13 +1310,14 @@ int launch_big_factor(const FactorPlan& P, const FactorView& a, const double* kv
         const int64_t ff = (int64_t)f * f;
         launches += big_assemble_t<double>(P, a, kval, idx, G, st);
         k_big_scale<<<gridfor(f, 256), 256, 0, st>>>(G, f, P.big_scale);
-        k_big_to32<<<gridfor(ff, 256), 256, 0, st>>>(G, F, f, P.big_scale);
+        k_big_to32<<<gridfor(ff, 256), 256, 0, st>>>(s, a, G, F, f, P.big_scale);
         launches += 2;
         launches += big_factor_t<float>(P, a, idx, F, (float*)P.big_w, st);
         k_big_writeback<<<gridfor(ff, 256), 256, 0, st>>>(s, a, F, G, f, c, P.big_scale);
+        // the solves' pivot-block inverses, from the unscaled FP64 L
         const int nblk = (c + kBigNB - 1) / kBigNB;
-        k_big_linv_unscale<<<gridfor((int64_t)nblk * kBigNB * kBigNB, 256), 256, 0, st>>>(
-            P.big_linv + P.big_linv_off[idx], c, P.big_scale);
+        if (nblk)
+            k_big_panel_inverse_all<<<dim3(kBigNB / 8, nblk), 256, 0, st>>>(s, a, G, P.big_linv + P.big_linv_off[idx]);
         launches += 2;
     } else {
         launches += big_assemble_t<double>(P, a, kval, idx, a.front + off, st);

@@ -45,6 +45,7 @@ struct FactorView {
     // reaches its large parent through the group's rank-K product), skipped elsewhere
     const signed char* skip = nullptr;
     double eps = 1e-8, dyn_thresh = 1e-13, dyn_value = 1e-7;
+    double eps32 = 0.0;  // sign-aware shift of the scaled FP32 large fronts' diagonal
 };
 
 struct FactorPlan {

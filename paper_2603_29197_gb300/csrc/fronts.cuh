@@ -26,8 +26,10 @@ __device__ __forceinline__ void tri_index(int t, int m, int& ii, int& jj) {
 
 // F[rel_j, rel_i] += U_ij over the lower triangle of a child's r×r update block (leading
 // dimension fc), spread over nt threads with four independent entries per step; the
-// block was written by another thread block (read through L2).
-__device__ __forceinline__ void extend_add(double* F, int f, const double* U, int fc, const int* rel, int r,
+// block was written by another thread block (read through L2).  T: the working type of
+// the front (FP64; FP32 for the mixed-precision batched kernel).
+template <class Real = double>
+__device__ __forceinline__ void extend_add(Real* F, int f, const double* U, int fc, const int* rel, int r,
                                            int tid, int nt) {
     const int T = r * (r + 1) / 2;
     for (int t = tid; t < T; t += 4 * nt) {
@@ -47,9 +49,14 @@ __device__ __forceinline__ void extend_add(double* F, int f, const double* U, in
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (off[u] >= 0) F[off[u]] += u4[u];
+            if (off[u] >= 0) F[off[u]] += (Real)u4[u];
     }
 }
+
+// reciprocal in the front's working type (FP64: two Newton steps from the approximate
+// reciprocal; FP32: the correctly rounded reciprocal)
+__device__ __forceinline__ double rcp_w(double d) { return recip(d); }
+__device__ __forceinline__ float rcp_w(float d) { return __frcp_rn(d); }
 
 // Pivot of column k (dynamic regularisation) and its reciprocal: computed once by the
 // calling thread; the caller broadcasts.  FP64 work on GB300 is scarce, so nothing is
@@ -100,23 +107,23 @@ __device__ __forceinline__ void tri_advance(int m, int stride, int& ii, int& jj)
 // threads apply column k to their rows: one barrier per column.  At the end of the
 // panel the columns are scaled in place (L) and their unscaled copy kept in W, then the
 // trailing rank-kPanel update gives each thread four independent entries per step.
-template <bool WARP>
-__device__ __forceinline__ int blocked_ldlt(double* F, double* W, double* bc, int f, int c, int first,
+template <bool WARP, class Real = double>
+__device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, int c, int first,
                                             const FactorView& a, int tid, int nt) {
     int nreg = 0;
     double* dinv = a.dinv + first;
-    double* sgn = bc + kPanel + 1;
-    for (int k = tid; k < c; k += nt) sgn[k] = a.dsign[first + k] > 0 ? 1.0 : -1.0;
+    Real* sgn = bc + kPanel + 1;
+    for (int k = tid; k < c; k += nt) sgn[k] = a.dsign[first + k] > 0 ? Real(1) : Real(-1);
     group_sync<WARP>();
     auto do_pivot = [&](int k) {  // thread 0 only
-        double* colk = F + (size_t)k * f;
-        double d = colk[k];
-        const bool pos = sgn[k] > 0.0;
-        const bool ok = pos ? (d >= a.dyn_thresh) : (d <= -a.dyn_thresh);
-        if (!ok) { d = pos ? a.dyn_value : -a.dyn_value; ++nreg; }
-        const double inv = recip(d);
+        Real* colk = F + (size_t)k * f;
+        Real d = colk[k];
+        const bool pos = sgn[k] > Real(0);
+        const bool ok = pos ? (d >= (Real)a.dyn_thresh) : (d <= -(Real)a.dyn_thresh);
+        if (!ok) { d = pos ? (Real)a.dyn_value : -(Real)a.dyn_value; ++nreg; }
+        const Real inv = rcp_w(d);
         colk[k] = d;
-        dinv[k] = inv;
+        dinv[k] = sizeof(Real) == 8 ? (double)inv : recip((double)d);
         bc[k % kPanel] = inv;
     };
     if (tid == 0 && c > 0) do_pivot(0);
@@ -125,11 +132,11 @@ __device__ __forceinline__ int blocked_ldlt(double* F, double* W, double* bc, in
         for (int p = 0; p < nb; ++p) {
             const int k = k0 + p;
             group_sync<WARP>();  // pivot k and column k final
-            const double* colk = F + (size_t)k * f;
-            const double inv = bc[k % kPanel];
+            const Real* colk = F + (size_t)k * f;
+            const Real inv = bc[k % kPanel];
             const int jend = k0 + nb;  // later columns of this panel: k+1 .. jend−1
             for (int i = k + 1 + tid; i < f; i += nt) {
-                const double l = colk[i] * inv;
+                const Real l = colk[i] * inv;
                 for (int j = k + 1; j < jend && j <= i; ++j) F[(size_t)j * f + i] -= l * colk[j];
                 if (i == k + 1 && k + 1 < jend) do_pivot(k + 1);  // i == k+1 only for tid 0
             }
@@ -138,10 +145,10 @@ __device__ __forceinline__ int blocked_ldlt(double* F, double* W, double* bc, in
         // scale the panel's columns (L) and keep their unscaled values in W
         for (int p = 0; p < nb; ++p) {
             const int k = k0 + p;
-            double* colk = F + (size_t)k * f;
-            const double inv = bc[k % kPanel];
+            Real* colk = F + (size_t)k * f;
+            const Real inv = bc[k % kPanel];
             for (int i = k + 1 + tid; i < f; i += nt) {
-                const double v = colk[i];
+                const Real v = colk[i];
                 W[i * kPanel + p] = v;
                 colk[i] = v * inv;
             }
@@ -150,11 +157,11 @@ __device__ __forceinline__ int blocked_ldlt(double* F, double* W, double* bc, in
         // trailing rank-nb update of rows/columns k0+nb .. f−1, four entries per thread
         const int base = k0 + nb, m = f - base;
         if (m > 0) {
-            const double* L0 = F + (size_t)k0 * f;
+            const Real* L0 = F + (size_t)k0 * f;
             const int T = m * (m + 1) / 2;
             for (int t = tid; t < T; t += 4 * nt) {
                 int ii[4], jj[4];
-                double acc[4];
+                Real acc[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int tu = t + u * nt;
@@ -164,8 +171,8 @@ __device__ __forceinline__ int blocked_ldlt(double* F, double* W, double* bc, in
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int i = base + ii[u], j = base + jj[u];
-                    const double* wr = W + j * kPanel;
-                    double x = F[(size_t)j * f + i];
+                    const Real* wr = W + j * kPanel;
+                    Real x = F[(size_t)j * f + i];
                     x -= L0[i] * wr[0];
                     if (nb > 1) x -= L0[f + i] * wr[1];
                     if (nb > 2) x -= L0[2 * f + i] * wr[2];
@@ -197,20 +204,20 @@ struct NoWait {
 // other fronts), wait() (the dataflow kernel waits there for the children), then the
 // extend-add of the children's update blocks (read through L2: in the dataflow kernel
 // they were written in the same launch) and the partial LDLᵀ.
-template <class Wait>
+template <class Wait, class Real = double>
 __device__ __forceinline__ bool thread_factor_front(int s, const FactorView& a, const double* __restrict__ kval,
                                                     const Wait& wait) {
     constexpr int LD = kThreadFront;
-    double F[LD * LD];
+    Real F[LD * LD];
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     for (int j = 0; j < f; ++j)
-        for (int i = j; i < f; ++i) F[j * LD + i] = 0.0;
+        for (int i = j; i < f; ++i) F[j * LD + i] = Real(0);
     for (int64_t e = a.amap_ptr[s]; e < a.amap_ptr[s + 1]; ++e) {
         const int off = (int)a.amap_off[e];
         const int col = off / f, row = off - col * f;
         double v = kval[a.amap_slot[e]];
         if (row == col) v += a.dsign[first + col] > 0 ? a.eps : -a.eps;
-        F[col * LD + row] = v;
+        F[col * LD + row] = (Real)v;
     }
     if (!wait()) return false;
     for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1]; ++k) {
@@ -219,24 +226,36 @@ __device__ __forceinline__ bool thread_factor_front(int s, const FactorView& a, 
         const double* U = a.front + a.front_off[ch] + (int64_t)cc * fc + cc;
         const int* rel = a.rel + a.upd_off[ch];
         for (int j = 0; j < r; ++j)
-            for (int i = j; i < r; ++i) F[rel[j] * LD + rel[i]] += __ldcg(U + j * fc + i);
+            for (int i = j; i < r; ++i) F[rel[j] * LD + rel[i]] += (Real)__ldcg(U + j * fc + i);
     }
     int nreg = 0;
     for (int k = 0; k < c; ++k) {
-        double d = F[k * LD + k], inv;
-        pivot(a, first + k, d, inv, nreg);
-        F[k * LD + k] = d;
-        a.dinv[first + k] = inv;
+        Real inv;
+        if constexpr (sizeof(Real) == 8) {
+            double d = F[k * LD + k], dinv;
+            pivot(a, first + k, d, dinv, nreg);
+            F[k * LD + k] = d;
+            a.dinv[first + k] = dinv;
+            inv = dinv;
+        } else {
+            Real d = F[k * LD + k];
+            const bool pos = a.dsign[first + k] > 0;
+            const bool ok = pos ? (d >= (Real)a.dyn_thresh) : (d <= -(Real)a.dyn_thresh);
+            if (!ok) { d = pos ? (Real)a.dyn_value : -(Real)a.dyn_value; ++nreg; }
+            F[k * LD + k] = d;
+            a.dinv[first + k] = recip((double)d);
+            inv = rcp_w(d);
+        }
         // rows from the bottom up, so F(j,k) with j < i is still unscaled when row i uses it
         for (int i = f - 1; i > k; --i) {
-            const double li = F[k * LD + i] * inv;
+            const Real li = F[k * LD + i] * inv;
             for (int j = k + 1; j <= i; ++j) F[j * LD + i] -= li * F[k * LD + j];
             F[k * LD + i] = li;
         }
     }
     double* G = a.front + a.front_off[s];
     for (int j = 0; j < f; ++j)
-        for (int i = 0; i < f; ++i) G[j * f + i] = i >= j ? F[j * LD + i] : 0.0;
+        for (int i = 0; i < f; ++i) G[j * f + i] = i >= j ? (double)F[j * LD + i] : 0.0;
     if (nreg) atomicAdd(a.nreg, nreg);
     return true;
 }
@@ -303,12 +322,12 @@ __host__ __device__ constexpr int wfactor_stride(int fmax) { return fmax * (fmax
 // warp-level variants for fronts of order ≤ kWarpFront (one warp per front, the front
 // in the warp's slice of shared memory, __syncwarp instead of block barriers)
 // ---------------------------------------------------------------------------
-template <class Wait>
+template <class Wait, class Real = double>
 __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, const double* __restrict__ kval,
-                                                  double* F, double* lk, int lane, const Wait& wait) {
+                                                  Real* F, Real* lk, int lane, const Wait& wait) {
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     const int ff = f * f;
-    for (int i = lane; i < ff; i += 32) F[i] = 0.0;
+    for (int i = lane; i < ff; i += 32) F[i] = Real(0);
     __syncwarp();
     // original entries (static regularisation on the diagonal): loads first, then stores
     {
@@ -327,7 +346,7 @@ __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, co
                 if (off[u] < 0) continue;
                 const int col = off[u] / f, row = off[u] - col * f;
                 if (row == col) v[u] += a.dsign[first + col] > 0 ? a.eps : -a.eps;
-                F[off[u]] = v[u];
+                F[off[u]] = (Real)v[u];
             }
         }
     }
@@ -351,12 +370,12 @@ __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, co
         const double* U = a.front + ci.u_off;
         const int* rel = a.rel + ci.rel_off;
         const int r = ci.r, fc = ci.fc;
-        extend_add(F, f, U, fc, rel, r, lane, 32);
+        extend_add<Real>(F, f, U, fc, rel, r, lane, 32);
         __syncwarp();
     }
-    const int nreg = blocked_ldlt<true>(F, lk, lk + kPanel * f, f, c, first, a, lane, 32);
+    const int nreg = blocked_ldlt<true, Real>(F, lk, lk + kPanel * f, f, c, first, a, lane, 32);
     double* G = a.front + a.front_off[s];
-    for (int i = lane; i < ff; i += 32) G[i] = F[i];
+    for (int i = lane; i < ff; i += 32) G[i] = (double)F[i];
     if (lane == 0 && nreg) atomicAdd(a.nreg, nreg);
     __syncwarp();
     return true;

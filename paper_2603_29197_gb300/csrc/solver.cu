@@ -257,14 +257,17 @@ struct qoco_gpu_solver {
     double *b_items = nullptr, *b_shift = nullptr, *b_aux = nullptr;
     std::vector<int> h_xo, h_yo, h_lo, h_ko, h_so;
     // the persistent batched kernel (batch_schedule 0 or 6): its arguments, the tile
-    // configuration picked at the first solve (warps per CTA, thread-front split), the
-    // persistent grid per warp count (2, 4, 8) and the captured launch graph
+    // configuration picked at the first solve (warps per CTA, thread-front split, resident
+    // warps per SM), the persistent grid per candidate and the captured launch graph
     bool fused = false;
     BatchIPMArgs bargs;
-    int fused_nw = 0, fused_split = 0;
-    int fused_grid[3] = {0, 0, 0};
-    double fused_tune_ms[6] = {0, 0, 0, 0, 0, 0};
+    int fused_nw = 0, fused_split = 0, fused_dense = 0;
+    int fused_grid[6] = {0, 0, 0, 0, 0, 0};  // [warp-count index · 2 + dense]
     int fp32_factors = 0, fp64_escalations = 0;
+    // mixed precision: FP32 large fronts allowed for this solve, and the number of
+    // consecutive FP32 factorisations whose refinement failed (two stop the retries)
+    bool mixed_ok = false;
+    int fp32_fail_streak = 0;
     // GMRES refinement (mixed precision): basis V ((restart + 1) × N), work vector, zero
     // vector, Hessenberg column / coefficients (device), dot-product partials
     double *kv_basis = nullptr, *kv_z = nullptr, *kv_zero = nullptr, *kv_h = nullptr, *kv_y = nullptr,
@@ -444,6 +447,7 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
     if ((rc = dalloc(S, &pd, (size_t)N))) return rc; f.dinv = pd;
     if ((rc = dalloc(S, &pi, 1))) return rc; f.nreg = pi;
     f.eps = S->st.static_reg;
+    f.eps32 = S->st.mixed_reg;
     f.dyn_thresh = S->st.dyn_reg_thresh;
     f.dyn_value = S->st.dyn_reg_value;
 
@@ -949,13 +953,23 @@ int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
         S->refine_steps += steps;
         S->last_berr = S->h_S->berr;
         bool ok = S->h_S->refine_done && std::isfinite(S->h_S->berr);
+        if (ok && S->plan.big_fp32) S->fp32_fail_streak = 0;
+        if (S->st.verbose >= 2)
+            printf("     refine: %d steps, backward error %.3e (%s factor)%s\n", steps, S->h_S->berr,
+                   S->plan.big_fp32 ? "FP32 large fronts" : "FP64", ok ? "" : " - target missed");
         if (!ok && S->plan.big_fp32 && S->kv_basis && std::isfinite(S->h_S->berr)) {
+            const int k0 = S->krylov_steps;
             int rc = gmres_refine(S, r, x, st, &ok);
             if (rc) return rc;
             S->last_berr = S->h_S->berr;
+            if (S->st.verbose >= 2)
+                printf("     GMRES: %d iterations, backward error %.3e%s\n", S->krylov_steps - k0, S->h_S->berr,
+                       ok ? "" : " - target missed, refactoring in FP64");
+            if (ok) S->fp32_fail_streak = 0;
         }
         if (ok || !S->plan.big_fp32) return 0;
         S->plan.big_fp32 = false;
+        ++S->fp32_fail_streak;
         ++S->fp64_escalations;
         int rc = factor_now(S, st);
         if (rc) return rc;
@@ -969,49 +983,57 @@ int reset_barrier(qoco_gpu_solver* S, cudaStream_t st) {
     return 0;
 }
 
-int fused_grid_index(int nw) { return nw == 2 ? 0 : nw == 4 ? 1 : 2; }
+int fused_grid_index(int nw, int dense) { return 2 * (nw == 1 ? 0 : nw == 2 ? 1 : 2) + dense; }
 
-// the batched kernel with tile configuration (nw, split) over the first nb instances of the
-// queue (all of them for a solve, a sample when tuning)
-int launch_fused(qoco_gpu_solver* S, int nw, int split, int nb, cudaStream_t st) {
+// the batched kernel with tile configuration (nw, split, dense) over the first nb instances
+// of the queue (all of them for a solve, a sample when tuning)
+int launch_fused(qoco_gpu_solver* S, int nw, int split, int dense, int nb, cudaStream_t st) {
     BatchIPMArgs A = S->bargs;
     const FactorPlan::InstSched& I = S->plan.isched[split ? 0 : 1];
     A.lv_ptr = I.d_lv_ptr;
     A.ent = I.d_ent;
     A.sched = I.d_sched;
     A.B.nb = nb;
-    const int grid = std::min(nb, S->fused_grid[fused_grid_index(nw)]);
-    return launch_batch_ipm(A, nw, grid, st);
+    const int grid = std::min(nb, S->fused_grid[fused_grid_index(nw, dense)]);
+    return launch_batch_ipm(A, nw, dense, grid, st);
 }
 
-// Tile configuration of the batched kernel: warps per CTA (2, 4, 8; more warps share an
-// instance's levels, fewer let more instances run side by side) × whether fronts of order
-// ≤ 8 get one thread each; each candidate solves the first (largest) instances of the
-// queue twice and the one with the fastest second run is kept.
+// Tile configuration of the batched kernel: warps per CTA (1, 2, 4; more warps share an
+// instance's levels, fewer let more instances run side by side) × 16 or 32 resident warps
+// per SM (128 or 64 registers per thread), fronts of order ≤ 8 one per thread; each
+// candidate solves the whole batch once (after one untimed launch that warms the caches)
+// and the fastest is kept.  A sample would mislead: the steady state of the persistent
+// queue needs several instances per CTA, and the largest grids hold ~2400 CTAs.
 int tune_fused(qoco_gpu_solver* S, cudaStream_t st) {
     cudaEvent_t e0, e1;
     QOCO_CUDA_TRY(cudaEventCreate(&e0));
     QOCO_CUDA_TRY(cudaEventCreate(&e1));
-    const int sample = std::min(S->bv.nb, 1024);
+    const int nb = S->bv.nb, split = 1;
     float best = 0.0f;
-    int rc = 0, c = 0;
-    for (int nw : {2, 4, 8})
-        for (int split = 0; split < 2 && !rc; ++split, ++c) {
-            if (!S->fused_grid[fused_grid_index(nw)]) continue;
-            float ms = 0.0f;
-            for (int rep = 0; rep < 2 && !rc; ++rep) {
-                QOCO_CUDA_TRY(cudaEventRecord(e0, st));
-                const int nl = launch_fused(S, nw, split, sample, st);
+    int rc = 0;
+    bool warm = false;
+    for (int nw : {1, 2, 4})
+        for (int dense = 0; dense < 2 && !rc; ++dense) {
+            if (!S->fused_grid[fused_grid_index(nw, dense)]) continue;
+            if (!warm) {
+                const int nl = launch_fused(S, nw, split, dense, nb, st);
                 if (nl < 0) { rc = nl; break; }
-                QOCO_CUDA_TRY(cudaEventRecord(e1, st));
-                if (cudaEventSynchronize(e1) != cudaSuccess) rc = QOCO_GPU_ERR_CUDA;
-                else cudaEventElapsedTime(&ms, e0, e1);
+                warm = true;
             }
-            S->fused_tune_ms[c] = ms;
+            float ms = 0.0f;
+            QOCO_CUDA_TRY(cudaEventRecord(e0, st));
+            const int nl = launch_fused(S, nw, split, dense, nb, st);
+            if (nl < 0) { rc = nl; break; }
+            QOCO_CUDA_TRY(cudaEventRecord(e1, st));
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = QOCO_GPU_ERR_CUDA;
+            else cudaEventElapsedTime(&ms, e0, e1);
+            if (S->st.verbose >= 2)
+                printf("     batch tile: %d warps per CTA, %d warps per SM: %.3f ms\n", nw, dense ? 32 : 16, ms);
             if (!rc && (!S->fused_nw || ms < best)) {
                 best = ms;
                 S->fused_nw = nw;
                 S->fused_split = split;
+                S->fused_dense = dense;
             }
         }
     cudaEventDestroy(e0);
@@ -1028,7 +1050,7 @@ int run_fused(qoco_gpu_solver* S, cudaStream_t st) {
     if (!S->fused_nw && (rc = tune_fused(S, st))) return rc;
     if (!S->bgraph.exec) {
         rc = capture_graph(S, &S->bgraph, [&](cudaStream_t cs) {
-            const int nl = launch_fused(S, S->fused_nw, S->fused_split, S->bv.nb, cs);
+            const int nl = launch_fused(S, S->fused_nw, S->fused_split, S->fused_dense, S->bv.nb, cs);
             if (nl < 0) return nl;
             launch_batch_summary(S->bv, S->d_S, cs);
             if (cudaMemcpyAsync(S->h_S, S->d_S, sizeof(IPMScalars), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
@@ -1061,7 +1083,9 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
     S->fp32_factors = 0;
     S->fp64_escalations = 0;
     S->krylov_steps = 0;
-    S->plan.big_fp32 = S->st.mixed_precision != 0 && S->plan.max_big_f > 0 && S->plan.big_work32;
+    S->mixed_ok = S->st.mixed_precision != 0 && S->plan.max_big_f > 0 && S->plan.big_work32;
+    S->fp32_fail_streak = 0;
+    S->plan.big_fp32 = S->mixed_ok;
     if ((rc = reset_barrier(S, st))) return rc;
     // initial point: K(W = I) [x; y; z] = [−c; b; h], s = −z, shift s and z into the cone
     S->launches += launch_w2_identity(cv, S->d_val, S->d_w2slot, S->d_w2ptr, st);
@@ -1131,6 +1155,8 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
             S->launches += launch_nt_scaling(cv, S->s, z, S->wbar, S->eta, S->lam, S->d_val, S->d_w2slot,
                                              S->d_w2ptr, st);
         }
+        // FP32 large fronts again after an FP64 escalation, unless the last two failed
+        S->plan.big_fp32 = S->mixed_ok && S->fp32_fail_streak < 2;
         if ((rc = factor_now(S, st))) return rc;
         // predictor
         if (n + p) { k_neg_copy<<<grid(n + p), 256, 0, st>>>(S->rhs, S->r, n + p); S->launches++; }
@@ -1212,6 +1238,9 @@ void fill_info(const qoco_gpu_solver* S, qoco_gpu_info* info) {
     info->fp32_factors = S->fp32_factors;
     info->fp64_escalations = S->fp64_escalations;
     info->krylov_steps = S->krylov_steps;
+    info->batch_warps = S->fused_nw;
+    info->batch_thread_fronts = S->fused_nw ? S->fused_split : 0;
+    info->batch_warps_per_sm = S->fused_nw ? (S->fused_dense ? 32 : 16) : 0;
     snprintf(info->message, sizeof info->message, "%s", S->msg.c_str());
 }
 
@@ -1404,9 +1433,12 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
         if ((rc = plan_batch_instances(S, nb, row))) return rc;
     const bool want_fused = bs == 0 || bs == 6;
     if (want_fused && S->plan.inst) {
-        for (int nw : {2, 4, 8})
-            if ((rc = batch_ipm_grid(nw, S->plan.inst_fmax, nb, &S->fused_grid[fused_grid_index(nw)]))) return rc;
-        S->fused = S->fused_grid[0] || S->fused_grid[1] || S->fused_grid[2];
+        for (int nw : {1, 2, 4})
+            for (int dense = 0; dense < 2; ++dense)
+                if ((rc = batch_ipm_grid(nw, dense, S->st.mixed_precision != 0, S->plan.inst_fmax, nb,
+                                         &S->fused_grid[fused_grid_index(nw, dense)])))
+                    return rc;
+        for (int g : S->fused_grid) S->fused = S->fused || g > 0;
     }
     // the factorisation entry points outside a batched solve (kkt_factor_at, backward)
     // use the shared kernels when the persistent kernel runs the solves
@@ -1448,6 +1480,7 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
         A.refine_tol = S->st.refine_tol; A.step_fraction = S->st.step_fraction;
         A.max_iter = S->st.max_iter; A.max_refine = S->st.max_refine;
         A.fmax = S->plan.inst_fmax;
+        A.mixed = S->st.mixed_precision != 0;
     }
     return 0;
 }
@@ -1478,6 +1511,7 @@ void qoco_gpu_default_settings(qoco_gpu_settings* s) {
     s->wait_polls = 0;
     s->verbose = 0;
     s->mixed_precision = 0;
+    s->mixed_reg = 0.0;
     s->batch_schedule = 0;
 }
 

@@ -162,3 +162,23 @@ def test_batch_with_a_front_beyond_one_warp_uses_the_shared_kernels(q):
     assert S.info()["batch_schedule_used"] == 5
     assert S.solve() == 0
     S.close()
+
+
+def test_persistent_batched_kernel_mixed_precision_matches_oracle(q):
+    """Mixed precision on the persistent batched kernel: every front factored in FP32,
+    the solves and refinement in FP64 (an instance whose refinement misses the target on
+    an FP32 factor is refactored in FP64); every instance reaches the oracle's solution
+    to the plain form's tolerances."""
+    probs = mpc_batch(count=64, tmin=10, tmax=60, seed=25)
+    S = q.BatchSolver(probs, mixed_precision=1)
+    assert S.info()["batch_schedule_used"] == 6
+    assert S.solve() == 0
+    info = S.batch_info()
+    assert np.all(info["status"] == 0)
+    sols = S.instance_solutions()
+    for i in (0, 5, 17, 40, 63):
+        ref = ipm.solve(probs[i])
+        assert ref.status == "solved"
+        assert abs(int(info["iters"][i]) - ref.iters) <= 3
+        _check_instance(probs[i], sols[i], ref)
+    S.close()

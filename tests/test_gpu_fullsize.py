@@ -58,3 +58,33 @@ def test_full_size_against_oracle_golden(name):
                     assert d <= 1e-5, (key, d)
     assert abs(info["iters"] - g["iters"]) <= 4, (info["iters"], g["iters"])
     assert_certificate(prob, sol)
+
+
+def test_full_size_lasso_mixed_precision_certificate():
+    """The lasso QP at full size (F 50000x100000, 1e-3 dense, 100 nonzeros per row; one
+    50440-row dense front, 4.1e13 flops per factorisation) solved in mixed precision (FP32
+    large front on the tensor cores, FP64 refinement).  The oracle cannot solve this size
+    in a test, so the solution is certified from the data alone: with g = Fᵀ(Fx − y), the
+    lasso optimality conditions |g_j| ≤ λ everywhere and g_j = −λ·sign(x_j) on the
+    (clear) support hold to the tolerance's accuracy, the KKT certificate of the QP form
+    holds, and the QP objective equals the lasso objective ½‖Fx − y‖² + λ‖x‖₁."""
+    import paper_2603_29197_gb300 as q
+    prob = lasso_qp(rows=50000, cols=100000, density=1e-3, seed=0)
+    S = q.Solver(prob, mixed_precision=1)
+    info = S.info()
+    assert info["max_front"] >= 50000 and info["large_fronts"] >= 1
+    assert S.solve() == 0
+    sol = S.solution()
+    F, y, lam = prob.meta["F"], prob.meta["y"], prob.meta["lam"]
+    x = sol["x"][:F.shape[1]]
+    res = F @ x - y
+    g = F.T @ res
+    assert np.max(np.abs(g)) <= lam * (1.0 + 1e-6)
+    supp = np.abs(x) > 1e-3 * np.max(np.abs(x))
+    assert supp.sum() > 100
+    assert np.max(np.abs(g[supp] + lam * np.sign(x[supp]))) <= 1e-5 * lam
+    obj = 0.5 * float(res @ res) + lam * float(np.abs(x).sum())
+    assert abs(obj - sol["info"]["pobj"]) <= 1e-6 * abs(obj)
+    assert sol["info"]["fp32_factors"] >= 1
+    assert_certificate(prob, sol)
+    S.close()
