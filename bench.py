@@ -732,6 +732,7 @@ def run_other(args, ws, rank, local):
            "ordering": {0: "auto", 1: "amd", 2: "nd", 3: "natural"}.get(info["ordering_used"], "?") +
                        (" (requested)" if args.ordering != "auto" else " (cost model)"),
            "fp32_factors": info["fp32_factors"], "fp64_escalations": info["fp64_escalations"],
+           "fp32_floor_raises": info["fp32_floor_raises"],
            "krylov_steps": info["krylov_steps"], "refine_steps": info["refine_steps"],
            "batch_schedule": info["batch_schedule_used"] if batch else None,
            "batch_tile": ({"warps_per_cta": info["batch_warps"], "thread_fronts": info["batch_thread_fronts"],

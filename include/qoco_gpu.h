@@ -88,21 +88,30 @@ typedef struct {
     int verbose;                        /* 0: silent; 1: one line per iteration on stdout;
                                            2: also one line per refinement of a solve */
     int mixed_precision;                /* 1: fronts of order ≥ 160 factored in FP32 (scaled
-                                           to a unit diagonal, FP32 accumulation, trailing
-                                           updates on the tensor cores as three TF32 products,
-                                           pivots below 1e-5 of the scaled diagonal replaced),
-                                           solves and refinement in FP64; a solve whose plain
+                                           symmetrically so that each row's largest entry is
+                                           1, FP32 accumulation, trailing updates on the tensor
+                                           cores as three TF32 products, pivots below a floor
+                                           replaced by ± the floor), solves and refinement in
+                                           FP64; an
+                                           FP32 factor that breaks down (a non-finite entry or
+                                           one above 1e30) is redone with a ten times larger
+                                           floor (1e-5 at the start of a solve, at most 1e-2);
+                                           a solve whose plain
                                            refinement stalls or misses refine_tol within
-                                           max_refine steps goes on with restarted GMRES on K
-                                           preconditioned by the factor (≤ 3 cycles of 30); if
-                                           that misses too, it refactors in FP64; the next
+                                           max_refine steps goes on with restarted GMRES on K,
+                                           row-scaled and preconditioned by the factor (≤ 3
+                                           cycles of 30, fewer when an FP64 refactor would cost
+                                           less than the iterations); on an FP32 factor a solve
+                                           must meet refine_tol both normwise and componentwise
+                                           (max_i |r − Kx|_i / (|K||x| + |r|)_i); if that
+                                           misses too, it refactors in FP64; the next
                                            iteration factors in FP32 again unless the last two
                                            FP32 factorisations failed.  Batches on the
                                            persistent kernel factor every front in FP32 and
                                            refactor an instance in FP64 when its refinement
                                            misses (default 0) */
     double mixed_reg;                   /* mixed precision: δ added to the diagonal of each
-                                           scaled FP32 front (unit diagonal), with the pivot's
+                                           scaled FP32 front (row maxima 1), with the pivot's
                                            sign (+ on x rows, − on y and z rows): a quasidefinite
                                            shift that bounds the FP32 elimination's growth; the
                                            refinement against the unregularised K removes it
@@ -151,6 +160,8 @@ typedef struct {
     int batch_warps;            /* batches on the persistent kernel, as chosen by its tuning:   */
     int batch_thread_fronts;    /* warps per CTA, whether fronts of order ≤ 8 get one thread, */
     int batch_warps_per_sm;     /* and the resident warps per SM it was compiled for (16, 32)  */
+    int fp32_floor_raises;      /* FP32 factorisations of the last solve that broke down and were
+                                   redone in FP32 with a ten times larger pivot floor */
     char message[160];
 } qoco_gpu_info;
 

@@ -59,7 +59,8 @@ class Info(C.Structure):
                 ("large_fronts", C.c_int), ("fp32_factors", C.c_int), ("fp64_escalations", C.c_int),
                 ("batch_schedule_used", C.c_int), ("krylov_steps", C.c_int),
                 ("batch_warps", C.c_int), ("batch_thread_fronts", C.c_int),
-                ("batch_warps_per_sm", C.c_int), ("message", C.c_char * 160)]
+                ("batch_warps_per_sm", C.c_int), ("fp32_floor_raises", C.c_int),
+                ("message", C.c_char * 160)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "message"}

@@ -105,7 +105,7 @@ __device__ __noinline__ void inst_factor(const BatchIPMArgs& A, int inst, double
         for (int t = t0 + (int)threadIdx.x; t < w0; t += NW * 32)
             thread_factor_front<NoWait, Real>(A.sched[t], A.F, A.kval, NoWait());
         for (int t = w0 + wid; t < e1; t += NW)
-            warp_factor_front<NoWait, Real>(A.sched[t], A.F, A.kval, Fr, Fr + A.fmax * A.fmax, lane, NoWait());
+            warp_factor_front<NoWait, Real, 4>(A.sched[t], A.F, A.kval, Fr, Fr + A.fmax * A.fmax, lane, NoWait());
         __syncthreads();
     }
 }
@@ -119,7 +119,7 @@ __device__ __noinline__ void inst_solve(const BatchIPMArgs& A, int inst, const d
     for (int k = k0; k < k1; ++k) {
         const int t0 = A.ent[3 * k], w0 = A.ent[3 * k + 1], e1 = A.ent[3 * k + 2];
         for (int t = t0 + (int)threadIdx.x; t < w0; t += NW * 32) thread_fwd_front(A.sched[t], A.F, rhs, A.sol_w, NoWait());
-        for (int t = w0 + wid; t < e1; t += NW) warp_fwd_front(A.sched[t], A.F, rhs, A.sol_w, V, P, lane, NoWait());
+        for (int t = w0 + wid; t < e1; t += NW) warp_fwd_front<NoWait, 4>(A.sched[t], A.F, rhs, A.sol_w, V, P, lane, NoWait());
         __syncthreads();
     }
     for (int k = k1 - 1; k >= k0; --k) {

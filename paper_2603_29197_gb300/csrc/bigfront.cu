@@ -34,9 +34,11 @@ namespace {
 
 int nsm();               // SM count of the current device (queried once, outside captures)
 
-// smallest signed pivot accepted in a scaled FP32 front (its diagonal is ±1 before the
-// elimination); smaller ones are set to ±kFp32PivotFloor
-constexpr double kFp32PivotFloor = 1e-5;
+// largest magnitude a scaled FP32 front's L, D or update entry may reach before the
+// factor counts as broken down: near the FP32 overflow threshold (entries well above the
+// FP64 factor's, up to 1e20 and more, still make a usable preconditioner when pivots
+// were floored)
+constexpr double kFp32Growth = 1e30;
 
 template <class T>
 __device__ __forceinline__ T rcp_t(T d);
@@ -122,10 +124,11 @@ __global__ void __launch_bounds__(256) k_big_diag(int s, int k0, int nb, FactorV
     }
     __syncthreads();
     int nreg = 0;
-    // FP32 fronts are scaled to a unit diagonal: a pivot below kFp32PivotFloor there is
-    // rounding noise of the FP32 elimination, and is replaced like a breakdown
-    const T thr = sizeof(T) == 4 ? (T)fmax(a.dyn_thresh, kFp32PivotFloor) : (T)a.dyn_thresh;
-    const T dval = sizeof(T) == 4 ? (T)fmax(a.dyn_value, kFp32PivotFloor) : (T)a.dyn_value;
+    // FP32 fronts are scaled so that no entry exceeds 1: a pivot below the floor *piv32
+    // there is rounding noise of the FP32 elimination, and is replaced like a breakdown
+    const double floor32 = sizeof(T) == 4 ? *a.piv32 : 0.0;
+    const T thr = (T)fmax(a.dyn_thresh, floor32);
+    const T dval = (T)fmax(a.dyn_value, floor32);
     auto pivot = [&](int k) {
         T d = D[k][k];
         const bool pos = s_sign[k] > 0;
@@ -827,14 +830,40 @@ __global__ void k_group_syrk_reduce(const double* __restrict__ part, int r, int 
     F[(int64_t)rel[j] * f + rel[i]] -= (T)sum;
 }
 
-// FP32 fronts are factored scaled: with σ_i = 1/√|G_ii| of the assembled FP64 front G,
-// F = ΣGΣ has a unit diagonal (its entries stay inside the FP32 range whatever the
-// spread of the −W² block, 1e±16 near the end of a solve), and its LDLᵀ (L̃, D̃) gives
-// G's as L = Σ⁻¹L̃Σ, D = Σ⁻¹D̃Σ⁻¹, update block Σ⁻¹ŨΣ⁻¹.
-__global__ void k_big_scale(const double* __restrict__ G, int f, double* __restrict__ sc) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < f; i += gridDim.x * blockDim.x) {
-        const double d = fabs(G[(int64_t)i * f + i]);
-        sc[i] = (d > 0.0 && isfinite(d)) ? 1.0 / sqrt(d) : 1.0;
+// FP32 fronts are factored scaled: with σ_i = 1/√(max_j |G_ij|) of the assembled FP64
+// front G (one pass of Ruiz's symmetric equilibration in the max norm), every entry of
+// F = ΣGΣ is at most 1 in magnitude (|G_ij| ≤ min(r_i, r_j) ≤ √(r_i r_j), r the row
+// maxima), whatever the spread of the −W² block (1e±16 near the end of a solve), and its
+// LDLᵀ (L̃, D̃) gives G's as L = Σ⁻¹L̃Σ, D = Σ⁻¹D̃Σ⁻¹, update block Σ⁻¹ŨΣ⁻¹.  (Scaling to
+// a unit diagonal instead leaves off-diagonal entries up to 1e8 where the diagonal is the
+// static regularisation alone, and the FP32 elimination's growth from them breaks it down.)
+// One CTA per 64 rows: the rows' entries left of the diagonal are read as 64-row strips of
+// the columns j ≤ i (contiguous per column), the entries below the diagonal as the rows'
+// own columns; every block reads about 64·f entries and no atomics are needed.
+constexpr int kScaleRows = 64;
+__global__ void __launch_bounds__(256) k_big_scale(const double* __restrict__ G, int f, double* __restrict__ sc) {
+    __shared__ double part[4][kScaleRows];
+    __shared__ double colm[kScaleRows];
+    const int i0 = blockIdx.x * kScaleRows;
+    const int r = threadIdx.x % kScaleRows, p = threadIdx.x / kScaleRows;
+    const int i = i0 + r;
+    double m = 0.0;
+    if (i < f)
+        for (int j = p; j <= i; j += 4) m = fmax(m, fabs(G[(int64_t)j * f + i]));
+    part[p][r] = m;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = w; q < kScaleRows; q += 8) {
+        const int col = i0 + q;
+        double cm = 0.0;
+        if (col < f)
+            for (int k = col + lane; k < f; k += 32) cm = fmax(cm, fabs(G[(int64_t)col * f + k]));
+        for (int o = 16; o > 0; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+        if (lane == 0) colm[q] = cm;
+    }
+    __syncthreads();
+    if (threadIdx.x < kScaleRows && i < f) {
+        const double rm = fmax(fmax(fmax(part[0][r], part[1][r]), fmax(part[2][r], part[3][r])), colm[r]);
+        sc[i] = (rm > 0.0 && isfinite(rm)) ? 1.0 / sqrt(rm) : 1.0;
     }
 }
 // F = ΣGΣ on the lower triangle (zeros above), plus the sign-aware shift δ on the
@@ -857,10 +886,12 @@ __global__ void k_big_writeback(int s, FactorView a, const float* __restrict__ F
                                 int c, const double* __restrict__ sc) {
     const int first = a.first[s];
     const int64_t n = (int64_t)f * f;
+    bool bad = false;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e / f), i = (int)(e - (int64_t)j * f);
         if (i < j) continue;
         const double v = (double)Fw[e];
+        bad |= !(fabs(v) <= kFp32Growth);  // also true for NaN
         if (j < c) {
             if (i == j) {
                 const double d = v / (sc[j] * sc[j]);
@@ -873,6 +904,7 @@ __global__ void k_big_writeback(int s, FactorView a, const float* __restrict__ F
             G[e] = v / (sc[i] * sc[j]);
         }
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(a.bad32, 1);
 }
 
 // ---- solves ------------------------------------------------------------------------
@@ -1302,14 +1334,15 @@ int launch_big_factor(const FactorPlan& P, const FactorView& a, const double* kv
     const int64_t off = P.big_front_off[idx];
     int launches = 0;
     if (P.big_fp32) {
-        // assembled in FP64, scaled symmetrically to a unit diagonal, factored in FP32, and
+        // assembled in FP64, scaled symmetrically (row maxima 1), factored in FP32, and
         // L, D, the update block and the diagonal blocks' inverses unscaled into FP64
         const int s = P.big_s[idx], c = P.big_c[idx];
         float* F = P.big_work32;
         double* G = a.front + off;
         const int64_t ff = (int64_t)f * f;
+        QOCO_CUDA_TRY(cudaMemsetAsync(a.bad32, 0, sizeof(int), st));
         launches += big_assemble_t<double>(P, a, kval, idx, G, st);
-        k_big_scale<<<gridfor(f, 256), 256, 0, st>>>(G, f, P.big_scale);
+        k_big_scale<<<(unsigned)((f + kScaleRows - 1) / kScaleRows), 256, 0, st>>>(G, f, P.big_scale);
         k_big_to32<<<gridfor(ff, 256), 256, 0, st>>>(s, a, G, F, f, P.big_scale);
         launches += 2;
         launches += big_factor_t<float>(P, a, idx, F, (float*)P.big_w, st);

@@ -69,16 +69,10 @@ __device__ __forceinline__ bool cta_factor_front(int s, const FactorView& a, con
     if (tid < nch && tid < 32) s_ci[tid] = a.cinfo[k0 + tid];
     __syncthreads();
     if (!wait()) return false;
-    for (int k = 0; k < nch; ++k) {
-        const ChildInfo ci = k < 32 ? s_ci[k] : a.cinfo[k0 + k];
-        const int fc = ci.fc, r = ci.r;
-        const double* U = a.front + ci.u_off;
-        const int* rel = a.rel + ci.rel_off;
-        extend_add(F, f, U, fc, rel, r, tid, nt);
-        __syncthreads();
-    }
+    extend_add_children<false, 8, double>(F, f, a, nch, [&](int k) { return k < 32 ? s_ci[k] : a.cinfo[k0 + k]; },
+                                          tid, nt);
     const int nreg = blocked_ldlt<false>(F, lk, lk + (size_t)kPanel * f, f, c, first, a, tid, nt);
-    if (tid == 0 && nreg) atomicAdd(a.nreg, nreg);
+    if (nreg) atomicAdd(a.nreg, nreg);  // the pivot thread's count
     if (in_smem)
         for (int64_t i = tid; i < ff; i += nt) G[i] = F[i];
     __syncthreads();
@@ -264,7 +258,7 @@ int selftest_wait_timeout(long long max_spins, cudaStream_t st) {
 __global__ void __launch_bounds__(kDataflowThreads) k_solve_dataflow(
     const int* __restrict__ items, int nitems, const int* __restrict__ tb_ptr, const int* __restrict__ sthread,
     FactorView a, const double* __restrict__ rhs, double* w, double* xp, double* x, int accumulate, int fmax,
-    int* fdone, int* bdone, DataflowState ds) {
+    int* fdone, int* bdone, DataflowState ds, int it0) {
     extern __shared__ double smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double* v = smem + (size_t)wid * fmax * (fmax + 1);
@@ -272,7 +266,7 @@ __global__ void __launch_bounds__(kDataflowThreads) k_solve_dataflow(
     for (;;) {
         int it = 0, stop = 0;
         if (lane == 0) {
-            it = (int)atomicAdd(ds.next, 1u);
+            it = (int)atomicAdd(ds.next, 1u) + it0;
             stop = *(volatile int*)ds.err;
         }
         it = __shfl_sync(0xffffffffu, it, 0);
@@ -355,12 +349,45 @@ int plan_dataflow_solve(FactorPlan& P, int max_warp_f, bool any_cta_front) {
 }
 
 int launch_solve_dataflow(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
-                          double* x, bool accumulate, const DataflowState& ds, cudaStream_t st) {
+                          double* x, bool accumulate, const DataflowState& ds, cudaStream_t st, bool bwd_only) {
     QOCO_CUDA_TRY(cudaMemsetAsync(ds.next, 0, sizeof(unsigned int), st));
     k_solve_dataflow<<<P.dataflow_grid, kDataflowThreads, dataflow_smem(P.dataflow_fmax), st>>>(
         P.d_items, P.nitems, P.d_tb_ptr, P.d_sthread, a, rhs, w, xp, x, accumulate ? 1 : 0, P.dataflow_fmax,
-        P.d_fdone, P.d_bdone, ds);
+        P.d_fdone, P.d_bdone, ds, bwd_only ? P.nitems : 0);
     return 1;
+}
+
+// The fused forward step of front s (order ≤ kWarpFront) by one warp, after its
+// factorisation has been published: it waits (bounded) for its children's forward steps,
+// then runs with F holding the factored front (leading dimension f) and v free shared
+// memory of at least f doubles.  The same arithmetic as the dataflow solve's step for a
+// front of this order (one thread up to kThreadFront, else one warp), so a fused forward
+// sweep gives the same bits as a separate one.
+__device__ __forceinline__ bool fused_fwd_warp(int s, const FactorView& a, const FwdFuse& fz, const DataflowState& ds,
+                                               const double* F, double* v, int lane) {
+    if (a.nrow[s] <= kThreadFront) {
+        bool ok = true;
+        if (lane == 0) {
+            auto wait = [&]() {
+                bool good = true;
+                for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1] && good; ++k)
+                    good = wait_epoch(fz.fdone + a.child[k], fz.epoch, ds.err, ds.max_spins);
+                __threadfence();
+                return good;
+            };
+            ok = thread_fwd_front(s, a, fz.rhs, fz.w, wait);
+        }
+        return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    }
+    auto wait = [&]() {
+        bool good = true;
+        for (int k = a.child_ptr[s] + lane; k < a.child_ptr[s + 1]; k += 32)
+            good = good && wait_epoch(fz.fdone + a.child[k], fz.epoch, ds.err, ds.max_spins);
+        good = __all_sync(0xffffffffu, good);
+        __threadfence();
+        return good;
+    };
+    return warp_fwd_front<decltype(wait), 8, false>(s, a, fz.rhs, fz.w, v, F, lane, wait);
 }
 
 // ---------------------------------------------------------------------------
@@ -373,7 +400,7 @@ int launch_solve_dataflow(const FactorPlan& P, const FactorView& a, const double
 __global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
     const int* __restrict__ items, int nitems, const int* __restrict__ tb_ptr, const int* __restrict__ tlist,
     const int* __restrict__ wg_ptr, const int* __restrict__ wlist, FactorView a, const double* __restrict__ kval,
-    int fmax, int* cdone, DataflowState ds) {
+    int fmax, int* cdone, DataflowState ds, FwdFuse fz) {
     extern __shared__ double smem[];
     __shared__ int s_it, s_stop;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -405,6 +432,22 @@ __global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
                     __threadfence();
                     atomicExch(cdone + s, ds.epoch);
                 }
+                // the fused forward step, after the factor is published: the parent's
+                // factorisation does not wait for it
+                if (ok && fz.rhs) {
+                    auto fwait = [&]() {
+                        bool good = true;
+                        for (int k = a.child_ptr[s]; k < a.child_ptr[s + 1] && good; ++k)
+                            good = wait_epoch(fz.fdone + a.child[k], fz.epoch, ds.err, ds.max_spins);
+                        __threadfence();
+                        return good;
+                    };
+                    ok = thread_fwd_front(s, a, fz.rhs, fz.w, fwait);
+                    if (ok) {
+                        __threadfence();
+                        atomicExch(fz.fdone + s, fz.epoch);
+                    }
+                }
             }
         } else if (kind == 1) {
             const int t = wg_ptr[idx] + wid;
@@ -425,6 +468,14 @@ __global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
                     __syncwarp();
                     if (lane == 0) atomicExch(cdone + s, ds.epoch);
                 }
+                if (ok && fz.rhs) {
+                    ok = fused_fwd_warp(s, a, fz, ds, F, F + fmax * fmax, lane);
+                    if (ok) {
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) atomicExch(fz.fdone + s, fz.epoch);
+                    }
+                }
             }
         } else {
             const int s = idx;
@@ -441,6 +492,15 @@ __global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
             if (ok) {
                 __threadfence();
                 if (threadIdx.x == 0) atomicExch(cdone + s, ds.epoch);
+            }
+            if (ok && fz.rhs) {
+                bool good = true;
+                if (wid == 0) good = fused_fwd_warp(s, a, fz, ds, smem, smem + (size_t)f * f, lane);
+                ok = __syncthreads_and(good) != 0;
+                if (ok) {
+                    __threadfence();
+                    if (threadIdx.x == 0) atomicExch(fz.fdone + s, fz.epoch);
+                }
             }
         }
         if (!__syncthreads_and(ok)) return;
@@ -469,11 +529,11 @@ int plan_dataflow_factor(FactorPlan& P, int fmax, bool any_large) {
 }
 
 int launch_factor_dataflow(const FactorPlan& P, const FactorView& a, const double* kval, const DataflowState& ds,
-                           cudaStream_t st) {
+                           cudaStream_t st, const FwdFuse& fz) {
     QOCO_CUDA_TRY(cudaMemsetAsync(ds.next, 0, sizeof(unsigned int), st));
     k_factor_dataflow<<<P.fdataflow_grid, kDataflowThreads, fdataflow_smem(P.fdataflow_fmax), st>>>(
         P.d_fitems, P.nfitems, P.d_ftb_ptr, P.d_thread, P.d_fwg_ptr, P.d_warp, a, kval, P.fdataflow_fmax,
-        P.d_cdone, ds);
+        P.d_cdone, ds, fz);
     return 1;
 }
 

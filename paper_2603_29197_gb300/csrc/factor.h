@@ -46,6 +46,11 @@ struct FactorView {
     const signed char* skip = nullptr;
     double eps = 1e-8, dyn_thresh = 1e-13, dyn_value = 1e-7;
     double eps32 = 0.0;  // sign-aware shift of the scaled FP32 large fronts' diagonal
+    // scaled FP32 large fronts: the smallest accepted signed pivot (one device double, raised
+    // by the host after a breakdown) and the breakdown flag the writeback sets when the
+    // factor holds a non-finite or overgrown entry
+    const double* piv32 = nullptr;
+    int* bad32 = nullptr;
 };
 
 struct FactorPlan {
@@ -159,10 +164,22 @@ int launch_inst_solve(const FactorPlan& P, const FactorView& a, const double* rh
 int selftest_wait_timeout(long long max_spins, cudaStream_t st);
 int plan_dataflow_solve(FactorPlan& P, int max_warp_f, bool any_cta_front);
 int plan_dataflow_factor(FactorPlan& P, int fmax, bool any_large);
+// The forward solve of one right-hand side fused into the dataflow factorisation: each
+// front runs its forward step (L u = b restricted to the front, w = D⁻¹u, its update
+// vector for the parent) right after its own factorisation, with the factor still on
+// chip, and publishes its factor and forward flags together.  rhs == nullptr: no fusion.
+struct FwdFuse {
+    const double* rhs = nullptr;
+    double* w = nullptr;
+    int* fdone = nullptr;  // the solve's forward flags
+    int epoch = 0;         // the solve epoch the backward launch will use
+};
 int launch_factor_dataflow(const FactorPlan& P, const FactorView& a, const double* kval, const DataflowState& ds,
-                           cudaStream_t st);
+                           cudaStream_t st, const FwdFuse& fz = FwdFuse());
+// bwd_only: the backward sweep alone, after a factorisation that fused the forward one
 int launch_solve_dataflow(const FactorPlan& P, const FactorView& a, const double* rhs, double* w, double* xp,
-                          double* x, bool accumulate, const DataflowState& ds, cudaStream_t st);
+                          double* x, bool accumulate, const DataflowState& ds, cudaStream_t st,
+                          bool bwd_only = false);
 int launch_factor(const FactorPlan& P, const FactorView& a, const double* kval, cudaStream_t st);
 // One large front (P.big_*[idx]): partial LDLᵀ, or the forward / backward solve step.
 int big_set_attributes();

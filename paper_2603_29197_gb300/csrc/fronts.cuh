@@ -24,32 +24,103 @@ __device__ __forceinline__ void tri_index(int t, int m, int& ii, int& jj) {
     ii = t - (j * m - (j * (j - 1)) / 2) + j;
 }
 
-// F[rel_j, rel_i] += U_ij over the lower triangle of a child's r×r update block (leading
-// dimension fc), spread over nt threads with four independent entries per step; the
-// block was written by another thread block (read through L2).  T: the working type of
-// the front (FP64; FP32 for the mixed-precision batched kernel).
-template <class Real = double>
-__device__ __forceinline__ void extend_add(Real* F, int f, const double* U, int fc, const int* rel, int r,
-                                           int tid, int nt) {
-    const int T = r * (r + 1) / 2;
-    for (int t = tid; t < T; t += 4 * nt) {
-        int off[4];
-        double u4[4];
+// barrier of the group that works on one front: its warp or its CTA
+template <bool WARP>
+__device__ __forceinline__ void group_sync() {
+    if constexpr (WARP) __syncwarp();
+    else __syncthreads();
+}
+
+// Extend-add of all of a front's children (their update blocks' lower triangles) into F,
+// with the loads of several children in flight at once.  Each thread queues up to Q entries
+// (child k, round m: round m of a child covers its lower-triangle entries tid + m·nt),
+// loading every entry's value and its target offset together; then it adds them child by
+// child in the children's order with a group barrier between two children (their targets
+// may coincide).  Every entry of F thus receives its contributions in the children's order,
+// as with one child at a time, and the loads of up to Q rounds cost one round trip.
+// ci_of(k) returns the k-th child's record and is called uniformly by the whole group.
+template <bool WARP, int Q, class Real, class CI>
+__device__ __forceinline__ void extend_add_children(Real* F, int f, const FactorView& a, int nch, const CI& ci_of,
+                                                    int tid, int nt) {
+    int ck = 0, cm = 0;  // cursor: child, round
+    while (ck < nch) {
+        int qk[Q], off[Q];
+        double val[Q];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int tu = t + u * nt;
-            off[u] = -1;
-            u4[u] = 0.0;
-            if (tu < T) {
-                int i, j;
-                tri_index(tu, r, i, j);
-                off[u] = rel[j] * f + rel[i];
-                u4[u] = __ldcg(U + (int64_t)j * fc + i);
+        for (int q = 0; q < Q; ++q) {
+            qk[q] = -1;
+            off[q] = -1;
+            val[q] = 0.0;
+            if (ck < nch) {
+                const ChildInfo ci = ci_of(ck);
+                const int r = ci.r, T = r * (r + 1) / 2;
+                const int t = tid + cm * nt;
+                qk[q] = ck;
+                if (t < T) {
+                    int i, j;
+                    tri_index(t, r, i, j);
+                    const int* rel = a.rel + ci.rel_off;
+                    off[q] = rel[j] * f + rel[i];
+                    val[q] = __ldcg(a.front + ci.u_off + (int64_t)j * ci.fc + i);
+                }
+                if (++cm * nt >= T) {
+                    cm = 0;
+                    ++ck;
+                }
             }
         }
+        int cur = qk[0];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (off[u] >= 0) F[off[u]] += (Real)u4[u];
+        for (int q = 0; q < Q; ++q) {
+            if (qk[q] < 0) break;
+            if (qk[q] != cur) {
+                group_sync<WARP>();
+                cur = qk[q];
+            }
+            if (off[q] >= 0) F[off[q]] += (Real)val[q];
+        }
+        group_sync<WARP>();
+    }
+}
+
+// The same for a forward solve's gathered vector: v[rel_i] += u_i over the children's
+// update vectors (r_k entries each), child by child, several children's loads in flight.
+template <int Q, class CI>
+__device__ __forceinline__ void gather_children_upd(double* v, const FactorView& a, int nch, const CI& ci_of, int lane) {
+    int ck = 0, cm = 0;
+    while (ck < nch) {
+        int qk[Q], idx[Q];
+        double val[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            qk[q] = -1;
+            idx[q] = -1;
+            val[q] = 0.0;
+            if (ck < nch) {
+                const ChildInfo ci = ci_of(ck);
+                const int i = lane + 32 * cm;
+                qk[q] = ck;
+                if (i < ci.r) {
+                    idx[q] = a.rel[ci.rel_off + i];
+                    val[q] = __ldcg(a.upd + ci.rel_off + i);
+                }
+                if (32 * ++cm >= ci.r) {
+                    cm = 0;
+                    ++ck;
+                }
+            }
+        }
+        int cur = qk[0];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (qk[q] < 0) break;
+            if (qk[q] != cur) {
+                __syncwarp();
+                cur = qk[q];
+            }
+            if (idx[q] >= 0) v[idx[q]] += val[q];
+        }
+        __syncwarp();
     }
 }
 
@@ -80,11 +151,6 @@ __device__ __forceinline__ void pivot(const FactorView& a, int col, double& d, d
 // ---------------------------------------------------------------------------
 constexpr int kPanel = 4;
 
-template <bool WARP>
-__device__ __forceinline__ void group_sync() {
-    if constexpr (WARP) __syncwarp();
-    else __syncthreads();
-}
 
 // first entry t0 of the column-major lower triangle of an m×m block handled by a thread
 // and the advance by `stride` entries
@@ -101,21 +167,27 @@ __device__ __forceinline__ void tri_advance(int m, int stride, int& ii, int& jj)
 // one parallel pass so that no pivot waits on a global load.
 //
 // GB300 runs a dependent FP64 FMA in ~64 cycles, so the panel step is arranged around
-// its serial pivot chain.  Within a panel the columns stay unscaled; thread t owns rows
-// k+1+t (+nt …), so thread 0 owns row k+1 and, as soon as it has applied column k to
-// its own diagonal entry, computes the next pivot and its reciprocal while the other
-// threads apply column k to their rows: one barrier per column.  At the end of the
-// panel the columns are scaled in place (L) and their unscaled copy kept in W, then the
-// trailing rank-kPanel update gives each thread four independent entries per step.
+// its serial pivot chain.  Within a panel the columns stay unscaled and thread t owns rows
+// k+1+t (+nt …).  One thread computes the pivots: in a warp, thread 0 (it owns row k+1 and,
+// as soon as it has applied column k to its own diagonal entry, computes the next pivot and
+// its reciprocal while the other lanes apply column k to their rows); in a CTA, the last
+// thread, which owns no row of a front of order ≤ nt − 31 and so runs the pivot chain
+// (next diagonal entry, pivot, reciprocal) in its own warp, beside the row updates of the
+// others: one barrier per column either way.  At the end of the panel the columns are
+// scaled in place (L) and their unscaled copy kept in W; then the trailing rank-kPanel
+// update gives each thread four independent entries per step, and in a CTA the pivot
+// thread first updates the next panel's first diagonal entry and computes its pivot.
+// Every entry sees the same operations in the same order whichever thread computes it.
 template <bool WARP, class Real = double>
 __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, int c, int first,
                                             const FactorView& a, int tid, int nt) {
     int nreg = 0;
     double* dinv = a.dinv + first;
     Real* sgn = bc + kPanel + 1;
+    const int piv = WARP ? 0 : nt - 1;  // the thread that computes the pivots
     for (int k = tid; k < c; k += nt) sgn[k] = a.dsign[first + k] > 0 ? Real(1) : Real(-1);
     group_sync<WARP>();
-    auto do_pivot = [&](int k) {  // thread 0 only
+    auto do_pivot = [&](int k) {  // the pivot thread only
         Real* colk = F + (size_t)k * f;
         Real d = colk[k];
         const bool pos = sgn[k] > Real(0);
@@ -126,7 +198,7 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
         dinv[k] = sizeof(Real) == 8 ? (double)inv : recip((double)d);
         bc[k % kPanel] = inv;
     };
-    if (tid == 0 && c > 0) do_pivot(0);
+    if (tid == piv && c > 0) do_pivot(0);
     for (int k0 = 0; k0 < c; k0 += kPanel) {
         const int nb = min(kPanel, c - k0);
         for (int p = 0; p < nb; ++p) {
@@ -135,10 +207,19 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
             const Real* colk = F + (size_t)k * f;
             const Real inv = bc[k % kPanel];
             const int jend = k0 + nb;  // later columns of this panel: k+1 .. jend−1
+            if constexpr (!WARP) {
+                if (tid == piv && k + 1 < jend) {
+                    const Real l = colk[k + 1] * inv;
+                    F[(size_t)(k + 1) * f + k + 1] -= l * colk[k + 1];
+                    do_pivot(k + 1);
+                }
+            }
             for (int i = k + 1 + tid; i < f; i += nt) {
                 const Real l = colk[i] * inv;
-                for (int j = k + 1; j < jend && j <= i; ++j) F[(size_t)j * f + i] -= l * colk[j];
-                if (i == k + 1 && k + 1 < jend) do_pivot(k + 1);  // i == k+1 only for tid 0
+                // in a CTA the diagonal entry (k+1, k+1) belongs to the pivot thread
+                const int j0 = (!WARP && i == k + 1) ? k + 2 : k + 1;
+                for (int j = j0; j < jend && j <= i; ++j) F[(size_t)j * f + i] -= l * colk[j];
+                if (WARP && i == k + 1 && k + 1 < jend) do_pivot(k + 1);  // i == k+1 only for tid 0
             }
         }
         group_sync<WARP>();
@@ -156,8 +237,23 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
         group_sync<WARP>();
         // trailing rank-nb update of rows/columns k0+nb .. f−1, four entries per thread
         const int base = k0 + nb, m = f - base;
+        const Real* L0 = F + (size_t)k0 * f;
+        auto trailing = [&](int i, int j) {
+            const Real* wr = W + j * kPanel;
+            Real x = F[(size_t)j * f + i];
+            x -= L0[i] * wr[0];
+            if (nb > 1) x -= L0[f + i] * wr[1];
+            if (nb > 2) x -= L0[2 * f + i] * wr[2];
+            if (nb > 3) x -= L0[3 * f + i] * wr[3];
+            return x;
+        };
+        // in a CTA the pivot thread takes the next pivot's diagonal entry first
+        const bool early = !WARP && base < c;
+        if (early && tid == piv) {
+            F[(size_t)base * f + base] = trailing(base, base);
+            do_pivot(base);
+        }
         if (m > 0) {
-            const Real* L0 = F + (size_t)k0 * f;
             const int T = m * (m + 1) / 2;
             for (int t = tid; t < T; t += 4 * nt) {
                 int ii[4], jj[4];
@@ -169,23 +265,17 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
                     else { ii[u] = 0; jj[u] = 0; }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int i = base + ii[u], j = base + jj[u];
-                    const Real* wr = W + j * kPanel;
-                    Real x = F[(size_t)j * f + i];
-                    x -= L0[i] * wr[0];
-                    if (nb > 1) x -= L0[f + i] * wr[1];
-                    if (nb > 2) x -= L0[2 * f + i] * wr[2];
-                    if (nb > 3) x -= L0[3 * f + i] * wr[3];
-                    acc[u] = x;
-                }
+                for (int u = 0; u < 4; ++u) acc[u] = trailing(base + ii[u], base + jj[u]);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (t + u * nt < T) F[(size_t)(base + jj[u]) * f + base + ii[u]] = acc[u];
+                for (int u = 0; u < 4; ++u) {
+                    const int tu = t + u * nt;
+                    if (tu < T && !(early && tu == 0))
+                        F[(size_t)(base + jj[u]) * f + base + ii[u]] = acc[u];
+                }
             }
         }
         group_sync<WARP>();
-        if (tid == 0 && base < c) do_pivot(base);
+        if (WARP && tid == piv && base < c) do_pivot(base);
     }
     return nreg;
 }
@@ -322,7 +412,7 @@ __host__ __device__ constexpr int wfactor_stride(int fmax) { return fmax * (fmax
 // warp-level variants for fronts of order ≤ kWarpFront (one warp per front, the front
 // in the warp's slice of shared memory, __syncwarp instead of block barriers)
 // ---------------------------------------------------------------------------
-template <class Wait, class Real = double>
+template <class Wait, class Real = double, int EAQ = 8>
 __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, const double* __restrict__ kval,
                                                   Real* F, Real* lk, int lane, const Wait& wait) {
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
@@ -356,8 +446,8 @@ __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, co
     if (lane < nch) mine = a.cinfo[k0 + lane];
     __syncwarp();
     if (!wait()) return false;
-    // extend-add of each child's update block, its lower triangle spread over the lanes
-    for (int k = 0; k < nch; ++k) {
+    // extend-add of the children's update blocks, several children's loads in flight
+    auto ci_of = [&](int k) {
         ChildInfo ci;
         if (k < 32) {
             ci.u_off = __shfl_sync(0xffffffffu, mine.u_off, k);
@@ -367,12 +457,9 @@ __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, co
         } else {
             ci = a.cinfo[k0 + k];
         }
-        const double* U = a.front + ci.u_off;
-        const int* rel = a.rel + ci.rel_off;
-        const int r = ci.r, fc = ci.fc;
-        extend_add<Real>(F, f, U, fc, rel, r, lane, 32);
-        __syncwarp();
-    }
+        return ci;
+    };
+    extend_add_children<true, EAQ, Real>(F, f, a, nch, ci_of, lane, 32);
     const int nreg = blocked_ldlt<true, Real>(F, lk, lk + kPanel * f, f, c, first, a, lane, 32);
     double* G = a.front + a.front_off[s];
     for (int i = lane; i < ff; i += 32) G[i] = (double)F[i];
@@ -391,41 +478,41 @@ __device__ __forceinline__ void warp_load_panel(const double* __restrict__ L, in
     for (; i < n; i += 32) P[i] = L[i];
 }
 
-template <class Wait>
+// LOADP = false: P already holds the panel (the front just factored, leading dimension f)
+template <class Wait, int EAQ = 8, bool LOADP = true>
 __device__ __forceinline__ bool warp_fwd_front(int s, const FactorView& a, const double* __restrict__ rhs,
-                                               double* __restrict__ w, double* v, double* P, int lane,
+                                               double* __restrict__ w, double* v, const double* P, int lane,
                                                const Wait& wait) {
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
-    warp_load_panel(a.front + a.front_off[s], f * c, P, lane);
+    if (LOADP) warp_load_panel(a.front + a.front_off[s], f * c, const_cast<double*>(P), lane);
     for (int i = lane; i < f; i += 32) v[i] = i < c ? rhs[a.perm[first + i]] : 0.0;
     const int k0 = a.child_ptr[s], nch = a.child_ptr[s + 1] - k0;
     ChildInfo mine;
     if (lane < nch) mine = a.cinfo[k0 + lane];
+    // the pivot reciprocals of the front's columns (c ≤ 64), loaded before the wait
+    const double* dinv = a.dinv + first;
+    const double dv0 = lane < c ? dinv[lane] : 0.0, dv1 = lane + 32 < c ? dinv[lane + 32] : 0.0;
     __syncwarp();
     if (!wait()) return false;
-    for (int k = 0; k < nch; ++k) {
-        int64_t ro;
-        int r;
+    auto ci_of = [&](int k) {
+        ChildInfo ci{0, 0, 0, 0};
         if (k < 32) {
-            ro = __shfl_sync(0xffffffffu, mine.rel_off, k);
-            r = __shfl_sync(0xffffffffu, mine.r, k);
+            ci.rel_off = __shfl_sync(0xffffffffu, mine.rel_off, k);
+            ci.r = __shfl_sync(0xffffffffu, mine.r, k);
         } else {
-            ro = a.cinfo[k0 + k].rel_off;
-            r = a.cinfo[k0 + k].r;
+            ci = a.cinfo[k0 + k];
         }
-        const int* rel = a.rel + ro;
-        const double* u = a.upd + ro;
-        for (int i = lane; i < r; i += 32) v[rel[i]] += __ldcg(u + i);
-        __syncwarp();
-    }
+        return ci;
+    };
+    gather_children_upd<EAQ>(v, a, nch, ci_of, lane);
     for (int k = 0; k < c; ++k) {
         const double xk = v[k];
         const double* colk = P + k * f;
         for (int i = k + 1 + lane; i < f; i += 32) v[i] -= colk[i] * xk;
         __syncwarp();
     }
-    const double* dinv = a.dinv + first;
-    for (int i = lane; i < c; i += 32) w[first + i] = v[i] * dinv[i];
+    if (lane < c) w[first + lane] = v[lane] * dv0;
+    if (lane + 32 < c) w[first + lane + 32] = v[lane + 32] * dv1;
     double* u = a.upd + a.upd_off[s];
     for (int i = c + lane; i < f; i += 32) u[i - c] = v[i];
     __syncwarp();
@@ -442,6 +529,7 @@ __device__ __forceinline__ bool warp_bwd_front(int s, const FactorView& a, const
     const int* R = a.rows + a.row_ptr[s];
     warp_load_panel(a.front + a.front_off[s], f * c, P, lane);
     const int r0 = lane < f ? R[lane] : 0, r1 = lane + 32 < f ? R[lane + 32] : 0;  // f ≤ 64
+    const int p0 = lane < c ? a.perm[first + lane] : 0, p1 = lane + 32 < c ? a.perm[first + lane + 32] : 0;
     if (!wait()) return false;
     if (lane < f) v[lane] = __ldcg(lane < c ? w + first + lane : xp + r0);
     if (lane + 32 < f) v[lane + 32] = __ldcg(lane + 32 < c ? w + first + lane + 32 : xp + r1);
@@ -456,11 +544,14 @@ __device__ __forceinline__ bool warp_bwd_front(int s, const FactorView& a, const
         for (int k = lane; k < i; k += 32) v[k] -= P[k * f + i] * xi;
         __syncwarp();
     }
-    for (int i = lane; i < c; i += 32) {
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i >= c) break;
         const double xi = v[i];
+        const int pi = h ? p1 : p0;
         xp[first + i] = xi;
-        if (accumulate) x[a.perm[first + i]] += xi;
-        else x[a.perm[first + i]] = xi;
+        if (accumulate) x[pi] += xi;
+        else x[pi] = xi;
     }
     __syncwarp();
     return true;

@@ -77,6 +77,17 @@ __global__ void k_scale_by_norm(const double* __restrict__ src, double* __restri
         dst[i] = s * src[i];
 }
 
+// dst = src / den (inverse = false) or src · den (inverse = true), den_i taken as 1 where
+// it is not a positive finite number (a row of zeros with a zero right-hand side)
+__global__ void k_row_scale(const double* __restrict__ src, const double* __restrict__ den, double* __restrict__ dst,
+                            int64_t N, int inverse) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = den[i];
+        const double dd = (d > 0.0 && isfinite(d)) ? d : 1.0;
+        dst[i] = inverse ? src[i] * dd : src[i] / dd;
+    }
+}
+
 unsigned vgrid(int64_t N) {
     const int64_t b = (N + 255) / 256;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, kKBlocks));
@@ -109,6 +120,11 @@ int launch_combination(const double* V, int64_t ld, int nv, const double* c, dou
 int launch_scale_by_norm(const double* src, double* dst, int64_t N, const double* nrm2, double sign,
                          cudaStream_t st) {
     k_scale_by_norm<<<vgrid(N), 256, 0, st>>>(src, dst, N, nrm2, sign);
+    return 1;
+}
+
+int launch_row_scale(const double* src, const double* den, double* dst, int64_t N, bool inverse, cudaStream_t st) {
+    k_row_scale<<<vgrid(N), 256, 0, st>>>(src, den, dst, N, inverse ? 1 : 0);
     return 1;
 }
 

@@ -1,6 +1,6 @@
 // FP64 vector kernels of the GMRES refinement (GMRES-IR: restarted GMRES on the KKT
-// matrix K, right-preconditioned by the LDLᵀ factor, used when plain refinement with a
-// factor that has FP32 large fronts does not reach its target).
+// matrix K, row-scaled and right-preconditioned by the LDLᵀ factor, used when plain
+// refinement with a factor that has FP32 large fronts does not reach its target).
 #pragma once
 
 #include <algorithm>
@@ -26,5 +26,9 @@ int launch_combination(const double* V, int64_t ld, int nv, const double* c, dou
 // dst = sign·src / √(*nrm2) (nrm2: one device scalar)
 int launch_scale_by_norm(const double* src, double* dst, int64_t N, const double* nrm2, double sign,
                          cudaStream_t st);
+
+// dst = D·src (inverse = false) or D⁻¹·src (inverse = true) for D = diag(1/den), the row
+// scaling of the GMRES refinement (den_i = (|K||x| + |r|)_i; 1 where not positive)
+int launch_row_scale(const double* src, const double* den, double* dst, int64_t N, bool inverse, cudaStream_t st);
 
 }  // namespace qoco

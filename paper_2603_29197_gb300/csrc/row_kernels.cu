@@ -137,53 +137,73 @@ __global__ void __launch_bounds__(kLongThreads) k_residual_long(KKTView K, const
     for (int k = 0; k < kResNV; ++k) partial[(int64_t)(nb + blockIdx.x) * kResNV + k] = v[k];
 }
 
-// res = r − K x (unregularised K), maxes |res|, |x|, |r|
-template <int LPR>
+// Componentwise (Oettli–Prager) backward error of one row: |res_i| / (|K||x| + |r|)_i;
+// a row whose denominator is 0 counts 0 when its residual is 0, else +inf.
+__device__ __forceinline__ double cw_ratio(double e, double dn) {
+    return dn > 0.0 ? fabs(e) / dn : (e == 0.0 ? 0.0 : __longlong_as_double(0x7ff0000000000000LL));
+}
+
+// res = r − K x (unregularised K); maxes |res|, |x|, |r| and (CW) the componentwise
+// backward error; den (optional, CW) = |K||x| + |r| per row
+template <int LPR, bool CW>
 __global__ void __launch_bounds__(kRowThreads) k_spmv_res(KKTView K, const double* __restrict__ x,
                                                          const double* __restrict__ r,
-                                                         double* __restrict__ res, double* partial) {
+                                                         double* __restrict__ res, double* __restrict__ den,
+                                                         double* partial) {
     constexpr int GPB = kRowThreads / LPR;
     const int grp = threadIdx.x / LPR, lane = threadIdx.x % LPR;
-    double v[3] = {0.0, 0.0, 0.0};
-    const bool is_max[3] = {true, true, true};
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool is_max[4] = {true, true, true, true};
     for (int base = blockIdx.x * GPB; base < K.N; base += gridDim.x * GPB) {
         const int row = base + grp;
-        double acc = 0.0;
+        double acc = 0.0, aac = 0.0;
         bool mine = row < K.N;
         if (mine) {
             const int64_t beg = K.rowptr[row], end = K.rowptr[row + 1];
             mine = end - beg <= kLongRow;
             if (mine)
-                for (int64_t t = beg + lane; t < end; t += LPR) acc += K.val[t] * x[K.colidx[t]];
+                for (int64_t t = beg + lane; t < end; t += LPR) {
+                    const double kv = K.val[t] * x[K.colidx[t]];
+                    acc += kv;
+                    if (CW) aac += fabs(kv);
+                }
         }
         acc = group_sum<LPR>(acc);
+        if (CW) aac = group_sum<LPR>(aac);
         if (mine && lane == 0) {
-            const double e = r[row] - acc;
+            const double e = r[row] - acc, dn = aac + fabs(r[row]);
             res[row] = e;
+            if (CW && den) den[row] = dn;
             v[0] = amax(v[0], e);
             v[1] = amax(v[1], x[row]);
             v[2] = amax(v[2], r[row]);
+            if (CW) v[3] = amax(v[3], cw_ratio(e, dn));
         }
     }
-    store_partials<3>(v, is_max, partial);
+    store_partials<4>(v, is_max, partial);
 }
 
 __global__ void __launch_bounds__(kLongThreads) k_spmv_res_long(KKTView K, const double* __restrict__ x,
                                                                const double* __restrict__ r,
-                                                               double* __restrict__ res, double* partial,
-                                                               int nb) {
+                                                               double* __restrict__ res, double* __restrict__ den,
+                                                               double* partial, int nb) {
     const int row = K.long_rows[blockIdx.x];
-    double a[1] = {0.0};
-    for (int64_t t = K.rowptr[row] + threadIdx.x; t < K.rowptr[row + 1]; t += kLongThreads)
-        a[0] += K.val[t] * x[K.colidx[t]];
-    block_sum<1>(a);
+    double a[2] = {0.0, 0.0};
+    for (int64_t t = K.rowptr[row] + threadIdx.x; t < K.rowptr[row + 1]; t += kLongThreads) {
+        const double kv = K.val[t] * x[K.colidx[t]];
+        a[0] += kv;
+        a[1] += fabs(kv);
+    }
+    block_sum<2>(a);
     if (threadIdx.x != 0) return;
-    const double e = r[row] - a[0];
+    const double e = r[row] - a[0], dn = a[1] + fabs(r[row]);
     res[row] = e;
-    double* out = partial + (int64_t)(nb + blockIdx.x) * 3;
+    if (den) den[row] = dn;
+    double* out = partial + (int64_t)(nb + blockIdx.x) * 4;
     out[0] = fabs(e);
     out[1] = fabs(x[row]);
     out[2] = fabs(r[row]);
+    out[3] = cw_ratio(e, dn);
 }
 
 // max_i Σ_j |K_ij|
@@ -270,15 +290,17 @@ __global__ void k_finalize_residual(const double* __restrict__ partial, int nb, 
 }
 
 __global__ void k_finalize_refine(const double* __restrict__ partial, int nb, IPMScalars* S) {
-    __shared__ double red[3];
-    reduce_columns(partial, nb, 3, 7u, red);
+    __shared__ double red[4];
+    reduce_columns(partial, nb, 4, 15u, red);
     if (threadIdx.x != 0) return;
     // a non-finite residual, iterate or right-hand side ends the refinement with a
     // non-finite backward error (the caller sees it and does not accept the solve)
     const bool finite = isfinite(red[0]) && isfinite(red[1]) && isfinite(red[2]);
     const double den = S->normK * red[1] + red[2];
-    const double be = !finite ? __longlong_as_double(0x7ff8000000000000LL) : den > 0.0 ? red[0] / den : 0.0;
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    const double be = !finite ? nan : den > 0.0 ? red[0] / den : 0.0;
     S->berr = be;
+    S->berr_cw = finite ? red[3] : nan;
     S->refine_den = den;
     S->refine_done = (!finite || be <= S->refine_tol) ? 1 : 0;
 }
@@ -309,6 +331,16 @@ int row_partials(int N, int n_long) { return (rows_blocks(N, 32) + n_long) * kRe
         default: KERNEL<32><<<rows_blocks(K.N, 32), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 32); break; \
     }
 
+#define QOCO_LPR_SWITCH2(lpr, KERNEL, B, ...)                                                                 \
+    switch (lpr) {                                                                                            \
+        case 1: KERNEL<1, B><<<rows_blocks(K.N, 1), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 1); break;   \
+        case 2: KERNEL<2, B><<<rows_blocks(K.N, 2), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 2); break;   \
+        case 4: KERNEL<4, B><<<rows_blocks(K.N, 4), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 4); break;   \
+        case 8: KERNEL<8, B><<<rows_blocks(K.N, 8), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 8); break;   \
+        case 16: KERNEL<16, B><<<rows_blocks(K.N, 16), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 16); break; \
+        default: KERNEL<32, B><<<rows_blocks(K.N, 32), kRowThreads, 0, st>>>(__VA_ARGS__); nb = rows_blocks(K.N, 32); break; \
+    }
+
 int launch_residual(const KKTView& K, int lpr, const double* xyz, const double* s, const double* c,
                     const double* b, const double* h, double* r, double* partial, int64_t cap,
                     IPMScalars* S, cudaStream_t st) {
@@ -320,11 +352,15 @@ int launch_residual(const KKTView& K, int lpr, const double* xyz, const double* 
     return K.n_long ? 3 : 2;
 }
 int launch_spmv_res(const KKTView& K, int lpr, const double* x, const double* r, double* res,
-                    double* partial, int64_t cap, IPMScalars* S, cudaStream_t st) {
-    if ((int64_t)(rows_blocks(K.N, lpr) + K.n_long) * 3 > cap) return -1;
+                    double* partial, int64_t cap, IPMScalars* S, cudaStream_t st, bool cw, double* den) {
+    if ((int64_t)(rows_blocks(K.N, lpr) + K.n_long) * 4 > cap) return -1;
     int nb = 0;
-    QOCO_LPR_SWITCH(lpr, k_spmv_res, K, x, r, res, partial)
-    if (K.n_long) k_spmv_res_long<<<K.n_long, kLongThreads, 0, st>>>(K, x, r, res, partial, nb);
+    if (cw) {
+        QOCO_LPR_SWITCH2(lpr, k_spmv_res, true, K, x, r, res, den, partial)
+    } else {
+        QOCO_LPR_SWITCH2(lpr, k_spmv_res, false, K, x, r, res, den, partial)
+    }
+    if (K.n_long) k_spmv_res_long<<<K.n_long, kLongThreads, 0, st>>>(K, x, r, res, den, partial, nb);
     k_finalize_refine<<<1, 1024, 0, st>>>(partial, nb + K.n_long, S);
     return K.n_long ? 3 : 2;
 }

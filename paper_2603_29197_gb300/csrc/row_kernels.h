@@ -35,6 +35,7 @@ struct IPMScalars {
     // refinement
     double normK, berr;
     double refine_den;        // ‖K‖∞‖x‖∞ + ‖r‖∞ of the last refinement residual (berr's denominator)
+    double berr_cw;           // componentwise backward error max_i |r − Kx|_i / (|K||x| + |r|)_i
     int refine_done, pad1;
     // shared state of the dataflow kernels: two spare words, the timeout flag, the
     // work-item counter (zeroed together before each solve)
@@ -53,8 +54,11 @@ int row_partials(int N, int n_long);
 int launch_residual(const KKTView& K, int lpr, const double* xyz, const double* s, const double* c,
                     const double* b, const double* h, double* r, double* partial, int64_t cap,
                     IPMScalars* S, cudaStream_t st);
+// cw: also the componentwise backward error (IPMScalars::berr_cw; 0 otherwise) and, when
+// den is given (N doubles), (|K||x| + |r|)_i per row
 int launch_spmv_res(const KKTView& K, int lpr, const double* x, const double* r, double* res,
-                    double* partial, int64_t cap, IPMScalars* S, cudaStream_t st);
+                    double* partial, int64_t cap, IPMScalars* S, cudaStream_t st, bool cw = false,
+                    double* den = nullptr);
 int launch_norm_inf(const KKTView& K, int lpr, double* partial, int64_t cap, IPMScalars* S,
                     cudaStream_t st);
 

@@ -203,8 +203,20 @@ struct PhaseProfiler {
     }
 };
 
+// Event pair timing one triangular solve on a factor with FP32 large fronts: the cost of a
+// GMRES iteration, against which an FP64 refactor is weighed.
+struct SolveTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    double ms = 0.0;  // the latest timed solve
+    ~SolveTimer() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 struct qoco_gpu_solver {
     qoco_gpu_settings st;
+    SolveTimer stimer;
     PhaseProfiler prof;
     int64_t h2d_bytes = 0, d2h_bytes = 0;
     KKTPattern K;
@@ -268,10 +280,16 @@ struct qoco_gpu_solver {
     // consecutive FP32 factorisations whose refinement failed (two stop the retries)
     bool mixed_ok = false;
     int fp32_fail_streak = 0;
+    // smallest signed pivot accepted in a scaled FP32 front, raised tenfold (up to
+    // kPiv32Max) after each breakdown of an FP32 factor within one solve
+    double piv32 = 0.0;
+    int fp32_floor_raises = 0;
     // GMRES refinement (mixed precision): basis V ((restart + 1) × N), work vector, zero
     // vector, Hessenberg column / coefficients (device), dot-product partials
     double *kv_basis = nullptr, *kv_z = nullptr, *kv_zero = nullptr, *kv_h = nullptr, *kv_y = nullptr,
            *kv_part = nullptr;
+    // GMRES row scaling: den = |K||x| + |r| per row at the start of a cycle, and a work vector
+    double *kv_den = nullptr, *kv_t = nullptr;
     int krylov_steps = 0;
     // adjoint: KKT position (row, column) of one slot of each data entry [P | A | G]
     int *d_adj_a = nullptr, *d_adj_b = nullptr;
@@ -281,6 +299,10 @@ struct qoco_gpu_solver {
     int64_t *d_data_slot = nullptr, *d_data_src = nullptr;
     int64_t n_data_slot = 0;
     int solve_epoch = 0;   // flag value of the latest dataflow solve
+    // the right-hand side whose forward sweep the latest dataflow factorisation ran (its
+    // result is in sol_w, flagged with fused_epoch), until the next solve uses or drops it
+    const double* fused_rhs = nullptr;
+    int fused_epoch = 0;
     int factor_epoch = 0;  // flag value of the latest dataflow factorisation
     qoco_gpu_info info;
     std::string msg;
@@ -302,6 +324,17 @@ int dcopy(qoco_gpu_solver* S, T** p, const std::vector<T>& v) {
     if (rc) return rc;
     if (!v.empty()) QOCO_CUDA_TRY(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
     S->h2d_bytes += (int64_t)(v.size() * sizeof(T));
+    return 0;
+}
+
+// Pivot floor of the scaled FP32 large fronts: start of each solve, and the largest the
+// breakdown retries raise it to (1e-5 → 1e-4 → 1e-3 → 1e-2) before refactoring in FP64.
+constexpr double kPiv32Start = 1e-5, kPiv32Max = 1e-2;
+
+int set_piv32(qoco_gpu_solver* S, double v, cudaStream_t st) {
+    S->piv32 = v;
+    QOCO_CUDA_TRY(cudaMemcpyAsync(const_cast<double*>(S->fv.piv32), &S->piv32, sizeof(double),
+                                  cudaMemcpyHostToDevice, st));
     return 0;
 }
 
@@ -601,10 +634,17 @@ int upload(qoco_gpu_solver* S, const double* c, const double* b, const double* h
             if ((rc = dalloc(S, &P.big_work32, (size_t)P.max_big_f * P.max_big_f))) return rc;
             if ((rc = dalloc(S, &P.big_split, (size_t)4 * P.max_big_f * 4 * kBigNB))) return rc;
             if ((rc = dalloc(S, &P.big_scale, (size_t)P.max_big_f))) return rc;
+            double* pv;
+            if ((rc = dalloc(S, &pv, 1))) return rc;
+            f.piv32 = pv;
+            if ((rc = dalloc(S, &f.bad32, 1))) return rc;
+            if ((rc = set_piv32(S, kPiv32Start, nullptr))) return rc;
             if ((rc = big_tma_setup(P))) return rc;
             const size_t R = kKrylovRestart;
             if ((rc = dalloc(S, &S->kv_basis, (R + 1) * (size_t)N))) return rc;
             if ((rc = dalloc(S, &S->kv_z, (size_t)N))) return rc;
+            if ((rc = dalloc(S, &S->kv_den, (size_t)N))) return rc;
+            if ((rc = dalloc(S, &S->kv_t, (size_t)N))) return rc;
             if ((rc = dalloc(S, &S->kv_zero, (size_t)N))) return rc;
             QOCO_CUDA_TRY(cudaMemset(S->kv_zero, 0, sizeof(double) * N));
             if ((rc = dalloc(S, &S->kv_h, 2 * (R + 2) + 1))) return rc;
@@ -732,14 +772,24 @@ int capture_graph(qoco_gpu_solver* S, qoco_gpu_solver::Graph* g, F launch) {
 // kernels every problem uses (dataflow launches, or level launches from graphs).
 constexpr int kSharedSchedule = 5;
 
-int factor_shared(qoco_gpu_solver* S, cudaStream_t st) {
+int factor_shared(qoco_gpu_solver* S, cudaStream_t st, const double* fwd_rhs) {
+    S->fused_rhs = nullptr;
     if (S->plan.fdataflow) {
         DataflowState ds;
         ds.next = &S->d_S->sched_next;
         ds.err = &S->d_S->bar_err;
         ds.epoch = ++S->factor_epoch;
         ds.max_spins = S->wait_polls;
-        const int rc = launch_factor_dataflow(S->plan, S->fv, S->d_val, ds, st);
+        FwdFuse fz;
+        if (fwd_rhs && S->plan.dataflow) {  // the forward sweep of fwd_rhs in the same launch
+            fz.rhs = fwd_rhs;
+            fz.w = S->sol_w;
+            fz.fdone = S->plan.d_fdone;
+            fz.epoch = ++S->solve_epoch;
+        }
+        const int rc = launch_factor_dataflow(S->plan, S->fv, S->d_val, ds, st, fz);
+        S->fused_rhs = fz.rhs;
+        S->fused_epoch = fz.epoch;
         if (rc < 0) return rc;
         S->launches += rc;
         return 0;
@@ -757,13 +807,15 @@ int factor_shared(qoco_gpu_solver* S, cudaStream_t st) {
 }
 
 int solve_shared(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStream_t st) {
+    const bool fused = S->fused_rhs && S->fused_rhs == r && !acc;
+    S->fused_rhs = nullptr;
     if (S->plan.dataflow) {
         DataflowState ds;
         ds.next = &S->d_S->sched_next;
         ds.err = &S->d_S->bar_err;
-        ds.epoch = ++S->solve_epoch;
+        ds.epoch = fused ? S->fused_epoch : ++S->solve_epoch;
         ds.max_spins = S->wait_polls;
-        const int rc = launch_solve_dataflow(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, ds, st);
+        const int rc = launch_solve_dataflow(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, ds, st, fused);
         if (rc < 0) return rc;
         S->launches += rc;
     } else {
@@ -789,18 +841,20 @@ int solve_shared(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaS
     return 0;
 }
 
-int factor_with(qoco_gpu_solver* S, int v, cudaStream_t st) {
+int factor_with(qoco_gpu_solver* S, int v, cudaStream_t st, const double* fwd_rhs) {
     if (v >= 1 && v <= 4) {
+        S->fused_rhs = nullptr;
         const int rc = launch_inst_factor(S->plan, S->fv, S->d_val, v, st);
         if (rc < 0) return rc;
         S->launches += rc;
         return 0;
     }
-    return factor_shared(S, st);
+    return factor_shared(S, st, fwd_rhs);
 }
 
 int solve_with(qoco_gpu_solver* S, int v, const double* r, double* x, bool acc, cudaStream_t st) {
     if (v >= 1 && v <= 4) {
+        S->fused_rhs = nullptr;
         const int rc = launch_inst_solve(S->plan, S->fv, r, S->sol_w, S->sol_xp, x, acc, v, st);
         if (rc < 0) return rc;
         S->launches += rc;
@@ -809,7 +863,9 @@ int solve_with(qoco_gpu_solver* S, int v, const double* r, double* x, bool acc, 
     return solve_shared(S, r, x, acc, st);
 }
 
-int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
+// fwd_rhs: a right-hand side whose forward sweep the factorisation may run on the way
+// (the next solve of fwd_rhs then runs only the backward sweep)
+int factor_now(qoco_gpu_solver* S, cudaStream_t st, const double* fwd_rhs = nullptr) {
     {
         Phase ph(S, QOCO_GPU_PHASE_ROW, st);
         const int nl = launch_norm_inf(S->kv, S->lpr, S->partial, S->partial_cap, S->d_S, st);
@@ -818,7 +874,7 @@ int factor_now(qoco_gpu_solver* S, cudaStream_t st) {
     }
     {
         Phase ph(S, QOCO_GPU_PHASE_FACTOR, st);
-        const int rc = factor_with(S, S->plan.inst ? S->plan.inst_variant : kSharedSchedule, st);
+        const int rc = factor_with(S, S->plan.inst ? S->plan.inst_variant : kSharedSchedule, st, fwd_rhs);
         if (rc) return rc;
     }
     QOCO_CUDA_TRY(cudaGetLastError());
@@ -832,33 +888,69 @@ int tri_solve(qoco_gpu_solver* S, const double* r, double* x, bool acc, cudaStre
     return solve_with(S, S->plan.inst ? S->plan.inst_variant : kSharedSchedule, r, x, acc, st);
 }
 
-int refine_residual(qoco_gpu_solver* S, const double* x, const double* r, double* res, cudaStream_t st) {
+int refine_residual(qoco_gpu_solver* S, const double* x, const double* r, double* res, cudaStream_t st,
+                    double* den = nullptr) {
     Phase ph(S, QOCO_GPU_PHASE_ROW, st);
-    const int nl = launch_spmv_res(S->kv, S->lpr, x, r, res, S->partial, S->partial_cap, S->d_S, st);
+    const int nl = launch_spmv_res(S->kv, S->lpr, x, r, res, S->partial, S->partial_cap, S->d_S, st,
+                                   S->plan.big_fp32 || den, den);
     if (nl < 0) return QOCO_GPU_ERR_INVALID_ARG;
     S->launches += nl;
     return 0;
 }
 
-// GMRES refinement (GMRES-IR, Carson & Higham 2017–2018): restarted GMRES on K x = r with
-// K the unregularised KKT matrix (FP64 products), right-preconditioned by the current
-// factor M (FP32 large fronts): the Krylov space of K·M⁻¹ is built from the residual of the
-// refined x, orthogonalised by classical Gram–Schmidt applied twice, its least-squares
-// problem reduced by Givens rotations on the host, and x += M⁻¹·V·y at the end of a cycle;
-// each cycle ends early when the GMRES residual estimate is below half the backward-error
-// target, and is followed by the true residual.  Sets *ok when the backward error of x
-// reaches refine_tol.
+// Acceptance of a refined solve: the normwise backward error ‖r − Kx‖∞ / (‖K‖∞‖x‖∞ +
+// ‖r‖∞) at refine_tol; on a factor with FP32 large fronts also the componentwise one,
+// max_i |r − Kx|_i / (|K||x| + |r|)_i, at refine_tol.  Near the end of a solve ‖K‖∞ is
+// ~1e16 (the −W² entries of inactive constraints), and a solve from an FP32 factor that
+// met the normwise target alone could still be wrong in the rows of small scale (the
+// equality rows), which stalled the interior-point iteration; an FP64 factor meets both
+// by far.
+bool solve_accepted(const qoco_gpu_solver* S) {
+    const IPMScalars& h = *S->h_S;
+    if (!h.refine_done || !std::isfinite(h.berr)) return false;
+    return !S->plan.big_fp32 || h.berr_cw <= S->st.refine_tol;
+}
+// progress measure of the refinement (≤ 1: accepted, up to the refine_done flag)
+double refine_error(const qoco_gpu_solver* S) {
+    const IPMScalars& h = *S->h_S;
+    const double e = h.berr / S->st.refine_tol;
+    return S->plan.big_fp32 ? std::fmax(e, h.berr_cw / S->st.refine_tol) : e;
+}
+
+// GMRES refinement (GMRES-IR, Carson & Higham 2017–2018) on K x = r, K the unregularised
+// KKT matrix (FP64 products), preconditioned by the current factor M (FP32 large fronts)
+// and row-scaled: with D = diag(1/(|K||x| + |r|)) fixed at the start of a cycle, GMRES runs
+// on D·K·M⁻¹·D⁻¹ (≈ I) from the scaled residual D(r − Kx), so that it minimises
+// ‖D(r − Kx)‖₂, a bound on the componentwise backward error (and, since every row's
+// denominator is at most ‖K‖∞‖x‖∞ + ‖r‖∞, on the normwise one).  The Krylov basis is
+// orthogonalised by classical Gram–Schmidt applied twice, the least-squares problem
+// reduced by Givens rotations on the host, and x += M⁻¹·D⁻¹·V·y at the end of a cycle;
+// each cycle ends early when the GMRES residual estimate is below half the target, and
+// is followed by the true residual.  Sets *ok when the solve is accepted.
+// GMRES iterations worth spending before an FP64 refactor is cheaper: a GMRES iteration
+// costs about 1.25 triangular solves (the timed one), an FP64 refactor its algorithmic
+// flops at ~1 TFLOP/s (this part's FP64 rate); between 10 and 3 cycles of kKrylovRestart.
+int gmres_budget(const qoco_gpu_solver* S) {
+    const double fp64_ms = S->S.flops / 1e9;
+    const double per = std::max(1.25 * S->stimer.ms, 1e-3);
+    return (int)std::min(3.0 * kKrylovRestart, std::max(10.0, fp64_ms / per));
+}
+
 int gmres_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st, bool* ok) {
     constexpr int R = kKrylovRestart, kCycles = 3;
+    const int budget = gmres_budget(S);
+    int used = 0;
     const int64_t N = S->N, ld = N;
     double* V = S->kv_basis;
     double* hd = S->kv_h;  // [0, R+2): first pass, [R+2, 2R+4): second pass, [2R+4]: ‖w‖²
+    double* den = S->kv_den;
     *ok = false;
     std::vector<double> H((size_t)(R + 1) * R, 0.0), cs(R), sn(R), g(R + 1), hc(2 * (R + 2) + 1), y(R);
     int rc;
-    for (int cycle = 0; cycle < kCycles; ++cycle) {
-        if ((rc = refine_residual(S, x, r, S->res, st))) return rc;
-        // β = ‖r − Kx‖₂, v_0 = (r − Kx)/β
+    for (int cycle = 0; cycle < kCycles && used < budget; ++cycle) {
+        if ((rc = refine_residual(S, x, r, S->res, st, den))) return rc;
+        // β = ‖D(r − Kx)‖₂, v_0 = D(r − Kx)/β
+        S->launches += launch_row_scale(S->res, den, S->res, N, false, st);
         S->launches += launch_dots(S->res, ld, 1, S->res, N, S->kv_part, hd, false, st);
         S->launches += launch_scale_by_norm(S->res, V, N, hd, 1.0, st);
         QOCO_CUDA_TRY(cudaMemcpyAsync(S->h_S, S->d_S, sizeof(IPMScalars), cudaMemcpyDeviceToHost, st));
@@ -867,9 +959,9 @@ int gmres_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
         if (S->prof.on) S->prof.flush();
         if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
         if (!std::isfinite(S->h_S->berr)) return 0;
-        if (S->h_S->refine_done) { *ok = true; return 0; }
+        if (solve_accepted(S)) { *ok = true; return 0; }
         const double beta = std::sqrt(hc[0]);
-        const double target = 0.5 * S->st.refine_tol * S->h_S->refine_den;
+        const double target = 0.5 * S->st.refine_tol;
         if (!(beta > 0.0)) return 0;
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
@@ -877,8 +969,10 @@ int gmres_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
         for (int j = 0; j < R; ++j) {
             double* vj = V + (int64_t)j * ld;
             double* w = V + (int64_t)(j + 1) * ld;
-            if ((rc = tri_solve(S, vj, S->kv_z, false, st))) return rc;              // z = M⁻¹ v_j
-            if ((rc = refine_residual(S, S->kv_z, S->kv_zero, w, st))) return rc;  // w = −K z
+            S->launches += launch_row_scale(vj, den, S->kv_t, N, true, st);             // D⁻¹ v_j
+            if ((rc = tri_solve(S, S->kv_t, S->kv_z, false, st))) return rc;           // z = M⁻¹ D⁻¹ v_j
+            if ((rc = refine_residual(S, S->kv_z, S->kv_zero, w, st))) return rc;      // w = −K z
+            S->launches += launch_row_scale(w, den, w, N, false, st);                   // w = −D K z
             // two classical Gram–Schmidt passes on the negated vector, then its norm
             S->launches += launch_dots(V, ld, j + 1, w, N, S->kv_part, hd, false, st);
             S->launches += launch_sub_combination(V, ld, j + 1, hd, w, N, st);
@@ -891,6 +985,7 @@ int gmres_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
             S->d2h_bytes += (int64_t)(sizeof(double) * hc.size());
             if (S->prof.on) S->prof.flush();
             ++S->krylov_steps;
+            ++used;
             double* h = &H[(size_t)j * (R + 1)];  // column j of the Hessenberg matrix
             for (int i = 0; i <= j; ++i) h[i] = -(hc[i] + hc[R + 2 + i]);
             h[j + 1] = std::sqrt(hc[2 * (R + 2)]);
@@ -908,9 +1003,9 @@ int gmres_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
             g[j + 1] = -sn[j] * g[j];
             g[j] = cs[j] * g[j];
             k = j + 1;
-            if (std::fabs(g[j + 1]) <= target || !(hc[2 * (R + 2)] > 0.0)) break;
+            if (std::fabs(g[j + 1]) <= target || !(hc[2 * (R + 2)] > 0.0) || used >= budget) break;
         }
-        // y = R⁻¹ g, x += M⁻¹ V y
+        // y = R⁻¹ g, x += M⁻¹ D⁻¹ V y
         for (int i = k - 1; i >= 0; --i) {
             double a = g[i];
             for (int c = i + 1; c < k; ++c) a -= H[(size_t)c * (R + 1) + i] * y[c];
@@ -918,12 +1013,13 @@ int gmres_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
         }
         QOCO_CUDA_TRY(cudaMemcpyAsync(S->kv_y, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
         S->launches += launch_combination(V, ld, k, S->kv_y, S->kv_z, N, st);
-        if ((rc = tri_solve(S, S->kv_z, x, true, st))) return rc;
+        S->launches += launch_row_scale(S->kv_z, den, S->kv_t, N, true, st);
+        if ((rc = tri_solve(S, S->kv_t, x, true, st))) return rc;
     }
     if ((rc = refine_residual(S, x, r, S->res, st))) return rc;
     if ((rc = sync_scalars(S, st))) return rc;
     if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
-    *ok = S->h_S->refine_done && std::isfinite(S->h_S->berr);
+    *ok = solve_accepted(S);
     return 0;
 }
 
@@ -933,8 +1029,13 @@ int gmres_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
 // too, the solve refactors in FP64 (for the rest of the current solve) and starts over.
 int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st) {
     for (;;) {
+        if (S->plan.big_fp32 && !S->stimer.a && cudaEventCreate(&S->stimer.a) == cudaSuccess)
+            if (cudaEventCreate(&S->stimer.b) != cudaSuccess) S->stimer.b = nullptr;
+        const bool timed = S->plan.big_fp32 && S->stimer.a && S->stimer.b;
+        if (timed) QOCO_CUDA_TRY(cudaEventRecord(S->stimer.a, st));
         int rc0 = tri_solve(S, r, x, false, st);
         if (rc0) return rc0;
+        if (timed) QOCO_CUDA_TRY(cudaEventRecord(S->stimer.b, st));
         int steps = 0;
         double prev = INFINITY;
         for (;;) {
@@ -943,27 +1044,53 @@ int solve_refine(qoco_gpu_solver* S, const double* r, double* x, cudaStream_t st
             QOCO_CUDA_TRY(cudaGetLastError());
             if ((rc = sync_scalars(S, st))) return rc;
             if (S->h_S->bar_err) return QOCO_GPU_ERR_DEVICE_TIMEOUT;
-            if (S->h_S->refine_done || steps >= S->st.max_refine) break;
+            if (timed && steps == 0) {
+                float ms = 0.0f;
+                if (cudaEventElapsedTime(&ms, S->stimer.a, S->stimer.b) == cudaSuccess) S->stimer.ms = ms;
+            }
+            if (solve_accepted(S) || steps >= S->st.max_refine) break;
+            const double err = refine_error(S);
             // an FP32 factor whose refinement no longer halves the error: GMRES takes over
-            if (S->plan.big_fp32 && S->kv_basis && steps >= 2 && !(S->h_S->berr < 0.5 * prev)) break;
-            prev = S->h_S->berr;
+            if (S->plan.big_fp32 && S->kv_basis && steps >= 2 && !(err < 0.5 * prev)) break;
+            prev = err;
             if ((rc = tri_solve(S, S->res, x, true, st))) return rc;
             ++steps;
         }
         S->refine_steps += steps;
         S->last_berr = S->h_S->berr;
-        bool ok = S->h_S->refine_done && std::isfinite(S->h_S->berr);
+        bool ok = solve_accepted(S);
         if (ok && S->plan.big_fp32) S->fp32_fail_streak = 0;
         if (S->st.verbose >= 2)
-            printf("     refine: %d steps, backward error %.3e (%s factor)%s\n", steps, S->h_S->berr,
-                   S->plan.big_fp32 ? "FP32 large fronts" : "FP64", ok ? "" : " - target missed");
+            printf("     refine: %d steps, backward error %.3e, componentwise %.3e (%s factor)%s\n", steps,
+                   S->h_S->berr, S->h_S->berr_cw, S->plan.big_fp32 ? "FP32 large fronts" : "FP64",
+                   ok ? "" : " - target missed");
+        if (!ok && S->plan.big_fp32) {
+            // a factor that broke down (a non-finite or overgrown entry in a scaled FP32
+            // front): FP32 again with a ten times larger pivot floor while it is below
+            // kPiv32Max, else FP64
+            int bad = 0;
+            QOCO_CUDA_TRY(cudaMemcpyAsync(&bad, S->fv.bad32, sizeof(int), cudaMemcpyDeviceToHost, st));
+            QOCO_CUDA_TRY(cudaStreamSynchronize(st));
+            S->d2h_bytes += (int64_t)sizeof(int);
+            if (bad && S->piv32 < 0.5 * kPiv32Max) {
+                int rc = set_piv32(S, 10.0 * S->piv32, st);
+                if (rc) return rc;
+                ++S->fp32_floor_raises;
+                if (S->st.verbose >= 2)
+                    printf("     FP32 factor broke down: refactoring with pivot floor %.0e\n", S->piv32);
+                if ((rc = factor_now(S, st))) return rc;
+                continue;
+            }
+            if (bad) S->h_S->berr = INFINITY;  // no GMRES on a broken factor
+        }
         if (!ok && S->plan.big_fp32 && S->kv_basis && std::isfinite(S->h_S->berr)) {
             const int k0 = S->krylov_steps;
             int rc = gmres_refine(S, r, x, st, &ok);
             if (rc) return rc;
             S->last_berr = S->h_S->berr;
             if (S->st.verbose >= 2)
-                printf("     GMRES: %d iterations, backward error %.3e%s\n", S->krylov_steps - k0, S->h_S->berr,
+                printf("     GMRES: %d iterations, backward error %.3e, componentwise %.3e%s\n",
+                       S->krylov_steps - k0, S->h_S->berr, S->h_S->berr_cw,
                        ok ? "" : " - target missed, refactoring in FP64");
             if (ok) S->fp32_fail_streak = 0;
         }
@@ -1085,13 +1212,15 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
     S->krylov_steps = 0;
     S->mixed_ok = S->st.mixed_precision != 0 && S->plan.max_big_f > 0 && S->plan.big_work32;
     S->fp32_fail_streak = 0;
+    S->fp32_floor_raises = 0;
     S->plan.big_fp32 = S->mixed_ok;
+    if (S->mixed_ok && (rc = set_piv32(S, kPiv32Start, st))) return rc;
     if ((rc = reset_barrier(S, st))) return rc;
     // initial point: K(W = I) [x; y; z] = [−c; b; h], s = −z, shift s and z into the cone
     S->launches += launch_w2_identity(cv, S->d_val, S->d_w2slot, S->d_w2ptr, st);
-    if ((rc = factor_now(S, st))) return rc;
     k_init_rhs<<<grid(N), 256, 0, st>>>(S->rhs, S->d_c, S->d_b, S->d_h, n, p, m);
     S->launches += 1;
+    if ((rc = factor_now(S, st, S->rhs))) return rc;
     if ((rc = solve_refine(S, S->rhs, S->d_cmb, st))) return rc;
     k_init_iterate<<<grid(N), 256, 0, st>>>(S->d_cmb, S->xyz, S->s, n, p, m);
     S->launches += 1;
@@ -1157,8 +1286,7 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
         }
         // FP32 large fronts again after an FP64 escalation, unless the last two failed
         S->plan.big_fp32 = S->mixed_ok && S->fp32_fail_streak < 2;
-        if ((rc = factor_now(S, st))) return rc;
-        // predictor
+        // predictor right-hand side first: the factorisation can run its forward sweep
         if (n + p) { k_neg_copy<<<grid(n + p), 256, 0, st>>>(S->rhs, S->r, n + p); S->launches++; }
         if (m) {
             Phase ph(S, QOCO_GPU_PHASE_CONE, st);
@@ -1166,6 +1294,8 @@ int run_solve(qoco_gpu_solver* S, cudaStream_t st) {
                          S->t1, S->t2, S->rhs + n + p, st);
             S->launches += cl;
         }
+        if ((rc = factor_now(S, st, S->rhs))) return rc;
+        // predictor
         if ((rc = solve_refine(S, S->rhs, S->d_aff, st))) return rc;
         if (m) {
             Phase ph(S, QOCO_GPU_PHASE_CONE, st);
@@ -1237,6 +1367,7 @@ void fill_info(const qoco_gpu_solver* S, qoco_gpu_info* info) {
     info->d2h_bytes = S->d2h_bytes;
     info->fp32_factors = S->fp32_factors;
     info->fp64_escalations = S->fp64_escalations;
+    info->fp32_floor_raises = S->fp32_floor_raises;
     info->krylov_steps = S->krylov_steps;
     info->batch_warps = S->fused_nw;
     info->batch_thread_fronts = S->fused_nw ? S->fused_split : 0;
