@@ -213,27 +213,36 @@ def fp64_peaks(q):
     return _FP64
 
 
-def kernel_source_digest():
-    """Digest of the CUDA sources: DRAM traffic measured by ncu is only reported while
-    the kernels are the ones it was measured on."""
+# The sources each profiled kernel is built from (its own file and the headers it
+# includes); the DRAM traffic ncu measured stays valid while these are unchanged.
+KERNEL_SOURCES = {
+    "k_factor_dataflow": ["factor.cu", "fronts.cuh", "factor.h", "common.cuh", "plan.h"],
+    "k_solve_dataflow": ["factor.cu", "fronts.cuh", "factor.h", "common.cuh", "plan.h"],
+}
+
+
+def kernel_source_digest(kernel=None):
+    """Digest of the CUDA sources of `kernel` (all of them when it has no entry in
+    KERNEL_SOURCES): DRAM traffic measured by ncu is only reported while the kernel is
+    the one it was measured on."""
     import hashlib
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2603_29197_gb300", "csrc")
-    for name in sorted(os.listdir(src)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(src, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    names = KERNEL_SOURCES.get(kernel) or [n for n in os.listdir(src) if n.endswith((".cu", ".cuh", ".h"))]
+    for name in sorted(names):
+        with open(os.path.join(src, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel, stages):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel`, from the ncu
     summary in profiles/ (a line `traffic <kernel> <stages> <bytes> <source digest>`),
-    or None when no capture matches this workload and these sources."""
+    or None when no capture matches this workload and this kernel's sources."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    digest = kernel_source_digest()
+    digest = kernel_source_digest(kernel)
     with open(path) as f:
         for line in f:
             t = line.split()
@@ -255,7 +264,8 @@ def roofline(profile, info, stages, fp64):
         flops = info["factor_flops"]
         ach = flops / (per_call_ms * 1e-3) / 1e9
         peak = max(fp64)
-        return {"kernel": "k_factor_dataflow (one launch per LDLᵀ factorisation)",
+        return {"kernel": "k_factor_dataflow (one launch per LDLᵀ factorisation, the predictor's forward "
+                          "sweep fused into it; achieved counts the factorisation's flops only)",
                 "bound": "alu", "achieved": ach, "peak": peak, "unit": "GFLOP/s",
                 "frac": ach / peak, "traffic": ncu_traffic("k_factor_dataflow", stages),
                 "per_launch_unit": f"{flops:.4g} algorithmic flops per factorisation",

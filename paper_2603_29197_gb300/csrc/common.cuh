@@ -56,17 +56,17 @@ __device__ __forceinline__ double warp_min_nonneg(double v) {
     return __longlong_as_double(b);
 }
 
-// 1/d by two Newton–Raphson steps r ← r + r(1 − d·r) from the hardware's approximate
-// reciprocal (relative error of the seed ≲ 2^-22, so two quadratic steps reach the
-// FP64 rounding level).  Four FMAs instead of an IEEE division sequence; d must be a
-// normal number (pivots are kept away from zero by the dynamic regularisation).
+// 1/d by one third-order (Chebyshev) step from the hardware's approximate reciprocal r:
+// with e = 1 − d·r, r(1 + e + e²) has relative error e³ (1 − d·r(1+e+e²) = e³ exactly),
+// and the seed's e ≲ 2^-22 puts e³ far below the FP64 rounding level.  Three dependent
+// FMAs, one fewer than two quadratic Newton steps; every FP64 instruction is scarce on
+// this part.  d must be a normal number (pivots are kept away from zero by the dynamic
+// regularisation).
 __device__ __forceinline__ double recip(double d) {
     double r;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-    double e = fma(-d, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-d, r, 1.0);
-    return fma(r, e, r);
+    const double e = fma(-d, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 
 

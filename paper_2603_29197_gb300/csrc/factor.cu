@@ -67,9 +67,10 @@ __device__ __forceinline__ bool cta_factor_front(int s, const FactorView& a, con
     // a small shared table
     __shared__ ChildInfo s_ci[32];
     if (tid < nch && tid < 32) s_ci[tid] = a.cinfo[k0 + tid];
+    stage_pivot_signs(lk + (size_t)kPanel * f, c, first, a, tid, nt);
     __syncthreads();
     if (!wait()) return false;
-    extend_add_children<false, 8, double>(F, f, a, nch, [&](int k) { return k < 32 ? s_ci[k] : a.cinfo[k0 + k]; },
+    extend_add_children<false, 12, double>(F, f, a, nch, [&](int k) { return k < 32 ? s_ci[k] : a.cinfo[k0 + k]; },
                                           tid, nt);
     const int nreg = blocked_ldlt<false>(F, lk, lk + (size_t)kPanel * f, f, c, first, a, tid, nt);
     if (nreg) atomicAdd(a.nreg, nreg);  // the pivot thread's count

@@ -178,6 +178,15 @@ __device__ __forceinline__ void tri_advance(int m, int stride, int& ii, int& jj)
 // update gives each thread four independent entries per step, and in a CTA the pivot
 // thread first updates the next panel's first diagonal entry and computes its pivot.
 // Every entry sees the same operations in the same order whichever thread computes it.
+// The pivot signs into bc[kPanel+1 ..] (called by the front's group before its dependency
+// wait, so that the global loads are off the critical path; blocked_ldlt's first barrier
+// publishes them).
+template <class Real>
+__device__ __forceinline__ void stage_pivot_signs(Real* bc, int c, int first, const FactorView& a, int tid, int nt) {
+    Real* sgn = bc + kPanel + 1;
+    for (int k = tid; k < c; k += nt) sgn[k] = a.dsign[first + k] > 0 ? Real(1) : Real(-1);
+}
+
 template <bool WARP, class Real = double>
 __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, int c, int first,
                                             const FactorView& a, int tid, int nt) {
@@ -185,7 +194,6 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
     double* dinv = a.dinv + first;
     Real* sgn = bc + kPanel + 1;
     const int piv = WARP ? 0 : nt - 1;  // the thread that computes the pivots
-    for (int k = tid; k < c; k += nt) sgn[k] = a.dsign[first + k] > 0 ? Real(1) : Real(-1);
     group_sync<WARP>();
     auto do_pivot = [&](int k) {  // the pivot thread only
         Real* colk = F + (size_t)k * f;
@@ -440,10 +448,12 @@ __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, co
             }
         }
     }
-    // child records of the first 32 children, one per lane (loaded before the wait)
+    // child records of the first 32 children, one per lane, and the pivot signs (loaded
+    // before the wait)
     const int k0 = a.child_ptr[s], nch = a.child_ptr[s + 1] - k0;
     ChildInfo mine;
     if (lane < nch) mine = a.cinfo[k0 + lane];
+    stage_pivot_signs(lk + kPanel * f, c, first, a, lane, 32);
     __syncwarp();
     if (!wait()) return false;
     // extend-add of the children's update blocks, several children's loads in flight
@@ -534,9 +544,18 @@ __device__ __forceinline__ bool warp_bwd_front(int s, const FactorView& a, const
     if (lane < f) v[lane] = __ldcg(lane < c ? w + first + lane : xp + r0);
     if (lane + 32 < f) v[lane + 32] = __ldcg(lane + 32 < c ? w + first + lane + 32 : xp + r1);
     __syncwarp();
-    for (int i = c; i < f; ++i) {
-        const double xi = v[i];
-        for (int k = lane; k < c; k += 32) v[k] -= P[k * f + i] * xi;
+    // the solved entries below the pivot block (i ≥ c) into each pivot row k < c: a register
+    // sum per lane in two interleaved partial sums (v_i for i ≥ c is read-only here, so the
+    // FMAs of one lane do not wait on shared memory)
+    for (int k = lane; k < c; k += 32) {
+        double a0 = v[k], a1 = 0.0;
+        int i = c;
+        for (; i + 1 < f; i += 2) {
+            a0 -= P[k * f + i] * v[i];
+            a1 -= P[k * f + i + 1] * v[i + 1];
+        }
+        if (i < f) a0 -= P[k * f + i] * v[i];
+        v[k] = a0 + a1;
     }
     __syncwarp();
     for (int i = c - 1; i > 0; --i) {
