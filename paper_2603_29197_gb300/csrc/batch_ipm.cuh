@@ -149,33 +149,48 @@ __device__ __noinline__ double inst_normK(const BatchIPMArgs& A, const Rows& R, 
 // res = r − K x on the instance's rows; returns the backward error (NaN when a value is
 // not finite)
 __device__ __noinline__ double inst_residual(const BatchIPMArgs& A, const Rows& R, const double* x, const double* r,
-                                double* res, double normK, double* red) {
-    double v[3] = {0.0, 0.0, 0.0};  // ‖res‖∞, ‖x‖∞, ‖r‖∞
+                                double* res, double normK, double* red, double* cw) {
+    // ‖res‖∞, ‖x‖∞, ‖r‖∞, max_i |res_i| / (|K||x| + |r|)_i (componentwise)
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = threadIdx.x; k < R.total; k += blockDim.x) {
         const int row = R.row(k);
-        double a = r[row];
-        for (int64_t t = A.K.rowptr[row]; t < A.K.rowptr[row + 1]; ++t) a -= A.kval[t] * x[A.K.colidx[t]];
+        double a = r[row], d = fabs(r[row]);
+        for (int64_t t = A.K.rowptr[row]; t < A.K.rowptr[row + 1]; ++t) {
+            const double kx = A.kval[t] * x[A.K.colidx[t]];
+            a -= kx;
+            d += fabs(kx);
+        }
         res[row] = a;
         v[0] = amax(v[0], a);
         v[1] = amax(v[1], x[row]);
         v[2] = amax(v[2], r[row]);
+        v[3] = amax(v[3], d > 0.0 ? a / d : (a == 0.0 ? 0.0 : a * __longlong_as_double(0x7ff0000000000000LL)));
     }
-    const int kind[3] = {1, 1, 1};
-    cta_reduce<3>(v, kind, red);
-    if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) return __longlong_as_double(0x7ff8000000000000LL);
+    const int kind[4] = {1, 1, 1, 1};
+    cta_reduce<4>(v, kind, red);
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
+        *cw = nan;
+        return nan;
+    }
+    *cw = v[3];
     const double den = normK * v[1] + v[2];
     return den > 0.0 ? v[0] / den : 0.0;
 }
 
 // x = K_ε⁻¹ r refined against K to the backward-error target (≤ max_refine steps);
-// returns whether the target was reached
+// returns whether the target was reached.  cw: the componentwise backward error must
+// reach it too (solves on an FP32 factor: near the end of a solve ‖K‖∞ is ~1e16, and a
+// solve that met the normwise target alone could still be wrong in the rows of small
+// scale, which slowed or broke the instance's iteration)
 template <int NW>
 __device__ bool inst_solve_refine(const BatchIPMArgs& A, int inst, const Rows& R, const double* r, double* x,
-                                  double normK, double* V, double* red) {
+                                  double normK, double* V, double* red, bool cw) {
     inst_solve<NW>(A, inst, r, x, 0, V);
     for (int steps = 0;; ++steps) {
-        const double be = inst_residual(A, R, x, r, A.res, normK, red);
-        if (be <= A.refine_tol) return true;
+        double bcw;
+        const double be = inst_residual(A, R, x, r, A.res, normK, red, &bcw);
+        if (be <= A.refine_tol && (!cw || bcw <= A.refine_tol)) return true;
         if (!(be == be) || steps >= A.max_refine) return false;  // NaN, or out of steps
         inst_solve<NW>(A, inst, A.res, x, 1, V);
     }
@@ -187,13 +202,13 @@ __device__ bool inst_solve_refine(const BatchIPMArgs& A, int inst, const Rows& R
 template <int NW, bool MIX>
 __device__ void inst_solve_mixed(const BatchIPMArgs& A, int inst, const Rows& R, const double* r, double* x,
                                  double normK, double* V, double* red, bool& fp32, int& fails) {
-    const bool ok = inst_solve_refine<NW>(A, inst, R, r, x, normK, V, red);
+    const bool ok = inst_solve_refine<NW>(A, inst, R, r, x, normK, V, red, MIX && fp32);
     if (MIX && fp32) {
         if (ok) { fails = 0; return; }
         ++fails;
         fp32 = false;
         inst_factor<NW, double>(A, inst, V);
-        inst_solve_refine<NW>(A, inst, R, r, x, normK, V, red);
+        inst_solve_refine<NW>(A, inst, R, r, x, normK, V, red, false);
     }
 }
 
