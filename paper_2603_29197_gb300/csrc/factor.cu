@@ -391,11 +391,20 @@ __device__ __forceinline__ bool fused_fwd_warp(int s, const FactorView& a, const
     return warp_fwd_front<decltype(wait), 8, false>(s, a, fz.rhs, fz.w, v, F, lane, wait);
 }
 
+// Shared memory per warp of the dataflow factorisation: one front of order ≤ fmax, or two
+// of order ≤ kPairFront (one per half-warp).
+__host__ __device__ __forceinline__ int fdataflow_warp_stride(int fmax) {
+    const int pf = fmax < kPairFront ? fmax : kPairFront;
+    const int one = wfactor_stride(fmax), two = 2 * wfactor_stride(pf);
+    return one > two ? one : two;
+}
+
 // ---------------------------------------------------------------------------
 // Dataflow factorisation: one launch, blocks of kDataflowThreads take items in level
 // order from an atomic counter.  Item kinds (low two bits): 0 = batch of up to 128
 // one-thread fronts, 1 = group of up to 4 warp fronts, 2 = one front for the whole
-// CTA.  A front waits (bounded polls) for its children's completion flags after its
+// CTA, 3 = group of up to 8 fronts of order ≤ kPairFront, two per warp (one per
+// half-warp).  A front waits (bounded polls) for its children's completion flags after its
 // independent assembly; the deadlock argument is the one of the dataflow solve.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
@@ -454,7 +463,7 @@ __global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
             const int t = wg_ptr[idx] + wid;
             if (t < wg_ptr[idx + 1]) {
                 const int s = wlist[t];
-                double* F = smem + (size_t)wid * wfactor_stride(fmax);
+                double* F = smem + (size_t)wid * fdataflow_warp_stride(fmax);
                 auto wait = [&]() {
                     bool good = true;
                     for (int k = a.child_ptr[s] + lane; k < a.child_ptr[s + 1]; k += 32)
@@ -478,6 +487,52 @@ __global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
                     }
                 }
             }
+        } else if (kind == 3) {
+            // two fronts of order ≤ kPairFront per warp, one per half (lanes 0–15, 16–31)
+            const int h = lane >> 4, hl = lane & 15;
+            const int pf = min(fmax, kPairFront);
+            const unsigned hmask = 0xffffu << (16 * h);
+            double* Fw = smem + (size_t)wid * fdataflow_warp_stride(fmax);
+            const int t = wg_ptr[idx] + 2 * wid + h;
+            bool good = true;
+            if (t < wg_ptr[idx + 1]) {
+                const int s = wlist[t];
+                double* F = Fw + (size_t)h * wfactor_stride(pf);
+                auto wait = [&]() {
+                    bool g2 = true;
+                    for (int k = a.child_ptr[s] + hl; k < a.child_ptr[s + 1]; k += 16)
+                        g2 = g2 && wait_epoch(cdone + a.child[k], ds.epoch, ds.err, ds.max_spins);
+                    g2 = __all_sync(hmask, g2);
+                    __threadfence();
+                    return g2;
+                };
+                good = warp_factor_front<decltype(wait), double, 8, 16>(s, a, kval, F, F + pf * pf, lane, wait);
+                if (good) {
+                    __threadfence();
+                    __syncwarp(hmask);
+                    if (hl == 0) atomicExch(cdone + s, ds.epoch);
+                }
+            }
+            __syncwarp();
+            // the fused forward steps of the two fronts, one after the other by the whole warp
+            if (fz.rhs) {
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int th = wg_ptr[idx] + 2 * wid + hh;
+                    if (th >= wg_ptr[idx + 1]) break;
+                    if (__shfl_sync(0xffffffffu, good ? 1 : 0, 16 * hh) == 0) continue;
+                    const int sh = wlist[th];
+                    double* Fh = Fw + (size_t)hh * wfactor_stride(pf);
+                    const bool g3 = fused_fwd_warp(sh, a, fz, ds, Fh, Fh + pf * pf, lane);
+                    if (g3) {
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) atomicExch(fz.fdone + sh, fz.epoch);
+                    } else {
+                        good = false;
+                    }
+                }
+            }
+            ok = good;
         } else {
             const int s = idx;
             const int f = a.nrow[s];
@@ -509,7 +564,7 @@ __global__ void __launch_bounds__(kDataflowThreads) k_factor_dataflow(
 }
 
 static size_t fdataflow_smem(int fmax) {
-    return (size_t)(kDataflowThreads / 32) * wfactor_stride(fmax) * sizeof(double);
+    return (size_t)(kDataflowThreads / 32) * fdataflow_warp_stride(fmax) * sizeof(double);
 }
 
 int plan_dataflow_factor(FactorPlan& P, int fmax, bool any_large) {

@@ -24,10 +24,11 @@ __device__ __forceinline__ void tri_index(int t, int m, int& ii, int& jj) {
     ii = t - (j * m - (j * (j - 1)) / 2) + j;
 }
 
-// barrier of the group that works on one front: its warp or its CTA
+// barrier of the group that works on one front: its warp (or the lanes of `mask`, when a
+// warp holds several fronts) or its CTA
 template <bool WARP>
-__device__ __forceinline__ void group_sync() {
-    if constexpr (WARP) __syncwarp();
+__device__ __forceinline__ void group_sync(unsigned mask = 0xffffffffu) {
+    if constexpr (WARP) __syncwarp(mask);
     else __syncthreads();
 }
 
@@ -41,7 +42,7 @@ __device__ __forceinline__ void group_sync() {
 // ci_of(k) returns the k-th child's record and is called uniformly by the whole group.
 template <bool WARP, int Q, class Real, class CI>
 __device__ __forceinline__ void extend_add_children(Real* F, int f, const FactorView& a, int nch, const CI& ci_of,
-                                                    int tid, int nt) {
+                                                    int tid, int nt, unsigned gmask = 0xffffffffu) {
     int ck = 0, cm = 0;  // cursor: child, round
     while (ck < nch) {
         int qk[Q], off[Q];
@@ -74,12 +75,12 @@ __device__ __forceinline__ void extend_add_children(Real* F, int f, const Factor
         for (int q = 0; q < Q; ++q) {
             if (qk[q] < 0) break;
             if (qk[q] != cur) {
-                group_sync<WARP>();
+                group_sync<WARP>(gmask);
                 cur = qk[q];
             }
             if (off[q] >= 0) F[off[q]] += (Real)val[q];
         }
-        group_sync<WARP>();
+        group_sync<WARP>(gmask);
     }
 }
 
@@ -189,12 +190,12 @@ __device__ __forceinline__ void stage_pivot_signs(Real* bc, int c, int first, co
 
 template <bool WARP, class Real = double>
 __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, int c, int first,
-                                            const FactorView& a, int tid, int nt) {
+                                            const FactorView& a, int tid, int nt, unsigned gmask = 0xffffffffu) {
     int nreg = 0;
     double* dinv = a.dinv + first;
     Real* sgn = bc + kPanel + 1;
     const int piv = WARP ? 0 : nt - 1;  // the thread that computes the pivots
-    group_sync<WARP>();
+    group_sync<WARP>(gmask);
     auto do_pivot = [&](int k) {  // the pivot thread only
         Real* colk = F + (size_t)k * f;
         Real d = colk[k];
@@ -211,7 +212,7 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
         const int nb = min(kPanel, c - k0);
         for (int p = 0; p < nb; ++p) {
             const int k = k0 + p;
-            group_sync<WARP>();  // pivot k and column k final
+            group_sync<WARP>(gmask);  // pivot k and column k final
             const Real* colk = F + (size_t)k * f;
             const Real inv = bc[k % kPanel];
             const int jend = k0 + nb;  // later columns of this panel: k+1 .. jend−1
@@ -230,7 +231,7 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
                 if (WARP && i == k + 1 && k + 1 < jend) do_pivot(k + 1);  // i == k+1 only for tid 0
             }
         }
-        group_sync<WARP>();
+        group_sync<WARP>(gmask);
         // scale the panel's columns (L) and keep their unscaled values in W
         for (int p = 0; p < nb; ++p) {
             const int k = k0 + p;
@@ -242,7 +243,7 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
                 colk[i] = v * inv;
             }
         }
-        group_sync<WARP>();
+        group_sync<WARP>(gmask);
         // trailing rank-nb update of rows/columns k0+nb .. f−1, four entries per thread
         const int base = k0 + nb, m = f - base;
         const Real* L0 = F + (size_t)k0 * f;
@@ -282,7 +283,7 @@ __device__ __forceinline__ int blocked_ldlt(Real* F, Real* W, Real* bc, int f, i
                 }
             }
         }
-        group_sync<WARP>();
+        group_sync<WARP>(gmask);
         if (WARP && tid == piv && base < c) do_pivot(base);
     }
     return nreg;
@@ -420,22 +421,31 @@ __host__ __device__ constexpr int wfactor_stride(int fmax) { return fmax * (fmax
 // warp-level variants for fronts of order ≤ kWarpFront (one warp per front, the front
 // in the warp's slice of shared memory, __syncwarp instead of block barriers)
 // ---------------------------------------------------------------------------
-template <class Wait, class Real = double, int EAQ = 8>
+// GW: the lanes that work on the front — the whole warp (32), or one half of it (16), when
+// a warp holds two fronts of order ≤ kPairFront (their instructions then issue together
+// wherever the two fronts' loops agree, which shares the FP64 issue slots, one warp
+// instruction occupying a sub-partition's FP64 unit for 64 cycles on this part).  lane is
+// the lane in the warp; the group's lanes are lane & ~(GW−1) … + GW−1.  wait() is called
+// by the group alone.
+template <class Wait, class Real = double, int EAQ = 8, int GW = 32>
 __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, const double* __restrict__ kval,
                                                   Real* F, Real* lk, int lane, const Wait& wait) {
+    static_assert(GW == 32 || GW == 16, "a front takes a warp or half of one");
+    const unsigned gmask = GW == 32 ? 0xffffffffu : (0xffffu << (lane & 16));
+    const int gl = lane & (GW - 1);  // lane in the group
     const int f = a.nrow[s], c = a.ncol[s], first = a.first[s];
     const int ff = f * f;
-    for (int i = lane; i < ff; i += 32) F[i] = Real(0);
-    __syncwarp();
+    for (int i = gl; i < ff; i += GW) F[i] = Real(0);
+    __syncwarp(gmask);
     // original entries (static regularisation on the diagonal): loads first, then stores
     {
         const int64_t e0 = a.amap_ptr[s], e1 = a.amap_ptr[s + 1];
-        for (int64_t e = e0 + lane; e < e1; e += 4 * 32) {
+        for (int64_t e = e0 + gl; e < e1; e += 4 * GW) {
             int off[4];
             double v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int64_t eu = e + u * 32;
+                const int64_t eu = e + u * GW;
                 off[u] = eu < e1 ? (int)a.amap_off[eu] : -1;
                 v[u] = eu < e1 ? kval[a.amap_slot[eu]] : 0.0;
             }
@@ -448,33 +458,33 @@ __device__ __forceinline__ bool warp_factor_front(int s, const FactorView& a, co
             }
         }
     }
-    // child records of the first 32 children, one per lane, and the pivot signs (loaded
+    // child records of the first GW children, one per lane, and the pivot signs (loaded
     // before the wait)
     const int k0 = a.child_ptr[s], nch = a.child_ptr[s + 1] - k0;
     ChildInfo mine;
-    if (lane < nch) mine = a.cinfo[k0 + lane];
-    stage_pivot_signs(lk + kPanel * f, c, first, a, lane, 32);
-    __syncwarp();
+    if (gl < nch) mine = a.cinfo[k0 + gl];
+    stage_pivot_signs(lk + kPanel * f, c, first, a, gl, GW);
+    __syncwarp(gmask);
     if (!wait()) return false;
     // extend-add of the children's update blocks, several children's loads in flight
     auto ci_of = [&](int k) {
         ChildInfo ci;
-        if (k < 32) {
-            ci.u_off = __shfl_sync(0xffffffffu, mine.u_off, k);
-            ci.rel_off = __shfl_sync(0xffffffffu, mine.rel_off, k);
-            ci.fc = __shfl_sync(0xffffffffu, mine.fc, k);
-            ci.r = __shfl_sync(0xffffffffu, mine.r, k);
+        if (k < GW) {
+            ci.u_off = __shfl_sync(gmask, mine.u_off, k, GW);
+            ci.rel_off = __shfl_sync(gmask, mine.rel_off, k, GW);
+            ci.fc = __shfl_sync(gmask, mine.fc, k, GW);
+            ci.r = __shfl_sync(gmask, mine.r, k, GW);
         } else {
             ci = a.cinfo[k0 + k];
         }
         return ci;
     };
-    extend_add_children<true, EAQ, Real>(F, f, a, nch, ci_of, lane, 32);
-    const int nreg = blocked_ldlt<true, Real>(F, lk, lk + kPanel * f, f, c, first, a, lane, 32);
+    extend_add_children<true, EAQ, Real>(F, f, a, nch, ci_of, gl, GW, gmask);
+    const int nreg = blocked_ldlt<true, Real>(F, lk, lk + kPanel * f, f, c, first, a, gl, GW, gmask);
     double* G = a.front + a.front_off[s];
-    for (int i = lane; i < ff; i += 32) G[i] = (double)F[i];
-    if (lane == 0 && nreg) atomicAdd(a.nreg, nreg);
-    __syncwarp();
+    for (int i = gl; i < ff; i += GW) G[i] = (double)F[i];
+    if (gl == 0 && nreg) atomicAdd(a.nreg, nreg);
+    __syncwarp(gmask);
     return true;
 }
 

@@ -98,10 +98,21 @@ void build_plan(const Symbolic& S, PlanHost* P) {
             P->ftb_ptr.push_back(L.off_thread + std::min(t + 128, L.n_thread));
             P->fitems.push_back((b << 2) | 0);
         }
-        for (int t = 0; t < L.n_warp; t += 4) {
+        // the level's warp fronts come in decreasing order: groups of 4 (one warp each),
+        // then, from the first of order ≤ kPairFront, groups of 8 (two per warp, neighbours
+        // in that order pairing fronts of about the same size)
+        int npair0 = L.n_warp;
+        for (int t = 0; t < L.n_warp; ++t)
+            if (P->warp[L.off_warp + t] >= 0 && f[P->warp[L.off_warp + t]] <= kPairFront) { npair0 = t; break; }
+        for (int t = 0; t < npair0; t += 4) {
             const int g = (int)P->fwg_ptr.size() - 1;
-            P->fwg_ptr.push_back(L.off_warp + std::min(t + 4, L.n_warp));
+            P->fwg_ptr.push_back(L.off_warp + std::min(t + 4, npair0));
             P->fitems.push_back((g << 2) | 1);
+        }
+        for (int t = npair0; t < L.n_warp; t += 8) {
+            const int g = (int)P->fwg_ptr.size() - 1;
+            P->fwg_ptr.push_back(L.off_warp + std::min(t + 8, L.n_warp));
+            P->fitems.push_back((g << 2) | 3);
         }
         for (int t = 0; t < L.n_small; ++t) P->fitems.push_back((P->small[L.off_small + t] << 2) | 2);
     }

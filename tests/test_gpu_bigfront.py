@@ -6,7 +6,8 @@ precision (FP32 fronts, FP64 solves and refinement), through the C ABI.
 * Mixed: the same factor agrees to FP32 accuracy, and refinement still reaches the
   1e-10 backward error on the unregularised K.
 * Solves: lasso and dense QPs whose trees end in large fronts match the oracle's solution
-  in both precisions (objective 1e-6, x, y, z 1e-5 relative), and the scaled lasso QP
+  in both precisions (objective 1e-6, x, y, z 1e-5 relative), including two whose FP32
+  root front breaks down near the end of the solve, and the scaled lasso QP
   (F 5000×10000, 50 nonzeros per row; a 4924-row root front) matches the stored oracle
   values.
 """
@@ -99,6 +100,11 @@ CASES = {
     "dense_qp_natural": (lambda: dense_qp(seed=1), dict(ordering=3)),
     "lasso_r500_c1000": (lambda: lasso_qp(rows=500, cols=1000, density=1e-2, seed=2), {}),
     "lasso_r1000_c2000_nd": (lambda: lasso_qp(rows=1000, cols=2000, density=1e-2, seed=3), dict(ordering=2)),
+    # AMD puts a ~400-row front at the root whose FP32 factor breaks down at the last
+    # iterations (pivots of 1e-9 next to 1e8): the pivot-floor retries, the componentwise
+    # acceptance and the FP64 refactor have to keep the solve on the oracle's solution
+    "lasso_r400_c800_amd": (lambda: lasso_qp(rows=400, cols=800, density=0.05, seed=0), dict(ordering=1)),
+    "lasso_r300_c700_amd": (lambda: lasso_qp(rows=300, cols=700, density=0.08, seed=0), dict(ordering=1)),
 }
 
 
