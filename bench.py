@@ -376,7 +376,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(uuid)
     clocks.start()
-    S.set_profiling(True)
+    # inside the timed region only the factorisation (the dominant phase) is timed by
+    # events: two per factorisation; the phase split comes from one more solve below
+    S.set_profiling(2)
     times, launches, iters = [], 0, []
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
@@ -399,12 +401,18 @@ def run_ours(args, ws, rank, local):
         torch.distributed.barrier()
     clk = clocks.stop()
     prof = S.profile()
+    # the phase split: one more solve, every phase timed (outside the timed region)
+    S.set_profiling(True)
+    if S.solve(stream.cuda_stream) != 0:
+        raise RuntimeError("profiled solve failed")
+    split = S.profile()
     S.set_profiling(False)
     info = S.info()
     info["m_cone"] = prob.m
     ms = statistics.mean(times)
     ms_max = reduce_max(ms, dev)
-    rl = roofline(prof, info, args.stages, fp64_peaks(q))
+    dominant = max(split, key=lambda k: split[k]["ms"])
+    rl = roofline(prof if dominant == "factor" else split, info, args.stages, fp64_peaks(q))
 
     e2e = None
     if not args.no_e2e:
@@ -427,7 +435,9 @@ def run_ours(args, ws, rank, local):
                "gpu_launches": launches,
                "refactor_gflops": info["factor_flops"] / (prof["factor"]["ms"] / max(1, prof["factor"]["calls"]) * 1e-3) / 1e9
                if prof["factor"]["calls"] else None,
-               "phase_ms_per_solve": {k: v["ms"] / args.steps for k, v in prof.items()},
+               "phase_ms_per_solve": {k: v["ms"] for k, v in split.items()},
+               "phase_note": "phase split of one solve after the timed region; inside it only the "
+                             "factorisation phase carries events",
                "roofline": rl, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
                "wall_s_timed": wall}
         print(json.dumps(out), flush=True)

@@ -318,7 +318,9 @@ int qoco_gpu_update_data(qoco_gpu_solver* solver, const double* P_val, const dou
                          const double* A_val, const double* b, const double* G_val,
                          const double* h, int on_device, void* stream);
 
-/* Turns per-phase CUDA-event timing on (1) or off (0) and clears the totals. */
+/* Turns per-phase CUDA-event timing on (1: every phase; 2: the factorisation phase alone,
+ * two events per factorisation, the lightest timing of the dominant kernel) or off (0)
+ * and clears the totals.  Other values: QOCO_GPU_ERR_INVALID_ARG. */
 int qoco_gpu_set_profiling(qoco_gpu_solver* solver, int on);
 /* Reads the per-phase totals accumulated since profiling was turned on. */
 int qoco_gpu_get_profile(const qoco_gpu_solver* solver, qoco_gpu_profile* out);

@@ -242,7 +242,8 @@ class Solver:
         return out
 
     def set_profiling(self, on=True):
-        rc = self.lib.qoco_gpu_set_profiling(self._h, 1 if on else 0)
+        """True/1: every phase; 2: the factorisation phase alone; False/0: off."""
+        rc = self.lib.qoco_gpu_set_profiling(self._h, 2 if on == 2 else (1 if on else 0))
         if rc != 0:
             raise SolverError(rc, "set_profiling")
 

@@ -148,32 +148,35 @@ __device__ __noinline__ double inst_normK(const BatchIPMArgs& A, const Rows& R, 
 
 // res = r − K x on the instance's rows; returns the backward error (NaN when a value is
 // not finite)
+// cw (optional): the componentwise backward error, computed only when asked for
 __device__ __noinline__ double inst_residual(const BatchIPMArgs& A, const Rows& R, const double* x, const double* r,
                                 double* res, double normK, double* red, double* cw) {
     // ‖res‖∞, ‖x‖∞, ‖r‖∞, max_i |res_i| / (|K||x| + |r|)_i (componentwise)
     double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool want_cw = cw != nullptr;
     for (int k = threadIdx.x; k < R.total; k += blockDim.x) {
         const int row = R.row(k);
         double a = r[row], d = fabs(r[row]);
         for (int64_t t = A.K.rowptr[row]; t < A.K.rowptr[row + 1]; ++t) {
             const double kx = A.kval[t] * x[A.K.colidx[t]];
             a -= kx;
-            d += fabs(kx);
+            if (want_cw) d += fabs(kx);
         }
         res[row] = a;
         v[0] = amax(v[0], a);
         v[1] = amax(v[1], x[row]);
         v[2] = amax(v[2], r[row]);
-        v[3] = amax(v[3], d > 0.0 ? a / d : (a == 0.0 ? 0.0 : a * __longlong_as_double(0x7ff0000000000000LL)));
+        if (want_cw)
+            v[3] = amax(v[3], d > 0.0 ? a / d : (a == 0.0 ? 0.0 : a * __longlong_as_double(0x7ff0000000000000LL)));
     }
     const int kind[4] = {1, 1, 1, 1};
     cta_reduce<4>(v, kind, red);
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
     if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
-        *cw = nan;
+        if (want_cw) *cw = nan;
         return nan;
     }
-    *cw = v[3];
+    if (want_cw) *cw = v[3];
     const double den = normK * v[1] + v[2];
     return den > 0.0 ? v[0] / den : 0.0;
 }
@@ -188,8 +191,8 @@ __device__ bool inst_solve_refine(const BatchIPMArgs& A, int inst, const Rows& R
                                   double normK, double* V, double* red, bool cw) {
     inst_solve<NW>(A, inst, r, x, 0, V);
     for (int steps = 0;; ++steps) {
-        double bcw;
-        const double be = inst_residual(A, R, x, r, A.res, normK, red, &bcw);
+        double bcw = 0.0;
+        const double be = inst_residual(A, R, x, r, A.res, normK, red, cw ? &bcw : nullptr);
         if (be <= A.refine_tol && (!cw || bcw <= A.refine_tol)) return true;
         if (!(be == be) || steps >= A.max_refine) return false;  // NaN, or out of steps
         inst_solve<NW>(A, inst, A.res, x, 1, V);

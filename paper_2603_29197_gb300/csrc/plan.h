@@ -12,7 +12,7 @@ constexpr int kMaxSolveFront = 26000; // solve kernels keep one front vector in 
 constexpr int kMaxFactorFront = 5600;  // CTA factor keeps a 4-column panel + signs in shared memory
 constexpr int kThreadFront = 8;     // fronts up to this order are handled by one thread
 constexpr int kWarpFront = 48;      // fronts up to this order are handled by one warp
-constexpr int kPairFront = 24;      // dataflow factorisation: two such fronts share a warp
+constexpr int kPairFront = 28;      // dataflow factorisation: two such fronts share a warp
 constexpr int kWarpsPerBlock = 4;    // warps per block of the warp-level kernels
 constexpr int kWideLevel = 2432;     // levels with at least this many fronts (16 per SM) use warps
 // Fronts at least this large are factored and solved by grid-wide kernel sequences

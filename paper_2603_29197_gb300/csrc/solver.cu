@@ -171,6 +171,7 @@ struct qoco_gpu_cones {
 // CUDA-event timing of the iteration's phases (enabled by qoco_gpu_set_profiling).
 struct PhaseProfiler {
     bool on = false;
+    bool factor_only = false;  // time the factorisation phase alone (two events per factorisation)
     std::vector<cudaEvent_t> pool;
     size_t used = 0;
     struct Rec { int phase; cudaEvent_t a, b; int64_t launches; };
@@ -346,7 +347,8 @@ struct Phase {
     cudaEvent_t a = nullptr;
     int64_t l0;
     Phase(qoco_gpu_solver* s_, int ph, cudaStream_t st_) : S(s_), phase(ph), st(st_), l0(s_->launches) {
-        if (S->prof.on && (a = S->prof.next())) cudaEventRecord(a, st);
+        if (S->prof.on && (!S->prof.factor_only || phase == QOCO_GPU_PHASE_FACTOR) && (a = S->prof.next()))
+            cudaEventRecord(a, st);
     }
     ~Phase() {
         if (!a) return;
@@ -2019,7 +2021,9 @@ int qoco_gpu_set_profiling(qoco_gpu_solver* S, int on) {
     if (!S) return QOCO_GPU_ERR_INVALID_ARG;
     QOCO_CUDA_TRY(cudaDeviceSynchronize());
     S->prof.flush();
+    if (on < 0 || on > 2) return QOCO_GPU_ERR_INVALID_ARG;
     S->prof.on = on != 0;
+    S->prof.factor_only = on == 2;
     memset(&S->prof.tot, 0, sizeof S->prof.tot);
     return 0;
 }
