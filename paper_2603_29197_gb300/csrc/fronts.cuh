@@ -377,14 +377,35 @@ __device__ __forceinline__ bool thread_fwd_front(int s, const FactorView& a, con
         const double* u = a.upd + a.upd_off[ch];
         for (int i = 0; i < r; ++i) v[rel[i]] += __ldcg(u + i);
     }
+    // the front's L (below the diagonal) and D⁻¹ in registers, every load issued before the
+    // first FMA (one memory round trip instead of one per column); the solve then runs on
+    // register copies with unrolled, bounds-checked loops
     const double* L = a.front + a.front_off[s];
-    for (int k = 0; k < c; ++k) {
-        const double xk = v[k];
-        for (int i = k + 1; i < f; ++i) v[i] -= L[k * f + i] * xk;
+    constexpr int T = kThreadFront;
+    double Lr[T * (T - 1) / 2], dr[T], vr[T];
+#pragma unroll
+    for (int k = 0, e = 0; k < T - 1; ++k)
+#pragma unroll
+        for (int i = k + 1; i < T; ++i, ++e) Lr[e] = (k < c && i < f) ? L[k * f + i] : 0.0;
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        dr[i] = i < c ? a.dinv[first + i] : 0.0;
+        vr[i] = i < f ? v[i] : 0.0;
     }
-    for (int i = 0; i < c; ++i) w[first + i] = v[i] * a.dinv[first + i];
+#pragma unroll
+    for (int k = 0, e = 0; k < T - 1; e += T - 1 - k, ++k) {
+        if (k >= c) break;
+        const double xk = vr[k];
+#pragma unroll
+        for (int i = k + 1; i < T; ++i)
+            if (i < f) vr[i] -= Lr[e + i - k - 1] * xk;
+    }
     double* u = a.upd + a.upd_off[s];
-    for (int i = c; i < f; ++i) u[i - c] = v[i];
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        if (i < c) w[first + i] = vr[i] * dr[i];
+        else if (i < f) u[i - c] = vr[i];
+    }
     return true;
 }
 
@@ -398,17 +419,39 @@ __device__ __forceinline__ bool thread_bwd_front(int s, const FactorView& a, con
     const int* Rg = a.rows + a.row_ptr[s];
     for (int i = c; i < f; ++i) R[i] = Rg[i];
     if (!wait()) return false;
-    for (int i = 0; i < f; ++i) v[i] = __ldcg(i < c ? w + first + i : xp + R[i]);
+    // the known values, L and the permutation in registers, every load issued before the
+    // first FMA; then the backward substitution on register copies
     const double* L = a.front + a.front_off[s];
-    for (int k = c - 1; k >= 0; --k) {
-        double acc = v[k];
-        for (int i = k + 1; i < f; ++i) acc -= L[k * f + i] * v[i];
-        v[k] = acc;
+    constexpr int T = kThreadFront;
+    double Lr[T * (T - 1) / 2], vr[T];
+    int pr[T];
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        vr[i] = i < c ? __ldcg(w + first + i) : i < f ? __ldcg(xp + R[i]) : 0.0;
+        pr[i] = i < c ? a.perm[first + i] : 0;
     }
-    for (int i = 0; i < c; ++i) {
-        xp[first + i] = v[i];
-        if (accumulate) x[a.perm[first + i]] += v[i];
-        else x[a.perm[first + i]] = v[i];
+#pragma unroll
+    for (int k = 0, e = 0; k < T - 1; ++k)
+#pragma unroll
+        for (int i = k + 1; i < T; ++i, ++e) Lr[e] = (k < c && i < f) ? L[k * f + i] : 0.0;
+#pragma unroll
+    for (int k = T - 2; k >= 0; --k) {
+        if (k < c) {
+            const int e = k * (T - 1) - k * (k - 1) / 2;  // start of column k in Lr
+            double acc = vr[k];
+#pragma unroll
+            for (int i = k + 1; i < T; ++i)
+                if (i < f) acc -= Lr[e + i - k - 1] * vr[i];
+            vr[k] = acc;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < T; ++i) {
+        if (i < c) {
+            xp[first + i] = vr[i];
+            if (accumulate) x[pr[i]] += vr[i];
+            else x[pr[i]] = vr[i];
+        }
     }
     return true;
 }

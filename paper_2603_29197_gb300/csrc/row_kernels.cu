@@ -235,13 +235,15 @@ __global__ void __launch_bounds__(kLongThreads) k_norm_inf_long(KKTView K, doubl
     if (threadIdx.x == 0) partial[nb + blockIdx.x] = a[0];
 }
 
-// one block: reduce NV columns of partial[nb][NV] in a fixed order into out[NV]
+// one block: reduce NV columns of partial[nb][NV] in a fixed order into out[NV], one warp
+// per column (lane-strided partial results, then a fixed shuffle tree), all columns at
+// once; max columns compare bit patterns (non-negative values; a NaN propagates)
 __device__ void reduce_columns(const double* partial, int nb, int NV, unsigned max_mask, double* out) {
-    __shared__ double sm[32];
-    for (int k = 0; k < NV; ++k) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    for (int k = wid; k < NV; k += nw) {
         const bool mx = (max_mask >> k) & 1u;
         double a = 0.0;
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        for (int i = lane; i < nb; i += 32) {
             const double t = partial[(int64_t)i * NV + k];
             if (mx) {
                 const long long bt = __double_as_longlong(t), ba = __double_as_longlong(a);
@@ -251,16 +253,9 @@ __device__ void reduce_columns(const double* partial, int nb, int NV, unsigned m
             }
         }
         a = mx ? warp_max_nonneg(a) : warp_sum(a);
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        if (lane == 0) sm[wid] = a;
-        __syncthreads();
-        if (wid == 0) {
-            double t = lane < (int)(blockDim.x >> 5) ? sm[lane] : 0.0;
-            t = mx ? warp_max_nonneg(t) : warp_sum(t);
-            if (lane == 0) out[k] = t;
-        }
-        __syncthreads();
+        if (lane == 0) out[k] = a;
     }
+    __syncthreads();
 }
 
 __global__ void k_finalize_residual(const double* __restrict__ partial, int nb, IPMScalars* S) {
