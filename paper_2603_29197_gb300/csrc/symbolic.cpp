@@ -174,15 +174,20 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int t
         evaluate(g, order_nd(g, st.nd_leaf), false, &E);
     } else {
         // AUTO: cost model = factor flops at an effective FP64 rate plus a per-level
-        // latency for the level-scheduled factor and solves; the independent trees of a
-        // batch overlap their level chains (up to 64 of them are counted), which favours
-        // the lower flop counts of AMD there (C5's MPC batch: 47.8k vs 44.6k solves/s)
-        // the two candidates are independent: ordered and evaluated on two host threads
+        // latency for the level-scheduled factor and solves.  The independent trees of a
+        // batch on the shared kernels overlap their level chains (up to 64 of them are
+        // counted), which favours the lower flop counts of AMD there; a batch on the
+        // persistent kernel (batch_schedule 0 or 6) walks each instance's tree inside one
+        // CTA, so an instance's chain of levels counts in full (MPC batch of 4096 on that
+        // kernel: ND 63k solves/s against AMD's 59–68k in FP64, 50k against 33k with FP32
+        // fronts).  The two candidates are independent: ordered and evaluated on two host
+        // threads.
         Evaluated En;
         std::thread tn([&]() { evaluate(g, order_nd(g, st.nd_leaf), false, &En); });
         evaluate(g, order_amd(g), false, &E);
         tn.join();
-        const double overlap = (double)std::max(1, std::min(trees, 64));
+        const bool persistent = trees > 1 && (st.batch_schedule == 0 || st.batch_schedule == 6);
+        const double overlap = persistent ? 1.0 : (double)std::max(1, std::min(trees, 64));
         auto cost = [&](const OrderingCost& c) { return c.flops / 2e11 + c.height * 4e-5 / overlap; };
         if (cost(En.cost) < cost(E.cost)) { E = std::move(En); used = QOCO_GPU_ORDER_ND; }
         else used = QOCO_GPU_ORDER_AMD;
