@@ -94,6 +94,30 @@ def test_repeated_solves_are_identical(q):
     assert a["info"]["iters"] == b["info"]["iters"]
 
 
+def test_profiling_modes(q):
+    """Mode 1 times every phase, mode 2 the factorisation alone (what bench.py uses inside
+    its timed region), 0 turns it off; the solution does not depend on the mode."""
+    prob = trajectory_socp(N=300, seed=2)
+    S = q.Solver(prob)
+    S.set_profiling(True)
+    assert S.solve() == 0
+    full = S.profile()
+    x1 = S.solution()["x"]
+    S.set_profiling(2)
+    assert S.solve() == 0
+    fac = S.profile()
+    x2 = S.solution()["x"]
+    S.set_profiling(False)
+    iters = S.info()["iters"]
+    assert full["factor"]["calls"] == iters + 1 and full["solve"]["calls"] >= 2 * iters
+    assert full["cone"]["calls"] > 0 and full["row"]["calls"] > 0
+    assert fac["factor"]["calls"] == iters + 1 and fac["factor"]["ms"] > 0.0
+    assert fac["solve"]["calls"] == fac["cone"]["calls"] == fac["row"]["calls"] == 0
+    np.testing.assert_array_equal(x1, x2)
+    assert S.lib.qoco_gpu_set_profiling(S._h, 3) == -10  # QOCO_GPU_ERR_INVALID_ARG
+    S.close()
+
+
 def test_max_iter_status(q):
     prob = dense_qp(n=60, p=10, m=90, rank=8, density=0.1, seed=4)
     S = q.Solver(prob, max_iter=2)
