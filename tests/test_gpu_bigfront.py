@@ -51,9 +51,13 @@ def test_large_front_factor_matches_textbook_ldlt(mixed):
     sg = ok.reg_signs(prob)
     Ke = _K(prob, s, z).toarray() + 1e-8 * np.diag(sg)
     Lo, Do = ok.dense_ldlt(Ke, signs=sg)
-    tol = 1e-8 if not mixed else 2e-3
-    np.testing.assert_allclose(D, Do, rtol=tol)
-    assert rel_inf(L, Lo) <= tol
+    # FP32 fronts: forward errors of an FP32 elimination, the pivots' relative error
+    # growing where a pivot cancels (7e-4 seen), L's normwise (3.6e-5 seen); the componentwise
+    # backward error (test below) is the tight check of the FP32 factor
+    tol_d = 1e-8 if not mixed else 2e-3
+    tol_l = 1e-8 if not mixed else 2e-4
+    np.testing.assert_allclose(D, Do, rtol=tol_d)
+    assert rel_inf(L, Lo) <= tol_l
     if mixed:
         assert rel_inf(L, Lo) >= 1e-12  # the large fronts really ran in FP32
     # refinement against the unregularised K recovers the FP64 backward error
