@@ -349,7 +349,9 @@ struct ND {
         for (const auto& o : outs) out->insert(out->end(), o.begin(), o.end());
     }
 
-    void run(std::vector<int> nodes, std::vector<int>* out, int depth) {
+    // hint: a node of `nodes` at an end of the parent's level structure (the parent's BFS
+    // root for the first part, its last node for the second), or −1
+    void run(std::vector<int> nodes, std::vector<int>* out, int depth, int hint = -1) {
         std::vector<int>& lev = mk.lev;
         if ((int)nodes.size() <= leaf) { leaf_amd(nodes, out); return; }
         const int t = mk.next_tag.fetch_add(1, std::memory_order_relaxed);
@@ -357,7 +359,7 @@ struct ND {
         // connected components; the first BFS (from nodes[0]) is also the first level
         // structure of the pseudo-peripheral search when the subgraph is connected
         std::vector<int> lptr;
-        int nl = bfs(nodes[0], t, lptr);
+        int nl = bfs(hint >= 0 ? hint : nodes[0], t, lptr);
         if ((int)q.size() < (int)nodes.size()) {
             std::vector<std::vector<int>> comps;
             std::vector<int> seen(q.begin(), q.end());
@@ -375,9 +377,12 @@ struct ND {
         }
         // pseudo-peripheral root: BFS from the least-degree node of the last level while
         // that deepens the level structure; the kept structure is restored from its
-        // saved queue instead of a repeated BFS
+        // saved queue instead of a repeated BFS.  A part that starts from the end of its
+        // parent's level structure keeps that first structure: the end is already far from
+        // the rest of the part (on stage-structured problems it is one end of the part's
+        // chain), and the search would cost about two more BFS passes per part.
         std::vector<int> keep_q, keep_l;
-        for (int it = 0; it < 8; ++it) {
+        for (int it = 0; it < (hint >= 0 ? 0 : 8); ++it) {
             int best = -1, bd = 1 << 30;
             for (int k = lptr[nl - 1]; k < lptr[nl]; ++k) {
                 int d = local_degree(q[k], t);
@@ -410,6 +415,7 @@ struct ND {
         }
         if (pick < 0) pick = median < 0 ? nl / 2 : median;
         // thin the separator: keep only level nodes touching the next level
+        const int hint1 = q[0], hint2 = q[S - 1];  // the ends of this level structure
         std::vector<int> part1, part2, sep;
         part1.reserve(lptr[pick + 1]);
         part2.reserve(S - lptr[pick + 1]);
@@ -433,18 +439,18 @@ struct ND {
         // new tags), so that the separator is ordered by AMD on exactly its own nodes
         if (S >= kNdParallelMin && depth < kNdMaxDepth) {
             std::vector<int> out1;
-            std::thread th([this, &part1, &out1, depth]() {
+            std::thread th([this, &part1, &out1, depth, hint1]() {
                 ND sub(g, mk, leaf);
-                sub.run(std::move(part1), &out1, depth + 1);
+                sub.run(std::move(part1), &out1, depth + 1, hint1);
             });
             std::vector<int> out2;
-            run(std::move(part2), &out2, depth + 1);
+            run(std::move(part2), &out2, depth + 1, hint2);
             th.join();
             out->insert(out->end(), out1.begin(), out1.end());
             out->insert(out->end(), out2.begin(), out2.end());
         } else {
-            run(std::move(part1), out, depth + 1);
-            run(std::move(part2), out, depth + 1);
+            run(std::move(part1), out, depth + 1, hint1);
+            run(std::move(part2), out, depth + 1, hint2);
         }
         amd_subset(g, mk, t, sep, out);
     }
