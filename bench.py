@@ -701,13 +701,19 @@ def run_other(args, ws, rank, local):
               "avg_ms": ms, "note": "latency-bound: per-instance level chains of small fronts"}
         f_ms = None
     # e2e: set-up from host data, solve, copy-back
-    e2e_s, sol = None, None
+    e2e_s, sol, e2e_split = None, None, None
     if not args.no_e2e:
         t0 = time.perf_counter()
         E = make()
+        t1 = time.perf_counter()
         st = E.solve(stream.cuda_stream)
+        t2 = time.perf_counter()
         sol = E.solution()
         e2e_s = reduce_max(time.perf_counter() - t0, dev)
+        ei = E.info()
+        e2e_split = {"setup_s": t1 - t0, "library_setup_s": ei["setup_time_s"],
+                     "analysis_s": ei["analysis_time_s"], "first_solve_s": t2 - t1,
+                     "copy_back_s": t0 + e2e_s - t2}
         E.close()
     # CPU oracle on a bounded sample
     from oracle import ipm
@@ -739,6 +745,7 @@ def run_other(args, ws, rank, local):
         metric, value, unit, hib = "time_to_1e-7_gap", ms * 1e-3, "s", False
         e2e = {"value": e2e_s, "unit": unit} if e2e_s else None
     if e2e:
+        e2e["split"] = e2e_split
         e2e.update({"h2d_bytes_per_step": int(sol["info"]["h2d_bytes"]),
                     "d2h_bytes_per_step": int(sol["info"]["d2h_bytes"]) + 8 * (S.n + 2 * S.m + S.p)})
     wl = {"mpc_batch": "mpc_batch_4096: horizons U{10..60}, state 4, control 2, Q^3 input cone, box bounds",

@@ -122,14 +122,20 @@ typedef struct {
                                            instances' interior-point iterations on chip (its
                                            tile configuration — warps per CTA, registers per
                                            thread — timed on the whole batch at the first
-                                           solve); 1–5 = the
+                                           solve, a search over 3–4 of the 6 tiles that
+                                           halves the warps per CTA while that pays); 1–5 = the
                                            host-driven iteration loop with per-instance factor
                                            and solve kernels, one CTA per instance at a time
                                            (1: 4 warps per CTA, fronts of order ≤ 8 one per
                                            thread; 2: 8 warps, same split; 3: 4 warps, every
                                            front one warp; 4: 8 warps, every front one warp)
-                                           or (5) the shared kernels of single problems
-                                           (default 0).  Other batches always use 5. */
+                                           or (5) the shared kernels of single problems;
+                                           7–12 = the persistent kernel with a fixed tile
+                                           instead of the tuning (7, 8: 1 warp per CTA; 9,
+                                           10: 2 warps; 11, 12: 4 warps; odd: 16 resident
+                                           warps per SM, even: 32), tuned all the same when
+                                           the batch cannot launch that tile (default 0).
+                                           Other batches always use 5. */
 } qoco_gpu_settings;
 
 typedef struct {

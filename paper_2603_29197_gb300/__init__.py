@@ -64,6 +64,24 @@ class _CSCHold:
         self.ptr = C.byref(self.s)
 
 
+# numpy mirror of qoco_csc (same field offsets), for tables of many matrices
+_CSC_DTYPE = np.dtype({"names": [f for f, _ in _lib.CSC._fields_],
+                       "formats": [np.int32, np.int32, np.int32, np.uintp, np.uintp, np.uintp],
+                       "offsets": [getattr(_lib.CSC, f).offset for f, _ in _lib.CSC._fields_],
+                       "itemsize": C.sizeof(_lib.CSC)})
+
+
+def _csc_row(tab, i, M, rows, cols):
+    """Fills tab[i] (a _CSC_DTYPE table) from the CSC matrix M; returns the int32/float64
+    copies that must stay alive for the call."""
+    M = M.tocsc() if hasattr(M, "tocsc") else M
+    colptr = np.ascontiguousarray(M.indptr, dtype=np.int32)
+    rowidx = np.ascontiguousarray(M.indices, dtype=np.int32)
+    val = np.ascontiguousarray(M.data, dtype=np.float64)
+    tab[i] = (rows, cols, rowidx.size, colptr.ctypes.data, rowidx.ctypes.data, val.ctypes.data)
+    return colptr, rowidx, val
+
+
 def _dptr(a):
     return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -326,23 +344,29 @@ class BatchSolver(Solver):
         nb = len(probs)
         holds = []
         ns, ms, ps, ls, nsocs = [], [], [], [], []
-        Ps, As, Gs = (_lib.CSC * nb)(), (_lib.CSC * nb)(), (_lib.CSC * nb)()
-        cs, bs, hs, qs = ((C.POINTER(C.c_double) * nb)(), (C.POINTER(C.c_double) * nb)(),
-                          (C.POINTER(C.c_double) * nb)(), (C.POINTER(C.c_int) * nb)())
+        # the per-instance CSC structs and pointer tables are filled as numpy arrays of
+        # addresses (one ctypes conversion per table, not one per instance)
+        Ps, As, Gs = (np.zeros(nb, dtype=_CSC_DTYPE) for _ in range(3))
+        cs, bs, hs, qs = (np.zeros(nb, dtype=np.uintp) for _ in range(4))
         for i, pr in enumerate(probs):
-            n, m, p, P, A, G, q = _problem_args(pr)
-            c, b, h = _vec(pr.c, n), _vec(pr.b, p), _vec(pr.h, m)
-            holds += [P, A, G, q, c, b, h]
+            n, m, p = int(pr.n), int(pr.m), int(pr.p)
+            q = np.ascontiguousarray(list(pr.q), dtype=np.int32)
+            Pm = pr.P if getattr(pr, "P", None) is not None and pr.P.nnz else None
+            for M, rows, tab in ((Pm, n, Ps), (pr.A if p else None, p, As), (pr.G if m else None, m, Gs)):
+                if M is not None:
+                    holds.append(_csc_row(tab, i, M, rows, n))
+            for v, k, tab in ((pr.c, n, cs), (pr.b, p, bs), (pr.h, m, hs)):
+                a = _vec(v, k)
+                if a is not None:
+                    holds.append(a)
+                    tab[i] = a.ctypes.data
+            holds.append(q)
+            if len(q):
+                qs[i] = q.ctypes.data
             ns.append(n); ms.append(m); ps.append(p); ls.append(int(pr.l)); nsocs.append(len(q))
-            if P.ptr is not None:
-                Ps[i] = P.s
-            if A.ptr is not None:
-                As[i] = A.s
-            Gs[i] = G.s
-            cs[i] = _dptr(c)
-            bs[i] = _dptr(b) if b is not None else C.POINTER(C.c_double)()
-            hs[i] = _dptr(h)
-            qs[i] = q.ctypes.data_as(C.POINTER(C.c_int)) if len(q) else C.POINTER(C.c_int)()
+        Ps, As, Gs = (t.ctypes.data_as(C.POINTER(_lib.CSC)) for t in (Ps, As, Gs))
+        cs, bs, hs = (t.ctypes.data_as(C.POINTER(C.POINTER(C.c_double))) for t in (cs, bs, hs))
+        qs = qs.ctypes.data_as(C.POINTER(C.POINTER(C.c_int)))
         arr = lambda v: (C.c_int * nb)(*v)  # noqa: E731
         self.n, self.m, self.p = sum(ns), sum(ms), sum(ps)
         self.N = self.n + self.m + self.p

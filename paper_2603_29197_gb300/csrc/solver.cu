@@ -1129,10 +1129,13 @@ int launch_fused(qoco_gpu_solver* S, int nw, int split, int dense, int nb, cudaS
 
 // Tile configuration of the batched kernel: warps per CTA (1, 2, 4; more warps share an
 // instance's levels, fewer let more instances run side by side) × 16 or 32 resident warps
-// per SM (128 or 64 registers per thread), fronts of order ≤ 8 one per thread; each
-// candidate solves the whole batch once (after one untimed launch that warms the caches)
-// and the fastest is kept.  A sample would mislead: the steady state of the persistent
-// queue needs several instances per CTA, and the largest grids hold ~2400 CTAs.
+// per SM (128 or 64 registers per thread), fronts of order ≤ 8 one per thread.  Each
+// candidate solves the whole batch once, after one untimed launch over one instance per
+// CTA that takes the first-launch costs; a sample would mislead: the steady state of the
+// persistent queue needs several instances per CTA, and the largest grids hold ~2400 CTAs.
+// The search assumes the time is unimodal in the warps per CTA: from 4 warps (16 per SM)
+// it halves the warps while that pays, then times the other residency of the best width
+// (MPC batch of 4096: 3 of the 6 launches; the six times were 65, 69, 71, 74, 93, 99 ms).
 int tune_fused(qoco_gpu_solver* S, cudaStream_t st) {
     cudaEvent_t e0, e1;
     QOCO_CUDA_TRY(cudaEventCreate(&e0));
@@ -1141,30 +1144,40 @@ int tune_fused(qoco_gpu_solver* S, cudaStream_t st) {
     float best = 0.0f;
     int rc = 0;
     bool warm = false;
-    for (int nw : {1, 2, 4})
-        for (int dense = 0; dense < 2 && !rc; ++dense) {
-            if (!S->fused_grid[fused_grid_index(nw, dense)]) continue;
-            if (!warm) {
-                const int nl = launch_fused(S, nw, split, dense, nb, st);
-                if (nl < 0) { rc = nl; break; }
-                warm = true;
-            }
-            float ms = 0.0f;
-            QOCO_CUDA_TRY(cudaEventRecord(e0, st));
-            const int nl = launch_fused(S, nw, split, dense, nb, st);
-            if (nl < 0) { rc = nl; break; }
-            QOCO_CUDA_TRY(cudaEventRecord(e1, st));
-            if (cudaEventSynchronize(e1) != cudaSuccess) rc = QOCO_GPU_ERR_CUDA;
-            else cudaEventElapsedTime(&ms, e0, e1);
-            if (S->st.verbose >= 2)
-                printf("     batch tile: %d warps per CTA, %d warps per SM: %.3f ms\n", nw, dense ? 32 : 16, ms);
-            if (!rc && (!S->fused_nw || ms < best)) {
-                best = ms;
-                S->fused_nw = nw;
-                S->fused_split = split;
-                S->fused_dense = dense;
-            }
+    // times candidate (nw, dense); false when it is not available or the launch failed
+    auto trial = [&](int nw, int dense, float* ms) -> bool {
+        *ms = 0.0f;
+        if (rc || !S->fused_grid[fused_grid_index(nw, dense)]) return false;
+        if (!warm) {
+            const int nl = launch_fused(S, nw, split, dense, std::min(nb, S->fused_grid[fused_grid_index(nw, dense)]), st);
+            if (nl < 0) { rc = nl; return false; }
+            warm = true;
         }
+        if (cudaEventRecord(e0, st) != cudaSuccess) { rc = QOCO_GPU_ERR_CUDA; return false; }
+        const int nl = launch_fused(S, nw, split, dense, nb, st);
+        if (nl < 0) { rc = nl; return false; }
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = QOCO_GPU_ERR_CUDA;
+            return false;
+        }
+        cudaEventElapsedTime(ms, e0, e1);
+        if (S->st.verbose >= 2)
+            printf("     batch tile: %d warps per CTA, %d warps per SM: %.3f ms\n", nw, dense ? 32 : 16, *ms);
+        if (!S->fused_nw || *ms < best) {
+            best = *ms;
+            S->fused_nw = nw;
+            S->fused_split = split;
+            S->fused_dense = dense;
+        }
+        return true;
+    };
+    float ms = 0.0f;
+    for (int nw = 4; nw >= 1 && !rc; nw /= 2) {
+        const int before = S->fused_nw;
+        if (!trial(nw, 0, &ms) && !rc && !trial(nw, 1, &ms)) continue;  // width unavailable: try the next
+        if (before && S->fused_nw == before) break;                      // halving did not pay
+    }
+    if (!rc && S->fused_nw) trial(S->fused_nw, 1 - S->fused_dense, &ms);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
@@ -1381,14 +1394,14 @@ int analyze_common(int n, int m, int p, const qoco_csc* P, const double* c, cons
                    const double* b, const qoco_csc* G, const double* h, int l, int nsoc, const int* q,
                    const qoco_gpu_settings* settings, bool check_vectors, qoco_gpu_settings* st,
                    KKTPattern* K, Symbolic* Y, std::string* msg, double* t_analysis, int* used,
-                   int trees = 1) {
+                   int trees = 1, const std::vector<int>* perm0 = nullptr, int perm0_ordering = 0) {
     if (settings) *st = *settings;
     else qoco_gpu_default_settings(st);
     int rc = validate_problem(n, m, p, P, c, A, b, G, h, l, nsoc, q, check_vectors, msg);
     if (rc) return rc;
     const double t0 = now_s();
     build_kkt_pattern(K, n, m, p, P, A, G, l, nsoc, q);
-    *used = analyze(*K, *st, Y, trees);
+    *used = analyze(*K, *st, Y, trees, perm0, perm0_ordering);
     *t_analysis = now_s() - t0;
     return 0;
 }
@@ -1468,6 +1481,83 @@ int stack_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc
         T->h_inf.push_back(hi);
     }
     return 0;
+}
+
+// The fill-reducing ordering of a batch's stack from one ordering per distinct instance
+// pattern (equal sizes, cone dimensions and P, A, G sparsity patterns): instances of the
+// same model (an MPC horizon, say) are ordered once.  perm0 (new → old, the stack's
+// numbering) takes the instances in order, each by its pattern's ordering mapped to the
+// instance's rows of the stack (x, y, its orthant rows, its SOC rows).  Returns the
+// ordering used.
+int batch_ordering(int nb, const int* n, const int* m, const int* p, const qoco_csc* P, const qoco_csc* A,
+                   const qoco_csc* G, const int* l, const int* nsoc, const int* const* q, const Stacked& T,
+                   const qoco_gpu_settings& st, std::vector<int>* perm0) {
+    auto pmat = [&](int i) -> const qoco_csc* { return csc_present(&P[i]) && P[i].nnz > 0 ? &P[i] : nullptr; };
+    auto amat = [&](int i) -> const qoco_csc* { return p[i] ? &A[i] : nullptr; };
+    auto gmat = [&](int i) -> const qoco_csc* { return m[i] ? &G[i] : nullptr; };
+    auto same_pattern = [&](const qoco_csc* a, const qoco_csc* b, int ncol) {
+        if (!a || !b) return a == b;
+        return a->nnz == b->nnz && std::equal(a->colptr, a->colptr + ncol + 1, b->colptr) &&
+               std::equal(a->rowidx, a->rowidx + a->nnz, b->rowidx);
+    };
+    auto same = [&](int i, int r) {
+        return n[i] == n[r] && m[i] == m[r] && p[i] == p[r] && l[i] == l[r] && nsoc[i] == nsoc[r] &&
+               std::equal(q[i], q[i] + nsoc[i], q[r]) && same_pattern(pmat(i), pmat(r), n[i]) &&
+               same_pattern(amat(i), amat(r), n[i]) && same_pattern(gmat(i), gmat(r), n[i]);
+    };
+    auto hash = [&](int i) {
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+        mix(n[i]); mix(m[i]); mix(p[i]); mix(l[i]); mix(nsoc[i]);
+        for (int k = 0; k < nsoc[i]; ++k) mix(q[i][k]);
+        for (const qoco_csc* M : {pmat(i), amat(i), gmat(i)}) {
+            if (!M) { mix(~0ull); continue; }
+            mix(M->nnz);
+            for (int j = 0; j <= n[i]; ++j) mix(M->colptr[j]);
+            for (int t = 0; t < M->nnz; ++t) mix(M->rowidx[t]);
+        }
+        return h;
+    };
+    std::vector<int> cls(nb), rep, count;
+    std::map<uint64_t, std::vector<int>> by_hash;  // hash → pattern classes
+    for (int i = 0; i < nb; ++i) {
+        std::vector<int>& cand = by_hash[hash(i)];
+        int c = -1;
+        for (int k : cand)
+            if (same(i, rep[k])) { c = k; break; }
+        if (c < 0) {
+            c = (int)rep.size();
+            rep.push_back(i);
+            count.push_back(0);
+            cand.push_back(c);
+        }
+        cls[i] = c;
+        ++count[c];
+    }
+    std::vector<KKTPattern> pats(rep.size());
+    for (size_t c = 0; c < rep.size(); ++c) {
+        const int r = rep[c];
+        build_kkt_pattern(&pats[c], n[r], m[r], p[r], pmat(r), amat(r), gmat(r), l[r], nsoc[r], q[r]);
+    }
+    std::vector<std::vector<int>> perms;
+    const int used = order_batch_patterns(pats, count, st, nb, &perms);
+    perm0->clear();
+    perm0->reserve((size_t)T.n + T.p + T.m);
+    const int nx = T.n, ny = T.p, L = T.l;
+    for (int i = 0; i < nb; ++i) {
+        const int xo = T.xo[i], yo = T.yo[i], lo = T.lo[i], so = T.so[i];
+        for (int o : perms[cls[i]]) {
+            int g;
+            if (o < n[i]) g = xo + o;
+            else if (o < n[i] + p[i]) g = nx + yo + (o - n[i]);
+            else {
+                const int r = o - n[i] - p[i];
+                g = nx + ny + (r < l[i] ? lo + r : L + so + (r - l[i]));
+            }
+            perm0->push_back(g);
+        }
+    }
+    return used;
 }
 
 // Per-instance schedules of a batch's factorisation and solves (see launch_inst_factor):
@@ -1562,9 +1652,9 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
     }
     if ((rc = dcopy(S, &pi, row))) return rc; B.inst_row = pi;
     const int bs = S->st.batch_schedule;
-    if ((bs >= 0 && bs < kSharedSchedule) || bs == 6)
+    const bool want_fused = bs == 0 || (bs >= 6 && bs <= 12);
+    if ((bs >= 0 && bs < kSharedSchedule) || want_fused)
         if ((rc = plan_batch_instances(S, nb, row))) return rc;
-    const bool want_fused = bs == 0 || bs == 6;
     if (want_fused && S->plan.inst) {
         for (int nw : {1, 2, 4})
             for (int dense = 0; dense < 2; ++dense)
@@ -1572,6 +1662,16 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
                                          &S->fused_grid[fused_grid_index(nw, dense)])))
                     return rc;
         for (int g : S->fused_grid) S->fused = S->fused || g > 0;
+        // schedules 7–12 fix the tile (warps per CTA 1, 1, 2, 2, 4, 4; 16 or 32 warps per
+        // SM); a tile this batch cannot launch is left to the tuning
+        if (bs >= 7) {
+            const int nw = 1 << ((bs - 7) / 2), dense = (bs - 7) % 2;
+            if (S->fused_grid[fused_grid_index(nw, dense)] > 0) {
+                S->fused_nw = nw;
+                S->fused_split = 1;
+                S->fused_dense = dense;
+            }
+        }
     }
     // the factorisation entry points outside a batched solve (kkt_factor_at, backward)
     // use the shared kernels when the persistent kernel runs the solves
@@ -1620,7 +1720,8 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
 
 int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
                const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
-               const int* q, const qoco_gpu_settings* settings, int trees);
+               const int* q, const qoco_gpu_settings* settings, int trees,
+               const std::vector<int>* perm0 = nullptr, int perm0_ordering = 0, double t_order = 0.0);
 
 }  // namespace
 
@@ -1701,7 +1802,8 @@ namespace {
 // qoco_gpu_setup for `trees` independent problems stacked block-diagonally (1: one problem)
 int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
                const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
-               const int* q, const qoco_gpu_settings* settings, int trees) {
+               const int* q, const qoco_gpu_settings* settings, int trees,
+               const std::vector<int>* perm0, int perm0_ordering, double t_order) {
     if (!out) return QOCO_GPU_ERR_INVALID_ARG;
     *out = nullptr;
     const double t0 = now_s();
@@ -1717,7 +1819,7 @@ int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, co
     int rc;
     try {
         rc = analyze_common(n, m, p, P, c, A, b, G, h, l, nsoc, q, settings, true, &S->st, &S->K, &S->S,
-                            &S->msg, &ta, &used, trees);
+                            &S->msg, &ta, &used, trees, perm0, perm0_ordering);
     } catch (const std::bad_alloc&) {
         rc = QOCO_GPU_ERR_OOM;
     }
@@ -1731,7 +1833,7 @@ int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, co
         qoco_gpu_cleanup(S);
         return rc;
     }
-    S->info.analysis_time_s = ta;
+    S->info.analysis_time_s = ta + t_order;
     S->info.ordering_used = used;
     S->info.setup_time_s = now_s() - t0;
     *out = S;
@@ -1763,10 +1865,25 @@ int qoco_gpu_setup_batch(qoco_gpu_solver** out, int nb, const int* n, const int*
     qoco_csc Pc{T.n, T.n, (int)T.Pi.size(), T.Pp.data(), T.Pi.data(), T.Pv.data()};
     qoco_csc Ac{T.p, T.n, (int)T.Ai.size(), T.Ap.data(), T.Ai.data(), T.Av.data()};
     qoco_csc Gc{T.m, T.n, (int)T.Gi.size(), T.Gp.data(), T.Gi.data(), T.Gv.data()};
+    // one ordering per distinct instance pattern (the natural ordering stays the stack's own)
+    qoco_gpu_settings st;
+    if (settings) st = *settings;
+    else qoco_gpu_default_settings(&st);
+    std::vector<int> perm0;
+    int used = 0;
+    const double t_ord = now_s();
+    if (st.ordering != QOCO_GPU_ORDER_NATURAL) {
+        try {
+            used = batch_ordering(nb, n, m, p, P, A, G, l, nsoc, q, T, st, &perm0);
+        } catch (const std::bad_alloc&) {
+            return QOCO_GPU_ERR_OOM;
+        }
+    }
+    const double t_order = now_s() - t_ord;
     qoco_gpu_solver* S = nullptr;
     rc = setup_impl(&S, T.n, T.m, T.p, T.Pi.empty() ? nullptr : &Pc, T.c.data(), T.p ? &Ac : nullptr,
                     T.p ? T.b.data() : nullptr, &Gc, T.h.data(), T.l, T.nsoc, T.q.empty() ? nullptr : T.q.data(),
-                    settings, nb);
+                    settings, nb, perm0.empty() ? nullptr : &perm0, used, t_order);
     if (rc) return rc;
     try {
         rc = batch_init(S, nb, T);

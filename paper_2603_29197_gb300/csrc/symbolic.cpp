@@ -159,12 +159,71 @@ OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm0) {
     return E.cost;
 }
 
-int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int trees) {
+bool auto_picks_nd(const OrderingCost& amd, const OrderingCost& nd, const qoco_gpu_settings& st, int trees) {
+    // AUTO: cost model = factor flops at an effective FP64 rate plus a per-level latency
+    // for the level-scheduled factor and solves.  The independent trees of a batch on the
+    // shared kernels overlap their level chains (up to 64 of them are counted), which
+    // favours the lower flop counts of AMD there; a batch on the persistent kernel
+    // (batch_schedule 0 or 6–12) walks each instance's tree inside one CTA, so an instance's
+    // chain of levels counts in full (MPC batch of 4096 on that kernel: ND 63k solves/s
+    // against AMD's 59–68k in FP64, 50k against 33k with FP32 fronts).
+    const bool persistent = trees > 1 && (st.batch_schedule == 0 || (st.batch_schedule >= 6 && st.batch_schedule <= 12));
+    const double overlap = persistent ? 1.0 : (double)std::max(1, std::min(trees, 64));
+    auto cost = [&](const OrderingCost& c) { return c.flops / 2e11 + c.height * 4e-5 / overlap; };
+    return cost(nd) < cost(amd);
+}
+
+int order_batch_patterns(const std::vector<KKTPattern>& pats, const std::vector<int>& count,
+                         const qoco_gpu_settings& st, int trees, std::vector<std::vector<int>>* perms) {
+    const int np = (int)pats.size();
+    const bool both = st.ordering != QOCO_GPU_ORDER_AMD && st.ordering != QOCO_GPU_ORDER_ND;
+    std::vector<std::vector<int>> pa(np), pn(np);
+    std::vector<OrderingCost> ca(np), cn(np);
+    // one pattern per task, on a few host threads (each result depends on its pattern only)
+    const int nth = std::max(1, std::min(np, (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()))));
+    auto work = [&](int t0) {
+        for (int c = t0; c < np; c += nth) {
+            const Graph g = kkt_graph(pats[c]);
+            if (st.ordering != QOCO_GPU_ORDER_ND) {
+                pa[c] = order_amd(g);
+                if (both) ca[c] = ordering_cost(pats[c], pa[c]);
+            }
+            if (st.ordering != QOCO_GPU_ORDER_AMD) {
+                pn[c] = order_nd(g, st.nd_leaf);
+                if (both) cn[c] = ordering_cost(pats[c], pn[c]);
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& t : pool) t.join();
+    int used = st.ordering;
+    if (both) {
+        // the batch's cost: flops add over the instances, the height is the tallest tree's
+        OrderingCost A, D;
+        for (int c = 0; c < np; ++c) {
+            A.flops += count[c] * ca[c].flops;
+            D.flops += count[c] * cn[c].flops;
+            A.height = std::max(A.height, ca[c].height);
+            D.height = std::max(D.height, cn[c].height);
+        }
+        used = auto_picks_nd(A, D, st, trees) ? QOCO_GPU_ORDER_ND : QOCO_GPU_ORDER_AMD;
+    }
+    *perms = used == QOCO_GPU_ORDER_ND ? std::move(pn) : std::move(pa);
+    return used;
+}
+
+int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int trees,
+            const std::vector<int>* perm0, int perm0_ordering) {
     const int N = K.N;
     Graph g = kkt_graph(K);
     int used = st.ordering;
     Evaluated E;
-    if (st.ordering == QOCO_GPU_ORDER_NATURAL) {
+    if (perm0) {
+        evaluate(g, *perm0, false, &E);
+        used = perm0_ordering;
+    } else if (st.ordering == QOCO_GPU_ORDER_NATURAL) {
         std::vector<int> perm0(N);
         std::iota(perm0.begin(), perm0.end(), 0);
         evaluate(g, perm0, true, &E);
@@ -173,23 +232,13 @@ int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int t
     } else if (st.ordering == QOCO_GPU_ORDER_ND) {
         evaluate(g, order_nd(g, st.nd_leaf), false, &E);
     } else {
-        // AUTO: cost model = factor flops at an effective FP64 rate plus a per-level
-        // latency for the level-scheduled factor and solves.  The independent trees of a
-        // batch on the shared kernels overlap their level chains (up to 64 of them are
-        // counted), which favours the lower flop counts of AMD there; a batch on the
-        // persistent kernel (batch_schedule 0 or 6) walks each instance's tree inside one
-        // CTA, so an instance's chain of levels counts in full (MPC batch of 4096 on that
-        // kernel: ND 63k solves/s against AMD's 59–68k in FP64, 50k against 33k with FP32
-        // fronts).  The two candidates are independent: ordered and evaluated on two host
-        // threads.
+        // AUTO: the two candidates are independent, ordered and evaluated on two host
+        // threads, and the cheaper by auto_picks_nd's model is kept
         Evaluated En;
         std::thread tn([&]() { evaluate(g, order_nd(g, st.nd_leaf), false, &En); });
         evaluate(g, order_amd(g), false, &E);
         tn.join();
-        const bool persistent = trees > 1 && (st.batch_schedule == 0 || st.batch_schedule == 6);
-        const double overlap = persistent ? 1.0 : (double)std::max(1, std::min(trees, 64));
-        auto cost = [&](const OrderingCost& c) { return c.flops / 2e11 + c.height * 4e-5 / overlap; };
-        if (cost(En.cost) < cost(E.cost)) { E = std::move(En); used = QOCO_GPU_ORDER_ND; }
+        if (auto_picks_nd(E.cost, En.cost, st, trees)) { E = std::move(En); used = QOCO_GPU_ORDER_ND; }
         else used = QOCO_GPU_ORDER_AMD;
     }
 

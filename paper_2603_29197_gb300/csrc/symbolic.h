@@ -93,9 +93,24 @@ struct OrderingCost {
 };
 OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm);
 
+// AUTO's choice between an AMD and an ND candidate of the same matrix or batch (`trees`
+// independent problems): true when the ND candidate is cheaper by the cost model.
+bool auto_picks_nd(const OrderingCost& amd, const OrderingCost& nd, const qoco_gpu_settings& st, int trees);
+
+// Orderings of a batch whose instances fall into a few distinct sparsity patterns
+// (count[c] instances share pats[c]): each pattern is ordered once, by AMD, ND or, for
+// AUTO, both, the choice made on the batch's totals (flops add over the instances, the
+// tree height is the tallest instance's).  perms[c] is pattern c's ordering (new → old,
+// in the pattern's own numbering).  Returns the ordering used.
+int order_batch_patterns(const std::vector<KKTPattern>& pats, const std::vector<int>& count,
+                         const qoco_gpu_settings& st, int trees, std::vector<std::vector<int>>* perms);
+
 // Full analysis for a given ordering choice; returns the ordering actually used.
 // `trees` is the number of independent problems stacked in K (a batch): their chains
 // of dependent fronts run side by side, which AUTO's cost model takes into account.
-int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int trees = 1);
+// With perm0 the ordering step is skipped: perm0 (new → old) is used as the fill-
+// reducing ordering and perm0_ordering is reported as the ordering used.
+int analyze(const KKTPattern& K, const qoco_gpu_settings& st, Symbolic* S, int trees = 1,
+            const std::vector<int>* perm0 = nullptr, int perm0_ordering = 0);
 
 }  // namespace qoco

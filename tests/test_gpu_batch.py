@@ -9,8 +9,12 @@ interior-point loop with per-instance scalars, through the C ABI.
   the same solution to rounding as a stand-alone solve.
 * The MPC batch of 4096 instances (horizons U{10..60}, state 4, control 2, Q³ input cone,
   box bounds) solves every instance; a seeded sample of 24 instances matches the oracle.
+* A batch's analysis orders each distinct instance pattern once: its factor flops, L
+  entries and supernodes are the sums of the instances' own analyses (host-only, the
+  same ordering), with patterns repeated and mixed, and its solves match the oracle.
 * The persistent batched kernel (one launch per batched solve, the default when every
-  front fits one warp) and each of its tile configurations match the oracle instance by
+  front fits one warp) and each of its tile configurations (tuned, or fixed by schedules
+  7–12) match the oracle instance by
   instance, are bitwise reproducible, and agree with the level-loop schedules.
 """
 import numpy as np
@@ -97,6 +101,30 @@ def test_mpc_batch_4096(q):
     S.close()
 
 
+@pytest.mark.parametrize("ordering", [1, 2])
+def test_batch_analysis_is_the_sum_of_the_instances(q, ordering):
+    # horizons 10..13 repeat the same four MPC patterns; a dense QP and a portfolio SOCP
+    # sit between them
+    probs = mpc_batch(count=12, tmin=10, tmax=13, seed=21)
+    probs = probs[:6] + [dense_qp(n=40, p=8, m=60, rank=6, density=0.1, seed=22),
+                         portfolio_socp(n=50, k=6, seed=23)] + probs[6:]
+    S = q.BatchSolver(probs, ordering=ordering)
+    info = S.info()
+    assert info["ordering_used"] == ordering
+    one = [q.analyze(pr, ordering=ordering)[0] for pr in probs]
+    assert info["factor_flops"] == sum(o["factor_flops"] for o in one)
+    assert info["l_nnz"] == sum(o["l_nnz"] for o in one)
+    assert info["n_supernodes"] == sum(o["n_supernodes"] for o in one)
+    assert S.solve() == 0
+    bi = S.batch_info()
+    sols = S.instance_solutions()
+    for i in (0, 6, 7, len(probs) - 1):
+        ref = ipm.solve(probs[i])
+        assert bi["status"][i] == 0
+        _check_instance(probs[i], sols[i], ref)
+    S.close()
+
+
 @pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5, 6])
 def test_batch_schedules_match_the_oracle(q, schedule):
     """Every layout of the per-instance factor/solve kernels (4 or 8 warps per CTA,
@@ -113,6 +141,28 @@ def test_batch_schedules_match_the_oracle(q, schedule):
         ref = ipm.solve(probs[i])
         assert ref.status == "solved"
         assert abs(int(info["iters"][i]) - ref.iters) <= 3
+        _check_instance(probs[i], sols[i], ref)
+    S.close()
+
+
+@pytest.mark.parametrize("schedule", [7, 8, 9, 10, 11, 12])
+def test_persistent_kernel_fixed_tiles_match_the_oracle(q, schedule):
+    """Every tile of the persistent kernel (1, 2 or 4 warps per CTA; 16 or 32 resident
+    warps per SM), fixed instead of tuned, solves the same instances to the oracle's
+    tolerances; the tuning times only some of them."""
+    probs = mpc_batch(count=48, tmin=10, tmax=60, seed=21)
+    S = q.BatchSolver(probs, batch_schedule=schedule)
+    assert S.solve() == 0
+    info = S.info()
+    assert info["batch_schedule_used"] == 6
+    assert info["batch_warps"] == 1 << ((schedule - 7) // 2)
+    assert info["batch_warps_per_sm"] == (32 if (schedule - 7) % 2 else 16)
+    bi = S.batch_info()
+    assert np.all(bi["status"] == 0)
+    sols = S.instance_solutions()
+    for i in (0, 19, 47):
+        ref = ipm.solve(probs[i])
+        assert abs(int(bi["iters"][i]) - ref.iters) <= 3
         _check_instance(probs[i], sols[i], ref)
     S.close()
 

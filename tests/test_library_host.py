@@ -69,6 +69,23 @@ def test_binding_structs_mirror_the_header(cname, pyname):
         assert C.sizeof(pytype) == C.sizeof(want[ctype]) * n, nm
 
 
+def test_batch_csc_table_reads_back_through_ctypes():
+    # the batch binding fills its qoco_csc tables as numpy records of addresses
+    import ctypes as C
+    from paper_2603_29197_gb300 import _CSC_DTYPE, _csc_row
+    tab = np.zeros(3, dtype=_CSC_DTYPE)
+    M = sp.random(7, 5, density=0.4, format="csc", random_state=1)
+    keep = _csc_row(tab, 1, M, 7, 5)
+    ptr = tab.ctypes.data_as(C.POINTER(_lib.CSC))
+    assert ptr[0].colptr is None or not bool(ptr[0].colptr)  # untouched rows stay NULL
+    got = ptr[1]
+    assert (got.n_rows, got.n_cols, got.nnz) == (7, 5, M.nnz)
+    assert [got.colptr[j] for j in range(6)] == list(M.indptr)
+    assert [got.rowidx[t] for t in range(M.nnz)] == list(M.indices)
+    assert [got.val[t] for t in range(M.nnz)] == list(M.data)
+    del keep
+
+
 def _tiny(**kw):
     P = sp.csc_matrix(np.array([[2.0, 0.5], [0.0, 1.0]]))
     A = sp.csc_matrix(np.array([[1.0, 1.0]]))
