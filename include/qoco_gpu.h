@@ -441,6 +441,20 @@ int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A,
                      const qoco_gpu_settings* settings, qoco_gpu_info* info, int* perm,
                      int* sn_ptr, int* sn_nrow, int* sn_level);
 
+/* The analysis qoco_gpu_setup_batch makes, on the host only (arguments as there, without
+ * the vectors c, b, h): the instances are validated and stacked block-diagonally, each
+ * distinct instance pattern (sizes, cone dimensions, P, A and G sparsity) is ordered and
+ * analysed once (paper §2.2: the analysis runs once per sparsity pattern) and the stack's
+ * KKT pattern and supernodal analysis are assembled from those; with the natural ordering
+ * the stack is analysed as one problem.  Outputs as for qoco_gpu_analyze, in the stack's
+ * numbering (x of every instance, then y, then every orthant row, then every SOC row).
+ * Errors as for qoco_gpu_setup_batch. */
+int qoco_gpu_analyze_batch(int batch, const int* n, const int* m, const int* p,
+                           const qoco_csc* P, const qoco_csc* A, const qoco_csc* G,
+                           const int* l, const int* nsoc, const int* const* q,
+                           const qoco_gpu_settings* settings, qoco_gpu_info* info, int* perm,
+                           int* sn_ptr, int* sn_nrow, int* sn_level);
+
 #ifdef __cplusplus
 }
 #endif

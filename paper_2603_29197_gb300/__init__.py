@@ -120,6 +120,64 @@ def _tptr(t):
     return C.c_void_p(0 if t is None else t.data_ptr())
 
 
+def _batch_tables(probs):
+    """The per-instance arguments of qoco_gpu_setup_batch / qoco_gpu_analyze_batch: the
+    arrays to keep alive, the size lists (n, m, p, l, nsoc) and the tables (P, c, A, b, G,
+    h, q).  The qoco_csc structs and pointer tables are filled as numpy arrays of
+    addresses (one ctypes conversion per table, not one per instance)."""
+    nb = len(probs)
+    holds = []
+    ns, ms, ps, ls, nsocs = [], [], [], [], []
+    Ps, As, Gs = (np.zeros(nb, dtype=_CSC_DTYPE) for _ in range(3))
+    cs, bs, hs, qs = (np.zeros(nb, dtype=np.uintp) for _ in range(4))
+    for i, pr in enumerate(probs):
+        n, m, p = int(pr.n), int(pr.m), int(pr.p)
+        q = np.ascontiguousarray(list(pr.q), dtype=np.int32)
+        Pm = pr.P if getattr(pr, "P", None) is not None and pr.P.nnz else None
+        for M, rows, tab in ((Pm, n, Ps), (pr.A if p else None, p, As), (pr.G if m else None, m, Gs)):
+            if M is not None:
+                holds.append(_csc_row(tab, i, M, rows, n))
+        for v, k, tab in ((pr.c, n, cs), (pr.b, p, bs), (pr.h, m, hs)):
+            a = _vec(v, k)
+            if a is not None:
+                holds.append(a)
+                tab[i] = a.ctypes.data
+        holds.append(q)
+        if len(q):
+            qs[i] = q.ctypes.data
+        ns.append(n); ms.append(m); ps.append(p); ls.append(int(pr.l)); nsocs.append(len(q))
+    dp = C.POINTER(C.POINTER(C.c_double))
+    tables = (Ps.ctypes.data_as(C.POINTER(_lib.CSC)), cs.ctypes.data_as(dp), As.ctypes.data_as(C.POINTER(_lib.CSC)),
+              bs.ctypes.data_as(dp), Gs.ctypes.data_as(C.POINTER(_lib.CSC)), hs.ctypes.data_as(dp),
+              qs.ctypes.data_as(C.POINTER(C.POINTER(C.c_int))))
+    return holds, (ns, ms, ps, ls, nsocs), tables
+
+
+def analyze_batch(probs, settings=None, **kw):
+    """Host-only analysis of a batch as qoco_gpu_setup_batch makes it (no GPU needed):
+    returns (info, perm, sn_ptr, f_s, level_s) in the stack's numbering."""
+    lib = load()
+    st = _settings(settings, kw)
+    nb = len(probs)
+    holds, (ns, ms, ps, ls, nsocs), (Ps, _, As, _, Gs, _, qs) = _batch_tables(probs)
+    arr = lambda v: (C.c_int * nb)(*v)  # noqa: E731
+    args = (nb, arr(ns), arr(ms), arr(ps), Ps, As, Gs, arr(ls), arr(nsocs), qs, C.byref(st))
+    info = Info()
+    N = sum(ns) + sum(ms) + sum(ps)
+    perm = np.zeros(N, dtype=np.int32)
+    ip = C.POINTER(C.c_int)
+    rc = lib.qoco_gpu_analyze_batch(*args, C.byref(info), perm.ctypes.data_as(ip), None, None, None)
+    if rc != 0:
+        raise ValueError(f"batch analysis failed: {STATUS_NAMES.get(rc, rc)}: {info.message.decode()}")
+    ns_ = info.n_supernodes
+    sn = np.zeros(ns_ + 1, dtype=np.int32)
+    fs = np.zeros(max(1, ns_), dtype=np.int32)
+    lv = np.zeros(max(1, ns_), dtype=np.int32)
+    lib.qoco_gpu_analyze_batch(*args, None, None, sn.ctypes.data_as(ip), fs.ctypes.data_as(ip), lv.ctypes.data_as(ip))
+    del holds
+    return info.as_dict(), perm, sn, fs[:ns_], lv[:ns_]
+
+
 def analyze(prob, settings=None, structure=False, **kw):
     """Host-only ordering + symbolic analysis (no GPU needed): returns (info, perm, sn_ptr),
     plus (f_s, level_s) per supernode when structure=True."""
@@ -342,31 +400,7 @@ class BatchSolver(Solver):
         self.lib = load()
         self.st = _settings(settings, kw)
         nb = len(probs)
-        holds = []
-        ns, ms, ps, ls, nsocs = [], [], [], [], []
-        # the per-instance CSC structs and pointer tables are filled as numpy arrays of
-        # addresses (one ctypes conversion per table, not one per instance)
-        Ps, As, Gs = (np.zeros(nb, dtype=_CSC_DTYPE) for _ in range(3))
-        cs, bs, hs, qs = (np.zeros(nb, dtype=np.uintp) for _ in range(4))
-        for i, pr in enumerate(probs):
-            n, m, p = int(pr.n), int(pr.m), int(pr.p)
-            q = np.ascontiguousarray(list(pr.q), dtype=np.int32)
-            Pm = pr.P if getattr(pr, "P", None) is not None and pr.P.nnz else None
-            for M, rows, tab in ((Pm, n, Ps), (pr.A if p else None, p, As), (pr.G if m else None, m, Gs)):
-                if M is not None:
-                    holds.append(_csc_row(tab, i, M, rows, n))
-            for v, k, tab in ((pr.c, n, cs), (pr.b, p, bs), (pr.h, m, hs)):
-                a = _vec(v, k)
-                if a is not None:
-                    holds.append(a)
-                    tab[i] = a.ctypes.data
-            holds.append(q)
-            if len(q):
-                qs[i] = q.ctypes.data
-            ns.append(n); ms.append(m); ps.append(p); ls.append(int(pr.l)); nsocs.append(len(q))
-        Ps, As, Gs = (t.ctypes.data_as(C.POINTER(_lib.CSC)) for t in (Ps, As, Gs))
-        cs, bs, hs = (t.ctypes.data_as(C.POINTER(C.POINTER(C.c_double))) for t in (cs, bs, hs))
-        qs = qs.ctypes.data_as(C.POINTER(C.POINTER(C.c_int)))
+        holds, (ns, ms, ps, ls, nsocs), (Ps, cs, As, bs, Gs, hs, qs) = _batch_tables(probs)
         arr = lambda v: (C.c_int * nb)(*v)  # noqa: E731
         self.n, self.m, self.p = sum(ns), sum(ms), sum(ps)
         self.N = self.n + self.m + self.p

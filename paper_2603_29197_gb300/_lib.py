@@ -125,6 +125,9 @@ SIGNATURES = {
     "qoco_gpu_analyze": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(CSC), C.POINTER(CSC),
                                    C.POINTER(CSC), C.c_int, C.c_int, _IP, C.POINTER(Settings),
                                    C.POINTER(Info), _IP, _IP, _IP, _IP]),
+    "qoco_gpu_analyze_batch": (C.c_int, [C.c_int, _IP, _IP, _IP, C.POINTER(CSC), C.POINTER(CSC),
+                                         C.POINTER(CSC), _IP, _IP, C.POINTER(_IP), C.POINTER(Settings),
+                                         C.POINTER(Info), _IP, _IP, _IP, _IP]),
 }
 
 _lib = None

@@ -14,6 +14,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "batch.h"
@@ -1394,19 +1395,27 @@ int analyze_common(int n, int m, int p, const qoco_csc* P, const double* c, cons
                    const double* b, const qoco_csc* G, const double* h, int l, int nsoc, const int* q,
                    const qoco_gpu_settings* settings, bool check_vectors, qoco_gpu_settings* st,
                    KKTPattern* K, Symbolic* Y, std::string* msg, double* t_analysis, int* used,
-                   int trees = 1, const std::vector<int>* perm0 = nullptr, int perm0_ordering = 0) {
+                   int trees = 1) {
     if (settings) *st = *settings;
     else qoco_gpu_default_settings(st);
     int rc = validate_problem(n, m, p, P, c, A, b, G, h, l, nsoc, q, check_vectors, msg);
     if (rc) return rc;
     const double t0 = now_s();
     build_kkt_pattern(K, n, m, p, P, A, G, l, nsoc, q);
-    *used = analyze(*K, *st, Y, trees, perm0, perm0_ordering);
+    *used = analyze(*K, *st, Y, trees);
     *t_analysis = now_s() - t0;
     return 0;
 }
 
 // ---- batches --------------------------------------------------------------------
+// an analysis made before the solver exists (a batch's, from its instance patterns)
+struct Prebuilt {
+    KKTPattern K;
+    Symbolic Y;
+    int used = 0;
+    double t_analysis = 0.0;
+};
+
 struct Stacked {
     int n = 0, m = 0, p = 0, l = 0, nsoc = 0;
     std::vector<int> Pp{0}, Pi, Ap{0}, Ai, Gp{0}, Gi, q;
@@ -1419,12 +1428,15 @@ bool csc_present(const qoco_csc* M) { return M && M->colptr && M->n_cols > 0; }
 
 // Block-diagonal stack of the instances: x and y in instance order; the cone's rows are
 // every instance's orthant rows (instance order), then every instance's SOC rows.
+// Without vectors (c == nullptr: an analysis only) c, b and h are left zero.
 int stack_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc* P, const double* const* c,
                 const qoco_csc* A, const double* const* b, const qoco_csc* G, const double* const* h,
                 const int* l, const int* nsoc, const int* const* q, Stacked* T, std::string* msg) {
+    const bool vec = c != nullptr;
     for (int i = 0; i < nb; ++i) {
-        int rc = validate_problem(n[i], m[i], p[i], csc_present(&P[i]) ? &P[i] : nullptr, c[i],
-                                  p[i] ? &A[i] : nullptr, b[i], &G[i], h[i], l[i], nsoc[i], q[i], true, msg);
+        int rc = validate_problem(n[i], m[i], p[i], csc_present(&P[i]) ? &P[i] : nullptr, vec ? c[i] : nullptr,
+                                  p[i] ? &A[i] : nullptr, vec ? b[i] : nullptr, &G[i], vec ? h[i] : nullptr, l[i],
+                                  nsoc[i], q[i], vec, msg);
         if (rc) {
             *msg = "instance " + std::to_string(i) + ": " + *msg;
             return rc;
@@ -1444,8 +1456,9 @@ int stack_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc
         const int xo = T->xo[i], yo = T->yo[i], lo = T->lo[i], so = T->so[i];
         double ci = 0.0, bi = 0.0, hi = 0.0;
         for (int j = 0; j < n[i]; ++j) {
-            T->c.push_back(c[i][j]);
-            ci = std::max(ci, std::fabs(c[i][j]));
+            const double cj = vec ? c[i][j] : 0.0;
+            T->c.push_back(cj);
+            ci = std::max(ci, std::fabs(cj));
             // column j of the instance's P, A and G
             if (csc_present(&P[i]))
                 for (int t = P[i].colptr[j]; t < P[i].colptr[j + 1]; ++t) {
@@ -1467,12 +1480,14 @@ int stack_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc
             T->Gp.push_back((int)T->Gi.size());
         }
         for (int j = 0; j < p[i]; ++j) {
-            T->b.push_back(b[i][j]);
-            bi = std::max(bi, std::fabs(b[i][j]));
+            const double bj = vec ? b[i][j] : 0.0;
+            T->b.push_back(bj);
+            bi = std::max(bi, std::fabs(bj));
         }
         for (int r = 0; r < m[i]; ++r) {
-            T->h[r < l[i] ? lo + r : L + so + (r - l[i])] = h[i][r];
-            hi = std::max(hi, std::fabs(h[i][r]));
+            const double hr = vec ? h[i][r] : 0.0;
+            T->h[r < l[i] ? lo + r : L + so + (r - l[i])] = hr;
+            hi = std::max(hi, std::fabs(hr));
         }
         for (int k = 0; k < nsoc[i]; ++k) T->q.push_back(q[i][k]);
         T->nu.push_back((double)(l[i] + nsoc[i]));
@@ -1483,15 +1498,14 @@ int stack_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc
     return 0;
 }
 
-// The fill-reducing ordering of a batch's stack from one ordering per distinct instance
-// pattern (equal sizes, cone dimensions and P, A, G sparsity patterns): instances of the
-// same model (an MPC horizon, say) are ordered once.  perm0 (new → old, the stack's
-// numbering) takes the instances in order, each by its pattern's ordering mapped to the
-// instance's rows of the stack (x, y, its orthant rows, its SOC rows).  Returns the
-// ordering used.
-int batch_ordering(int nb, const int* n, const int* m, const int* p, const qoco_csc* P, const qoco_csc* A,
+// The KKT pattern and symbolic analysis of a batch's stack from one analysis per distinct
+// instance pattern (equal sizes, cone dimensions and P, A, G sparsity patterns): instances
+// of the same model (an MPC horizon, say) are ordered and analysed once, and the stack's
+// arrays are their relabelled copies (stack_analysis), the same as analysing the stack
+// with the instances' orderings concatenated.  Returns the ordering used.
+int batch_analysis(int nb, const int* n, const int* m, const int* p, const qoco_csc* P, const qoco_csc* A,
                    const qoco_csc* G, const int* l, const int* nsoc, const int* const* q, const Stacked& T,
-                   const qoco_gpu_settings& st, std::vector<int>* perm0) {
+                   const qoco_gpu_settings& st, KKTPattern* K, Symbolic* Y) {
     auto pmat = [&](int i) -> const qoco_csc* { return csc_present(&P[i]) && P[i].nnz > 0 ? &P[i] : nullptr; };
     auto amat = [&](int i) -> const qoco_csc* { return p[i] ? &A[i] : nullptr; };
     auto gmat = [&](int i) -> const qoco_csc* { return m[i] ? &G[i] : nullptr; };
@@ -1541,22 +1555,32 @@ int batch_ordering(int nb, const int* n, const int* m, const int* p, const qoco_
     }
     std::vector<std::vector<int>> perms;
     const int used = order_batch_patterns(pats, count, st, nb, &perms);
-    perm0->clear();
-    perm0->reserve((size_t)T.n + T.p + T.m);
-    const int nx = T.n, ny = T.p, L = T.l;
-    for (int i = 0; i < nb; ++i) {
-        const int xo = T.xo[i], yo = T.yo[i], lo = T.lo[i], so = T.so[i];
-        for (int o : perms[cls[i]]) {
-            int g;
-            if (o < n[i]) g = xo + o;
-            else if (o < n[i] + p[i]) g = nx + yo + (o - n[i]);
-            else {
-                const int r = o - n[i] - p[i];
-                g = nx + ny + (r < l[i] ? lo + r : L + so + (r - l[i]));
-            }
-            perm0->push_back(g);
-        }
+    std::vector<Symbolic> syms(rep.size());
+    {
+        // the patterns' own analyses, a few per host thread
+        const int np = (int)rep.size();
+        const int nth = std::max(1, std::min(np, (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()))));
+        std::vector<std::thread> pool;
+        auto work = [&](int t0) {
+            for (int c = t0; c < np; c += nth) analyze(pats[c], st, &syms[c], 1, &perms[c], used);
+        };
+        for (int t = 1; t < nth; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (auto& t : pool) t.join();
     }
+    StackLayout L;
+    L.n = T.n; L.p = T.p; L.m = T.m; L.l = T.l;
+    L.xo = T.xo; L.yo = T.yo; L.lo = T.lo; L.so = T.so; L.ko = T.ko;
+    L.Poff.resize(nb + 1);
+    L.Aoff.resize(nb + 1);
+    L.Goff.resize(nb + 1);
+    for (int i = 0; i <= nb; ++i) {
+        // an instance's data starts at the stack column of its first x
+        L.Poff[i] = T.Pp[T.xo[i]];
+        L.Aoff[i] = T.Ap[T.xo[i]];
+        L.Goff[i] = T.Gp[T.xo[i]];
+    }
+    stack_analysis(pats, syms, cls, L, T.q, T.Pv.data(), T.Av.data(), T.Gv.data(), K, Y);
     return used;
 }
 
@@ -1720,8 +1744,7 @@ int batch_init(qoco_gpu_solver* S, int nb, const Stacked& T) {
 
 int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
                const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
-               const int* q, const qoco_gpu_settings* settings, int trees,
-               const std::vector<int>* perm0 = nullptr, int perm0_ordering = 0, double t_order = 0.0);
+               const int* q, const qoco_gpu_settings* settings, int trees, Prebuilt* pre = nullptr);
 
 }  // namespace
 
@@ -1789,6 +1812,62 @@ int qoco_gpu_analyze(int n, int m, int p, const qoco_csc* P, const qoco_csc* A, 
     return 0;
 }
 
+int qoco_gpu_analyze_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc* P,
+                           const qoco_csc* A, const qoco_csc* G, const int* l, const int* nsoc,
+                           const int* const* q, const qoco_gpu_settings* settings, qoco_gpu_info* info,
+                           int* perm, int* sn_ptr, int* sn_nrow, int* sn_level) {
+    if (nb <= 0 || !n || !m || !p || !P || !A || !G || !l || !nsoc || !q) return QOCO_GPU_ERR_INVALID_ARG;
+    qoco_gpu_settings st;
+    if (settings) st = *settings;
+    else qoco_gpu_default_settings(&st);
+    Stacked T;
+    Prebuilt pre;
+    std::string msg;
+    int rc;
+    const double t0 = now_s();
+    try {
+        rc = stack_batch(nb, n, m, p, P, nullptr, A, nullptr, G, nullptr, l, nsoc, q, &T, &msg);
+        if (!rc && T.m == 0) rc = QOCO_GPU_ERR_NOT_IMPLEMENTED;
+        if (!rc && st.ordering == QOCO_GPU_ORDER_NATURAL) {
+            qoco_csc Pc{T.n, T.n, (int)T.Pi.size(), T.Pp.data(), T.Pi.data(), T.Pv.data()};
+            qoco_csc Ac{T.p, T.n, (int)T.Ai.size(), T.Ap.data(), T.Ai.data(), T.Av.data()};
+            qoco_csc Gc{T.m, T.n, (int)T.Gi.size(), T.Gp.data(), T.Gi.data(), T.Gv.data()};
+            double ta = 0.0;
+            rc = analyze_common(T.n, T.m, T.p, T.Pi.empty() ? nullptr : &Pc, nullptr, T.p ? &Ac : nullptr, nullptr,
+                                &Gc, nullptr, T.l, T.nsoc, T.q.empty() ? nullptr : T.q.data(), &st, false, &st,
+                                &pre.K, &pre.Y, &msg, &ta, &pre.used, nb);
+        } else if (!rc) {
+            pre.used = batch_analysis(nb, n, m, p, P, A, G, l, nsoc, q, T, st, &pre.K, &pre.Y);
+        }
+    } catch (const std::bad_alloc&) {
+        rc = QOCO_GPU_ERR_OOM;
+    }
+    if (info) {
+        memset(info, 0, sizeof *info);
+        snprintf(info->message, sizeof info->message, "%s", msg.c_str());
+    }
+    if (rc) return rc;
+    const KKTPattern& K = pre.K;
+    const Symbolic& Y = pre.Y;
+    if (info) {
+        info->analysis_time_s = now_s() - t0;
+        info->kkt_dim = K.N;
+        info->kkt_nnz = K.nnz();
+        info->l_nnz = Y.l_nnz;
+        info->front_entries = Y.front_entries;
+        info->factor_flops = Y.flops;
+        info->n_supernodes = Y.ns;
+        info->n_levels = Y.n_levels;
+        info->max_front = Y.max_front;
+        info->ordering_used = pre.used;
+    }
+    if (perm) memcpy(perm, Y.perm.data(), sizeof(int) * K.N);
+    if (sn_ptr) memcpy(sn_ptr, Y.sn_first.data(), sizeof(int) * (Y.ns + 1));
+    if (sn_nrow) memcpy(sn_nrow, Y.sn_nrow.data(), sizeof(int) * Y.ns);
+    if (sn_level) memcpy(sn_level, Y.level.data(), sizeof(int) * Y.ns);
+    return 0;
+}
+
 int qoco_gpu_setup(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
                    const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
                    const int* q, const qoco_gpu_settings* settings) {
@@ -1802,8 +1881,7 @@ namespace {
 // qoco_gpu_setup for `trees` independent problems stacked block-diagonally (1: one problem)
 int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, const double* c,
                const qoco_csc* A, const double* b, const qoco_csc* G, const double* h, int l, int nsoc,
-               const int* q, const qoco_gpu_settings* settings, int trees,
-               const std::vector<int>* perm0, int perm0_ordering, double t_order) {
+               const int* q, const qoco_gpu_settings* settings, int trees, Prebuilt* pre) {
     if (!out) return QOCO_GPU_ERR_INVALID_ARG;
     *out = nullptr;
     const double t0 = now_s();
@@ -1817,11 +1895,22 @@ int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, co
     double ta = 0.0;
     int used = 0;
     int rc;
-    try {
-        rc = analyze_common(n, m, p, P, c, A, b, G, h, l, nsoc, q, settings, true, &S->st, &S->K, &S->S,
-                            &S->msg, &ta, &used, trees, perm0, perm0_ordering);
-    } catch (const std::bad_alloc&) {
-        rc = QOCO_GPU_ERR_OOM;
+    if (pre) {
+        // a batch analysed from its instances' patterns (already validated)
+        if (settings) S->st = *settings;
+        else qoco_gpu_default_settings(&S->st);
+        S->K = std::move(pre->K);
+        S->S = std::move(pre->Y);
+        ta = pre->t_analysis;
+        used = pre->used;
+        rc = 0;
+    } else {
+        try {
+            rc = analyze_common(n, m, p, P, c, A, b, G, h, l, nsoc, q, settings, true, &S->st, &S->K, &S->S,
+                                &S->msg, &ta, &used, trees);
+        } catch (const std::bad_alloc&) {
+            rc = QOCO_GPU_ERR_OOM;
+        }
     }
     if (rc) {
         delete S;
@@ -1833,7 +1922,7 @@ int setup_impl(qoco_gpu_solver** out, int n, int m, int p, const qoco_csc* P, co
         qoco_gpu_cleanup(S);
         return rc;
     }
-    S->info.analysis_time_s = ta + t_order;
+    S->info.analysis_time_s = ta;
     S->info.ordering_used = used;
     S->info.setup_time_s = now_s() - t0;
     *out = S;
@@ -1865,25 +1954,25 @@ int qoco_gpu_setup_batch(qoco_gpu_solver** out, int nb, const int* n, const int*
     qoco_csc Pc{T.n, T.n, (int)T.Pi.size(), T.Pp.data(), T.Pi.data(), T.Pv.data()};
     qoco_csc Ac{T.p, T.n, (int)T.Ai.size(), T.Ap.data(), T.Ai.data(), T.Av.data()};
     qoco_csc Gc{T.m, T.n, (int)T.Gi.size(), T.Gp.data(), T.Gi.data(), T.Gv.data()};
-    // one ordering per distinct instance pattern (the natural ordering stays the stack's own)
+    // one analysis per distinct instance pattern (the natural ordering is the stack's own)
     qoco_gpu_settings st;
     if (settings) st = *settings;
     else qoco_gpu_default_settings(&st);
-    std::vector<int> perm0;
-    int used = 0;
-    const double t_ord = now_s();
-    if (st.ordering != QOCO_GPU_ORDER_NATURAL) {
+    Prebuilt pre;
+    const bool by_pattern = st.ordering != QOCO_GPU_ORDER_NATURAL;
+    if (by_pattern) {
+        const double ta = now_s();
         try {
-            used = batch_ordering(nb, n, m, p, P, A, G, l, nsoc, q, T, st, &perm0);
+            pre.used = batch_analysis(nb, n, m, p, P, A, G, l, nsoc, q, T, st, &pre.K, &pre.Y);
         } catch (const std::bad_alloc&) {
             return QOCO_GPU_ERR_OOM;
         }
+        pre.t_analysis = now_s() - ta;
     }
-    const double t_order = now_s() - t_ord;
     qoco_gpu_solver* S = nullptr;
     rc = setup_impl(&S, T.n, T.m, T.p, T.Pi.empty() ? nullptr : &Pc, T.c.data(), T.p ? &Ac : nullptr,
                     T.p ? T.b.data() : nullptr, &Gc, T.h.data(), T.l, T.nsoc, T.q.empty() ? nullptr : T.q.data(),
-                    settings, nb, perm0.empty() ? nullptr : &perm0, used, t_order);
+                    settings, nb, by_pattern ? &pre : nullptr);
     if (rc) return rc;
     try {
         rc = batch_init(S, nb, T);

@@ -105,6 +105,37 @@ bool auto_picks_nd(const OrderingCost& amd, const OrderingCost& nd, const qoco_g
 int order_batch_patterns(const std::vector<KKTPattern>& pats, const std::vector<int>& count,
                          const qoco_gpu_settings& st, int trees, std::vector<std::vector<int>>* perms);
 
+// Where each instance of a batch sits in the block-diagonal stack: its x rows, y rows,
+// orthant rows and SOC rows (prefix offsets over the instances, nb + 1 entries each; the
+// stack's rows are all x, then all y, then every orthant row, then every SOC row), its
+// SOCs, and the first entry of its data in the stack's P, A and G value arrays.
+struct StackLayout {
+    int n = 0, p = 0, m = 0, l = 0;
+    std::vector<int> xo, yo, lo, so, ko;
+    std::vector<int64_t> Poff, Aoff, Goff;  // nb + 1 each
+    int nb() const { return (int)xo.size() - 1; }
+    // stack row of instance i's local KKT row o (local numbering x | y | z, z = orthant
+    // rows then SOC rows)
+    int row(int i, int o) const {
+        const int ni = xo[i + 1] - xo[i], pi = yo[i + 1] - yo[i], li = lo[i + 1] - lo[i];
+        if (o < ni) return xo[i] + o;
+        if (o < ni + pi) return n + yo[i] + (o - ni);
+        const int r = o - ni - pi;
+        return n + p + (r < li ? lo[i] + r : l + so[i] + (r - li));
+    }
+};
+
+// The KKT pattern and analysis of a block-diagonal stack assembled from each distinct
+// instance pattern's own (pats[c], syms[c]; instance i has pattern cls[i]) by mapping
+// rows, columns, supernodes and value slots to the stack: the result equals what
+// build_kkt_pattern and analyze give on the stack with the instances' orderings
+// concatenated (an elimination forest is postordered tree by tree, and amalgamation and
+// absorption never cross trees).  q: the stack's SOC dimensions; Pv, Av, Gv: the stack's
+// data values.  Runs on a few host threads over the instances.
+void stack_analysis(const std::vector<KKTPattern>& pats, const std::vector<Symbolic>& syms,
+                    const std::vector<int>& cls, const StackLayout& L, const std::vector<int>& q,
+                    const double* Pv, const double* Av, const double* Gv, KKTPattern* K, Symbolic* S);
+
 // Full analysis for a given ordering choice; returns the ordering actually used.
 // `trees` is the number of independent problems stacked in K (a batch): their chains
 // of dependent fronts run side by side, which AUTO's cost model takes into account.

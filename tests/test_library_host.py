@@ -215,3 +215,58 @@ def test_nested_dissection_of_many_components_is_reproducible(lib):
     perms = [q.analyze(pr, ordering=2)[1] for _ in range(3)]
     assert all(np.array_equal(perms[0], p) for p in perms[1:])
     assert sorted(perms[0].tolist()) == list(range(len(perms[0])))
+
+
+def _stack_rows(probs):
+    """Stack row of every instance's local KKT row (x | y | z, z = orthant then SOC rows),
+    in the block-diagonal layout qoco_gpu_setup_batch uses."""
+    nt, pt, lt = (sum(int(getattr(pr, k)) for pr in probs) for k in ("n", "p", "l"))
+    xo = yo = lo = so = 0
+    out = []
+    for pr in probs:
+        n, p, m, l = int(pr.n), int(pr.p), int(pr.m), int(pr.l)
+        r = np.arange(m)
+        z = np.where(r < l, nt + pt + lo + r, nt + pt + lt + so + (r - l))
+        out.append(np.concatenate([xo + np.arange(n), nt + yo + np.arange(p), z]))
+        xo, yo, lo, so = xo + n, yo + p, lo + l, so + (m - l)
+    return out
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_batch_analysis_is_the_instances_analyses_stacked(lib, order):
+    # repeated MPC patterns (horizons 10..13) with other models between them: the batch's
+    # ordering, supernodes, front orders and levels are each instance's own, relabelled
+    probs = mpc_batch(count=20, tmin=10, tmax=13, seed=5)
+    probs = probs[:9] + [dense_qp(n=40, p=8, m=60, rank=6, density=0.1, seed=22),
+                         portfolio_socp(n=50, k=6, seed=23), trajectory_socp(N=12, seed=6)] + probs[9:]
+    info, perm, sn, fs, lv = q.analyze_batch(probs, ordering=order)
+    one = [q.analyze(pr, ordering=order, structure=True) for pr in probs]
+    assert info["ordering_used"] == order
+    for k in ("factor_flops", "l_nnz", "n_supernodes", "kkt_nnz", "kkt_dim", "front_entries"):
+        assert info[k] == sum(o[0][k] for o in one), k
+    assert info["max_front"] == max(o[0]["max_front"] for o in one)
+    assert info["n_levels"] == max(o[0]["n_levels"] for o in one)
+    rows = _stack_rows(probs)
+    co = so = 0
+    for i, (inf, pm, s, f, v) in enumerate(one):
+        N, ns = len(pm), inf["n_supernodes"]
+        assert np.array_equal(perm[co:co + N], rows[i][pm]), i
+        assert np.array_equal(sn[so:so + ns + 1], s + co), i
+        assert np.array_equal(fs[so:so + ns], f) and np.array_equal(lv[so:so + ns], v), i
+        co, so = co + N, so + ns
+    assert co == len(perm) and sn[-1] == co
+
+
+def test_batch_analysis_auto_and_natural(lib):
+    probs = mpc_batch(count=24, tmin=10, tmax=30, seed=9)
+    auto = q.analyze_batch(probs)[0]
+    assert auto["ordering_used"] in (1, 2)
+    pick = q.analyze_batch(probs, ordering=auto["ordering_used"])[0]
+    assert pick["factor_flops"] == auto["factor_flops"]
+    nat = q.analyze_batch(probs, ordering=3)[0]
+    assert nat["ordering_used"] == 3 and nat["kkt_nnz"] == auto["kkt_nnz"]
+    bad = list(probs)
+    bad[5] = _tiny(l=2)
+    with pytest.raises(ValueError) as e:
+        q.analyze_batch(bad)
+    assert "instance 5" in str(e.value)
