@@ -8,8 +8,10 @@
 //    denser than dense_factor·√N are ordered last.  Written from the paper's
 //    description with per-node std::vector lists instead of one packed workspace.
 //  * order_nd: nested dissection by breadth-first level structures from a
-//    pseudo-peripheral node (George & Liu): a thin middle level is the vertex
-//    separator, parts are dissected recursively and ordered before their separator;
+//    pseudo-peripheral node (George & Liu): a level that is small and splits the nodes
+//    evenly (least size × larger side, each side ≥ 20%), thinned to the nodes touching
+//    the next level, is the vertex separator; parts are dissected recursively and
+//    ordered before their separator;
 //    parts at or below `leaf_size` nodes (or without a usable separator) are ordered
 //    by AMD.  Gives the O(log N)-deep elimination trees that level-scheduled GPU
 //    factorisation needs on banded / stage-structured problems.
@@ -317,16 +319,17 @@ struct ND {
         amd_subset(g, mk, t, nodes, out);
     }
 
-    // Independent components (a batch's instances) in their order; large sets of them
-    // are split into contiguous ranges of about equal node counts, one host thread per
-    // range, and the ranges' orders are concatenated in component order.
-    void run_components(std::vector<std::vector<int>>& comps, std::vector<int>* out, int depth) {
+    // Independent components (a batch's instances, or a part that a separator split) in
+    // their order; large sets of them are split into contiguous ranges of about equal
+    // node counts, one host thread per range, and the ranges' orders are concatenated in
+    // component order.  hint0: a starting node for the first component (see run), or −1.
+    void run_components(std::vector<std::vector<int>>& comps, std::vector<int>* out, int depth, int hint0) {
         int64_t total = 0;
         for (const auto& c : comps) total += (int64_t)c.size();
         const int hw = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
         const int nth = (int)std::min<int64_t>(hw, (int64_t)comps.size());
         if (depth >= kNdMaxDepth || total < kNdParallelMin || nth < 2) {
-            for (auto& c : comps) run(std::move(c), out, depth);
+            for (size_t k = 0; k < comps.size(); ++k) run(std::move(comps[k]), out, depth, k ? -1 : hint0);
             return;
         }
         std::vector<size_t> cut(1, 0);
@@ -344,7 +347,7 @@ struct ND {
                 ND sub(g, mk, leaf);
                 for (size_t k = cut[r]; k < cut[r + 1]; ++k) sub.run(std::move(comps[k]), &outs[r], kNdMaxDepth);
             });
-        for (size_t k = cut[0]; k < cut[1]; ++k) run(std::move(comps[k]), &outs[0], kNdMaxDepth);
+        for (size_t k = cut[0]; k < cut[1]; ++k) run(std::move(comps[k]), &outs[0], kNdMaxDepth, k ? -1 : hint0);
         for (auto& t : ths) t.join();
         for (const auto& o : outs) out->insert(out->end(), o.begin(), o.end());
     }
@@ -372,7 +375,8 @@ struct ND {
                 seen.insert(seen.end(), q.begin(), q.end());
             }
             for (int v : seen) lev[v] = -1;
-            run_components(comps, out, depth);
+            // the first component is the hint's: it keeps the hint as its start
+            run_components(comps, out, depth, hint);
             return;
         }
         // pseudo-peripheral root: BFS from the least-degree node of the last level while
@@ -404,14 +408,18 @@ struct ND {
         }
         const int S = (int)nodes.size();
         if (nl < 3) { clear_lev(); amd_subset(g, mk, t, nodes, out); return; }
-        // separator level: smallest level whose both sides hold ≥ 20% of the nodes,
-        // else the median level
-        int pick = -1, psize = 1 << 30, median = -1;
+        // separator level: among the levels whose both sides hold ≥ 20% of the nodes, the
+        // one with the least size × larger side (a small separator, and balanced parts:
+        // on a chain of equal levels that is the middle one, and the dissection tree stays
+        // log₂-deep instead of peeling 20% per level); else the median level
+        int pick = -1, median = -1;
+        double pcost = 0.0;
         for (int k = 1; k < nl - 1; ++k) {
             int before = lptr[k], after = S - lptr[k + 1];
             int sz = lptr[k + 1] - lptr[k];
             if (median < 0 && lptr[k + 1] >= S / 2) median = k;
-            if (before >= S / 5 && after >= S / 5 && sz < psize) { psize = sz; pick = k; }
+            const double cost = (double)sz * std::max(before, after);
+            if (before >= S / 5 && after >= S / 5 && (pick < 0 || cost < pcost)) { pcost = cost; pick = k; }
         }
         if (pick < 0) pick = median < 0 ? nl / 2 : median;
         // thin the separator: keep only level nodes touching the next level

@@ -1950,6 +1950,7 @@ int qoco_gpu_setup_batch(qoco_gpu_solver** out, int nb, const int* n, const int*
         rc = QOCO_GPU_ERR_OOM;
     }
     if (rc) return rc;
+    const double t_stacked = now_s();
     if (T.m == 0) return QOCO_GPU_ERR_NOT_IMPLEMENTED;  // a batch needs cone rows
     qoco_csc Pc{T.n, T.n, (int)T.Pi.size(), T.Pp.data(), T.Pi.data(), T.Pv.data()};
     qoco_csc Ac{T.p, T.n, (int)T.Ai.size(), T.Ap.data(), T.Ai.data(), T.Av.data()};
@@ -1974,6 +1975,8 @@ int qoco_gpu_setup_batch(qoco_gpu_solver** out, int nb, const int* n, const int*
                     T.p ? T.b.data() : nullptr, &Gc, T.h.data(), T.l, T.nsoc, T.q.empty() ? nullptr : T.q.data(),
                     settings, nb, by_pattern ? &pre : nullptr);
     if (rc) return rc;
+    const double t_device = S->info.setup_time_s;  // setup_impl: upload and launch plans
+    const double t_init = now_s();
     try {
         rc = batch_init(S, nb, T);
     } catch (const std::bad_alloc&) {
@@ -1984,6 +1987,11 @@ int qoco_gpu_setup_batch(qoco_gpu_solver** out, int nb, const int* n, const int*
         return rc;
     }
     S->info.setup_time_s = now_s() - t0;
+    if (S->st.verbose >= 2)
+        printf("batch set-up %.3f s: stack %.3f, analysis %.3f, upload and plans %.3f, batch plans %.3f\n",
+               S->info.setup_time_s, t_stacked - t0, S->info.analysis_time_s,
+               t_device - (by_pattern ? 0.0 : S->info.analysis_time_s),
+               now_s() - t_init);
     *out = S;
     return 0;
 }
