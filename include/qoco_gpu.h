@@ -79,7 +79,8 @@ typedef struct {
     double refine_tol;                  /* normwise backward-error target (1e-10) */
     double step_fraction;               /* 0.99 */
     int ordering;                       /* QOCO_GPU_ORDER_* (AUTO) */
-    int nd_leaf;                        /* ND stops splitting below this many nodes (64) */
+    int nd_leaf;                        /* ND stops splitting below this many nodes; 0:
+                                           automatic, N_K/2048 clamped to 64..256 (0) */
     int64_t wait_polls;                 /* polls (each sleeps ~32–64 ns) a device-side dependency
                                            wait of the dataflow factor/solve kernels may take
                                            before it gives up and the call returns

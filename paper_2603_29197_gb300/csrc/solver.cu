@@ -1764,7 +1764,7 @@ void qoco_gpu_default_settings(qoco_gpu_settings* s) {
     s->refine_tol = 1e-10;
     s->step_fraction = 0.99;
     s->ordering = QOCO_GPU_ORDER_AUTO;
-    s->nd_leaf = 64;
+    s->nd_leaf = 0;
     s->wait_polls = 0;
     s->verbose = 0;
     s->mixed_precision = 0;

@@ -93,6 +93,10 @@ struct OrderingCost {
 };
 OrderingCost ordering_cost(const KKTPattern& K, const std::vector<int>& perm);
 
+// ND's leaf size for a graph of N nodes: the setting, or when it is ≤ 0 an automatic
+// size from N.
+int nd_leaf_size(const qoco_gpu_settings& st, int N);
+
 // AUTO's choice between an AMD and an ND candidate of the same matrix or batch (`trees`
 // independent problems): true when the ND candidate is cheaper by the cost model.
 bool auto_picks_nd(const OrderingCost& amd, const OrderingCost& nd, const qoco_gpu_settings& st, int trees);

@@ -38,6 +38,16 @@ def test_default_settings(lib):
     assert st.max_iter == 200 and st.static_reg == 1e-8 and st.step_fraction == 0.99
     assert st.max_refine == 10 and st.refine_tol == 1e-10
     assert st.mixed_precision == 0 and st.batch_schedule == 0
+    assert st.nd_leaf == 0  # automatic
+
+
+def test_nd_leaf_is_automatic_by_size(lib):
+    # N_K / 2048 clamped to 64..256: a 20000-stage trajectory (540k KKT rows) gets leaves
+    # of 256, an MPC instance of horizon 60 (1260 rows) leaves of 64
+    big = trajectory_socp(N=20000)
+    assert np.array_equal(q.analyze(big, ordering=2)[1], q.analyze(big, ordering=2, nd_leaf=256)[1])
+    small = mpc_batch(count=1, tmin=60, tmax=60)[0]
+    assert np.array_equal(q.analyze(small, ordering=2)[1], q.analyze(small, ordering=2, nd_leaf=64)[1])
 
 
 def _header_struct(name):
