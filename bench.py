@@ -215,16 +215,20 @@ def fp64_peaks(q):
 
 # The sources each profiled kernel is built from (its own file and the headers it
 # includes); the DRAM traffic ncu measured stays valid while these are unchanged.
+# the kernel's own CUDA sources and the host sources that shape the supernodal tree it
+# walks (ordering, amalgamation, plan): a change to either changes its DRAM traffic
 KERNEL_SOURCES = {
-    "k_factor_dataflow": ["factor.cu", "fronts.cuh", "factor.h", "common.cuh", "plan.h"],
-    "k_solve_dataflow": ["factor.cu", "fronts.cuh", "factor.h", "common.cuh", "plan.h"],
+    "k_factor_dataflow": ["factor.cu", "fronts.cuh", "factor.h", "common.cuh", "plan.h", "plan.cpp",
+                          "ordering.cpp", "symbolic.cpp"],
+    "k_solve_dataflow": ["factor.cu", "fronts.cuh", "factor.h", "common.cuh", "plan.h", "plan.cpp",
+                         "ordering.cpp", "symbolic.cpp"],
 }
 
 
 def kernel_source_digest(kernel=None):
-    """Digest of the CUDA sources of `kernel` (all of them when it has no entry in
-    KERNEL_SOURCES): DRAM traffic measured by ncu is only reported while the kernel is
-    the one it was measured on."""
+    """Digest of the sources of `kernel` (KERNEL_SOURCES; every CUDA source when it has
+    no entry there): DRAM traffic measured by ncu is only reported while the kernel and
+    the tree it walks are the ones it was measured on."""
     import hashlib
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2603_29197_gb300", "csrc")
