@@ -267,6 +267,39 @@ def test_batch_analysis_is_the_instances_analyses_stacked(lib, order):
     assert co == len(perm) and sn[-1] == co
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_batch_analysis_edge_layouts(lib, order):
+    # instances without equality rows, without an orthant, without P, and with only an
+    # orthant, repeated and interleaved: every branch of the stack's row map
+    rng = np.random.default_rng(3)
+
+    def inst(n, p, l, q, with_P=True):
+        m = l + sum(q)
+        G = sp.csc_matrix(rng.standard_normal((m, n)) * (rng.random((m, n)) < 0.6))
+        P = sp.csc_matrix(np.triu(np.eye(n) * 2.0 + 0.1)) if with_P else sp.csc_matrix((n, n))
+        A = sp.csc_matrix(rng.standard_normal((p, n))) if p else sp.csc_matrix((0, n))
+        for M in (G, P, A):
+            M.sort_indices()
+        return Problem(n=n, m=m, p=p, P=P, c=rng.standard_normal(n), A=A, b=np.ones(p), G=G,
+                       h=np.ones(m), l=l, q=list(q))
+    kinds = [(6, 0, 3, [3]), (5, 2, 0, [3, 2]), (4, 1, 4, [], False), (7, 0, 0, [4, 3]), (5, 2, 3, [2])]
+    probs = []
+    for r in range(3):
+        for k in kinds:
+            probs.append(inst(*k))
+    info, perm, sn, fs, lv = q.analyze_batch(probs, ordering=order)
+    one = [q.analyze(pr, ordering=order, structure=True) for pr in probs]
+    assert info["factor_flops"] == sum(o[0]["factor_flops"] for o in one)
+    assert info["kkt_nnz"] == sum(o[0]["kkt_nnz"] for o in one)
+    rows = _stack_rows(probs)
+    co = so = 0
+    for i, (inf, pm, s, f, v) in enumerate(one):
+        N, ns = len(pm), inf["n_supernodes"]
+        assert np.array_equal(perm[co:co + N], rows[i][pm]), i
+        assert np.array_equal(sn[so:so + ns + 1], s + co) and np.array_equal(fs[so:so + ns], f), i
+        co, so = co + N, so + ns
+
+
 def test_batch_analysis_auto_and_natural(lib):
     probs = mpc_batch(count=24, tmin=10, tmax=30, seed=9)
     auto = q.analyze_batch(probs)[0]
