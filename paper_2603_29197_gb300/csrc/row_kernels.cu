@@ -84,14 +84,26 @@ __global__ void __launch_bounds__(kRowThreads) k_residual(KKTView K, const doubl
         if (mine) {
             const int64_t beg = K.rowptr[row], end = K.rowptr[row + 1];
             mine = end - beg <= kLongRow;
-            if (mine)
-                for (int64_t t = beg + lane; t < end; t += LPR) {
+            if (mine) {
+                // a row's columns are sorted (x, then y, then z): each lane runs its x, y and z
+                // entries as three straight loops, one FP64 multiply-add per entry (a per-entry
+                // three-way branch made diverging lanes issue every branch's add); y and z rows
+                // use only their x part
+                int64_t t = beg + lane;
+                for (; t < end; t += LPR) {
                     const int j = K.colidx[t];
-                    const double kv = K.val[t] * xyz[j];
-                    if (j < n) a0 += kv;
-                    else if (j < n + p) a1 += kv;
-                    else a2 += kv;
+                    if (j >= n) break;
+                    a0 += K.val[t] * xyz[j];
                 }
+                if (row < n) {
+                    for (; t < end; t += LPR) {
+                        const int j = K.colidx[t];
+                        if (j >= n + p) break;
+                        a1 += K.val[t] * xyz[j];
+                    }
+                    for (; t < end; t += LPR) a2 += K.val[t] * xyz[K.colidx[t]];
+                }
+            }
         }
         a0 = group_sum<LPR>(a0);
         a1 = group_sum<LPR>(a1);
