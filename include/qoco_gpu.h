@@ -246,7 +246,8 @@ int qoco_gpu_solution_device(const qoco_gpu_solver* solver, const double** x,
  * Each instance follows the conventions above (orthant rows first in its G).  Layout of
  * the stacked iterate returned by qoco_gpu_get_solution: see qoco_gpu_batch_offsets.
  * Errors: as qoco_gpu_setup (the message names the failing instance);
- * NOT_IMPLEMENTED when no instance has a cone row. */
+ * NOT_IMPLEMENTED when an instance has no cone row (m = 0: its barrier parameter
+ * ν = l + nsoc would be zero). */
 int qoco_gpu_setup_batch(qoco_gpu_solver** out, int batch, const int* n, const int* m,
                          const int* p, const qoco_csc* P, const double* const* c,
                          const qoco_csc* A, const double* const* b, const qoco_csc* G,

@@ -1434,6 +1434,11 @@ int stack_batch(int nb, const int* n, const int* m, const int* p, const qoco_csc
                 const int* l, const int* nsoc, const int* const* q, Stacked* T, std::string* msg) {
     const bool vec = c != nullptr;
     for (int i = 0; i < nb; ++i) {
+        if (m[i] <= 0) {
+            // the per-instance barrier parameter μ = sᵀz / ν needs ν = l + nsoc > 0
+            *msg = "instance " + std::to_string(i) + ": a batch instance needs cone rows (m > 0)";
+            return QOCO_GPU_ERR_NOT_IMPLEMENTED;
+        }
         int rc = validate_problem(n[i], m[i], p[i], csc_present(&P[i]) ? &P[i] : nullptr, vec ? c[i] : nullptr,
                                   p[i] ? &A[i] : nullptr, vec ? b[i] : nullptr, &G[i], vec ? h[i] : nullptr, l[i],
                                   nsoc[i], q[i], vec, msg);

@@ -313,3 +313,11 @@ def test_batch_analysis_auto_and_natural(lib):
     with pytest.raises(ValueError) as e:
         q.analyze_batch(bad)
     assert "instance 5" in str(e.value)
+    # an instance without cone rows has no barrier parameter: rejected by name
+    n = 3
+    eq = Problem(n=n, m=0, p=1, P=sp.csc_matrix(np.eye(n)), c=np.ones(n), A=sp.csc_matrix(np.ones((1, n))),
+                 b=np.ones(1), G=sp.csc_matrix((0, n)), h=np.zeros(0), l=0, q=[])
+    with pytest.raises(ValueError) as e:
+        q.analyze_batch(probs[:2] + [eq] + probs[2:])
+    assert "instance 2" in str(e.value) and "cone rows" in str(e.value)
+    assert _lib.STATUS_NAMES[_lib.ERR_NOT_IMPLEMENTED] in str(e.value)
