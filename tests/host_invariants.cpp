@@ -195,6 +195,7 @@ int main(int argc, char** argv) {
     check(S.n_levels == maxlev + 1, "level count");
     // launch plan
     int df_solve_checked = 0, df_factor_checked = 0;
+    int kinds[4] = {0, 0, 0, 0};  // dataflow factorisation items of each kind
     {
         PlanHost P;
         build_plan(S, &P);
@@ -237,10 +238,19 @@ int main(int argc, char** argv) {
             for (size_t it = 0; it < P.fitems.size(); ++it) {
                 const int kind = P.fitems[it] & 3, idx = P.fitems[it] >> 2;
                 std::vector<int> members;
+                // 0: a batch of one-thread fronts; 1: a group of warp fronts; 3: a group of
+                // fronts two to a warp; 2: one CTA front
                 if (kind == 0) for (int t = P.ftb_ptr[idx]; t < P.ftb_ptr[idx + 1]; ++t) members.push_back(P.thread[t]);
-                else if (kind == 1) for (int t = P.fwg_ptr[idx]; t < P.fwg_ptr[idx + 1]; ++t) members.push_back(P.warp[t]);
-                else members.push_back(idx);
+                else if (kind == 1 || kind == 3) {
+                    for (int t = P.fwg_ptr[idx]; t < P.fwg_ptr[idx + 1]; ++t) {
+                        members.push_back(P.warp[t]);
+                        if (kind == 3) check(P.warp[t] >= 0 && S.sn_nrow[P.warp[t]] <= kPairFront, "pair front order", t);
+                    }
+                } else members.push_back(idx);
+                ++kinds[kind];
                 for (int x : members) {
+                    check(x >= 0 && x < ns, "factor item front index", x);
+                    if (x < 0 || x >= ns) continue;
                     check(item_of[x] < 0, "factor item once", x);
                     item_of[x] = (int)it;
                 }
@@ -255,7 +265,7 @@ int main(int argc, char** argv) {
         std::printf("%d failures\n", fails);
         return 1;
     }
-    std::printf("ok N=%d supernodes=%d levels=%d dataflow plans checked: solve %d factor %d\n", N, ns,
-                S.n_levels, df_solve_checked, df_factor_checked);
+    std::printf("ok N=%d supernodes=%d levels=%d dataflow plans checked: solve %d factor %d items %d %d %d %d\n",
+                N, ns, S.n_levels, df_solve_checked, df_factor_checked, kinds[0], kinds[1], kinds[2], kinds[3]);
     return 0;
 }

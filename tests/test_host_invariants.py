@@ -70,6 +70,9 @@ CASES = {
     "portfolio": (lambda: portfolio_socp(n=600, k=30, seed=4), 1, (0, 1, 2, 3)),
     "lasso": (lambda: lasso_qp(rows=300, cols=600, density=0.02, seed=5), 1, (0, 1, 2)),
     "mpc_stack": (lambda: _stack(mpc_batch(count=40, tmin=10, tmax=60, seed=6)), 40, (0, 1, 2)),
+    # levels wide enough (≥ 2432 fronts above one thread's order) for the dataflow
+    # factorisation's one-thread batches, warp groups and two-to-a-warp groups
+    "trajectory_wide": (lambda: trajectory_socp(N=20000, seed=3), 1, (2,)),
     # a dense Schur complement on the equality rows: thin children with updates of more
     # than 1024 rows are absorbed into the root front (columns re-emitted out of postorder)
     "lasso_absorb": (lambda: lasso_qp(rows=5000, cols=10000, density=1e-2, seed=0), 1, (1,)),
@@ -87,6 +90,9 @@ def test_symbolic_analysis_invariants(checker, tmp_path, name):
         assert r.stdout.startswith("ok"), r.stdout
         if name == "mpc_stack":  # all fronts fit a warp: both dataflow plans were checked
             assert "solve 1 factor 1" in r.stdout, r.stdout
+        if name == "trajectory_wide":  # every kind of dataflow factorisation item occurs
+            items = [int(v) for v in r.stdout.split("items")[1].split()[:4]]
+            assert "factor 1" in r.stdout and min(items) > 0, r.stdout
 
 
 @pytest.mark.parametrize("plant", ["plant_rel", "plant_map"])
